@@ -1,0 +1,96 @@
+"""Seeded synthetic pencils shaped like the paper's workloads.
+
+This module builds inputs only: matrices with prescribed or random spectra,
+the contour description, and the random starting blocks that the method
+draws (passed to both the CUDA library and the oracle as inputs).  It holds
+none of the method's arithmetic and imports neither the oracle nor the
+library.
+
+Complex Gaussian entries have Re, Im ~ N(0, 1/2) (E|g|^2 = 1), drawn from
+numpy's PCG64 generator, so the same seed gives the same pencil on every
+machine.
+
+Workloads (the paper's own matrices -- NEP QC324/QC2534, the benzene FEM and
+transport matrices -- are not available; these stand in for them):
+
+  prescribed(n, ...)   A = V diag(lam) V^{-1}, B = I, cond(V) set exactly
+                       through V = U diag(s) W^H with Haar-like U, W.
+                       Config "plain FEAST n=256": 40 eigenvalues uniform in
+                       a disk of radius 0.95 (a 5 % margin inside the unit
+                       circle), 216 uniform in the annulus 1.5 < |lam| < 4,
+                       cond(V) = 100, circle c = 0, r = 1, 8 midpoint nodes,
+                       m0 = 64.
+  gaussian_pencil(n)   A = G/sqrt(n) + D, B = I + 0.05 G'/sqrt(n); D keeps
+                       the first n/64 diagonal entries at 0 and puts the rest
+                       on the circle of radius 3, so that about n/64
+                       eigenvalues sit near the origin.  Config "Bi-FEAST
+                       n=4096": ellipse c = 0.2+0.1i, semi-axes 0.6 and 0.3,
+                       Gauss-Legendre K = 16 (32 systems), m0 = 128.
+"""
+import numpy as np
+
+
+def cgauss(rng, *shape):
+    """Complex Gaussian with E|g|^2 = 1."""
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * np.sqrt(0.5)
+
+
+def haar_unitary(rng, n):
+    """Q factor of a complex Gaussian matrix with the phases of diag(R) removed."""
+    q, r = np.linalg.qr(cgauss(rng, n, n))
+    d = np.diagonal(r)
+    return q * (d / np.abs(d))[None, :]
+
+
+def uniform_disk(rng, k, r_in, r_out):
+    """k points uniform (by area) in the annulus r_in <= |z| < r_out."""
+    rad = np.sqrt(rng.uniform(r_in * r_in, r_out * r_out, k))
+    ang = rng.uniform(0.0, 2.0 * np.pi, k)
+    return rad * np.exp(1j * ang)
+
+
+def prescribed(n=256, m_in=40, r_in=0.95, ann=(1.5, 4.0), cond=100.0, seed=1, m0=64,
+               center=0.0, radius=1.0):
+    """A = V diag(lam) V^{-1} with a prescribed spectrum, B = I.
+
+    Returns dict(A, B=None, lam, V, Vinv, U0, Vrand, contour, N_e, m0)."""
+    rng = np.random.default_rng(seed)
+    lam_in = center + radius * uniform_disk(rng, m_in, 0.0, r_in)
+    lam_out = center + radius * uniform_disk(rng, n - m_in, ann[0], ann[1])
+    lam = np.concatenate([lam_in, lam_out])
+    Uq = haar_unitary(rng, n)
+    Wq = haar_unitary(rng, n)
+    s = np.logspace(0.0, -np.log10(cond), n)
+    V = (Uq * s[None, :]) @ Wq.conj().T
+    Vinv = (Wq * (1.0 / s)[None, :]) @ Uq.conj().T
+    A = (V * lam[None, :]) @ Vinv
+    U0 = cgauss(rng, n, m0)
+    Vrand = cgauss(rng, n, m0)
+    return dict(A=A, B=None, lam=lam, lam_inside=lam_in, V=V, Vinv=Vinv, U0=U0, Vrand=Vrand,
+                contour=dict(c=complex(center), R=float(radius), a=1.0, rule="trap_mid"),
+                N_e=8, m0=m0, seed=seed)
+
+
+def gaussian_pencil(n=4096, seed=2, m0=128, K=16, zero_block=None, b_eps=0.05):
+    """A = G/sqrt(n) + D, B = I + b_eps G'/sqrt(n) (complex Gaussian G, G')."""
+    rng = np.random.default_rng(seed)
+    k0 = n // 64 if zero_block is None else zero_block
+    G = cgauss(rng, n, n)
+    A = G / np.sqrt(n)
+    del G
+    idx = np.arange(k0, n)
+    A[idx, idx] += 3.0 * np.exp(2j * np.pi * (idx - k0) / max(1, n - k0))
+    Gb = cgauss(rng, n, n)
+    B = Gb * (b_eps / np.sqrt(n))
+    del Gb
+    B[np.arange(n), np.arange(n)] += 1.0
+    U0 = cgauss(rng, n, m0)
+    Vrand = cgauss(rng, n, m0)
+    return dict(A=A, B=B, U0=U0, Vrand=Vrand,
+                contour=dict(c=0.2 + 0.1j, R=0.6, a=0.5, rule="gauss"),
+                N_e=K, m0=m0, seed=seed)
+
+
+def random_block(n, m, seed):
+    """A seeded complex Gaussian n x m block."""
+    return cgauss(np.random.default_rng(seed), n, m)
