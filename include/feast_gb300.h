@@ -1,0 +1,214 @@
+/*
+ * feast_gb300.h -- C ABI of the GB300 (sm_103a) non-Hermitian FEAST library.
+ *
+ * The library finds the eigenpairs (lambda, x) of A x = lambda B x whose
+ * eigenvalues lie inside an elliptical domain C (the problem of Sec. 2 of
+ * Tang, Kestyn & Polizzi, "A New Highly Parallel Non-Hermitian Eigensolver"),
+ * by subspace iteration (Algorithm R-FEAST) or Bauer bi-iteration (Algorithm
+ * Bi-FEAST) accelerated by the quadrature filter of Sec. 3:
+ *
+ *   rho(M) U = sum_k sigma_k (phi_k B - A)^{-1} (B U)                (Eq. Rasp)
+ *   left:      sum_k conj(sigma_k) (phi_k B - A)^{-H} (B^H V)         (Eq. quadf_surMconj)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved complex128 (feast_z).  Matrices are
+ *   column-major with a leading dimension; n x m blocks passed to or returned
+ *   from the library have leading dimension n.
+ * - Any matrix/vector pointer may be HOST memory (pageable or pinned) or
+ *   DEVICE memory of the current CUDA device (unified addressing: the library
+ *   copies every input into its own device buffers and every output back with
+ *   cudaMemcpyDefault).  Caller memory is never retained after a call returns.
+ * - All GPU work is enqueued on the stream given to feast_create (NULL = the
+ *   legacy default stream).  A call returns after its work is complete
+ *   (results in host buffers are valid; device outputs are complete on that
+ *   stream).
+ * - Errors are returned as feast_status; nothing aborts or traps.  After a
+ *   FEAST_ERR_CUDA status the handle should be destroyed.
+ * - Not thread-safe per handle; distinct handles are independent.
+ */
+#ifndef FEAST_GB300_H
+#define FEAST_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } feast_z;
+
+typedef enum {
+  FEAST_OK = 0,
+  FEAST_ERR_ARG = 1,            /* invalid size, pointer or option                      */
+  FEAST_ERR_ALLOC = 2,          /* device allocation failed                             */
+  FEAST_ERR_SINGULAR_SHIFT = 3, /* a shifted matrix phi_k B - A had an exact zero pivot */
+  FEAST_ERR_REFINE_NOCONV = 4,  /* reserved: refinement did not reach its tolerance     */
+  FEAST_ERR_M0_TOO_SMALL = 5,   /* every Ritz value of the subspace lies inside C       */
+  FEAST_ERR_NOCONV = 6,         /* max_iter reached; results are still returned         */
+  FEAST_ERR_NONFINITE = 7,      /* NaN or Inf appeared in the input or the iteration    */
+  FEAST_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up                   */
+  FEAST_ERR_CUDA = 9,           /* a CUDA runtime call failed                           */
+  FEAST_ERR_STATE = 10          /* call out of order (e.g. no factorisation yet)        */
+} feast_status;
+
+/* Quadrature rules of Sec. 3 (Eq. quadrature_for_pi) and the meaning of N_e:
+ *   TRAP_MID : q = N_e nodes at angles 2 pi (j + 1/2) / N_e (composite midpoint
+ *              rule; on a circle rho(mu) = 1 / (1 + ((mu - c)/R)^N_e)).
+ *   TRAP_END : the paper's trapezoid with t_1 = -1, t_K = 1, K = N_e, q = 2(K-1).
+ *   GAUSS    : Gauss-Legendre with K = N_e nodes per half, q = 2K.
+ *   CUSTOM   : q = q_custom caller-supplied nodes and weights (host memory),
+ *              e.g. piecewise contours glued from several curves (Sec. 5.4). */
+typedef enum {
+  FEAST_RULE_TRAP_MID = 0,
+  FEAST_RULE_TRAP_END = 1,
+  FEAST_RULE_GAUSS = 2,
+  FEAST_RULE_CUSTOM = 3
+} feast_rule;
+
+/* The ellipse of Eq. ellipses: centre c, semi-axes R (real direction) and
+ * R * aspect (imaginary direction).  The domain test for candidates always
+ * uses this ellipse, also for CUSTOM nodes. */
+typedef struct {
+  feast_z center;
+  double R;
+  double aspect;
+  int rule;               /* feast_rule */
+  int N_e;
+  const feast_z* nodes;   /* CUSTOM only (host) */
+  const feast_z* weights; /* CUSTOM only (host) */
+  int q_custom;           /* CUSTOM only */
+} feast_contour;
+
+typedef enum { FEAST_ALGO_R = 0, FEAST_ALGO_BI = 1 } feast_algo;
+
+/* FP64: every shifted system factored and solved in complex128 (DMMA tensor path).
+ * MIXED: factors in complex64 with the trailing updates on the tensor cores,
+ *        solves in low precision, and the FP64 accuracy recovered by
+ *        iterative refinement: the correction solve takes the FP64 residual
+ *        of the initial iterate X_k0 = U (phi_k - Theta)^{-1}, which every
+ *        shift shares (R_k = (A U - B U Theta)(phi_k - Theta)^{-1}). */
+typedef enum { FEAST_PREC_FP64 = 0, FEAST_PREC_MIXED = 1 } feast_precision;
+
+typedef struct {
+  int algo;          /* feast_algo                                             */
+  int precision;     /* feast_precision                                        */
+  double tol;        /* stop when every candidate has
+                        ||A x - lam B x|| / (||A||_2 ||x||) <= tol (default 1e-10) */
+  int max_iter;      /* default 20                                             */
+  double cand_tol;   /* candidate test ||A u - lam B u|| / ||u|| <= cand_tol
+                        (Sec. 5, default 1e-4)                                 */
+  int panel;         /* LU panel width (0 = library default)                   */
+  int timing;        /* nonzero: record per-phase CUDA-event times in stats    */
+} feast_options;
+
+typedef struct {
+  int iters;
+  int m_found;
+  double max_res;        /* max normalised residual over candidates, last iteration */
+  double normA;          /* ||A||_2 estimate used for normalisation                */
+  double t_factor_ms;    /* times are filled only when options.timing != 0          */
+  double t_filter_ms;
+  double t_rr_ms;
+  double t_total_ms;
+  double t_update_ms;    /* summed duration of the LU trailing-update launches     */
+  int update_launches;   /* number of those launches in the last factorisation     */
+  int res_hist_len;
+  double res_hist[64];   /* max candidate residual per iteration (inf if none)      */
+  int count_hist[64];    /* candidate count per iteration                          */
+} feast_stats;
+
+typedef struct feast_handle feast_handle;
+
+/* Default options: BI, MIXED, tol 1e-10, max_iter 20, cand_tol 1e-4. */
+void feast_default_options(feast_options* o);
+
+/* Create a handle for the pencil (A, B) of order n with subspace size m0.
+ *   A    : n x n, leading dimension lda >= n, host or device; copied.
+ *   B    : n x n (ldb >= n) or NULL for the standard problem B = I.
+ *   c    : contour and quadrature rule (Sec. 3); nodes and weights are computed
+ *          on the host (Eq. ellipses, Eq. pi, Eq. quadrature_for_pi).
+ *   m0   : subspace dimension p of Sec. 4, 1 <= m0 <= n and m0 <= 160.
+ *   stream : a cudaStream_t, or NULL.
+ * The handle owns the device copies of A and B, the q factorisations and all
+ * workspace until feast_destroy.  Returns FEAST_ERR_ARG for n < 1, m0 > n,
+ * N_e < 1 or a NULL A; FEAST_ERR_ALLOC if device memory runs out. */
+feast_status feast_create(feast_handle** h, int64_t n, const feast_z* A, int64_t lda,
+                          const feast_z* B, int64_t ldb, const feast_contour* c, int m0,
+                          const feast_options* o, void* stream);
+
+void feast_destroy(feast_handle* h);
+
+const char* feast_status_str(feast_status s);
+
+/* Number of linear systems q and their nodes phi_k / weights sigma_k (host
+ * arrays of q entries each, either may be NULL). */
+feast_status feast_get_quadrature(const feast_handle* h, int* q, feast_z* nodes, feast_z* weights);
+
+/* Form every shifted matrix phi_k B - A and factor it once (Sec. 5.5: one
+ * factorisation per linear system for the whole iteration): P_k S_k = L_k U_k
+ * by blocked Gaussian elimination with partial pivoting (largest |Re|+|Im|,
+ * lowest row on ties).  FEAST_ERR_SINGULAR_SHIFT if some exact pivot is zero
+ * (the factor is still stored).  Called implicitly by filter/solve when no
+ * factorisation exists yet; an explicit call always forms and factors again. */
+feast_status feast_factor(feast_handle* h);
+
+/* Copy out the factorisation of shift k (0 <= k < q) for inspection:
+ * LU (n x n complex128, packed unit-L and U, ld n) and piv (n int32, LAPACK
+ * style: row i was exchanged with piv[i], 0-based).  Either may be NULL. */
+feast_status feast_get_factor(feast_handle* h, int k, feast_z* LU, int32_t* piv);
+
+/* Solve one shifted system with the stored factor: side 0 solves
+ * (phi_k B - A) X = R, side 1 solves (phi_k B - A)^H X = R (Eq. Rasp,
+ * Eq. Lasp).  R and X are n x nrhs (ld n), nrhs <= m0.  In MIXED precision
+ * this is the low-precision solve alone (no refinement). */
+feast_status feast_solve_shift(feast_handle* h, int k, int side, const feast_z* R, feast_z* X,
+                               int nrhs);
+
+/* The filter (Eq. Rasp and Eq. Lasp):
+ *   Q    = sum_k sigma_k (phi_k B - A)^{-1} B Y
+ *   Qhat = sum_k conj(sigma_k) (phi_k B - A)^{-H} B^H Yhat   (if Yhat != NULL)
+ * Y, Yhat, Q, Qhat are n x m0.  theta (m0 complex, may be NULL) supplies Ritz
+ * values for the MIXED refinement's initial iterate; the mathematical result
+ * does not depend on it.  Sums over k run in a fixed order (deterministic). */
+feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat,
+                          const feast_z* theta, feast_z* Q, feast_z* Qhat);
+
+/* Rayleigh-Ritz (R-FEAST steps 4-5 / Bi-FEAST steps 6-7) on the filtered blocks.
+ * Q (and Qhat for Bi-FEAST; NULL selects R-FEAST's one-sided projection) are
+ * replaced in FP64 by orthonormal bases of their spans, the reduced pencil
+ * (A^, B^) = (V^H A U, V^H B U) is solved for Lambda^, W, Z with
+ * Z^H B^ W = I, and the Ritz vectors X = U W (unit 2-norm columns) and
+ * Xl = V Z (scaled so Xl^H B X = I) are returned with their eigenvalues
+ * lambda (m0) and residuals res[i] = ||A x_i - lambda_i B x_i|| / ||A||_2
+ * (m0 doubles).  m_inside counts pairs that are candidates (inside C and
+ * ||A x - lambda B x|| <= cand_tol).  Xl, res, m_inside may be NULL. */
+feast_status feast_rayleigh_ritz(feast_handle* h, const feast_z* Q, const feast_z* Qhat,
+                                 feast_z* lambda, feast_z* X, feast_z* Xl, double* res,
+                                 int* m_inside);
+
+/* The whole iteration (Algorithm R-FEAST or Bi-FEAST, with the Sec. 5
+ * candidate monitoring).  Y0 (n x m0) is the random starting block; Vrand
+ * (n x m0, Bi-FEAST only, may be NULL = Y0) builds V0 = Vrand (Vrand^H B Y0)^{-H}
+ * so that V0^H B Y0 = I.  On return the first m_found entries of lambda
+ * (m0 slots), columns of X and Xl (n x m0 each; Xl may be NULL) and res are
+ * the converged candidates sorted by (Re lambda, Im lambda).  Returns
+ * FEAST_ERR_NOCONV if max_iter iterations did not converge (outputs valid).
+ * stats may be NULL. */
+feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vrand,
+                         feast_z* lambda, feast_z* X, feast_z* Xl, double* res, int* m_found,
+                         feast_stats* stats);
+
+/* Timings of the last factorisation and of the last feast_solve on this handle
+ * (filled when options.timing != 0; normA always).  stats must not be NULL. */
+feast_status feast_get_stats(const feast_handle* h, feast_stats* stats);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a diagnostic counter; no paper counterpart). */
+uint64_t feast_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEAST_GB300_H */

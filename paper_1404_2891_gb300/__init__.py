@@ -1,0 +1,324 @@
+"""Python binding of the GB300 non-Hermitian FEAST library (include/feast_gb300.h).
+
+Argument marshalling only: every step of the method runs in libfeast_gb300.so.
+Arrays may be numpy complex128 arrays (host) or torch complex128 CUDA tensors
+(device); matrices are passed column-major, as the C ABI expects.  Results come
+back as numpy arrays unless ``out_device=True`` is given, in which case they are
+torch CUDA tensors.
+
+The functions carry the C names: feast_create, feast_factor, feast_get_factor,
+feast_solve_shift, feast_filter, feast_rayleigh_ritz, feast_solve,
+feast_get_quadrature, feast_destroy.  The library must be built first
+(``paper_1404_2891_gb300.build.build()``); importing this module loads it and
+raises if it is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfeast_gb300.so")
+
+FEAST_OK = 0
+FEAST_ERR_ARG = 1
+FEAST_ERR_ALLOC = 2
+FEAST_ERR_SINGULAR_SHIFT = 3
+FEAST_ERR_REFINE_NOCONV = 4
+FEAST_ERR_M0_TOO_SMALL = 5
+FEAST_ERR_NOCONV = 6
+FEAST_ERR_NONFINITE = 7
+FEAST_ERR_DEVICE_TIMEOUT = 8
+FEAST_ERR_CUDA = 9
+FEAST_ERR_STATE = 10
+
+RULES = {"trap_mid": 0, "trap_end": 1, "gauss": 2, "custom": 3}
+ALGOS = {"R": 0, "BI": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class feast_z(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class feast_contour(ctypes.Structure):
+    _fields_ = [("center", feast_z), ("R", ctypes.c_double), ("aspect", ctypes.c_double),
+                ("rule", ctypes.c_int), ("N_e", ctypes.c_int),
+                ("nodes", ctypes.POINTER(feast_z)), ("weights", ctypes.POINTER(feast_z)),
+                ("q_custom", ctypes.c_int)]
+
+
+class feast_options(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("cand_tol", ctypes.c_double), ("panel", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+class feast_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("m_found", ctypes.c_int), ("max_res", ctypes.c_double),
+                ("normA", ctypes.c_double), ("t_factor_ms", ctypes.c_double),
+                ("t_filter_ms", ctypes.c_double), ("t_rr_ms", ctypes.c_double),
+                ("t_total_ms", ctypes.c_double), ("t_update_ms", ctypes.c_double),
+                ("update_launches", ctypes.c_int), ("res_hist_len", ctypes.c_int),
+                ("res_hist", ctypes.c_double * 64), ("count_hist", ctypes.c_int * 64)]
+
+
+class FeastError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+_lib = None
+
+# every symbol declared in include/feast_gb300.h
+SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_status_str",
+           "feast_get_quadrature", "feast_factor", "feast_get_factor", "feast_solve_shift",
+           "feast_filter", "feast_rayleigh_ritz", "feast_solve", "feast_kernel_launches",
+           "feast_get_stats")
+
+
+def load(path=LIB_PATH):
+    """Load the shared library (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_1404_2891_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.feast_default_options.argtypes = [ctypes.POINTER(feast_options)]
+    lib.feast_default_options.restype = None
+    lib.feast_create.argtypes = [ctypes.POINTER(P), ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64,
+                                 ctypes.POINTER(feast_contour), ctypes.c_int, ctypes.POINTER(feast_options), P]
+    lib.feast_create.restype = ctypes.c_int
+    lib.feast_destroy.argtypes = [P]
+    lib.feast_destroy.restype = None
+    lib.feast_status_str.argtypes = [ctypes.c_int]
+    lib.feast_status_str.restype = ctypes.c_char_p
+    lib.feast_get_quadrature.argtypes = [P, ctypes.POINTER(ctypes.c_int), P, P]
+    lib.feast_get_quadrature.restype = ctypes.c_int
+    lib.feast_factor.argtypes = [P]
+    lib.feast_factor.restype = ctypes.c_int
+    lib.feast_get_factor.argtypes = [P, ctypes.c_int, P, P]
+    lib.feast_get_factor.restype = ctypes.c_int
+    lib.feast_solve_shift.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int]
+    lib.feast_solve_shift.restype = ctypes.c_int
+    lib.feast_filter.argtypes = [P, P, P, P, P, P]
+    lib.feast_filter.restype = ctypes.c_int
+    lib.feast_rayleigh_ritz.argtypes = [P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+    lib.feast_rayleigh_ritz.restype = ctypes.c_int
+    lib.feast_solve.argtypes = [P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(feast_stats)]
+    lib.feast_solve.restype = ctypes.c_int
+    lib.feast_kernel_launches.argtypes = []
+    lib.feast_kernel_launches.restype = ctypes.c_uint64
+    lib.feast_get_stats.argtypes = [P, ctypes.POINTER(feast_stats)]
+    lib.feast_get_stats.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def feast_kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(load().feast_kernel_launches())
+
+
+def status_str(s):
+    return load().feast_status_str(int(s)).decode()
+
+
+def _check(status, where, allow=()):
+    if status != FEAST_OK and status not in allow:
+        raise FeastError(status, where)
+    return status
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _colmajor(x):
+    """(pointer, keepalive) for a 1-D or 2-D complex128 array in column-major order."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        t = x
+        if t.dtype != torch.complex128:
+            raise TypeError("torch inputs must be complex128")
+        if t.dim() == 2:
+            t = t.mT.contiguous()  # row-major storage of A^T = column-major storage of A
+        else:
+            t = t.contiguous()
+        return t.data_ptr(), t
+    a = np.asarray(x, dtype=np.complex128)
+    a = np.asfortranarray(a) if a.ndim == 2 else np.ascontiguousarray(a)
+    return a.ctypes.data, a
+
+
+def _out(shape, device, dtype=np.complex128):
+    if device:
+        import torch
+        tdt = torch.complex128 if dtype == np.complex128 else (torch.float64 if dtype == np.float64 else torch.int32)
+        t = torch.empty(tuple(reversed(shape)), dtype=tdt, device="cuda")  # column-major view later
+        return t.data_ptr(), t
+    a = np.zeros(shape, dtype=dtype, order="F")
+    return a.ctypes.data, a
+
+
+def _finish(buf, device):
+    if device:
+        return buf.mT if buf.dim() == 2 else buf
+    return buf
+
+
+class Handle:
+    """Owns a feast_handle*; freed by feast_destroy or garbage collection."""
+
+    def __init__(self, ptr, n, m0, q, algo):
+        self.ptr, self.n, self.m0, self.q, self.algo = ptr, n, m0, q, algo
+
+    def __del__(self):
+        try:
+            feast_destroy(self)
+        except Exception:
+            pass
+
+
+def make_contour(center=0.0, R=1.0, aspect=1.0, rule="trap_mid", N_e=8, nodes=None, weights=None):
+    c = feast_contour()
+    c.center = feast_z(complex(center).real, complex(center).imag)
+    c.R, c.aspect = float(R), float(aspect)
+    c.rule = RULES[rule]
+    c.N_e = int(N_e)
+    c._keep = []
+    if rule == "custom":
+        nz = (feast_z * len(nodes))(*[feast_z(complex(v).real, complex(v).imag) for v in nodes])
+        wz = (feast_z * len(weights))(*[feast_z(complex(v).real, complex(v).imag) for v in weights])
+        c.nodes = ctypes.cast(nz, ctypes.POINTER(feast_z))
+        c.weights = ctypes.cast(wz, ctypes.POINTER(feast_z))
+        c.q_custom = len(nodes)
+        c._keep = [nz, wz]
+    return c
+
+
+def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False):
+    o = feast_options()
+    load().feast_default_options(ctypes.byref(o))
+    o.algo = ALGOS[algo]
+    o.precision = PRECISIONS[precision]
+    o.tol, o.max_iter, o.cand_tol, o.panel, o.timing = float(tol), int(max_iter), float(cand_tol), int(panel), int(timing)
+    return o
+
+
+# ---------------------------------------------------------------- entry points
+def feast_create(A, B, contour, m0, options, stream=None):
+    """feast_create: A, B (None = identity) n x n complex128; contour from make_contour;
+    options from make_options; stream: torch.cuda.Stream or raw cudaStream_t (int) or None."""
+    lib = load()
+    n = A.shape[0]
+    pa, ka = _colmajor(A)
+    pb, kb = _colmajor(B)
+    h = ctypes.c_void_p()
+    sp = None
+    if stream is not None:
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    s = lib.feast_create(ctypes.byref(h), n, pa, n, pb, n, ctypes.byref(contour), int(m0),
+                         ctypes.byref(options), sp)
+    _check(s, "feast_create")
+    q = ctypes.c_int()
+    lib.feast_get_quadrature(h, ctypes.byref(q), None, None)
+    return Handle(h, n, int(m0), q.value, options.algo)
+
+
+def feast_destroy(h):
+    if h is not None and h.ptr:
+        load().feast_destroy(h.ptr)
+        h.ptr = None
+
+
+def feast_get_quadrature(h):
+    lib = load()
+    q = h.q
+    nodes = (feast_z * q)()
+    weights = (feast_z * q)()
+    _check(lib.feast_get_quadrature(h.ptr, None, nodes, weights), "feast_get_quadrature")
+    z = np.array([complex(v.re, v.im) for v in nodes])
+    w = np.array([complex(v.re, v.im) for v in weights])
+    return z, w
+
+
+def feast_get_stats(h):
+    st = feast_stats()
+    _check(load().feast_get_stats(h.ptr, ctypes.byref(st)), "feast_get_stats")
+    return dict(normA=st.normA, t_factor_ms=st.t_factor_ms, t_update_ms=st.t_update_ms,
+                update_launches=st.update_launches, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms)
+
+
+def feast_factor(h, allow_singular=False):
+    allow = (FEAST_ERR_SINGULAR_SHIFT,) if allow_singular else ()
+    return _check(load().feast_factor(h.ptr), "feast_factor", allow)
+
+
+def feast_get_factor(h, k):
+    LU = np.zeros((h.n, h.n), dtype=np.complex128, order="F")
+    piv = np.zeros(h.n, dtype=np.int32)
+    _check(load().feast_get_factor(h.ptr, int(k), LU.ctypes.data, piv.ctypes.data), "feast_get_factor")
+    return LU, piv
+
+
+def feast_solve_shift(h, k, side, R, out_device=False):
+    pr, kr = _colmajor(R)
+    nrhs = R.shape[1] if R.ndim == 2 else 1
+    px, X = _out((h.n, nrhs), out_device)
+    _check(load().feast_solve_shift(h.ptr, int(k), int(side), pr, px, nrhs), "feast_solve_shift")
+    return _finish(X, out_device)
+
+
+def feast_filter(h, Y, Yhat=None, theta=None, out_device=False):
+    py, ky = _colmajor(Y)
+    pyh, kyh = _colmajor(Yhat)
+    pt, kt = _colmajor(theta)
+    pq, Q = _out((h.n, h.m0), out_device)
+    pqh, Qh = (_out((h.n, h.m0), out_device) if Yhat is not None else (None, None))
+    _check(load().feast_filter(h.ptr, py, pyh, pt, pq, pqh), "feast_filter")
+    return _finish(Q, out_device), (_finish(Qh, out_device) if Yhat is not None else None)
+
+
+def feast_rayleigh_ritz(h, Q, Qhat=None, out_device=False):
+    pq, kq = _colmajor(Q)
+    pqh, kqh = _colmajor(Qhat)
+    lam = np.zeros(h.m0, dtype=np.complex128)
+    res = np.zeros(h.m0, dtype=np.float64)
+    px, X = _out((h.n, h.m0), out_device)
+    pxl, Xl = (_out((h.n, h.m0), out_device) if Qhat is not None else (None, None))
+    mi = ctypes.c_int()
+    _check(load().feast_rayleigh_ritz(h.ptr, pq, pqh, lam.ctypes.data, px, pxl, res.ctypes.data,
+                                      ctypes.byref(mi)), "feast_rayleigh_ritz")
+    return dict(lam=lam, X=_finish(X, out_device), Xl=_finish(Xl, out_device) if Qhat is not None else None,
+                res=res, m_inside=mi.value)
+
+
+def feast_solve(h, Y0, Vrand=None, out_device=False, allow_noconv=True):
+    py, ky = _colmajor(Y0)
+    pv, kv = _colmajor(Vrand)
+    lam = np.zeros(h.m0, dtype=np.complex128)
+    res = np.zeros(h.m0, dtype=np.float64)
+    px, X = _out((h.n, h.m0), out_device)
+    pxl, Xl = (_out((h.n, h.m0), out_device) if h.algo == ALGOS["BI"] else (None, None))
+    mf = ctypes.c_int()
+    st = feast_stats()
+    s = load().feast_solve(h.ptr, py, pv, lam.ctypes.data, px, pxl, res.ctypes.data, ctypes.byref(mf),
+                           ctypes.byref(st))
+    _check(s, "feast_solve", (FEAST_ERR_NOCONV,) if allow_noconv else ())
+    k = mf.value
+    Xf = _finish(X, out_device)
+    out = dict(status=s, converged=(s == FEAST_OK), m_found=k, lam=lam[:k], res=res[:k],
+               X=Xf[:, :k], iters=st.iters, max_res=st.max_res, normA=st.normA,
+               t_factor_ms=st.t_factor_ms, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms,
+               t_total_ms=st.t_total_ms,
+               res_hist=list(st.res_hist[:st.res_hist_len]), count_hist=list(st.count_hist[:st.res_hist_len]))
+    if Xl is not None:
+        out["Xl"] = _finish(Xl, out_device)[:, :k]
+    return out

@@ -1,0 +1,261 @@
+// Element-wise and column-wise kernels.  All of them are HBM- or latency-bound;
+// the heavy one is the accumulation sum_k sigma_k X_k of Eq. Rasp / Eq. Lasp,
+// which streams the q solution blocks once in a fixed order of k.
+#include "blas1.cuh"
+
+namespace {
+
+template <typename T>
+__global__ void k_form_shifted(const double2* A, long long lda, const double2* B, long long ldb,
+                               const double2* z, int q, int n, cplx<T>* S, long long strideS) {
+  __shared__ double2 sz[256];
+  for (int k = threadIdx.x; k < q && k < 256; k += blockDim.x) sz[k] = z[k];
+  __syncthreads();
+  const size_t total = (size_t)n * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx % n, j = idx / n;
+    const double2 a = A[i + j * lda];
+    const double2 b = B ? B[i + j * ldb] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+    for (int k = 0; k < q; ++k) {
+      const double2 zk = k < 256 ? sz[k] : z[k];
+      const double2 v = csub<double>(cmul<double>(zk, b), a);
+      S[(size_t)k * strideS + idx] = cconv<T, double>(v);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_accumulate(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* c0,
+                             const double2* Y, const int32_t* rowmap, double2* Q) {
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % n);
+    const int i = (int)(idx / n);
+    double2 acc = make_double2(0.0, 0.0);
+    if (c0 && Y) acc = cmul<double>(c0[i], Y[idx]);
+    for (int b = 0; b < q; ++b) {
+      const int rr = rowmap ? rowmap[(size_t)b * n + r] : r;
+      const cplx<T> x = Xs[(size_t)b * total + (size_t)i * n + rr];
+      cfma<double>(acc, coef[(size_t)b * m + i], cconv<double, T>(x));
+    }
+    Q[idx] = acc;
+  }
+}
+
+__global__ void k_select(const double2* E, const double2* F, const int* use_res, int n, int m, double2* R) {
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n);
+    R[idx] = use_res[i] ? E[idx] : F[idx];
+  }
+}
+
+__device__ double block_sum256(double v) {
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += red[k];
+  return t;
+}
+
+__device__ double2 block_csum256(double2 v) {
+  const double a = block_sum256(v.x);
+  const double b = block_sum256(v.y);
+  return make_double2(a, b);
+}
+
+__global__ void __launch_bounds__(256) k_col_norms(const double2* X, int n, double* nrm) {
+  const double2* x = X + (size_t)blockIdx.x * n;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) s += cnorm2<double>(x[r]);
+  s = block_sum256(s);
+  if (threadIdx.x == 0) nrm[blockIdx.x] = sqrt(s);
+}
+
+__global__ void k_scale_cols(double2* X0, double2* X1, double2* X2, int n, int m, const double* nrm,
+                             const double2* d) {
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n);
+    double2 f;
+    if (nrm) {
+      const double v = nrm[i];
+      f = make_double2(v > 0.0 ? 1.0 / v : 0.0, 0.0);
+    } else {
+      const double2 dv = d[i];
+      f = (dv.x == 0.0 && dv.y == 0.0) ? make_double2(1.0, 0.0) : crecip<double>(cconj<double>(dv));
+    }
+    if (X0) X0[idx] = cmul<double>(X0[idx], f);
+    if (X1) X1[idx] = cmul<double>(X1[idx], f);
+    if (X2) X2[idx] = cmul<double>(X2[idx], f);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_residual(const double2* AX, const double2* BX, const double2* lam, int conj_lam, int n, double2* E,
+           double* res, const double* xn) {
+  const int i = blockIdx.x;
+  double2 l = lam[i];
+  if (conj_lam) l.y = -l.y;
+  const size_t off = (size_t)i * n;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) {
+    const double2 e = csub<double>(AX[off + r], cmul<double>(BX[off + r], l));
+    E[off + r] = e;
+    s += cnorm2<double>(e);
+  }
+  s = block_sum256(s);
+  if (threadIdx.x == 0) res[i] = sqrt(s) / (xn ? xn[i] : 1.0);
+}
+
+__global__ void __launch_bounds__(256) k_col_dots(const double2* X, const double2* Y, int n, double2* d) {
+  const size_t off = (size_t)blockIdx.x * n;
+  double2 s = make_double2(0.0, 0.0);
+  for (int r = threadIdx.x; r < n; r += 256) s = cadd<double>(s, cmulc<double>(X[off + r], Y[off + r]));
+  s = block_csum256(s);
+  if (threadIdx.x == 0) d[blockIdx.x] = s;
+}
+
+__global__ void k_conj_transpose(const double2* src, int n, int m, double2* dst) {
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = idx % n, c = idx / n;
+    dst[c + r * m] = cconj<double>(src[idx]);
+  }
+}
+
+__global__ void k_identity(double2* M, int m) {
+  const size_t total = (size_t)m * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x)
+    M[idx] = make_double2((idx % m) == (idx / m) ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void k_gather_cols(const double2* src, const int* idx, int k, int n, int m, double2* out) {
+  const size_t total = (size_t)n * m;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e % n, c = e / n;
+    out[e] = (int)c < k ? src[r + (size_t)idx[c] * n] : make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_normalize_vec(double2* x, int n, double* nrm) {
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) s += cnorm2<double>(x[r]);
+  s = block_sum256(s);
+  const double v = sqrt(s);
+  const double inv = v > 0.0 ? 1.0 / v : 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) x[r] = cscale<double>(x[r], inv);
+  if (threadIdx.x == 0) *nrm = v;
+}
+
+__global__ void k_check_finite(const double2* X, size_t count, unsigned* flags) {
+  bool bad = false;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = X[e];
+    if (!isfinite(v.x) || !isfinite(v.y)) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, (unsigned)DEVFLAG_NONFINITE);
+}
+
+unsigned grid_for(size_t total) {
+  size_t g = (total + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g ? g : 1);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t form_shifted(const double2* A, long long lda, const double2* B, long long ldb, const double2* z,
+                         int q, int n, cplx<T>* S, long long strideS, cudaStream_t s) {
+  feast_count_launch();
+  k_form_shifted<T><<<grid_for((size_t)n * n), 256, 0, s>>>(A, lda, B, ldb, z, q, n, S, strideS);
+  return cudaGetLastError();
+}
+template cudaError_t form_shifted<double>(const double2*, long long, const double2*, long long, const double2*, int, int, double2*, long long, cudaStream_t);
+template cudaError_t form_shifted<float>(const double2*, long long, const double2*, long long, const double2*, int, int, float2*, long long, cudaStream_t);
+
+template <typename T>
+cudaError_t accumulate(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* c0,
+                       const double2* Y, const int32_t* rowmap, double2* Q, cudaStream_t s) {
+  feast_count_launch();
+  k_accumulate<T><<<grid_for((size_t)n * m), 256, 0, s>>>(Xs, q, n, m, coef, c0, Y, rowmap, Q);
+  return cudaGetLastError();
+}
+template cudaError_t accumulate<double>(const double2*, int, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
+template cudaError_t accumulate<float>(const float2*, int, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
+
+cudaError_t select_columns(const double2* E, const double2* F, const int* use_res, int n, int m, double2* R,
+                           cudaStream_t s) {
+  feast_count_launch();
+  k_select<<<grid_for((size_t)n * m), 256, 0, s>>>(E, F, use_res, n, m, R);
+  return cudaGetLastError();
+}
+
+cudaError_t column_norms(const double2* X, int n, int m, double* nrm, cudaStream_t s) {
+  feast_count_launch();
+  k_col_norms<<<m, 256, 0, s>>>(X, n, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_columns_inv(double2* X0, double2* X1, double2* X2, int n, int m, const double* nrm,
+                              const double2* d, cudaStream_t s) {
+  feast_count_launch();
+  k_scale_cols<<<grid_for((size_t)n * m), 256, 0, s>>>(X0, X1, X2, n, m, nrm, d);
+  return cudaGetLastError();
+}
+
+cudaError_t residual_columns(const double2* AX, const double2* BX, const double2* lam, int conj_lam, int n,
+                             int m, double2* E, double* res, const double* xn, cudaStream_t s) {
+  feast_count_launch();
+  k_residual<<<m, 256, 0, s>>>(AX, BX, lam, conj_lam, n, E, res, xn);
+  return cudaGetLastError();
+}
+
+cudaError_t column_dots(const double2* X, const double2* Y, int n, int m, double2* d, cudaStream_t s) {
+  feast_count_launch();
+  k_col_dots<<<m, 256, 0, s>>>(X, Y, n, d);
+  return cudaGetLastError();
+}
+
+cudaError_t conj_transpose(const double2* src, int n, int m, double2* dst, cudaStream_t s) {
+  feast_count_launch();
+  k_conj_transpose<<<grid_for((size_t)n * m), 256, 0, s>>>(src, n, m, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(double2* M, int m, cudaStream_t s) {
+  feast_count_launch();
+  k_identity<<<grid_for((size_t)m * m), 256, 0, s>>>(M, m);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_columns(const double2* src, const int* idx, int k, int n, int m, double2* out, cudaStream_t s) {
+  feast_count_launch();
+  k_gather_cols<<<grid_for((size_t)n * m), 256, 0, s>>>(src, idx, k, n, m, out);
+  return cudaGetLastError();
+}
+
+cudaError_t normalize_vector(double2* x, int n, double* nrm, cudaStream_t s) {
+  feast_count_launch();
+  k_normalize_vec<<<1, 256, 0, s>>>(x, n, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t check_finite(const double2* X, size_t count, unsigned* flags, cudaStream_t s) {
+  feast_count_launch();
+  k_check_finite<<<grid_for(count), 256, 0, s>>>(X, count, flags);
+  return cudaGetLastError();
+}

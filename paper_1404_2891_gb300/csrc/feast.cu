@@ -1,0 +1,942 @@
+// The C ABI of include/feast_gb300.h: handle, quadrature (Sec. 3), the
+// factor-once shifted LUs, the filter (Eq. Rasp / Eq. Lasp), Rayleigh-Ritz
+// (Algorithms R-FEAST and Bi-FEAST) and the iteration with the Sec. 5
+// candidate monitoring.  All arithmetic runs in the kernels of this library;
+// the host only orders launches, computes the q quadrature nodes and weights
+// and takes the per-iteration decisions from a few hundred bytes of results.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/feast_gb300.h"
+#include "blas1.cuh"
+#include "gemm.cuh"
+#include "lu.cuh"
+#include "small.cuh"
+#include "tc_update.cuh"
+
+using zc = std::complex<double>;
+
+static std::atomic<unsigned long long> g_launches{0};
+void feast_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+inline double2 d2(zc v) { return make_double2(v.real(), v.imag()); }
+inline zc zz(double2 v) { return zc(v.x, v.y); }
+
+// ---------------------------------------------------------------- quadrature (host)
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on P_K (three-term
+// recurrence), weights 2 / ((1 - t^2) P_K'(t)^2).
+void gauss_legendre(int K, std::vector<double>& t, std::vector<double>& w) {
+  t.assign(K, 0.0);
+  w.assign(K, 0.0);
+  for (int k = 1; k <= K; ++k) {
+    double x = std::cos(M_PI * (k - 0.25) / (K + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int j = 2; j <= K; ++j) {
+        const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (K == 1) { p0 = 1.0; p1 = x; }
+      dp = K * (p0 - x * p1) / (1.0 - x * x);
+      const double step = p1 / dp;
+      x -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = x;
+    for (int j = 2; j <= K; ++j) {
+      const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = K * (p0 - x * p1) / (1.0 - x * x);
+    t[K - k] = x;  // increasing order
+    w[K - k] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// Eq. ellipses: phi(t) = c + R (cos th + i a sin th), th = pi/2 (1 + t), and dphi/dt.
+zc ellipse(double t, zc c, double R, double a) {
+  const double th = 0.5 * M_PI * (1.0 + t);
+  return c + R * zc(std::cos(th), a * std::sin(th));
+}
+zc ellipse_d(double t, double R, double a) {
+  const double th = 0.5 * M_PI * (1.0 + t);
+  return R * 0.5 * M_PI * zc(-std::sin(th), a * std::cos(th));
+}
+
+// Eq. quadrature_for_pi: sigma_k = w_k phi'(t_k) / (2 pi i) over both folded halves (Eq. pi).
+bool build_quadrature(const feast_contour& c, std::vector<zc>& z, std::vector<zc>& s) {
+  const zc cc(c.center.re, c.center.im);
+  const double R = c.R, a = c.aspect;
+  const zc twopii(0.0, 2.0 * M_PI);
+  z.clear();
+  s.clear();
+  if (c.rule == FEAST_RULE_CUSTOM) {
+    if (!c.nodes || !c.weights || c.q_custom < 1) return false;
+    for (int k = 0; k < c.q_custom; ++k) {
+      z.push_back(zc(c.nodes[k].re, c.nodes[k].im));
+      s.push_back(zc(c.weights[k].re, c.weights[k].im));
+    }
+    return true;
+  }
+  if (c.N_e < 1) return false;
+  if (c.rule == FEAST_RULE_TRAP_MID) {
+    const int q = c.N_e;
+    for (int j = 0; j < q; ++j) {
+      const double th = 2.0 * M_PI * (j + 0.5) / q;
+      const double t = 2.0 * th / M_PI - 1.0;
+      z.push_back(ellipse(t, cc, R, a));
+      s.push_back((4.0 / q) * ellipse_d(t, R, a) / twopii);
+    }
+    return true;
+  }
+  std::vector<double> t, w;
+  const int K = c.N_e;
+  if (c.rule == FEAST_RULE_GAUSS) {
+    gauss_legendre(K, t, w);
+    for (int k = 0; k < K; ++k) { z.push_back(ellipse(t[k], cc, R, a)); s.push_back(w[k] * ellipse_d(t[k], R, a) / twopii); }
+    for (int k = 0; k < K; ++k) {
+      const double t2 = 2.0 - t[k];
+      z.push_back(ellipse(t2, cc, R, a));
+      s.push_back(w[k] * ellipse_d(t2, R, a) / twopii);
+    }
+    return true;
+  }
+  if (c.rule == FEAST_RULE_TRAP_END) {
+    if (K < 2) return false;
+    // endpoints of the two folded halves coincide pairwise: q = 2(K - 1) points,
+    // angle-uniform on the closed contour, each with the full step h = 2/(K-1).
+    const double h = 2.0 / (K - 1);
+    for (int k = 0; k < K; ++k) {
+      const double tk = -1.0 + h * k;
+      z.push_back(ellipse(tk, cc, R, a));
+      const double wk = (k == 0 || k == K - 1) ? h : h;  // h/2 + h/2 at the merged endpoints
+      s.push_back(wk * ellipse_d(tk, R, a) / twopii);
+    }
+    for (int k = K - 2; k >= 1; --k) {
+      const double t2 = 2.0 - (-1.0 + h * k);
+      z.push_back(ellipse(t2, cc, R, a));
+      s.push_back(h * ellipse_d(t2, R, a) / twopii);
+    }
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the handle
+struct feast_handle {
+  int64_t n = 0;
+  int m0 = 0, q = 0;
+  feast_options opt;
+  cudaStream_t st = nullptr;
+  bool hasB = false;
+  zc center;
+  double R = 1.0, aspect = 1.0;
+  std::vector<zc> z, w;
+  double normA = 0.0;
+  bool factored = false;
+  feast_status factor_status = FEAST_OK;
+  int nb = 64, nbs = 64;
+  // device data
+  double2 *A = nullptr, *B = nullptr, *dz = nullptr;
+  void* S = nullptr;
+  int32_t *piv = nullptr, *perm = nullptr, *pinv = nullptr;
+  int* info = nullptr;
+  unsigned* flags = nullptr;
+  void *Xs = nullptr, *Xsh = nullptr;
+  double2 *Y = nullptr, *Yh = nullptr, *Rr = nullptr, *Rl = nullptr, *Q = nullptr, *Qh = nullptr;
+  double2 *Qo = nullptr, *Qho = nullptr, *AQ = nullptr, *BQ = nullptr, *AhQ = nullptr, *BhQ = nullptr;
+  double2 *X = nullptr, *Xl = nullptr, *AX = nullptr, *BX = nullptr, *AhX = nullptr, *BhX = nullptr;
+  double2 *E = nullptr, *Eh = nullptr, *tmp = nullptr;
+  double2 *Ahat = nullptr, *Bhat = nullptr, *LUB = nullptr, *Cm = nullptr, *Zs = nullptr, *V = nullptr;
+  double2 *W = nullptr, *LUW = nullptr, *Minv = nullptr, *Zl = nullptr, *lam = nullptr, *dd = nullptr;
+  double2 *coef = nullptr, *coefh = nullptr, *c0 = nullptr, *c0h = nullptr;
+  int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *useresh = nullptr, *colidx = nullptr;
+  double *res = nullptr, *resl = nullptr, *xn = nullptr, *xln = nullptr, *scal = nullptr;
+  void* orth_scratch = nullptr;
+  std::vector<void*> allocs;
+  // host mirrors of the last Rayleigh-Ritz step
+  std::vector<zc> h_lam;
+  std::vector<double> h_res, h_resl;
+  bool have_rr = false;
+  // timing
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double t_factor = 0, t_filter = 0, t_rr = 0, t_update = 0;
+  int n_update = 0;
+  std::vector<cudaEvent_t> upd_ev;
+};
+
+namespace {
+
+feast_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FEAST_OK;
+  if (e == cudaErrorMemoryAllocation) return FEAST_ERR_ALLOC;
+  return FEAST_ERR_CUDA;
+}
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(feast_handle* h, P** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(v);
+  *p = reinterpret_cast<P*>(v);
+  return cudaSuccess;
+}
+
+bool mixed(const feast_handle* h) { return h->opt.precision == FEAST_PREC_MIXED; }
+
+template <typename T>
+LuBatch<T> lu_view(feast_handle* h) {
+  LuBatch<T> lu;
+  lu.S = reinterpret_cast<cplx<T>*>(h->S);
+  lu.ld = h->n;
+  lu.stride = h->n * h->n;
+  lu.n = (int)h->n;
+  lu.q = h->q;
+  lu.piv = h->piv;
+  lu.perm = h->perm;
+  lu.pinv = h->pinv;
+  lu.info = h->info;
+  lu.flags = h->flags;
+  return lu;
+}
+
+cudaError_t zg(feast_handle* h, int opA, int opB, int M, int N, int K, zc alpha, const double2* A, long long lda,
+               const double2* B, long long ldb, zc beta, double2* C, long long ldc) {
+  GemmArgs<double> g;
+  g.M = M; g.N = N; g.K = K; g.batch = 1;
+  g.alpha = d2(alpha); g.beta = d2(beta);
+  g.A = A; g.lda = lda; g.opA = opA;
+  g.B = B; g.ldb = ldb; g.opB = opB;
+  g.C = C; g.ldc = ldc;
+  return gemm_batched<double>(g, h->st);
+}
+
+feast_status read_flags(feast_handle* h) {
+  unsigned f = 0;
+  CK(cudaMemcpyAsync(&f, h->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (f & DEVFLAG_TIMEOUT) return FEAST_ERR_DEVICE_TIMEOUT;
+  if (f & DEVFLAG_NONFINITE) return FEAST_ERR_NONFINITE;
+  return FEAST_OK;
+}
+
+void ev_mark(feast_handle* h, int i) {
+  if (h->opt.timing) cudaEventRecord(h->ev[i], h->st);
+}
+double ev_ms(feast_handle* h, int a, int b) {
+  if (!h->opt.timing) return 0.0;
+  float ms = 0.f;
+  cudaEventSynchronize(h->ev[b]);
+  cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]);
+  return ms;
+}
+
+// ---------------------------------------------------------------- factorisation
+// Trailing-update wrapper that brackets every launch with CUDA events (timing mode).
+template <typename T>
+struct UpdateTimer {
+  TrailingUpdateFn<T> inner;
+  void* ctx;
+  feast_handle* h;
+  int used;
+  double ms;
+};
+
+template <typename T>
+cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, void* c, cudaStream_t s) {
+  auto* t = reinterpret_cast<UpdateTimer<T>*>(c);
+  if (lu.n - k0 - w <= 0) return cudaSuccess;
+  cudaEventRecord(t->h->upd_ev[2 * t->used], s);
+  cudaError_t e = t->inner(lu, k0, w, t->ctx, s);
+  cudaEventRecord(t->h->upd_ev[2 * t->used + 1], s);
+  ++t->used;
+  return e;
+}
+
+template <typename T>
+feast_status factor_impl(feast_handle* h) {
+  LuBatch<T> lu = lu_view<T>(h);
+  CK(form_shifted<T>(h->A, h->n, h->hasB ? h->B : nullptr, h->n, h->dz, h->q, (int)h->n, lu.S, lu.stride, h->st));
+  TrailingUpdateFn<T> upd = nullptr;
+  void* ctx = nullptr;
+  select_trailing_update<T>(&upd, &ctx);
+  if (!upd) upd = default_trailing_update<T>;
+  UpdateTimer<T> timer{upd, ctx, h, 0, 0.0};
+  if (h->opt.timing) {
+    const int panels = (int)((h->n + h->nb - 1) / h->nb);
+    while ((int)h->upd_ev.size() < 2 * panels) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->upd_ev.push_back(e);
+    }
+    CK(lu_factor_batched<T>(lu, h->nb, timed_update<T>, &timer, h->st));
+  } else {
+    CK(lu_factor_batched<T>(lu, h->nb, upd, ctx, h->st));
+  }
+  std::vector<int> info(h->q);
+  CK(cudaMemcpyAsync(info.data(), h->info, sizeof(int) * h->q, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->t_update = 0.0;
+  h->n_update = timer.used;
+  for (int i = 0; i < timer.used; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->upd_ev[2 * i], h->upd_ev[2 * i + 1]);
+    h->t_update += ms;
+  }
+  feast_status fs = read_flags(h);
+  if (fs == FEAST_ERR_NONFINITE) return fs;
+  for (int k = 0; k < h->q; ++k)
+    if (info[k] != 0) return FEAST_ERR_SINGULAR_SHIFT;
+  return fs;
+}
+
+feast_status ensure_factored(feast_handle* h) {
+  if (h->factored) return h->factor_status;
+  ev_mark(h, 0);
+  feast_status s = mixed(h) ? factor_impl<float>(h) : factor_impl<double>(h);
+  ev_mark(h, 1);
+  h->t_factor = ev_ms(h, 0, 1);
+  h->factored = true;
+  h->factor_status = s;
+  return s;
+}
+
+// ---------------------------------------------------------------- filter
+// Right: Q = c0 .* Y + sum_k coef_k .* S_k^{-1} R;  left: Qh = c0h .* Yh + sum_k coefh_k .* S_k^{-H} Rh
+template <typename T>
+feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, bool use_c0, const double2* Rh,
+                         const double2* Yhc0, double2* Qout, double2* Qhout) {
+  LuBatch<T> lu = lu_view<T>(h);
+  const int n = (int)h->n, m = h->m0;
+  cplx<T>* Xs = reinterpret_cast<cplx<T>*>(h->Xs);
+  CK(rows_gather<T>(lu, R, Xs, m, true, h->st));
+  CK(lu_solve_batched<T>(lu, 0, Xs, m, h->nbs, h->st));
+  CK(accumulate<T>(Xs, h->q, n, m, h->coef, use_c0 ? h->c0 : nullptr, use_c0 ? Yc0 : nullptr, nullptr, Qout, h->st));
+  if (Rh) {
+    cplx<T>* Xsh = reinterpret_cast<cplx<T>*>(h->Xsh);
+    CK(rows_gather<T>(lu, Rh, Xsh, m, false, h->st));
+    CK(lu_solve_batched<T>(lu, 1, Xsh, m, h->nbs, h->st));
+    CK(accumulate<T>(Xsh, h->q, n, m, h->coefh, use_c0 ? h->c0h : nullptr, use_c0 ? Yhc0 : nullptr, lu.pinv,
+                     Qhout, h->st));
+  }
+  return FEAST_OK;
+}
+
+// Host-side coefficients.  Plain form: coef_k = sigma_k.  Residual form for
+// column i (Ritz value theta_i not within 5 % of R of any node):
+//   S_k^{-1} B x = x / (phi_k - theta) + S_k^{-1} (A x - theta B x) / (phi_k - theta)
+// so coef_k,i = sigma_k / (phi_k - theta_i) and c0_i = sum_k coef_k,i = rho(theta_i).
+feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* use_out) {
+  const int q = h->q, m = h->m0;
+  std::vector<double2> coef((size_t)q * m), coefh((size_t)q * m), c0(m), c0h(m);
+  std::vector<int> use(m, 0);
+  for (int i = 0; i < m; ++i) {
+    bool u = false;
+    if (theta && std::isfinite(theta[i].real()) && std::isfinite(theta[i].imag())) {
+      double dmin = 1e300;
+      for (int k = 0; k < q; ++k) dmin = std::min(dmin, std::abs(h->z[k] - theta[i]));
+      u = dmin >= 0.05 * h->R;
+    }
+    use[i] = u;
+    zc acc = 0.0;
+    for (int k = 0; k < q; ++k) {
+      const zc g = u ? h->w[k] / (h->z[k] - theta[i]) : h->w[k];
+      acc += g;
+      coef[(size_t)k * m + i] = d2(g);
+      coefh[(size_t)k * m + i] = d2(std::conj(g));
+    }
+    c0[i] = d2(u ? acc : zc(0.0));
+    c0h[i] = d2(u ? std::conj(acc) : zc(0.0));
+  }
+  CK(cudaMemcpyAsync(h->coef, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->coefh, coefh.data(), coefh.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->c0, c0.data(), c0.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->c0h, c0h.data(), c0h.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->useres, use.data(), m * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));  // the host vectors go out of scope
+  if (use_out) *use_out = use;
+  return FEAST_OK;
+}
+
+feast_status run_filter(feast_handle* h, const double2* R, const double2* Yc0, bool use_c0, const double2* Rh,
+                        const double2* Yhc0) {
+  return mixed(h) ? filter_impl<float>(h, R, Yc0, use_c0, Rh, Yhc0, h->Q, h->Qh)
+                  : filter_impl<double>(h, R, Yc0, use_c0, Rh, Yhc0, h->Q, h->Qh);
+}
+
+// ---------------------------------------------------------------- Rayleigh-Ritz
+feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
+  const int n = (int)h->n, m = h->m0;
+  const bool bi = Qhin != nullptr;
+  const size_t blk = (size_t)n * m * sizeof(double2);
+  const zc one(1.0), zero(0.0);
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned), h->st));
+  CK(cudaMemcpyAsync(h->Qo, Qin, blk, cudaMemcpyDeviceToDevice, h->st));
+  CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st));
+  if (bi) {
+    CK(cudaMemcpyAsync(h->Qho, Qhin, blk, cudaMemcpyDeviceToDevice, h->st));
+    CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
+  }
+  const double2* Vb = bi ? h->Qho : h->Qo;
+  CK(zg(h, OP_N, OP_N, n, m, n, one, h->A, n, h->Qo, n, zero, h->AQ, n));
+  const double2* BQp = h->Qo;
+  if (h->hasB) {
+    CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Qo, n, zero, h->BQ, n));
+    BQp = h->BQ;
+  }
+  CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, h->AQ, n, zero, h->Ahat, m));
+  CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, BQp, n, zero, h->Bhat, m));
+  // reduced problem: C = B^{-1} A^, Schur form, eigenvectors
+  const size_t sm = (size_t)m * m * sizeof(double2);
+  CK(cudaMemcpyAsync(h->LUB, h->Bhat, sm, cudaMemcpyDeviceToDevice, h->st));
+  CK(small_lu(h->LUB, m, h->pivB, h->flags, h->st));
+  CK(cudaMemcpyAsync(h->Cm, h->Ahat, sm, cudaMemcpyDeviceToDevice, h->st));
+  CK(small_lu_solve(h->LUB, h->pivB, m, h->Cm, m, 0, h->st));
+  CK(small_schur(h->Cm, h->Zs, h->lam, m, h->flags, h->st));
+  CK(small_trevc(h->Cm, h->V, m, h->st));
+  CK(zg(h, OP_N, OP_N, m, m, m, one, h->Zs, m, h->V, m, zero, h->W, m));
+  // Ritz vectors and residuals
+  CK(zg(h, OP_N, OP_N, n, m, m, one, h->Qo, n, h->W, m, zero, h->X, n));
+  CK(zg(h, OP_N, OP_N, n, m, m, one, h->AQ, n, h->W, m, zero, h->AX, n));
+  double2* BXp = h->X;
+  if (h->hasB) {
+    CK(zg(h, OP_N, OP_N, n, m, m, one, h->BQ, n, h->W, m, zero, h->BX, n));
+    BXp = h->BX;
+  }
+  CK(column_norms(h->X, n, m, h->xn, h->st));
+  CK(scale_columns_inv(h->X, h->AX, h->hasB ? h->BX : nullptr, n, m, h->xn, nullptr, h->st));
+  CK(residual_columns(h->AX, BXp, h->lam, 0, n, m, h->E, h->res, nullptr, h->st));
+  if (bi) {
+    CK(zg(h, OP_C, OP_N, n, m, n, one, h->A, n, h->Qho, n, zero, h->AhQ, n));
+    const double2* BhQp = h->Qho;
+    if (h->hasB) {
+      CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Qho, n, zero, h->BhQ, n));
+      BhQp = h->BhQ;
+    }
+    CK(cudaMemcpyAsync(h->LUW, h->W, sm, cudaMemcpyDeviceToDevice, h->st));
+    CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
+    CK(set_identity(h->Minv, m, h->st));
+    CK(small_lu_solve(h->LUW, h->pivW, m, h->Minv, m, 0, h->st));
+    CK(conj_transpose(h->Minv, m, m, h->Zl, h->st));
+    CK(small_lu_solve(h->LUB, h->pivB, m, h->Zl, m, 1, h->st));
+    CK(zg(h, OP_N, OP_N, n, m, m, one, h->Qho, n, h->Zl, m, zero, h->Xl, n));
+    CK(zg(h, OP_N, OP_N, n, m, m, one, h->AhQ, n, h->Zl, m, zero, h->AhX, n));
+    double2* BhXp = h->Xl;
+    if (h->hasB) {
+      CK(zg(h, OP_N, OP_N, n, m, m, one, BhQp, n, h->Zl, m, zero, h->BhX, n));
+      BhXp = h->BhX;
+    }
+    CK(column_dots(h->Xl, BXp, n, m, h->dd, h->st));
+    CK(scale_columns_inv(h->Xl, h->AhX, h->hasB ? h->BhX : nullptr, n, m, nullptr, h->dd, h->st));
+    CK(column_norms(h->Xl, n, m, h->xln, h->st));
+    CK(residual_columns(h->AhX, BhXp, h->lam, 1, n, m, h->Eh, h->resl, h->xln, h->st));
+  }
+  h->h_lam.resize(m);
+  h->h_res.resize(m);
+  h->h_resl.assign(m, 0.0);
+  std::vector<double2> lam(m);
+  CK(cudaMemcpyAsync(lam.data(), h->lam, m * sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_res.data(), h->res, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (bi) CK(cudaMemcpyAsync(h->h_resl.data(), h->resl, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  for (int i = 0; i < m; ++i) h->h_lam[i] = zz(lam[i]);
+  h->have_rr = true;
+  return read_flags(h);
+}
+
+bool inside_ellipse(const feast_handle* h, zc l) {
+  const double x = (l.real() - h->center.real()) / h->R;
+  const double y = (l.imag() - h->center.imag()) / (h->R * h->aspect);
+  return x * x + y * y < 1.0;
+}
+
+// candidates of the last Rayleigh-Ritz step, sorted by (Re, Im)
+std::vector<int> candidates(const feast_handle* h) {
+  std::vector<int> idx;
+  for (int i = 0; i < h->m0; ++i) {
+    const zc l = h->h_lam[i];
+    if (!std::isfinite(l.real()) || !std::isfinite(l.imag())) continue;
+    if (!std::isfinite(h->h_res[i])) continue;
+    if (inside_ellipse(h, l) && h->h_res[i] <= h->opt.cand_tol) idx.push_back(i);
+  }
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    const zc la = h->h_lam[a], lb = h->h_lam[b];
+    if (la.real() != lb.real()) return la.real() < lb.real();
+    return la.imag() < lb.imag();
+  });
+  return idx;
+}
+
+feast_status copy_in(feast_handle* h, double2* dst, const feast_z* src, size_t count) {
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(double2), cudaMemcpyDefault, h->st));
+  return FEAST_OK;
+}
+feast_status copy_out(feast_handle* h, feast_z* dst, const double2* src, size_t count) {
+  if (!dst) return FEAST_OK;
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(double2), cudaMemcpyDefault, h->st));
+  return FEAST_OK;
+}
+
+feast_status estimate_norm2(feast_handle* h) {
+  const int n = (int)h->n;
+  std::vector<double2> ones(n, make_double2(1.0, 0.0));
+  double2* x = h->tmp;
+  double2* y = h->tmp + n;
+  CK(cudaMemcpyAsync(x, ones.data(), n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(normalize_vector(x, n, h->scal, h->st));
+  for (int it = 0; it < 50; ++it) {
+    CK(zg(h, OP_N, OP_N, n, 1, n, 1.0, h->A, n, x, n, 0.0, y, n));
+    CK(zg(h, OP_C, OP_N, n, 1, n, 1.0, h->A, n, y, n, 0.0, x, n));
+    CK(normalize_vector(x, n, h->scal, h->st));
+  }
+  double s = 0.0;
+  CK(cudaMemcpyAsync(&s, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->normA = std::sqrt(s);
+  return FEAST_OK;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+uint64_t feast_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void feast_default_options(feast_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->algo = FEAST_ALGO_BI;
+  o->precision = FEAST_PREC_MIXED;
+  o->tol = 1e-10;
+  o->max_iter = 20;
+  o->cand_tol = 1e-4;
+  o->panel = 0;
+  o->timing = 0;
+}
+
+const char* feast_status_str(feast_status s) {
+  switch (s) {
+    case FEAST_OK: return "ok";
+    case FEAST_ERR_ARG: return "invalid argument";
+    case FEAST_ERR_ALLOC: return "device allocation failed";
+    case FEAST_ERR_SINGULAR_SHIFT: return "a shifted matrix is exactly singular";
+    case FEAST_ERR_REFINE_NOCONV: return "refinement did not converge";
+    case FEAST_ERR_M0_TOO_SMALL: return "subspace too small";
+    case FEAST_ERR_NOCONV: return "no convergence within max_iter";
+    case FEAST_ERR_NONFINITE: return "non-finite value";
+    case FEAST_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case FEAST_ERR_CUDA: return "CUDA error";
+    case FEAST_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+void feast_destroy(feast_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->upd_ev) cudaEventDestroy(e);
+  delete h;
+}
+
+feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64_t lda, const feast_z* B,
+                          int64_t ldb, const feast_contour* c, int m0, const feast_options* o, void* stream) {
+  if (!out) return FEAST_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || !A || !c || lda < n || (B && ldb < n) || m0 < 1 || m0 > n || m0 > 160) return FEAST_ERR_ARG;
+  if (c->R <= 0.0 || c->aspect <= 0.0) return FEAST_ERR_ARG;
+  feast_handle* h = new (std::nothrow) feast_handle();
+  if (!h) return FEAST_ERR_ALLOC;
+  if (o) h->opt = *o; else feast_default_options(&h->opt);
+  if (h->opt.tol <= 0) h->opt.tol = 1e-10;
+  if (h->opt.max_iter < 1) h->opt.max_iter = 20;
+  if (h->opt.max_iter > 64) h->opt.max_iter = 64;
+  if (h->opt.cand_tol <= 0) h->opt.cand_tol = 1e-4;
+  if (h->opt.algo != FEAST_ALGO_R && h->opt.algo != FEAST_ALGO_BI) { delete h; return FEAST_ERR_ARG; }
+  if (h->opt.precision != FEAST_PREC_FP64 && h->opt.precision != FEAST_PREC_MIXED) { delete h; return FEAST_ERR_ARG; }
+  h->n = n;
+  h->m0 = m0;
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  h->hasB = B != nullptr;
+  h->center = zc(c->center.re, c->center.im);
+  h->R = c->R;
+  h->aspect = c->aspect;
+  if (!build_quadrature(*c, h->z, h->w) || h->z.size() > 256) { delete h; return FEAST_ERR_ARG; }
+  h->q = (int)h->z.size();
+  const bool mx = h->opt.precision == FEAST_PREC_MIXED;
+  h->nb = h->opt.panel > 0 ? std::min(h->opt.panel, mx ? 128 : 64) : 64;
+  h->nbs = 64;
+  const size_t esz = mx ? sizeof(float2) : sizeof(double2);
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
+  auto fail = [&](cudaError_t e) { feast_destroy(h); return cuda_status(e); };
+  cudaError_t e;
+#define AL(p, bytes) if ((e = dalloc(h, &(p), (bytes))) != cudaSuccess) return fail(e)
+  AL(h->A, nn * sizeof(double2));
+  if (h->hasB) AL(h->B, nn * sizeof(double2));
+  AL(h->dz, h->q * sizeof(double2));
+  AL(h->S, nn * h->q * esz);
+  AL(h->piv, (size_t)h->q * n * sizeof(int32_t));
+  AL(h->perm, (size_t)h->q * n * sizeof(int32_t));
+  AL(h->pinv, (size_t)h->q * n * sizeof(int32_t));
+  AL(h->info, h->q * sizeof(int));
+  AL(h->flags, 64);
+  AL(h->Xs, nm * std::max(h->q, 2) * esz);
+  if (h->opt.algo == FEAST_ALGO_BI) AL(h->Xsh, nm * h->q * esz);
+  double2** blocks[] = {&h->Y, &h->Yh, &h->Rr, &h->Rl, &h->Q, &h->Qh, &h->Qo, &h->Qho, &h->AQ, &h->BQ,
+                        &h->AhQ, &h->BhQ, &h->X, &h->Xl, &h->AX, &h->BX, &h->AhX, &h->BhX, &h->E, &h->Eh, &h->tmp};
+  for (double2** p : blocks) AL(*p, nm * sizeof(double2) + 2 * n * sizeof(double2));
+  double2** smalls[] = {&h->Ahat, &h->Bhat, &h->LUB, &h->Cm, &h->Zs, &h->V, &h->W, &h->LUW, &h->Minv, &h->Zl};
+  for (double2** p : smalls) AL(*p, mm * sizeof(double2));
+  AL(h->lam, m0 * sizeof(double2));
+  AL(h->dd, m0 * sizeof(double2));
+  AL(h->coef, (size_t)h->q * m0 * sizeof(double2));
+  AL(h->coefh, (size_t)h->q * m0 * sizeof(double2));
+  AL(h->c0, m0 * sizeof(double2));
+  AL(h->c0h, m0 * sizeof(double2));
+  AL(h->pivB, m0 * sizeof(int));
+  AL(h->pivW, m0 * sizeof(int));
+  AL(h->useres, m0 * sizeof(int));
+  AL(h->useresh, m0 * sizeof(int));
+  AL(h->colidx, m0 * sizeof(int));
+  AL(h->res, m0 * sizeof(double));
+  AL(h->resl, m0 * sizeof(double));
+  AL(h->xn, m0 * sizeof(double));
+  AL(h->xln, m0 * sizeof(double));
+  AL(h->scal, 64);
+  AL(h->orth_scratch, orth_scratch_bytes((int)n, m0));
+#undef AL
+  if (h->opt.timing)
+    for (auto& ev : h->ev) cudaEventCreate(&ev);
+  std::vector<double2> zd(h->q);
+  for (int k = 0; k < h->q; ++k) zd[k] = d2(h->z[k]);
+  if ((e = cudaMemcpyAsync(h->dz, zd.data(), h->q * sizeof(double2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemsetAsync(h->flags, 0, 64, h->st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy2DAsync(h->A, n * sizeof(double2), A, lda * sizeof(double2), n * sizeof(double2), n,
+                             cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
+  if (h->hasB && (e = cudaMemcpy2DAsync(h->B, n * sizeof(double2), B, ldb * sizeof(double2), n * sizeof(double2), n,
+                                       cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
+  if ((e = check_finite(h->A, nn, h->flags, h->st)) != cudaSuccess) return fail(e);
+  if (h->hasB && (e = check_finite(h->B, nn, h->flags, h->st)) != cudaSuccess) return fail(e);
+  feast_status s = read_flags(h);
+  if (s != FEAST_OK) { feast_destroy(h); return s; }
+  s = estimate_norm2(h);
+  if (s != FEAST_OK) { feast_destroy(h); return s; }
+  *out = h;
+  return FEAST_OK;
+}
+
+feast_status feast_get_quadrature(const feast_handle* h, int* q, feast_z* nodes, feast_z* weights) {
+  if (!h) return FEAST_ERR_ARG;
+  if (q) *q = h->q;
+  for (int k = 0; k < h->q; ++k) {
+    if (nodes) { nodes[k].re = h->z[k].real(); nodes[k].im = h->z[k].imag(); }
+    if (weights) { weights[k].re = h->w[k].real(); weights[k].im = h->w[k].imag(); }
+  }
+  return FEAST_OK;
+}
+
+feast_status feast_get_stats(const feast_handle* h, feast_stats* st) {
+  if (!h || !st) return FEAST_ERR_ARG;
+  std::memset(st, 0, sizeof(*st));
+  st->normA = h->normA;
+  st->t_factor_ms = h->t_factor;
+  st->t_update_ms = h->t_update;
+  st->update_launches = h->n_update;
+  st->t_filter_ms = h->t_filter;
+  st->t_rr_ms = h->t_rr;
+  return FEAST_OK;
+}
+
+feast_status feast_factor(feast_handle* h) {
+  if (!h) return FEAST_ERR_ARG;
+  h->factored = false;  // an explicit call always forms and factors again
+  return ensure_factored(h);
+}
+
+feast_status feast_get_factor(feast_handle* h, int k, feast_z* LU, int32_t* piv) {
+  if (!h || k < 0 || k >= h->q) return FEAST_ERR_ARG;
+  if (!h->factored) return FEAST_ERR_STATE;
+  const size_t nn = (size_t)h->n * h->n;
+  if (LU) {
+    if (mixed(h)) {
+      std::vector<float2> tmp(nn);
+      CK(cudaMemcpyAsync(tmp.data(), reinterpret_cast<float2*>(h->S) + k * nn, nn * sizeof(float2),
+                         cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      std::vector<double2> d(nn);
+      for (size_t i = 0; i < nn; ++i) d[i] = make_double2(tmp[i].x, tmp[i].y);
+      CK(cudaMemcpyAsync(LU, d.data(), nn * sizeof(double2), cudaMemcpyDefault, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    } else {
+      CK(cudaMemcpyAsync(LU, reinterpret_cast<double2*>(h->S) + k * nn, nn * sizeof(double2), cudaMemcpyDefault, h->st));
+    }
+  }
+  if (piv) CK(cudaMemcpyAsync(piv, h->piv + (size_t)k * h->n, h->n * sizeof(int32_t), cudaMemcpyDefault, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return FEAST_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+feast_status solve_shift_impl(feast_handle* h, int k, int side, int nrhs, double2* out) {
+  LuBatch<T> lu = lu_view<T>(h);
+  const size_t nn = (size_t)h->n * h->n;
+  lu.S += nn * k;
+  lu.piv += (size_t)k * h->n;
+  lu.perm += (size_t)k * h->n;
+  lu.pinv += (size_t)k * h->n;
+  lu.info += k;
+  lu.q = 1;
+  cplx<T>* X = reinterpret_cast<cplx<T>*>(h->Xs);
+  cplx<T>* X2 = X + (size_t)h->n * nrhs;
+  CK(rows_gather<T>(lu, h->Rr, X, nrhs, side == 0, h->st));
+  CK(lu_solve_batched<T>(lu, side, X, nrhs, h->nbs, h->st));
+  const cplx<T>* res = X;
+  if (side == 1) {
+    CK(rows_scatter<T>(lu, X, X2, nrhs, h->st));
+    res = X2;
+  }
+  // widen into `out` through the accumulation kernel with unit coefficients
+  std::vector<double2> ones((size_t)nrhs, make_double2(1.0, 0.0));
+  CK(cudaMemcpyAsync(h->coef, ones.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(accumulate<T>(res, 1, (int)h->n, nrhs, h->coef, nullptr, nullptr, nullptr, out, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return FEAST_OK;
+}
+}  // namespace
+
+extern "C" {
+
+feast_status feast_solve_shift(feast_handle* h, int k, int side, const feast_z* R, feast_z* X, int nrhs) {
+  if (!h || k < 0 || k >= h->q || (side != 0 && side != 1) || !R || !X || nrhs < 1 || nrhs > h->m0)
+    return FEAST_ERR_ARG;
+  feast_status s = ensure_factored(h);
+  if (s != FEAST_OK && s != FEAST_ERR_SINGULAR_SHIFT) return s;
+  const size_t cnt = (size_t)h->n * nrhs;
+  if ((s = copy_in(h, h->Rr, R, cnt)) != FEAST_OK) return s;
+  s = mixed(h) ? solve_shift_impl<float>(h, k, side, nrhs, h->tmp) : solve_shift_impl<double>(h, k, side, nrhs, h->tmp);
+  if (s != FEAST_OK) return s;
+  if ((s = copy_out(h, X, h->tmp, cnt)) != FEAST_OK) return s;
+  CK(cudaStreamSynchronize(h->st));
+  return FEAST_OK;
+}
+
+feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat, const feast_z* theta, feast_z* Q,
+                          feast_z* Qhat) {
+  if (!h || !Y || !Q || (Yhat && !Qhat)) return FEAST_ERR_ARG;
+  if (Yhat && h->opt.algo != FEAST_ALGO_BI) return FEAST_ERR_ARG;
+  feast_status s = ensure_factored(h);
+  if (s != FEAST_OK) return s;
+  const int n = (int)h->n, m = h->m0;
+  const size_t cnt = (size_t)n * m;
+  const zc one(1.0), zero(0.0);
+  if ((s = copy_in(h, h->Y, Y, cnt)) != FEAST_OK) return s;
+  if (Yhat && (s = copy_in(h, h->Yh, Yhat, cnt)) != FEAST_OK) return s;
+  std::vector<zc> th;
+  const bool resform = theta && mixed(h);
+  if (resform) {
+    std::vector<double2> t(m);
+    CK(cudaMemcpyAsync(t.data(), theta, m * sizeof(double2), cudaMemcpyDefault, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < m; ++i) th.push_back(zz(t[i]));
+  }
+  if ((s = upload_coefs(h, resform ? th.data() : nullptr, nullptr)) != FEAST_OK) return s;
+  // right-hand sides: B Y (plain) or (A Y - B Y Theta) per column (residual form)
+  double2* BY = h->Y;
+  if (h->hasB) { CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Y, n, zero, h->BX, n)); BY = h->BX; }
+  const double2* R = BY;
+  if (resform) {
+    CK(cudaMemcpyAsync(h->lam, theta, m * sizeof(double2), cudaMemcpyDefault, h->st));
+    CK(zg(h, OP_N, OP_N, n, m, n, one, h->A, n, h->Y, n, zero, h->AX, n));
+    CK(residual_columns(h->AX, BY, h->lam, 0, n, m, h->E, h->res, nullptr, h->st));
+    CK(select_columns(h->E, BY, h->useres, n, m, h->Rr, h->st));
+    R = h->Rr;
+  }
+  const double2* Rh = nullptr;
+  if (Yhat) {
+    double2* BhY = h->Yh;
+    if (h->hasB) { CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Yh, n, zero, h->BhX, n)); BhY = h->BhX; }
+    Rh = BhY;
+    if (resform) {
+      CK(zg(h, OP_C, OP_N, n, m, n, one, h->A, n, h->Yh, n, zero, h->AhX, n));
+      CK(residual_columns(h->AhX, BhY, h->lam, 1, n, m, h->Eh, h->resl, nullptr, h->st));
+      CK(select_columns(h->Eh, BhY, h->useres, n, m, h->Rl, h->st));
+      Rh = h->Rl;
+    }
+  }
+  if ((s = run_filter(h, R, h->Y, resform, Rh, h->Yh)) != FEAST_OK) return s;
+  if ((s = copy_out(h, Q, h->Q, cnt)) != FEAST_OK) return s;
+  if (Yhat && (s = copy_out(h, Qhat, h->Qh, cnt)) != FEAST_OK) return s;
+  CK(cudaStreamSynchronize(h->st));
+  return read_flags(h);
+}
+
+feast_status feast_rayleigh_ritz(feast_handle* h, const feast_z* Q, const feast_z* Qhat, feast_z* lambda, feast_z* X,
+                                 feast_z* Xl, double* res, int* m_inside) {
+  if (!h || !Q || !lambda) return FEAST_ERR_ARG;
+  if (Qhat && h->opt.algo != FEAST_ALGO_BI) return FEAST_ERR_ARG;
+  const int n = (int)h->n, m = h->m0;
+  const size_t cnt = (size_t)n * m;
+  feast_status s;
+  if ((s = copy_in(h, h->Q, Q, cnt)) != FEAST_OK) return s;
+  if (Qhat && (s = copy_in(h, h->Qh, Qhat, cnt)) != FEAST_OK) return s;
+  if ((s = rr_impl(h, h->Q, Qhat ? h->Qh : nullptr)) != FEAST_OK) return s;
+  std::vector<double2> lam(m);
+  for (int i = 0; i < m; ++i) lam[i] = d2(h->h_lam[i]);
+  CK(cudaMemcpyAsync(lambda, lam.data(), m * sizeof(double2), cudaMemcpyDefault, h->st));
+  if ((s = copy_out(h, X, h->X, cnt)) != FEAST_OK) return s;
+  if (Qhat && (s = copy_out(h, Xl, h->Xl, cnt)) != FEAST_OK) return s;
+  std::vector<double> r(m);
+  for (int i = 0; i < m; ++i) r[i] = h->h_res[i] / h->normA;
+  if (res) CK(cudaMemcpyAsync(res, r.data(), m * sizeof(double), cudaMemcpyDefault, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (m_inside) *m_inside = (int)candidates(h).size();
+  return FEAST_OK;
+}
+
+feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vrand, feast_z* lambda, feast_z* Xout,
+                         feast_z* Xlout, double* res, int* m_found, feast_stats* stats) {
+  if (!h || !Y0 || !lambda) return FEAST_ERR_ARG;
+  const bool bi = h->opt.algo == FEAST_ALGO_BI;
+  const int n = (int)h->n, m = h->m0;
+  const size_t cnt = (size_t)n * m;
+  const zc one(1.0), zero(0.0);
+  feast_stats st;
+  std::memset(&st, 0, sizeof(st));
+  if (h->opt.timing) cudaEventRecord(h->ev[2], h->st);
+  h->t_filter = h->t_rr = 0.0;
+  feast_status s = ensure_factored(h);
+  st.t_factor_ms = h->t_factor;
+  if (s != FEAST_OK) return s;
+  if ((s = copy_in(h, h->Y, Y0, cnt)) != FEAST_OK) return s;
+  if (bi) {
+    // Bi-FEAST step 2: V0 = Vr (Vr^H B Y0)^{-H}
+    if ((s = copy_in(h, h->Yh, Vrand ? Vrand : Y0, cnt)) != FEAST_OK) return s;
+    const double2* BY0 = h->Y;
+    if (h->hasB) { CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Y, n, zero, h->BX, n)); BY0 = h->BX; }
+    CK(zg(h, OP_C, OP_N, m, m, n, one, h->Yh, n, BY0, n, zero, h->LUW, m));
+    CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
+    CK(set_identity(h->Minv, m, h->st));
+    CK(small_lu_solve(h->LUW, h->pivW, m, h->Minv, m, 0, h->st));
+    CK(cudaMemcpyAsync(h->tmp, h->Yh, cnt * sizeof(double2), cudaMemcpyDeviceToDevice, h->st));
+    CK(zg(h, OP_N, OP_C, n, m, m, one, h->tmp, n, h->Minv, m, zero, h->Yh, n));
+  }
+  int prev = -1;
+  bool converged = false;
+  std::vector<int> cand;
+  double max_res = INFINITY;
+  int it = 0;
+  for (it = 1; it <= h->opt.max_iter; ++it) {
+    ev_mark(h, 0);
+    const bool resform = mixed(h) && it > 1;
+    const double2 *R, *Rh = nullptr, *Yc0 = nullptr, *Yhc0 = nullptr;
+    if (it == 1) {
+      if ((s = upload_coefs(h, nullptr, nullptr)) != FEAST_OK) return s;
+      double2* BY = h->Y;
+      if (h->hasB) { CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Y, n, zero, h->BX, n)); BY = h->BX; }
+      R = BY;
+      if (bi) {
+        double2* BhY = h->Yh;
+        if (h->hasB) { CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Yh, n, zero, h->BhX, n)); BhY = h->BhX; }
+        Rh = BhY;
+      }
+    } else if (!resform) {
+      if ((s = upload_coefs(h, nullptr, nullptr)) != FEAST_OK) return s;
+      R = h->hasB ? h->BX : h->X;  // B U with U the unit Ritz vectors of the last step
+      if (bi) Rh = h->hasB ? h->BhX : h->Xl;
+    } else {
+      if ((s = upload_coefs(h, h->h_lam.data(), nullptr)) != FEAST_OK) return s;
+      const double2* BXp = h->hasB ? h->BX : h->X;
+      CK(select_columns(h->E, BXp, h->useres, n, m, h->Rr, h->st));
+      R = h->Rr;
+      Yc0 = h->X;
+      if (bi) {
+        const double2* BhXp = h->hasB ? h->BhX : h->Xl;
+        CK(select_columns(h->Eh, BhXp, h->useres, n, m, h->Rl, h->st));
+        Rh = h->Rl;
+        Yhc0 = h->Xl;
+      }
+    }
+    if ((s = run_filter(h, R, Yc0, resform, Rh, Yhc0)) != FEAST_OK) return s;
+    ev_mark(h, 1);
+    if ((s = rr_impl(h, h->Q, bi ? h->Qh : nullptr)) != FEAST_OK) return s;
+    ev_mark(h, 3);
+    h->t_filter += ev_ms(h, 0, 1);
+    h->t_rr += ev_ms(h, 1, 3);
+    cand = candidates(h);
+    const int count = (int)cand.size();
+    max_res = count ? 0.0 : INFINITY;
+    for (int i : cand) max_res = std::max(max_res, h->h_res[i] / h->normA);
+    if (it - 1 < 64) {
+      st.res_hist[it - 1] = max_res;
+      st.count_hist[it - 1] = count;
+      st.res_hist_len = it;
+    }
+    if (count > 0 && count == prev && max_res <= h->opt.tol) {
+      converged = true;
+      break;
+    }
+    prev = count;
+  }
+  if (it > h->opt.max_iter) it = h->opt.max_iter;
+  // outputs: candidates first, sorted by (Re, Im)
+  const int k = (int)cand.size();
+  std::vector<double2> lam(m, make_double2(0.0, 0.0));
+  std::vector<double> r(m, 0.0);
+  for (int j = 0; j < k; ++j) {
+    lam[j] = d2(h->h_lam[cand[j]]);
+    r[j] = h->h_res[cand[j]] / h->normA;
+  }
+  CK(cudaMemcpyAsync(lambda, lam.data(), m * sizeof(double2), cudaMemcpyDefault, h->st));
+  if (res) CK(cudaMemcpyAsync(res, r.data(), m * sizeof(double), cudaMemcpyDefault, h->st));
+  std::vector<int> idx(m, 0);
+  for (int j = 0; j < k; ++j) idx[j] = cand[j];
+  CK(cudaMemcpyAsync(h->colidx, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  if (Xout) {
+    CK(gather_columns(h->X, h->colidx, k, n, m, h->tmp, h->st));
+    if ((s = copy_out(h, Xout, h->tmp, cnt)) != FEAST_OK) return s;
+  }
+  if (Xlout && bi) {
+    CK(gather_columns(h->Xl, h->colidx, k, n, m, h->tmp, h->st));
+    if ((s = copy_out(h, Xlout, h->tmp, cnt)) != FEAST_OK) return s;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  if (m_found) *m_found = k;
+  st.iters = it;
+  st.m_found = k;
+  st.max_res = max_res;
+  st.normA = h->normA;
+  st.t_filter_ms = h->t_filter;
+  st.t_rr_ms = h->t_rr;
+  if (h->opt.timing) {
+    cudaEventRecord(h->ev[3], h->st);
+    st.t_total_ms = ev_ms(h, 2, 3);
+  }
+  if (stats) *stats = st;
+  return converged ? FEAST_OK : FEAST_ERR_NOCONV;
+}
+
+}  // extern "C"

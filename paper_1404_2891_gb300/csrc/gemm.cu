@@ -1,0 +1,215 @@
+// Batched complex GEMM kernels.
+//
+// complex128: FP64 tensor cores through mma.sync.m16n8k8.f64 (DMMA).  A
+//   complex product is four real products (re*re - im*im, re*im + im*re),
+//   each an MMA on planar re/im tiles staged in shared memory.
+// complex64 : FP32 SIMT (FFMA) register-blocked kernel, the portable fallback
+//   of the mixed path; the LU trailing update has its own tcgen05 kernel.
+#include "gemm.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64;
+
+// ---------------------------------------------------------------- operand loads
+template <typename T>
+__device__ __forceinline__ cplx<T> load_op(const cplx<T>* P, long long ld, int op, int r, int c,
+                                           int R, int Cn) {
+  // element (r, c) of op(P), where op(P) is R x Cn
+  if (r >= R || c >= Cn) return czero<T>();
+  if (op == OP_N) return P[(size_t)r + (size_t)c * ld];
+  cplx<T> v = P[(size_t)c + (size_t)r * ld];
+  if (op == OP_C) v.y = -v.y;
+  return v;
+}
+
+// ---------------------------------------------------------------- FP64 / DMMA
+constexpr int BK64 = 8;
+
+__device__ __forceinline__ void dmma16n8k8(double (&c)[4], const double (&a)[4], const double (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
+}
+
+// 256 threads = 8 warps as 4 (M) x 2 (N); each warp owns 16 x 32 of the 64 x 64 tile,
+// i.e. one m16 row block and four n8 column blocks, with separate re/im accumulators.
+__global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
+  __shared__ double As[2][2][BK64][BM + 1];  // [buf][re/im][k][m]
+  __shared__ double Bs[2][2][BK64][BN + 1];  // [buf][re/im][k][n]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp & 3, wn = warp >> 2;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const size_t b = blockIdx.z;
+  const double2* A = g.A + b * g.strideA;
+  const double2* B = g.B + b * g.strideB;
+  double2* C = g.C + b * g.strideC;
+
+  double acc_re[4][4], acc_im[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc_re[j][e] = acc_im[j][e] = 0.0;
+
+  double2 ra[2], rb[2];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int idx = tid + r * 256;
+      int m, k;
+      if (g.opA == OP_N) { m = idx & 63; k = idx >> 6; } else { k = idx & 7; m = idx >> 3; }
+      ra[r] = load_op<double>(A, g.lda, g.opA, m0 + m, k0 + k, g.M, g.K);
+      int n, kk;
+      if (g.opB == OP_N) { kk = idx & 7; n = idx >> 3; } else { n = idx & 63; kk = idx >> 6; }
+      rb[r] = load_op<double>(B, g.ldb, g.opB, k0 + kk, n0 + n, g.K, g.N);
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int idx = tid + r * 256;
+      int m, k;
+      if (g.opA == OP_N) { m = idx & 63; k = idx >> 6; } else { k = idx & 7; m = idx >> 3; }
+      As[buf][0][k][m] = ra[r].x;
+      As[buf][1][k][m] = ra[r].y;
+      int n, kk;
+      if (g.opB == OP_N) { kk = idx & 7; n = idx >> 3; } else { n = idx & 63; kk = idx >> 6; }
+      Bs[buf][0][kk][n] = rb[r].x;
+      Bs[buf][1][kk][n] = rb[r].y;
+    }
+  };
+
+  const int nk = (g.K + BK64 - 1) / BK64;
+  if (nk > 0) {
+    gload(0);
+    sstore(0);
+  }
+  __syncthreads();
+  const int gq = lane >> 2, tq = lane & 3;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < nk) gload((kt + 1) * BK64);
+    // A fragment (16 x 8): a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
+    double are[4], aim[4], aimn[4];
+    const int mr = wm * 16 + gq;
+    are[0] = As[buf][0][tq][mr];     aim[0] = As[buf][1][tq][mr];
+    are[1] = As[buf][0][tq][mr + 8]; aim[1] = As[buf][1][tq][mr + 8];
+    are[2] = As[buf][0][tq + 4][mr]; aim[2] = As[buf][1][tq + 4][mr];
+    are[3] = As[buf][0][tq + 4][mr + 8]; aim[3] = As[buf][1][tq + 4][mr + 8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) aimn[e] = -aim[e];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // B fragment (8 x 8): b0 (t, g), b1 (t+4, g)
+      const int nc = wn * 32 + j * 8 + gq;
+      double bre[2] = {Bs[buf][0][tq][nc], Bs[buf][0][tq + 4][nc]};
+      double bim[2] = {Bs[buf][1][tq][nc], Bs[buf][1][tq + 4][nc]};
+      dmma16n8k8(acc_re[j], are, bre);
+      dmma16n8k8(acc_re[j], aimn, bim);
+      dmma16n8k8(acc_im[j], are, bim);
+      dmma16n8k8(acc_im[j], aim, bre);
+    }
+    if (kt + 1 < nk) sstore(buf ^ 1);
+    __syncthreads();
+  }
+  // epilogue: C fragment c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+  const bool beta_zero = (g.beta.x == 0.0 && g.beta.y == 0.0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = m0 + wm * 16 + gq + ((e >> 1) ? 8 : 0);
+      const int c = n0 + wn * 32 + j * 8 + tq * 2 + (e & 1);
+      if (r < g.M && c < g.N) {
+        double2 v = make_double2(acc_re[j][e], acc_im[j][e]);
+        double2 out = cmul<double>(g.alpha, v);
+        double2* p = C + (size_t)r + (size_t)c * g.ldc;
+        if (!beta_zero) out = cadd<double>(out, cmul<double>(g.beta, *p));
+        *p = out;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FP32 SIMT
+constexpr int BK32 = 16;
+
+// 256 threads, each computing a 4 x 4 block of the 64 x 64 tile.
+__global__ void __launch_bounds__(256) k_cgemm_simt(GemmArgs<float> g) {
+  __shared__ float2 As[BK32][BM + 1];
+  __shared__ float2 Bs[BK32][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const size_t b = blockIdx.z;
+  const float2* A = g.A + b * g.strideA;
+  const float2* B = g.B + b * g.strideB;
+  float2* C = g.C + b * g.strideC;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  for (int k0 = 0; k0 < g.K; k0 += BK32) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int idx = tid + r * 256;  // 1024 elements = 64 x 16
+      int m, k;
+      if (g.opA == OP_N) { m = idx & 63; k = idx >> 6; } else { k = idx & 15; m = idx >> 4; }
+      As[k][m] = load_op<float>(A, g.lda, g.opA, m0 + m, k0 + k, g.M, g.K);
+      int n, kk;
+      if (g.opB == OP_N) { kk = idx & 15; n = idx >> 4; } else { n = idx & 63; kk = idx >> 6; }
+      Bs[kk][n] = load_op<float>(B, g.ldb, g.opB, k0 + kk, n0 + n, g.K, g.N);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK32; ++k) {
+      float2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[k][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma<float>(acc[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+  const bool beta_zero = (g.beta.x == 0.f && g.beta.y == 0.f);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = m0 + tx + 16 * i, c = n0 + ty + 16 * j;
+      if (r < g.M && c < g.N) {
+        float2 out = cmul<float>(g.alpha, acc[i][j]);
+        float2* p = C + (size_t)r + (size_t)c * g.ldc;
+        if (!beta_zero) out = cadd<float>(out, cmul<float>(g.beta, *p));
+        *p = out;
+      }
+    }
+}
+
+}  // namespace
+
+template <>
+cudaError_t gemm_batched<double>(const GemmArgs<double>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  dim3 grid(ceil_div(g.M, BM), ceil_div(g.N, BN), g.batch);
+  feast_count_launch();
+  k_zgemm_dmma<<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t gemm_batched<float>(const GemmArgs<float>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  dim3 grid(ceil_div(g.M, BM), ceil_div(g.N, BN), g.batch);
+  feast_count_launch();
+  k_cgemm_simt<<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}

@@ -1,0 +1,23 @@
+// Batched complex GEMM used by every dense contraction of the FP64 path and
+// by the FP32 fallback of the mixed path:
+//     C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b],   b = 0 .. batch-1
+// column-major operands, op in {N, T, C}, per-batch element strides (0 = shared).
+#pragma once
+#include "common.cuh"
+
+template <typename T>
+struct GemmArgs {
+  int M = 0, N = 0, K = 0, batch = 1;
+  cplx<T> alpha, beta;
+  const cplx<T>* A = nullptr;
+  long long lda = 0, strideA = 0;
+  int opA = OP_N;
+  const cplx<T>* B = nullptr;
+  long long ldb = 0, strideB = 0;
+  int opB = OP_N;
+  cplx<T>* C = nullptr;
+  long long ldc = 0, strideC = 0;
+};
+
+template <typename T>
+cudaError_t gemm_batched(const GemmArgs<T>& g, cudaStream_t s);

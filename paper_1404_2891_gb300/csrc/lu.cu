@@ -1,0 +1,386 @@
+// Batched right-looking blocked LU with partial pivoting (P S = L U) for the
+// q shifted matrices phi_k B - A, each factored once and reused for every
+// right-hand side and iteration (Sec. 5.5 of the paper), and the blocked
+// triangular solves of Eq. Rasp (S X = R) and Eq. Lasp (S^H X = R).
+//
+// Per panel of width w:  (1) panel factorisation, one CTA per shift, pivot =
+// largest |Re|+|Im| with the lowest row on ties; (2) the panel's interchanges
+// applied to the other columns and U12 = L11^{-1} A12; (3) the trailing update
+// A22 -= L21 U12 as one batched contraction over all shifts.
+#include "lu.cuh"
+
+namespace {
+
+constexpr int PANEL_THREADS = 512;
+constexpr int MAX_NB = 128;
+
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& v, int& i, T v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+k_panel(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, int32_t* piv, int* info,
+        unsigned* flags) {
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  cplx<T>* A = S + (size_t)b * stride;
+  int32_t* pv = piv + (size_t)b * n;
+  __shared__ T red_v[PANEL_THREADS / 32];
+  __shared__ int red_i[PANEL_THREADS / 32];
+  __shared__ int s_p;
+  __shared__ cplx<T> s_u[MAX_NB];
+  const int jend = k0 + w;
+  for (int col = k0; col < jend; ++col) {
+    // 1. pivot search over rows col .. n-1 (ascending per thread, strict > keeps the lowest)
+    T best = T(-1);
+    int bi = n;
+    for (int i = col + tid; i < n; i += PANEL_THREADS) {
+      T v = cabs1<T>(A[(size_t)i + (size_t)col * ld]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      T v2 = __shfl_down_sync(0xffffffffu, best, off);
+      int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+      argmax_merge<T>(best, bi, v2, i2);
+    }
+    if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      T v = red_v[0];
+      int ii = red_i[0];
+      for (int k = 1; k < PANEL_THREADS / 32; ++k) argmax_merge<T>(v, ii, red_v[k], red_i[k]);
+      if (ii >= n) {  // the column held only NaN: keep the diagonal, flag it
+        ii = col;
+        atomicOr(flags, (unsigned)DEVFLAG_NONFINITE);
+      }
+      pv[col] = ii;
+      s_p = ii;
+    }
+    __syncthreads();
+    const int p = s_p;
+    // 2. interchange rows col and p inside the panel
+    if (p != col) {
+      for (int j = k0 + tid; j < jend; j += PANEL_THREADS) {
+        cplx<T> t1 = A[(size_t)col + (size_t)j * ld];
+        A[(size_t)col + (size_t)j * ld] = A[(size_t)p + (size_t)j * ld];
+        A[(size_t)p + (size_t)j * ld] = t1;
+      }
+    }
+    __syncthreads();
+    // 3. scale the column below the pivot
+    const cplx<T> d = A[(size_t)col + (size_t)col * ld];
+    const bool zero = (d.x == T(0) && d.y == T(0));
+    if (zero) {
+      if (tid == 0) {
+        atomicCAS(&info[b], 0, col + 1);
+        atomicOr(flags, (unsigned)DEVFLAG_SINGULAR);
+      }
+    } else {
+      const cplx<T> r = crecip<T>(d);
+      for (int i = col + 1 + tid; i < n; i += PANEL_THREADS)
+        A[(size_t)i + (size_t)col * ld] = cmul<T>(A[(size_t)i + (size_t)col * ld], r);
+    }
+    for (int j = col + 1 + tid; j < jend; j += PANEL_THREADS) s_u[j - k0] = A[(size_t)col + (size_t)j * ld];
+    __syncthreads();
+    // 4. rank-1 update of the rest of the panel
+    if (!zero) {
+      for (int i = col + 1 + tid; i < n; i += PANEL_THREADS) {
+        const cplx<T> l = A[(size_t)i + (size_t)col * ld];
+        for (int j = col + 1; j < jend; ++j) {
+          cplx<T>& a = A[(size_t)i + (size_t)j * ld];
+          a = csub<T>(a, cmul<T>(l, s_u[j - k0]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Interchanges of one panel applied to 32 "other" columns per CTA, then, for
+// columns right of the panel, U12 = L11^{-1} A12 (unit lower, column-oriented).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_laswp_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, const int32_t* piv) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* L = reinterpret_cast<cplx<T>*>(smem_raw);  // w x w, [r * w + s]
+  cplx<T>* X = L + w * w;                              // w x 32, [r * 32 + cc]
+  const int b = blockIdx.y, tid = threadIdx.x;
+  cplx<T>* A = S + (size_t)b * stride;
+  const int32_t* pv = piv + (size_t)b * n;
+  const int nother = n - w;
+  const int o = blockIdx.x * 32 + (tid & 31);
+  const bool valid = o < nother;
+  const int c = valid ? (o < k0 ? o : o + w) : 0;
+  const bool right = valid && c >= k0 + w;
+  if (tid < 32 && valid) {
+    for (int r = 0; r < w; ++r) {
+      const int p = pv[k0 + r];
+      if (p != k0 + r) {
+        cplx<T> t1 = A[(size_t)(k0 + r) + (size_t)c * ld];
+        A[(size_t)(k0 + r) + (size_t)c * ld] = A[(size_t)p + (size_t)c * ld];
+        A[(size_t)p + (size_t)c * ld] = t1;
+      }
+    }
+  }
+  // does any column of this CTA lie right of the panel?
+  const int o_last = min(blockIdx.x * 32 + 31, nother - 1);
+  const bool any_right = (o_last >= k0);
+  if (!any_right) return;
+  for (int idx = tid; idx < w * w; idx += 256) {
+    const int r = idx % w, s2 = idx / w;
+    L[r * w + s2] = A[(size_t)(k0 + r) + (size_t)(k0 + s2) * ld];
+  }
+  __syncthreads();
+  const int cc = tid & 31;
+  for (int r = tid >> 5; r < w; r += 8) X[r * 32 + cc] = right ? A[(size_t)(k0 + r) + (size_t)c * ld] : czero<T>();
+  __syncthreads();
+  for (int s2 = 0; s2 < w - 1; ++s2) {
+    const cplx<T> xs = X[s2 * 32 + cc];
+    for (int r = s2 + 1 + (tid >> 5); r < w; r += 8)
+      X[r * 32 + cc] = csub<T>(X[r * 32 + cc], cmul<T>(L[r * w + s2], xs));
+    __syncthreads();
+  }
+  if (right)
+    for (int r = tid >> 5; r < w; r += 8) A[(size_t)(k0 + r) + (size_t)c * ld] = X[r * 32 + cc];
+}
+
+// Row permutation vector from the interchange sequence: perm = P applied to 0..n-1.
+__global__ void k_piv_to_perm(const int32_t* piv, int32_t* perm, int32_t* pinv, int n) {
+  const int b = blockIdx.x;
+  const int32_t* pv = piv + (size_t)b * n;
+  int32_t* pm = perm + (size_t)b * n;
+  int32_t* pi = pinv + (size_t)b * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) pm[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < n; ++k) {
+      const int p = pv[k];
+      if (p != k && p >= 0 && p < n) { int t = pm[k]; pm[k] = pm[p]; pm[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) pi[pm[i]] = i;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, void*, cudaStream_t s) {
+  const int rest = lu.n - k0 - w;
+  if (rest <= 0) return cudaSuccess;
+  GemmArgs<T> g;
+  g.M = rest; g.N = rest; g.K = w; g.batch = lu.q;
+  g.alpha = mk<T>(T(-1), T(0));
+  g.beta = mk<T>(T(1), T(0));
+  g.A = lu.S + (size_t)(k0 + w) + (size_t)k0 * lu.ld;        g.lda = lu.ld; g.strideA = lu.stride; g.opA = OP_N;
+  g.B = lu.S + (size_t)k0 + (size_t)(k0 + w) * lu.ld;        g.ldb = lu.ld; g.strideB = lu.stride; g.opB = OP_N;
+  g.C = lu.S + (size_t)(k0 + w) + (size_t)(k0 + w) * lu.ld;  g.ldc = lu.ld; g.strideC = lu.stride;
+  return gemm_batched<T>(g, s);
+}
+template cudaError_t default_trailing_update<double>(const LuBatch<double>&, int, int, void*, cudaStream_t);
+template cudaError_t default_trailing_update<float>(const LuBatch<float>&, int, int, void*, cudaStream_t);
+
+namespace {
+
+// ---------------------------------------------------------------- solves
+enum DiagMode { D_LOWER_UNIT = 0, D_UPPER = 1, D_UPPER_H = 2, D_LOWER_H = 3 };
+
+// Solve with the w x w diagonal block at (k0, k0) for 32 right-hand sides per CTA.
+//  D_LOWER_UNIT : L_kk x = b            (forward)
+//  D_UPPER      : U_kk x = b            (backward)
+//  D_UPPER_H    : U_kk^H x = b          (forward, lower non-unit)
+//  D_LOWER_H    : L_kk^H x = b          (backward, upper unit)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_trsm_diag(const cplx<T>* S, long long ld, long long stride, cplx<T>* Xg, long long ldx,
+            long long stridex, int k0, int w, int m, int mode) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* D = reinterpret_cast<cplx<T>*>(smem_raw);  // [r * w + s] = S[k0 + r, k0 + s]
+  cplx<T>* X = D + w * w;                              // [r * 32 + cc]
+  const int b = blockIdx.y, tid = threadIdx.x, cc = tid & 31, rg = tid >> 5;
+  const cplx<T>* A = S + (size_t)b * stride;
+  cplx<T>* Xb = Xg + (size_t)b * stridex;
+  const int c = blockIdx.x * 32 + cc;
+  const bool valid = c < m;
+  for (int idx = tid; idx < w * w; idx += 256) {
+    const int r = idx % w, s2 = idx / w;
+    D[r * w + s2] = A[(size_t)(k0 + r) + (size_t)(k0 + s2) * ld];
+  }
+  for (int r = rg; r < w; r += 8) X[r * 32 + cc] = valid ? Xb[(size_t)(k0 + r) + (size_t)c * ldx] : czero<T>();
+  __syncthreads();
+  if (mode == D_LOWER_UNIT || mode == D_UPPER_H) {
+    for (int s2 = 0; s2 < w; ++s2) {
+      if (mode == D_UPPER_H) {
+        if (rg == 0) X[s2 * 32 + cc] = cdiv<T>(X[s2 * 32 + cc], cconj<T>(D[s2 * w + s2]));
+        __syncthreads();
+      }
+      const cplx<T> xs = X[s2 * 32 + cc];
+      for (int r = s2 + 1 + rg; r < w; r += 8) {
+        const cplx<T> l = (mode == D_LOWER_UNIT) ? D[r * w + s2] : cconj<T>(D[s2 * w + r]);
+        X[r * 32 + cc] = csub<T>(X[r * 32 + cc], cmul<T>(l, xs));
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int s2 = w - 1; s2 >= 0; --s2) {
+      if (mode == D_UPPER) {
+        if (rg == 0) X[s2 * 32 + cc] = cdiv<T>(X[s2 * 32 + cc], D[s2 * w + s2]);
+        __syncthreads();
+      }
+      const cplx<T> xs = X[s2 * 32 + cc];
+      for (int r = rg; r < s2; r += 8) {
+        const cplx<T> u = (mode == D_UPPER) ? D[r * w + s2] : cconj<T>(D[s2 * w + r]);
+        X[r * 32 + cc] = csub<T>(X[r * 32 + cc], cmul<T>(u, xs));
+      }
+      __syncthreads();
+    }
+  }
+  if (valid)
+    for (int r = rg; r < w; r += 8) Xb[(size_t)(k0 + r) + (size_t)c * ldx] = X[r * 32 + cc];
+}
+
+template <typename T>
+__global__ void k_rows_gather(const double2* R, const int32_t* perm, cplx<T>* X, int n, int m,
+                              bool permute) {
+  const size_t b = blockIdx.y;
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n);
+    const size_t c = idx / n;
+    const int src = permute ? perm[b * n + i] : i;
+    X[b * total + idx] = cconv<T, double>(R[(size_t)src + c * n]);
+  }
+}
+
+template <typename T>
+__global__ void k_rows_scatter(const cplx<T>* V, const int32_t* perm, cplx<T>* Out, int n, int m) {
+  const size_t b = blockIdx.y;
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n);
+    const size_t c = idx / n;
+    Out[b * total + (size_t)perm[b * n + i] + c * n] = V[b * total + idx];
+  }
+}
+
+template <typename T>
+size_t diag_smem(int w) { return (size_t)(w * w + w * 32) * sizeof(cplx<T>); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> upd, void* ctx,
+                              cudaStream_t s) {
+  if (nb < 1 || nb > MAX_NB || diag_smem<T>(nb) > 227 * 1024) return cudaErrorInvalidValue;
+  if (!upd) upd = default_trailing_update<T>;
+  cudaError_t e = cudaFuncSetAttribute(k_laswp_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)diag_smem<T>(nb));
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(lu.info, 0, sizeof(int) * lu.q, s);
+  for (int k0 = 0; k0 < lu.n; k0 += nb) {
+    const int w = min(nb, lu.n - k0);
+    feast_count_launch();
+    k_panel<T><<<lu.q, PANEL_THREADS, 0, s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv, lu.info, lu.flags);
+    const int nother = lu.n - w;
+    if (nother > 0) {
+      dim3 grid(ceil_div(nother, 32), lu.q);
+      feast_count_launch();
+      k_laswp_trsm<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv);
+    }
+    e = upd(lu, k0, w, ctx, s);
+    if (e != cudaSuccess) return e;
+  }
+  feast_count_launch();
+  k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, int nbs, cudaStream_t s) {
+  if (nbs < 1 || nbs > MAX_NB || diag_smem<T>(nbs) > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)diag_smem<T>(nbs));
+  if (e != cudaSuccess) return e;
+  const int n = lu.n;
+  const long long ldx = n, sx = (long long)n * m;
+  auto diag = [&](int k0, int w, int mode) {
+    dim3 grid(ceil_div(m, 32), lu.q);
+    feast_count_launch();
+    k_trsm_diag<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, X, ldx, sx, k0, w, m, mode);
+  };
+  auto update = [&](int M, int K, const cplx<T>* Aop, int opA, int row_out, int row_in) {
+    if (M <= 0) return cudaSuccess;
+    GemmArgs<T> g;
+    g.M = M; g.N = m; g.K = K; g.batch = lu.q;
+    g.alpha = mk<T>(T(-1), T(0));
+    g.beta = mk<T>(T(1), T(0));
+    g.A = Aop; g.lda = lu.ld; g.strideA = lu.stride; g.opA = opA;
+    g.B = X + row_in; g.ldb = ldx; g.strideB = sx; g.opB = OP_N;
+    g.C = X + row_out; g.ldc = ldx; g.strideC = sx;
+    return gemm_batched<T>(g, s);
+  };
+  const cplx<T>* F = lu.S;
+  const long long ld = lu.ld;
+  if (side == 0) {
+    for (int k0 = 0; k0 < n; k0 += nbs) {  // L y = P r
+      const int w = min(nbs, n - k0);
+      diag(k0, w, D_LOWER_UNIT);
+      e = update(n - k0 - w, w, F + (size_t)(k0 + w) + (size_t)k0 * ld, OP_N, k0 + w, k0);
+      if (e != cudaSuccess) return e;
+    }
+    const int last = ((n - 1) / nbs) * nbs;
+    for (int k0 = last; k0 >= 0; k0 -= nbs) {  // U x = y
+      const int w = min(nbs, n - k0);
+      diag(k0, w, D_UPPER);
+      e = update(k0, w, F + (size_t)(k0) * ld, OP_N, 0, k0);
+      if (e != cudaSuccess) return e;
+    }
+  } else {
+    for (int k0 = 0; k0 < n; k0 += nbs) {  // U^H w = r
+      const int w = min(nbs, n - k0);
+      diag(k0, w, D_UPPER_H);
+      // rows k0+w.. of op(A) = (U[k0:k0+w, k0+w:])^H
+      e = update(n - k0 - w, w, F + (size_t)k0 + (size_t)(k0 + w) * ld, OP_C, k0 + w, k0);
+      if (e != cudaSuccess) return e;
+    }
+    const int last = ((n - 1) / nbs) * nbs;
+    for (int k0 = last; k0 >= 0; k0 -= nbs) {  // L^H v = w
+      const int w = min(nbs, n - k0);
+      diag(k0, w, D_LOWER_H);
+      // rows 0..k0 of op(A) = (L[k0:k0+w, 0:k0])^H
+      e = update(k0, w, F + (size_t)k0, OP_C, 0, k0);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rows_gather(const LuBatch<T>& lu, const double2* R, cplx<T>* X, int m, bool permute,
+                        cudaStream_t s) {
+  dim3 grid(ceil_div((size_t)lu.n * m, 256 * 4), lu.q);
+  feast_count_launch();
+  k_rows_gather<T><<<grid, 256, 0, s>>>(R, lu.perm, X, lu.n, m, permute);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rows_scatter(const LuBatch<T>& lu, const cplx<T>* V, cplx<T>* Out, int m, cudaStream_t s) {
+  dim3 grid(ceil_div((size_t)lu.n * m, 256 * 4), lu.q);
+  feast_count_launch();
+  k_rows_scatter<T><<<grid, 256, 0, s>>>(V, lu.perm, Out, lu.n, m);
+  return cudaGetLastError();
+}
+
+template cudaError_t lu_factor_batched<double>(const LuBatch<double>&, int, TrailingUpdateFn<double>, void*, cudaStream_t);
+template cudaError_t lu_factor_batched<float>(const LuBatch<float>&, int, TrailingUpdateFn<float>, void*, cudaStream_t);
+template cudaError_t lu_solve_batched<double>(const LuBatch<double>&, int, double2*, int, int, cudaStream_t);
+template cudaError_t lu_solve_batched<float>(const LuBatch<float>&, int, float2*, int, int, cudaStream_t);
+template cudaError_t rows_gather<double>(const LuBatch<double>&, const double2*, double2*, int, bool, cudaStream_t);
+template cudaError_t rows_gather<float>(const LuBatch<float>&, const double2*, float2*, int, bool, cudaStream_t);
+template cudaError_t rows_scatter<double>(const LuBatch<double>&, const double2*, double2*, int, cudaStream_t);
+template cudaError_t rows_scatter<float>(const LuBatch<float>&, const float2*, float2*, int, cudaStream_t);

@@ -1,0 +1,48 @@
+// Batched dense complex LU with partial pivoting and the triangular solves
+// that reuse it, for the q shifted systems (phi_k B - A) of Eq. Rasp.
+#pragma once
+#include "common.cuh"
+#include "gemm.cuh"
+
+// q matrices of order n, column-major, leading dimension ld, batch stride `stride`.
+template <typename T>
+struct LuBatch {
+  cplx<T>* S = nullptr;
+  long long ld = 0, stride = 0;
+  int n = 0, q = 0;
+  int32_t* piv = nullptr;   // q x n, LAPACK style (0-based): row i exchanged with piv[i]
+  int32_t* perm = nullptr;  // q x n, row i of P S is row perm[i] of S
+  int32_t* pinv = nullptr;  // q x n, inverse permutation: pinv[perm[i]] = i
+  int* info = nullptr;      // q ints: 0 or 1 + first column with an exact zero pivot
+  unsigned* flags = nullptr;
+};
+
+// Trailing-update hook: C -= L21 * U12 for all shifts of one panel step.
+// Defaults to gemm_batched<T>; the mixed path installs its tensor-core kernel.
+template <typename T>
+using TrailingUpdateFn = cudaError_t (*)(const LuBatch<T>& lu, int k0, int w, void* ctx, cudaStream_t s);
+
+// The batched-GEMM trailing update (used when no other kernel is installed).
+template <typename T>
+cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, void* ctx, cudaStream_t s);
+
+template <typename T>
+cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> upd, void* ctx,
+                              cudaStream_t s);
+
+// X (q x n x m, leading dimension n, batch stride n*m) overwritten with
+//   side 0:  S_b^{-1} X_b          side 1:  S_b^{-H} X_b
+// using the stored factors; `X` must already hold P R (side 0) or R (side 1),
+// see rows_gather; the final P^T of side 1 is applied by rows_scatter.
+template <typename T>
+cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, int nbs,
+                             cudaStream_t s);
+
+// X_b[i, c] = R[perm_b[i], c]   (R: n x m double2, shared by all b; X in T)
+template <typename T>
+cudaError_t rows_gather(const LuBatch<T>& lu, const double2* R, cplx<T>* X, int m, bool permute,
+                        cudaStream_t s);
+// Out_b[perm_b[i], c] = V_b[i, c]  in place through a scratch copy
+template <typename T>
+cudaError_t rows_scatter(const LuBatch<T>& lu, const cplx<T>* V, cplx<T>* Out, int m,
+                         cudaStream_t s);

@@ -1,0 +1,23 @@
+// FP64 kernels for the reduced (m0 x m0) problem of the Rayleigh-Ritz step and
+// for the orthonormal bases of the filtered blocks.
+#pragma once
+#include "common.cuh"
+
+// In-place orthonormalisation of the n x m block Q (ld n) by classical
+// Gram-Schmidt applied twice, one cooperative launch with bounded grid barriers.
+// scratch: >= 2 * grid * m double2 + 4 unsigned (see orth_scratch_bytes).
+size_t orth_scratch_bytes(int n, int m);
+cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s);
+
+// Single-CTA dense kernels on m x m column-major matrices (ld m) in global memory.
+// LU with partial pivoting in place (piv: m ints).
+cudaError_t small_lu(double2* M, int m, int* piv, unsigned* flags, cudaStream_t s);
+// X (m x nrhs, ld m) <- M^{-1} X (trans = 0) or M^{-H} X (trans = 1) with the factors of small_lu.
+cudaError_t small_lu_solve(const double2* LU, const int* piv, int m, double2* X, int nrhs, int trans,
+                           cudaStream_t s);
+// Schur form of the m x m matrix C (overwritten by the upper triangular T) by
+// Householder reduction to Hessenberg form and shifted complex QR iterations;
+// Z (m x m) receives the unitary Schur vectors (C = Z T Z^H); lam the diagonal of T.
+cudaError_t small_schur(double2* C, double2* Z, double2* lam, int m, unsigned* flags, cudaStream_t s);
+// Eigenvectors of the upper triangular T (V, m x m, unit diagonal entry, back substitution).
+cudaError_t small_trevc(const double2* T, double2* V, int m, cudaStream_t s);

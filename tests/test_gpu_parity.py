@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, at sizes that span several tiles and a ragged tail.
+
+Tolerances (FP64 path): every quantity below is a backward-stable computation
+in binary64, so its error is bounded by a small multiple of n * u * cond; the
+tests use 1e-11 relative on well-conditioned data.  Mixed path: the factor is
+complex64 (u32 = 6e-8) and the solves are complex64, so single solves carry a
+relative error of about cond(S) * n * u32 (1e-4 bound at these sizes), and
+full FEAST results are held to the FP64 gate (residual <= 1e-10)."""
+import numpy as np
+import pytest
+
+import workloads
+from helpers import U32, U64, contour_args, lib, relerr, residuals
+from oracle import brute, contour as ct, dense, feast
+
+pytestmark = pytest.mark.gpu
+
+
+def small_prescribed(n=300, m_in=12, m0=40, seed=11):
+    return workloads.prescribed(n=n, m_in=m_in, seed=seed, m0=m0)
+
+
+def small_pencil(n=320, m0=24, seed=12):
+    return workloads.gaussian_pencil(n=n, seed=seed, m0=m0, K=4, zero_block=8)
+
+
+def make(fg, cfg, precision, algo="BI", B=None, m0=None, **kw):
+    return fg.feast_create(cfg["A"], B, fg.make_contour(**contour_args(cfg)), m0 or cfg["m0"],
+                           fg.make_options(algo=algo, precision=precision, **kw))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_quadrature_matches_oracle(precision):
+    fg = lib()
+    for rule, K in (("trap_mid", 8), ("gauss", 6), ("trap_end", 5)):
+        cfg = small_prescribed(n=40, m_in=4, m0=8)
+        cfg["contour"]["rule"] = rule
+        cfg["N_e"] = K
+        cfg["contour"]["a"] = 0.6
+        h = make(fg, cfg, precision)
+        z, w = fg.feast_get_quadrature(h)
+        zr, wr = ct.quadrature(cfg["contour"]["c"], cfg["contour"]["R"], 0.6, rule, K)
+        assert np.allclose(z, zr, atol=1e-15) and np.allclose(w, wr, atol=1e-15)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("generalized", [False, True])
+def test_factor_backward_error_and_pivots(precision, generalized):
+    fg = lib()
+    cfg = small_pencil() if generalized else small_prescribed()
+    B = cfg["B"] if generalized else None
+    h = make(fg, cfg, precision, B=B)
+    fg.feast_factor(h)
+    z, _ = fg.feast_get_quadrature(h)
+    n = cfg["A"].shape[0]
+    Bm = np.eye(n) if B is None else B
+    u = U64 if precision == "fp64" else U32
+    for k in range(h.q):
+        S = z[k] * Bm - cfg["A"]
+        LU, piv = fg.feast_get_factor(h, k)
+        L, U = dense.unpack(LU)
+        P = dense.permutation_matrix(piv.astype(np.int64))
+        err = np.linalg.norm(P @ S - L @ U) / np.linalg.norm(S)
+        assert err <= 8 * n * u, (k, err)
+        if precision == "fp64":
+            # same elimination order and pivot rule as the oracle: identical pivots
+            _, piv_ref, _ = dense.lu_factor(S)
+            assert np.array_equal(piv.astype(np.int64), piv_ref), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shift_solves_match_oracle(precision):
+    fg = lib()
+    cfg = small_pencil()
+    h = make(fg, cfg, precision, B=cfg["B"])
+    z, _ = fg.feast_get_quadrature(h)
+    R = workloads.random_block(cfg["A"].shape[0], 19, seed=5)
+    tol = 1e-11 if precision == "fp64" else 2e-4
+    for k in (0, h.q // 2, h.q - 1):
+        S = z[k] * cfg["B"] - cfg["A"]
+        LU, piv, _ = dense.lu_factor(S)
+        for side in (0, 1):
+            X = fg.feast_solve_shift(h, k, side, R)
+            Xr = dense.lu_solve(LU, piv, R) if side == 0 else dense.lu_solve_adjoint(LU, piv, R)
+            assert relerr(X, Xr) < tol, (k, side, relerr(X, Xr))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_filter_matches_oracle(precision):
+    fg = lib()
+    cfg = small_pencil()
+    A, B = cfg["A"], cfg["B"]
+    h = make(fg, cfg, precision, B=B)
+    z, w = fg.feast_get_quadrature(h)
+    factors = feast.factor_shifts(A, B, z)
+    Y, Yh = cfg["U0"], cfg["Vrand"]
+    Q, Qh = fg.feast_filter(h, Y, Yh)
+    Qr = feast.filter_right(factors, B, w, Y)
+    Qhr = feast.filter_left(factors, B, w, Yh)
+    tol = 1e-11 if precision == "fp64" else 2e-4
+    assert relerr(Q, Qr) < tol, relerr(Q, Qr)
+    assert relerr(Qh, Qhr) < tol, relerr(Qh, Qhr)
+    # with Ritz values supplied (the refinement's initial iterate), the result is the same
+    theta = np.linspace(-0.3, 0.4, cfg["m0"]) + 0.05j
+    Q2, Qh2 = fg.feast_filter(h, Y, Yh, theta=theta)
+    assert relerr(Q2, Qr) < tol, relerr(Q2, Qr)
+    assert relerr(Qh2, Qhr) < tol, relerr(Qh2, Qhr)
+
+
+def test_residual_form_filter_is_exact_on_ritz_pairs():
+    # With an exact eigenpair (theta, x), the refinement's initial iterate is already
+    # the solution, so the mixed filter returns rho(theta) x to FP64 accuracy.
+    fg = lib()
+    cfg = small_prescribed()
+    h = make(fg, cfg, "mixed", algo="R")
+    V = cfg["V"]
+    sel = np.arange(cfg["m0"])
+    X = V[:, sel] / np.linalg.norm(V[:, sel], axis=0)
+    theta = cfg["lam"][sel]
+    Q, _ = fg.feast_filter(h, X, None, theta=theta)
+    z, w = fg.feast_get_quadrature(h)
+    ref = X * ct.rho(theta, z, w)[None, :]
+    assert relerr(Q, ref) < 1e-11, relerr(Q, ref)
+
+
+def test_rayleigh_ritz_matches_oracle():
+    fg = lib()
+    cfg = small_prescribed()
+    A = cfg["A"]
+    h = make(fg, cfg, "fp64")
+    z, w = fg.feast_get_quadrature(h)
+    factors = feast.factor_shifts(A, None, z)
+    # three oracle iterations, so that the inside Ritz pairs have residuals ~1e-5
+    U, V = cfg["U0"], feast.initial_left(None, cfg["U0"], cfg["Vrand"])
+    for _ in range(3):
+        Q = feast.filter_right(factors, None, w, U)
+        Qh = feast.filter_left(factors, None, w, V)
+        lam_o, W, Z, Qo, Qho = feast.rayleigh_ritz_bi(A, None, Q, Qh)
+        U, V = Qo @ W, Qho @ Z
+        U, V = U / np.linalg.norm(U, axis=0), V / np.linalg.norm(V, axis=0)
+    Q = feast.filter_right(factors, None, w, U)
+    Qh = feast.filter_left(factors, None, w, V)
+    out = fg.feast_rayleigh_ritz(h, Q, Qh)
+    lam_r, W, Z, Qo, Qho = feast.rayleigh_ritz_bi(A, None, Q, Qh)
+    # compare the Ritz values that are candidates on both sides
+    Xr = Qo @ W
+    Xr = Xr / np.linalg.norm(Xr, axis=0)
+    res_r = feast.right_residuals(A, None, lam_r, Xr)
+    c = cfg["contour"]
+    keep_r = ct.inside(lam_r, c["c"], c["R"], c["a"]) & (res_r < 1e-3)
+    res_g = out["res"] * feast.norm2_estimate(A, np.ones(A.shape[0]))
+    keep_g = ct.inside(out["lam"], c["c"], c["R"], c["a"]) & (res_g < 1e-3)
+    assert keep_r.sum() == keep_g.sum() > 0
+    err = feast.match_eigenvalues(out["lam"][keep_g], lam_r[keep_r], 1.0)
+    assert err.max() < 1e-11, err.max()
+    # Ritz vectors: unit norm, and the left ones B-biorthogonal to the right ones
+    X, Xl = out["X"], out["Xl"]
+    assert np.allclose(np.linalg.norm(X, axis=0), 1.0, atol=1e-12)
+    G = Xl.conj().T @ X
+    assert np.allclose(np.diag(G), 1.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("algo", ["R", "BI"])
+def test_feast_prescribed_n256(precision, algo):
+    """Plain-FEAST workload at full size (n = 256, 8 midpoint nodes, m0 = 64)."""
+    fg = lib()
+    cfg = workloads.prescribed()
+    A = cfg["A"]
+    h = make(fg, cfg, precision, algo=algo, tol=1e-12, max_iter=20)
+    out = fg.feast_solve(h, cfg["U0"], cfg["Vrand"])
+    assert out["converged"], out["res_hist"]
+    assert out["m_found"] == 40
+    normA = feast.norm2_estimate(A, np.ones(A.shape[0]))
+    r = residuals(A, None, out["lam"], out["X"], normA)
+    assert r.max() <= 1e-10, r.max()
+    err = feast.match_eigenvalues(out["lam"], cfg["lam_inside"], 1.0)
+    # eigenvalue error <= cond(lambda) * residual; cond(V) = 100
+    assert err.max() <= (1e-10 if algo == "BI" else 1e-8), err.max()
+    ref = feast.feast(A, None, cfg["contour"], 8, 64, algo, cfg["U0"], cfg["Vrand"], tol=1e-12, max_iter=20)
+    err2 = feast.match_eigenvalues(out["lam"], ref["lam"], 1.0)
+    assert err2.max() <= (1e-10 if algo == "BI" else 1e-8), err2.max()
+    if algo == "BI":
+        X, Y = out["X"], out["Xl"]
+        assert np.allclose(Y.conj().T @ X, np.eye(40), atol=1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bifeast_generalized_vs_brute_force(precision):
+    fg = lib()
+    cfg = workloads.gaussian_pencil(n=520, seed=13, m0=24, K=8, zero_block=9)
+    A, B = cfg["A"], cfg["B"]
+    c = cfg["contour"]
+    h = make(fg, cfg, precision, B=B, max_iter=15)
+    out = fg.feast_solve(h, cfg["U0"], cfg["Vrand"])
+    ref = brute.inside_spectrum(A, B, c["c"], c["R"], c["a"])
+    assert out["converged"] and out["m_found"] == len(ref)
+    err = feast.match_eigenvalues(out["lam"], ref, c["R"])
+    assert err.max() < 1e-10, err.max()
+    normA = feast.norm2_estimate(A, np.ones(A.shape[0]))
+    r = residuals(A, B, out["lam"], out["X"], normA)
+    assert r.max() <= 1e-10, r.max()
+    X, Y = out["X"], out["Xl"]
+    assert np.allclose(Y.conj().T @ B @ X, np.eye(len(ref)), atol=1e-8)
