@@ -16,6 +16,7 @@
 #include "blas1.cuh"
 #include "gemm.cuh"
 #include "lu.cuh"
+#include "norm2.cuh"
 #include "small.cuh"
 #include "tc_update.cuh"
 
@@ -165,6 +166,7 @@ struct feast_handle {
   int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *useresh = nullptr, *colidx = nullptr;
   double *res = nullptr, *resl = nullptr, *xn = nullptr, *xln = nullptr, *scal = nullptr;
   void* orth_scratch = nullptr;
+  void* pw_scratch = nullptr;
   std::vector<void*> allocs;
   // host mirrors of the last Rayleigh-Ritz step
   std::vector<zc> h_lam;
@@ -496,22 +498,12 @@ feast_status copy_out(feast_handle* h, feast_z* dst, const double2* src, size_t 
 }
 
 feast_status estimate_norm2(feast_handle* h) {
-  const int n = (int)h->n;
-  std::vector<double2> ones(n, make_double2(1.0, 0.0));
-  double2* x = h->tmp;
-  double2* y = h->tmp + n;
-  CK(cudaMemcpyAsync(x, ones.data(), n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
-  CK(normalize_vector(x, n, h->scal, h->st));
-  for (int it = 0; it < 50; ++it) {
-    CK(zg(h, OP_N, OP_N, n, 1, n, 1.0, h->A, n, x, n, 0.0, y, n));
-    CK(zg(h, OP_C, OP_N, n, 1, n, 1.0, h->A, n, y, n, 0.0, x, n));
-    CK(normalize_vector(x, n, h->scal, h->st));
-  }
+  CK(norm2_power(h->A, h->n, (int)h->n, 50, h->pw_scratch, h->scal, h->flags, h->st));
   double s = 0.0;
   CK(cudaMemcpyAsync(&s, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  h->normA = std::sqrt(s);
-  return FEAST_OK;
+  h->normA = s;
+  return read_flags(h);
 }
 
 }  // namespace
@@ -625,6 +617,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->xln, m0 * sizeof(double));
   AL(h->scal, 64);
   AL(h->orth_scratch, orth_scratch_bytes((int)n, m0));
+  AL(h->pw_scratch, norm2_scratch_bytes((int)n));
 #undef AL
   if (h->opt.timing)
     for (auto& ev : h->ev) cudaEventCreate(&ev);

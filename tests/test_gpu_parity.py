@@ -44,6 +44,17 @@ def test_quadrature_matches_oracle(precision):
         assert np.allclose(z, zr, atol=1e-15) and np.allclose(w, wr, atol=1e-15)
 
 
+@pytest.mark.parametrize("n", [1, 45, 300])
+def test_norm2_estimate_matches_oracle(n):
+    # the residual normalisation: 50 power iterations on A^H A from the all-ones vector
+    fg = lib()
+    rng = np.random.default_rng(n)
+    A = workloads.cgauss(rng, n, n) + np.diag(np.linspace(1, 3, n))
+    h = fg.feast_create(A, None, fg.make_contour(), 1, fg.make_options())
+    ref = feast.norm2_estimate(A, np.ones(n), iters=50)
+    assert abs(fg.feast_get_stats(h)["normA"] - ref) <= 1e-12 * ref
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("generalized", [False, True])
 def test_factor_backward_error_and_pivots(precision, generalized):
