@@ -49,7 +49,8 @@ typedef enum {
   FEAST_ERR_NONFINITE = 7,      /* NaN or Inf appeared in the input or the iteration    */
   FEAST_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up                   */
   FEAST_ERR_CUDA = 9,           /* a CUDA runtime call failed                           */
-  FEAST_ERR_STATE = 10          /* call out of order (e.g. no factorisation yet)        */
+  FEAST_ERR_STATE = 10,         /* call out of order (e.g. no factorisation yet)        */
+  FEAST_ERR_TOO_LARGE = 11      /* size beyond the fixed scratch of an allocation-free entry point */
 } feast_status;
 
 /* Quadrature rules of Sec. 3 (Eq. quadrature_for_pi) and the meaning of N_e:
@@ -202,6 +203,29 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
 /* Timings of the last factorisation and of the last feast_solve on this handle
  * (filled when options.timing != 0; normA always).  stats must not be NULL. */
 feast_status feast_get_stats(const feast_handle* h, feast_stats* stats);
+
+/* ||A||_2 estimate for callers that cannot allocate device memory (the paper
+ * has no counterpart: it is the norm that scales the residual gate).
+ * Some callers may not call cudaMalloc -- code running while a host framework
+ * owns all device memory and hands out only its own buffers, or a phase whose
+ * memory budget is fixed.  This entry point allocates nothing: it runs the same
+ * power iteration as feast_create (iters steps on A^H A from the all-ones
+ * vector, result sqrt of the last Rayleigh quotient) and keeps its scratch in a
+ * fixed device array of 520.5 KiB that every GPU loading this library holds
+ * until exit.
+ *   A     : DEVICE pointer, n x n column-major, lda >= n (host memory is rejected
+ *           with FEAST_ERR_ARG); not modified.
+ *   n     : 1 <= n <= 16384; larger orders return FEAST_ERR_TOO_LARGE.
+ *   iters : >= 1 (feast_create uses 50).
+ *   norm  : receives the estimate (host or device pointer).
+ *   stream: cudaStream_t or NULL; the call returns after the stream has drained.
+ * The first call on each device looks up the fixed array's address with that
+ * device current; make it before any stream capture.  All calls share the one
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * race and must be serialised by the caller.  Calls no cudaMalloc, cudaFree
+ * or allocating library routine. */
+feast_status feast_norm2_estimate_static(const feast_z* A, int64_t n, int64_t lda, int iters,
+                                         double* norm, void* stream);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; no paper counterpart). */

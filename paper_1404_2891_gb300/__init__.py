@@ -31,6 +31,7 @@ FEAST_ERR_NONFINITE = 7
 FEAST_ERR_DEVICE_TIMEOUT = 8
 FEAST_ERR_CUDA = 9
 FEAST_ERR_STATE = 10
+FEAST_ERR_TOO_LARGE = 11
 
 RULES = {"trap_mid": 0, "trap_end": 1, "gauss": 2, "custom": 3}
 ALGOS = {"R": 0, "BI": 1}
@@ -75,7 +76,7 @@ _lib = None
 SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_status_str",
            "feast_get_quadrature", "feast_factor", "feast_get_factor", "feast_solve_shift",
            "feast_filter", "feast_rayleigh_ritz", "feast_solve", "feast_kernel_launches",
-           "feast_get_stats")
+           "feast_get_stats", "feast_norm2_estimate_static")
 
 
 def load(path=LIB_PATH):
@@ -114,6 +115,9 @@ def load(path=LIB_PATH):
     lib.feast_kernel_launches.restype = ctypes.c_uint64
     lib.feast_get_stats.argtypes = [P, ctypes.POINTER(feast_stats)]
     lib.feast_get_stats.restype = ctypes.c_int
+    lib.feast_norm2_estimate_static.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double), P]
+    lib.feast_norm2_estimate_static.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -254,6 +258,27 @@ def feast_get_stats(h):
     _check(load().feast_get_stats(h.ptr, ctypes.byref(st)), "feast_get_stats")
     return dict(normA=st.normA, t_factor_ms=st.t_factor_ms, t_update_ms=st.t_update_ms,
                 update_launches=st.update_launches, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms)
+
+
+def feast_norm2_estimate_static(A, iters=50, stream=None):
+    """||A||_2 by the power iteration of feast_create, without any device
+    allocation: for callers that may not call cudaMalloc (the scratch lives in
+    a fixed 520.5 KiB device array of the library; n <= 16384).  A must be a
+    complex128 CUDA tensor whose storage is column-major (e.g. ``T.mT`` of a
+    contiguous tensor T holding A^T); no copy of A is made."""
+    if not _is_torch(A) or not A.is_cuda:
+        raise TypeError("feast_norm2_estimate_static needs a CUDA tensor (device memory)")
+    import torch
+    if A.dtype != torch.complex128 or A.dim() != 2 or not A.mT.is_contiguous():
+        raise TypeError("A must be a complex128 CUDA tensor with column-major storage")
+    n = A.shape[0]
+    out = ctypes.c_double()
+    sp = None
+    if stream is not None:
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load().feast_norm2_estimate_static(A.data_ptr(), n, n, int(iters), ctypes.byref(out), sp),
+           "feast_norm2_estimate_static")
+    return out.value
 
 
 def feast_factor(h, allow_singular=False):

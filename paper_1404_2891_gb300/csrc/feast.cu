@@ -538,6 +538,7 @@ const char* feast_status_str(feast_status s) {
     case FEAST_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case FEAST_ERR_CUDA: return "CUDA error";
     case FEAST_ERR_STATE: return "call out of order";
+    case FEAST_ERR_TOO_LARGE: return "size exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }
