@@ -167,6 +167,7 @@ struct feast_handle {
   double *res = nullptr, *resl = nullptr, *xn = nullptr, *xln = nullptr, *scal = nullptr;
   void* orth_scratch = nullptr;
   void* pw_scratch = nullptr;
+  TcStaging staging;
   std::vector<void*> allocs;
   // host mirrors of the last Rayleigh-Ritz step
   std::vector<zc> h_lam;
@@ -279,7 +280,7 @@ feast_status factor_impl(feast_handle* h) {
   CK(form_shifted<T>(h->A, h->n, h->hasB ? h->B : nullptr, h->n, h->dz, h->q, (int)h->n, lu.S, lu.stride, h->st));
   TrailingUpdateFn<T> upd = nullptr;
   void* ctx = nullptr;
-  select_trailing_update<T>(&upd, &ctx);
+  select_trailing_update<T>(&upd, &ctx, &h->staging);
   if (!upd) upd = default_trailing_update<T>;
   UpdateTimer<T> timer{upd, ctx, h, 0, 0.0};
   if (h->opt.timing) {
@@ -619,6 +620,13 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->scal, 64);
   AL(h->orth_scratch, orth_scratch_bytes((int)n, m0));
   AL(h->pw_scratch, norm2_scratch_bytes((int)n));
+  if (mx) {
+    AL(h->staging.Ast, tc_staging_bytes_A(n, h->q));
+    AL(h->staging.Bst, tc_staging_bytes_B(n, h->q));
+    h->staging.rows_max = 2 * n;
+    h->staging.cols_max = n;
+    h->staging.q = h->q;
+  }
 #undef AL
   if (h->opt.timing)
     for (auto& ev : h->ev) cudaEventCreate(&ev);

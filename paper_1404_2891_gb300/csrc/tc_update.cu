@@ -1,14 +1,450 @@
-// Trailing-update selection for the batched shifted LU.
+// LU trailing update A22 -= L21 U12 on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in TMEM, operands staged by TMA), for all q
+// shifted matrices of one panel step.
+//
+// Arithmetic.  The complex64 matrices are stored interleaved, so a column of
+// n complex numbers is a column of 2n floats: rows 2i (Re) and 2i+1 (Im).
+// Reading the trailing block C and U12 that way, C~ (2M x N) and U~ (2K x N)
+// are real matrices, and with the real 2M x 2K operand A' that expands each
+// entry l of L21 into [[Re l, -Im l], [Im l, Re l]],
+//        C~ -= A' U~          (4 real products per complex product).
+// Each real operand is split into bfloat16 high and low parts
+// (x = hi + lo, |lo| <= 2^-9 |x|), and the product is taken as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation, about 16 significant bits.
+//
+// Kernel.  One CTA owns a 128-row stripe of C~ (64 complex rows) of one
+// shift and loops over the column tiles (BN = 128):
+//   warp 0   TMA producer: the stripe's A' once, then U~ tiles, two stages
+//   warp 1   TMEM allocation and the MMA issuer (one thread)
+//   warps 2-5 epilogue: TMEM -> registers, C~ -= D with coalesced 128-byte
+//            accesses (adjacent lanes hold the Re/Im rows of one complex row)
+// Two TMEM accumulator buffers (2 x 128 columns) let the MMAs of tile t+1 run
+// while the epilogue drains tile t.  Every mbarrier wait is bounded; on
+// timeout the CTA raises DEVFLAG_TIMEOUT, drains, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "tc_update.cuh"
 
+namespace {
+
+constexpr int TC_BM = 128;      // rows of C~ per stripe (= 64 complex rows)
+constexpr int TC_BN = 128;      // columns per tile
+constexpr int TC_KP = 128;      // staged K width (2 * nb, nb <= 64), bf16 elements
+constexpr int TC_BOX_K = 64;    // 64 bf16 = 128 bytes = one swizzle row
+constexpr int TC_THREADS = 192; // 6 warps
+constexpr int A_BYTES = 2 * 2 * TC_BM * TC_BOX_K * 2;        // hi/lo x 2 k-boxes x 128 rows x 128 B = 64 KB
+constexpr int B_STAGE_BYTES = 2 * 2 * TC_BN * TC_BOX_K * 2;  // 64 KB
+constexpr int TC_SMEM = 1024 + A_BYTES + 2 * B_STAGE_BYTES + 256;  // 197,888 bytes
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity: false after about two
+// seconds of GPU time (%globaltimer, nanoseconds).
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned addr = smem_u32(bar);
+  const unsigned long long t0 = gtime();
+  for (unsigned long long it = 0;; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && gtime() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(unsigned saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N = TC_BN.
+constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_BN >> 3) << 17) |
+                           ((unsigned)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// ---------------------------------------------------------------- operand staging
+// A' stage: [shift][hi,lo][row 0..2*rest)[kk 0..TC_KP) bf16; B stage: [shift][hi,lo][col][kk].
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ __nv_bfloat162 pair(__nv_bfloat16 a, __nv_bfloat16 b) {
+  __nv_bfloat162 r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+
+// One block stages 32 complex rows of L21 (blockIdx.z = 0) or 32 columns of
+// U12 (blockIdx.z = 1) of one shift: coalesced loads into a shared tile, then
+// coalesced 4-byte (bf16 pair) stores of the staged rows.
+constexpr int ST_ROWS = 32;
+
+__global__ void __launch_bounds__(256)
+k_stage_operands(const float2* S, long long ld, long long stride, int k0, int w, int rest, __nv_bfloat16* Ast,
+                 __nv_bfloat16* Bst, long long rows_max, long long cols_max) {
+  __shared__ float2 tile[ST_ROWS][TC_KP / 2 + 1];  // [row or column][k]
+  const int b = blockIdx.y, tid = threadIdx.x;
+  const float2* Sb = S + (size_t)b * stride;
+  const int base = blockIdx.x * ST_ROWS;
+  const bool isA = blockIdx.z == 0;
+  if (isA) {
+    const int r = tid & 31;
+    for (int k = tid >> 5; k < TC_KP / 2; k += 8) {
+      const int i = base + r;
+      tile[r][k] = (i < rest && k < w) ? Sb[(size_t)(k0 + w + i) + (size_t)(k0 + k) * ld] : make_float2(0.f, 0.f);
+    }
+  } else {
+    const int k = tid & 63;
+    for (int c = tid >> 6; c < ST_ROWS; c += 4) {
+      const int j = base + c;
+      tile[c][k] = (j < rest && k < w) ? Sb[(size_t)(k0 + k) + (size_t)(k0 + w + j) * ld] : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  constexpr int WORDS = TC_KP / 2;  // bf16 pairs per staged row
+  if (isA) {
+    // per complex row i: A' rows 2i ([Re, -Im] pairs) and 2i+1 ([Im, Re] pairs), hi and lo
+    for (int e = tid; e < ST_ROWS * 2 * 2 * WORDS; e += 256) {
+      const int k = e % WORDS;
+      const int rr = (e / WORDS) % (2 * ST_ROWS);  // A' row within the block
+      const int h = e / (WORDS * 2 * ST_ROWS);     // 0 = hi, 1 = lo
+      const int i = base + (rr >> 1);
+      if (i >= rest) continue;
+      const float2 l = tile[rr >> 1][k];
+      const float x0 = (rr & 1) ? l.y : l.x;
+      const float x1 = (rr & 1) ? l.x : -l.y;
+      __nv_bfloat16 h0, l0, h1, l1;
+      split_bf16(x0, h0, l0);
+      split_bf16(x1, h1, l1);
+      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(
+          Ast + (((size_t)b * 2 + h) * rows_max + 2 * (size_t)base + rr) * TC_KP);
+      dst[k] = h ? pair(l0, l1) : pair(h0, h1);
+    }
+  } else {
+    for (int e = tid; e < ST_ROWS * 2 * WORDS; e += 256) {
+      const int k = e % WORDS;
+      const int c = (e / WORDS) % ST_ROWS;
+      const int h = e / (WORDS * ST_ROWS);
+      const int j = base + c;
+      if (j >= rest) continue;
+      const float2 u = tile[c][k];
+      __nv_bfloat16 hr, lr, him, lim;
+      split_bf16(u.x, hr, lr);
+      split_bf16(u.y, him, lim);
+      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(Bst + (((size_t)b * 2 + h) * cols_max + (size_t)j) * TC_KP);
+      dst[k] = h ? pair(lr, lim) : pair(hr, him);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- the GEMM
+struct TcArgs {
+  float* S;            // q matrices, complex64 interleaved, as floats
+  long long ld2;       // 2 * ld (floats per column)
+  long long stride2;   // 2 * stride (floats per matrix)
+  long long c_off;     // float offset of C~ (row 2*(k0+w), column k0+w) inside a matrix
+  int rest;            // complex rows/columns of the trailing block
+  int kbox;            // number of 64-wide K boxes actually staged (1 or 2)
+  unsigned* flags;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = smem;                     // [hi k0, hi k1, lo k0, lo k1] x 16 KB
+  unsigned char* sB = smem + A_BYTES;           // 2 stages x [hi k0, hi k1, lo k0, lo k1] x 16 KB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + A_BYTES + 2 * B_STAGE_BYTES);
+  uint64_t* a_full = bars + 0;
+  uint64_t* b_full = bars + 1;   // [2]
+  uint64_t* b_empty = bars + 3;  // [2]
+  uint64_t* d_full = bars + 5;   // [2]
+  uint64_t* d_empty = bars + 7;  // [2]
+  uint64_t* mma_done = bars + 9;
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 10);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stripe = blockIdx.x, shift = blockIdx.y;
+  const int ntiles = (a.rest + TC_BN - 1) / TC_BN;
+  const int row0 = stripe * TC_BM;  // first row of C~ in this stripe
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+      mbar_init(&d_full[s], 1);
+      mbar_init(&d_empty[s], 4);
+    }
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const unsigned tmem_base = *tmem_slot;
+  const unsigned a_bytes = (unsigned)(2 * a.kbox * TC_BM * TC_BOX_K * 2);
+  const unsigned b_bytes = (unsigned)(2 * a.kbox * TC_BN * TC_BOX_K * 2);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // A' stripe once
+      mbar_expect_tx(a_full, a_bytes);
+      for (int h = 0; h < 2; ++h)
+        for (int kb = 0; kb < a.kbox; ++kb)
+          tma_load_3d(sA + (h * 2 + kb) * (TC_BM * 128), &mapA, a_full, kb * TC_BOX_K, row0, shift * 2 + h);
+      int last[2] = {-1, -1};
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t & 1;
+        if (t >= 2 && !mbar_wait(&b_empty[s], ((t >> 1) - 1) & 1)) {
+          atomicOr(a.flags, (unsigned)DEVFLAG_TIMEOUT);
+          break;
+        }
+        mbar_expect_tx(&b_full[s], b_bytes);
+        unsigned char* dst = sB + s * B_STAGE_BYTES;
+        for (int h = 0; h < 2; ++h)
+          for (int kb = 0; kb < a.kbox; ++kb)
+            tma_load_3d(dst + (h * 2 + kb) * (TC_BN * 128), &mapB, &b_full[s], kb * TC_BOX_K, t * TC_BN, shift * 2 + h);
+        last[s] = t;
+      }
+      // no copy may still be writing shared memory when the block exits
+      mbar_wait(a_full, 0);
+      for (int s = 0; s < 2; ++s)
+        if (last[s] >= 0) mbar_wait(&b_full[s], (last[s] >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(a_full, 0);
+      fence_after();
+      bool issued = false;
+      for (int t = 0; ok && t < ntiles; ++t) {
+        const int s = t & 1;
+        if (!mbar_wait(&b_full[s], (t >> 1) & 1)) { ok = false; break; }
+        if (t >= 2 && !mbar_wait(&d_empty[s], ((t >> 1) - 1) & 1)) { ok = false; break; }
+        fence_after();
+        const unsigned d = tmem_base + (unsigned)(s * TC_BN);
+        const unsigned aBase = smem_u32(sA), bBase = smem_u32(sB + s * B_STAGE_BYTES);
+        unsigned acc = 0;
+        // hi*hi, hi*lo, lo*hi
+        for (int term = 0; term < 3; ++term) {
+          const int ha = term == 2 ? 1 : 0, hb = term == 1 ? 1 : 0;
+          for (int kk = 0; kk < a.kbox * 4; ++kk) {
+            const int kb = kk >> 2, ko = (kk & 3) * 32;
+            const uint64_t ad = sw128_desc(aBase + (ha * 2 + kb) * (TC_BM * 128) + ko);
+            const uint64_t bd = sw128_desc(bBase + (hb * 2 + kb) * (TC_BN * 128) + ko);
+            mma_bf16(d, ad, bd, acc);
+            acc = 1;
+          }
+        }
+        mma_commit(&b_empty[s]);
+        mma_commit(&d_full[s]);
+        issued = true;
+      }
+      if (!ok) atomicOr(a.flags, (unsigned)DEVFLAG_TIMEOUT);
+      if (issued) {  // every MMA of this block has completed before TMEM is freed
+        mma_commit(mma_done);
+        mbar_wait(mma_done, 0);
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter (warp % 4)
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;  // row within the stripe
+    const long long R = row0 + r;       // row of C~
+    float* Cb = a.S + (size_t)shift * a.stride2 + a.c_off;
+    const bool row_ok = R < 2LL * a.rest;
+    for (int t = 0; t < ntiles; ++t) {
+      const int s = t & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&d_full[s], (t >> 1) & 1));  // warp-uniform
+      if (!ok) {
+        if (lane == 0) atomicOr(a.flags, (unsigned)DEVFLAG_TIMEOUT);
+        break;
+      }
+      fence_after();
+      const int col0 = t * TC_BN;
+      for (int c = 0; c < TC_BN / 32; ++c) {
+        float cv[32], v[32];
+        const int cbase = col0 + c * 32;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int col = cbase + u;
+          cv[u] = (row_ok && col < a.rest) ? __ldcs(Cb + R + (size_t)col * a.ld2) : 0.f;
+        }
+        const unsigned taddr = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(s * TC_BN + c * 32);
+        tmem_ld16(taddr, *reinterpret_cast<float(*)[16]>(&v[0]));
+        tmem_ld16(taddr + 16, *reinterpret_cast<float(*)[16]>(&v[16]));
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int col = cbase + u;
+          if (row_ok && col < a.rest) __stcs(Cb + R + (size_t)col * a.ld2, cv[u] - v[u]);
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d_empty[s]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * TC_BN));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+bool encode_stage_map(CUtensorMap* m, void* base, long long rows, long long rows_max, int q2, int box_rows) {
+  EncodeFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)TC_KP, (cuuint64_t)rows, (cuuint64_t)q2};
+  cuuint64_t strides[2] = {(cuuint64_t)TC_KP * 2, (cuuint64_t)rows_max * TC_KP * 2};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BOX_K, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, void* vctx, cudaStream_t s) {
+  const int rest = lu.n - k0 - w;
+  if (rest <= 0) return cudaSuccess;
+  TcStaging* ctx = reinterpret_cast<TcStaging*>(vctx);
+  if (w > TC_KP / 2 || !ctx || !ctx->Ast || ctx->rows_max < 2LL * lu.n || ctx->q < lu.q)
+    return default_trailing_update<float>(lu, k0, w, nullptr, s);
+  {
+    dim3 grid(ceil_div((size_t)rest, ST_ROWS), lu.q, 2);
+    feast_count_launch();
+    k_stage_operands<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(lu.S), lu.ld, lu.stride, k0, w, rest,
+                                          reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
+                                          reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max, ctx->cols_max);
+  }
+  CUtensorMap mA, mB;
+  if (!encode_stage_map(&mA, ctx->Ast, 2LL * rest, ctx->rows_max, 2 * lu.q, TC_BM)) return cudaErrorInvalidValue;
+  if (!encode_stage_map(&mB, ctx->Bst, rest, ctx->cols_max, 2 * lu.q, TC_BN)) return cudaErrorInvalidValue;
+  TcArgs a;
+  a.S = reinterpret_cast<float*>(lu.S);
+  a.ld2 = 2 * lu.ld;
+  a.stride2 = 2 * lu.stride;
+  a.c_off = 2LL * (k0 + w) + (long long)(k0 + w) * a.ld2;
+  a.rest = rest;
+  a.kbox = (2 * w + TC_BOX_K - 1) / TC_BOX_K;
+  a.flags = lu.flags;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(ceil_div(2 * (size_t)rest, TC_BM), lu.q);
+  feast_count_launch();
+  k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(mA, mB, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_staging_bytes_A(long long n, int q) { return (size_t)q * 2 * (2 * (size_t)n) * TC_KP * sizeof(__nv_bfloat16); }
+size_t tc_staging_bytes_B(long long n, int q) { return (size_t)q * 2 * (size_t)n * TC_KP * sizeof(__nv_bfloat16); }
+
 template <>
-void select_trailing_update<double>(TrailingUpdateFn<double>* fn, void** ctx) {
-  *fn = nullptr;  // default: gemm_batched<double> (mma.sync f64)
+void select_trailing_update<double>(TrailingUpdateFn<double>* fn, void** ctx, TcStaging*) {
+  *fn = nullptr;  // complex128: the DMMA batched GEMM (mma.sync f64)
   *ctx = nullptr;
 }
 
 template <>
-void select_trailing_update<float>(TrailingUpdateFn<float>* fn, void** ctx) {
-  *fn = nullptr;
-  *ctx = nullptr;
+void select_trailing_update<float>(TrailingUpdateFn<float>* fn, void** ctx, TcStaging* staging) {
+  *fn = tc_trailing_update;
+  *ctx = staging;
 }

@@ -2,6 +2,20 @@
 #pragma once
 #include "lu.cuh"
 
-// complex128: the DMMA batched GEMM; complex64: the tcgen05 kernel when available.
+// Staging for the tensor-core update: bf16 high/low parts of the expanded
+// L21 panel (A', 2 * rest rows) and of U12 (rest rows), K-major, 256 B rows.
+// Owned by the handle; sized for order n and q shifts by tc_staging_bytes.
+struct TcStaging {
+  void* Ast = nullptr;       // q x 2 x (2n) x 128 bf16
+  void* Bst = nullptr;       // q x 2 x n x 128 bf16
+  long long rows_max = 0;    // 2n
+  long long cols_max = 0;    // n
+  int q = 0;
+};
+size_t tc_staging_bytes_A(long long n, int q);
+size_t tc_staging_bytes_B(long long n, int q);
+
+// complex128: the DMMA batched GEMM (fn = nullptr); complex64: the tcgen05
+// kernel, with ctx pointing at the handle's TcStaging.
 template <typename T>
-void select_trailing_update(TrailingUpdateFn<T>* fn, void** ctx);
+void select_trailing_update(TrailingUpdateFn<T>* fn, void** ctx, TcStaging* staging);

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import workloads
-from helpers import contour_args, lib, relerr
+from helpers import MIXED_TOL, contour_args, lib, relerr
 from oracle import contour as ct, dense, feast
 
 pytestmark = pytest.mark.gpu
@@ -23,7 +23,7 @@ def test_ragged_orders_filter(n, precision):
     z, w = fg.feast_get_quadrature(h)
     Q, Qh = fg.feast_filter(h, Y, Y)
     factors = feast.factor_shifts(A, None, z)
-    tol = 1e-11 if precision == "fp64" else 1e-4
+    tol = 1e-11 if precision == "fp64" else MIXED_TOL
     assert relerr(Q, feast.filter_right(factors, None, w, Y)) < tol
     assert relerr(Qh, feast.filter_left(factors, None, w, Y)) < tol
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import workloads
-from helpers import U32, U64, contour_args, lib, relerr, residuals
+from helpers import MIXED_TOL, U32, U64, contour_args, lib, relerr, residuals
 from oracle import brute, contour as ct, dense, feast
 
 pytestmark = pytest.mark.gpu
@@ -87,7 +87,7 @@ def test_shift_solves_match_oracle(precision):
     h = make(fg, cfg, precision, B=cfg["B"])
     z, _ = fg.feast_get_quadrature(h)
     R = workloads.random_block(cfg["A"].shape[0], 19, seed=5)
-    tol = 1e-11 if precision == "fp64" else 2e-4
+    tol = 1e-11 if precision == "fp64" else MIXED_TOL
     for k in (0, h.q // 2, h.q - 1):
         S = z[k] * cfg["B"] - cfg["A"]
         LU, piv, _ = dense.lu_factor(S)
@@ -109,7 +109,7 @@ def test_filter_matches_oracle(precision):
     Q, Qh = fg.feast_filter(h, Y, Yh)
     Qr = feast.filter_right(factors, B, w, Y)
     Qhr = feast.filter_left(factors, B, w, Yh)
-    tol = 1e-11 if precision == "fp64" else 2e-4
+    tol = 1e-11 if precision == "fp64" else MIXED_TOL
     assert relerr(Q, Qr) < tol, relerr(Q, Qr)
     assert relerr(Qh, Qhr) < tol, relerr(Qh, Qhr)
     # with Ritz values supplied (the refinement's initial iterate), the result is the same
