@@ -10,6 +10,7 @@
 #include <complex>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/feast_gb300.h"
@@ -168,6 +169,10 @@ struct feast_handle {
   void* orth_scratch = nullptr;
   void* pw_scratch = nullptr;
   TcStaging staging;
+  void* schur_log = nullptr;
+  double2* gemm_ws = nullptr;  // split-K partial products
+  float2* s32 = nullptr;       // FP32 Schur work: C, Z, V, W, lambda (m0 x m0 each)
+  size_t gemm_ws_elems = 0;
   std::vector<void*> allocs;
   // host mirrors of the last Rayleigh-Ritz step
   std::vector<zc> h_lam;
@@ -218,6 +223,7 @@ LuBatch<T> lu_view(feast_handle* h) {
   lu.pinv = h->pinv;
   lu.info = h->info;
   lu.flags = h->flags;
+  if (std::is_same<T, float>::value && h->staging.Ast) lu.tc = &h->staging;
   return lu;
 }
 
@@ -229,6 +235,8 @@ cudaError_t zg(feast_handle* h, int opA, int opB, int M, int N, int K, zc alpha,
   g.A = A; g.lda = lda; g.opA = opA;
   g.B = B; g.ldb = ldb; g.opB = opB;
   g.C = C; g.ldc = ldc;
+  g.ws = h->gemm_ws;
+  g.ws_elems = h->gemm_ws_elems;
   return gemm_batched<double>(g, h->st);
 }
 
@@ -413,9 +421,37 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   CK(small_lu(h->LUB, m, h->pivB, h->flags, h->st));
   CK(cudaMemcpyAsync(h->Cm, h->Ahat, sm, cudaMemcpyDeviceToDevice, h->st));
   CK(small_lu_solve(h->LUB, h->pivB, m, h->Cm, m, 0, h->st));
-  CK(small_schur(h->Cm, h->Zs, h->lam, m, h->flags, h->st));
-  CK(small_trevc(h->Cm, h->V, m, h->st));
-  CK(zg(h, OP_N, OP_N, m, m, m, one, h->Zs, m, h->V, m, zero, h->W, m));
+  // Schur form and eigenvectors in FP32, then two FP64 refinement sweeps:
+  // E = W^{-1} C W (DMMA products), lam = diag(E), W <- W (I + Delta).
+  {
+    const size_t mm = (size_t)m * m;
+    float2* C32 = h->s32;
+    float2* Z32 = C32 + mm;
+    float2* V32 = Z32 + mm;
+    float2* W32 = V32 + mm;
+    float2* lam32 = W32 + mm;
+    CK(to_c64(h->Cm, C32, mm, h->st));
+    CK(small_schur<float>(C32, Z32, lam32, m, h->flags, h->schur_log, h->st));
+    CK(small_trevc<float>(C32, V32, m, h->st));
+    GemmArgs<float> g32;
+    g32.M = m; g32.N = m; g32.K = m;
+    g32.alpha = make_float2(1.f, 0.f);
+    g32.beta = make_float2(0.f, 0.f);
+    g32.A = Z32; g32.lda = m; g32.B = V32; g32.ldb = m; g32.C = W32; g32.ldc = m;
+    CK(gemm_batched<float>(g32, h->st));
+    CK(to_c128(W32, h->W, mm, h->st));
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      CK(cudaMemcpyAsync(h->LUW, h->W, sm, cudaMemcpyDeviceToDevice, h->st));
+      CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
+      CK(set_identity(h->Minv, m, h->st));
+      CK(small_lu_solve(h->LUW, h->pivW, m, h->Minv, m, 0, h->st));
+      CK(zg(h, OP_N, OP_N, m, m, m, one, h->Cm, m, h->W, m, zero, h->V, m));
+      CK(zg(h, OP_N, OP_N, m, m, m, one, h->Minv, m, h->V, m, zero, h->Zs, m));
+      CK(eig_refine_step(h->Zs, h->Ahat, h->lam, m, h->st));
+      CK(zg(h, OP_N, OP_N, m, m, m, one, h->W, m, h->Ahat, m, zero, h->LUW, m));
+      CK(cudaMemcpyAsync(h->W, h->LUW, sm, cudaMemcpyDeviceToDevice, h->st));
+    }
+  }
   // Ritz vectors and residuals
   CK(zg(h, OP_N, OP_N, n, m, m, one, h->Qo, n, h->W, m, zero, h->X, n));
   CK(zg(h, OP_N, OP_N, n, m, m, one, h->AQ, n, h->W, m, zero, h->AX, n));
@@ -620,6 +656,10 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->scal, 64);
   AL(h->orth_scratch, orth_scratch_bytes((int)n, m0));
   AL(h->pw_scratch, norm2_scratch_bytes((int)n));
+  AL(h->schur_log, schur_log_bytes(m0));
+  h->gemm_ws_elems = (size_t)64 * 160 * 160;
+  AL(h->gemm_ws, h->gemm_ws_elems * sizeof(double2));
+  AL(h->s32, (size_t)5 * m0 * m0 * sizeof(float2));
   if (mx) {
     AL(h->staging.Ast, tc_staging_bytes_A(n, h->q));
     AL(h->staging.Bst, tc_staging_bytes_B(n, h->q));

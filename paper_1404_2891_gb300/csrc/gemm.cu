@@ -42,10 +42,15 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const size_t b = blockIdx.z;
+  const int split = (int)(blockIdx.z % g.splitk);
+  const size_t b = blockIdx.z / g.splitk;
   const double2* A = g.A + b * g.strideA;
   const double2* B = g.B + b * g.strideB;
   double2* C = g.C + b * g.strideC;
+  // K range of this block (the whole of K unless split-K is on)
+  const int kchunk = ((g.K + g.splitk - 1) / g.splitk + BK64 - 1) / BK64 * BK64;
+  const int kbeg = split * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
 
   double acc_re[4][4], acc_im[4][4];
 #pragma unroll
@@ -60,10 +65,10 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
       int idx = tid + r * 256;
       int m, k;
       if (g.opA == OP_N) { m = idx & 63; k = idx >> 6; } else { k = idx & 7; m = idx >> 3; }
-      ra[r] = load_op<double>(A, g.lda, g.opA, m0 + m, k0 + k, g.M, g.K);
+      ra[r] = load_op<double>(A, g.lda, g.opA, m0 + m, k0 + k, g.M, kend);
       int n, kk;
       if (g.opB == OP_N) { kk = idx & 7; n = idx >> 3; } else { n = idx & 63; kk = idx >> 6; }
-      rb[r] = load_op<double>(B, g.ldb, g.opB, k0 + kk, n0 + n, g.K, g.N);
+      rb[r] = load_op<double>(B, g.ldb, g.opB, k0 + kk, n0 + n, kend, g.N);
     }
   };
   auto sstore = [&](int buf) {
@@ -81,16 +86,16 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
     }
   };
 
-  const int nk = (g.K + BK64 - 1) / BK64;
+  const int nk = kend > kbeg ? (kend - kbeg + BK64 - 1) / BK64 : 0;
   if (nk > 0) {
-    gload(0);
+    gload(kbeg);
     sstore(0);
   }
   __syncthreads();
   const int gq = lane >> 2, tq = lane & 3;
   for (int kt = 0; kt < nk; ++kt) {
     const int buf = kt & 1;
-    if (kt + 1 < nk) gload((kt + 1) * BK64);
+    if (kt + 1 < nk) gload(kbeg + (kt + 1) * BK64);
     // A fragment (16 x 8): a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
     double are[4], aim[4], aimn[4];
     const int mr = wm * 16 + gq;
@@ -116,6 +121,7 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
   }
   // epilogue: C fragment c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
   const bool beta_zero = (g.beta.x == 0.0 && g.beta.y == 0.0);
+  double2* part = g.splitk > 1 ? g.ws + (size_t)blockIdx.z * g.M * g.N : nullptr;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
 #pragma unroll
@@ -124,6 +130,10 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
       const int c = n0 + wn * 32 + j * 8 + tq * 2 + (e & 1);
       if (r < g.M && c < g.N) {
         double2 v = make_double2(acc_re[j][e], acc_im[j][e]);
+        if (part) {  // split-K: raw partial sum, reduced later in a fixed order
+          part[(size_t)r + (size_t)c * g.M] = v;
+          continue;
+        }
         double2 out = cmul<double>(g.alpha, v);
         double2* p = C + (size_t)r + (size_t)c * g.ldc;
         if (!beta_zero) out = cadd<double>(out, cmul<double>(g.beta, *p));
@@ -196,12 +206,49 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(GemmArgs<float> g) {
 
 }  // namespace
 
+namespace {
+// C = alpha * sum_{s < S} P_s + beta * C, the splits summed in increasing s.
+__global__ void k_splitk_reduce(GemmArgs<double> g) {
+  const size_t mn = (size_t)g.M * g.N;
+  const size_t total = mn * g.batch;
+  const bool beta_zero = (g.beta.x == 0.0 && g.beta.y == 0.0);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / mn, rc = e % mn;
+    const int r = (int)(rc % g.M), c = (int)(rc / g.M);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int sp = 0; sp < g.splitk; ++sp) acc = cadd<double>(acc, g.ws[(b * g.splitk + sp) * mn + rc]);
+    double2* p = g.C + b * g.strideC + (size_t)r + (size_t)c * g.ldc;
+    double2 out = cmul<double>(g.alpha, acc);
+    if (!beta_zero) out = cadd<double>(out, cmul<double>(g.beta, *p));
+    *p = out;
+  }
+}
+}  // namespace
+
 template <>
-cudaError_t gemm_batched<double>(const GemmArgs<double>& g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  dim3 grid(ceil_div(g.M, BM), ceil_div(g.N, BN), g.batch);
+cudaError_t gemm_batched<double>(const GemmArgs<double>& g0, cudaStream_t s) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return cudaSuccess;
+  GemmArgs<double> g = g0;
+  const size_t tiles = (size_t)ceil_div(g.M, BM) * ceil_div(g.N, BN) * g.batch;
+  int S = 1;
+  // split only when the tiles fill less than half of the 152 SMs, and keep the
+  // split grid within one wave (one 256-thread block per SM)
+  if (g.ws && tiles < 76 && g.K >= 8 * BK64 * 4) {
+    S = (int)(152 / tiles);
+    S = min(S, g.K / (BK64 * 4));
+    while (S > 1 && (size_t)S * g.M * g.N * g.batch > g.ws_elems) --S;
+  }
+  g.splitk = S;
+  dim3 grid(ceil_div(g.M, BM), ceil_div(g.N, BN), g.batch * S);
   feast_count_launch();
   k_zgemm_dmma<<<grid, 256, 0, s>>>(g);
+  if (S > 1) {
+    const size_t total = (size_t)g.M * g.N * g.batch;
+    const size_t want = (total + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 8 ? want : 152 * 8);
+    feast_count_launch();
+    k_splitk_reduce<<<blocks, 256, 0, s>>>(g);
+  }
   return cudaGetLastError();
 }
 

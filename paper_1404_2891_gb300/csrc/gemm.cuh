@@ -17,6 +17,12 @@ struct GemmArgs {
   int opB = OP_N;
   cplx<T>* C = nullptr;
   long long ldc = 0, strideC = 0;
+  // Optional split-K workspace (complex128 path): when M x N spans few tiles and
+  // K is long, K is cut into chunks whose partial products land here and are
+  // summed in a fixed order by a second kernel (deterministic).
+  cplx<T>* ws = nullptr;
+  size_t ws_elems = 0;
+  int splitk = 1;  // set by gemm_batched
 };
 
 template <typename T>

@@ -9,6 +9,10 @@
 // A22 -= L21 U12 as one batched contraction over all shifts.
 #include "lu.cuh"
 
+#include <type_traits>
+
+#include "tc_update.cuh"
+
 namespace {
 
 constexpr int PANEL_THREADS = 512;
@@ -72,25 +76,29 @@ k_panel(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, int32_
     // 3. scale the column below the pivot
     const cplx<T> d = A[(size_t)col + (size_t)col * ld];
     const bool zero = (d.x == T(0) && d.y == T(0));
-    if (zero) {
-      if (tid == 0) {
-        atomicCAS(&info[b], 0, col + 1);
-        atomicOr(flags, (unsigned)DEVFLAG_SINGULAR);
-      }
-    } else {
-      const cplx<T> r = crecip<T>(d);
-      for (int i = col + 1 + tid; i < n; i += PANEL_THREADS)
-        A[(size_t)i + (size_t)col * ld] = cmul<T>(A[(size_t)i + (size_t)col * ld], r);
+    if (zero && tid == 0) {
+      atomicCAS(&info[b], 0, col + 1);
+      atomicOr(flags, (unsigned)DEVFLAG_SINGULAR);
     }
     for (int j = col + 1 + tid; j < jend; j += PANEL_THREADS) s_u[j - k0] = A[(size_t)col + (size_t)j * ld];
     __syncthreads();
-    // 4. rank-1 update of the rest of the panel
+    // 4. scale the column below the pivot and apply the rank-1 update to the rest
+    // of the panel in one pass; each row segment is read in chunks of 8 independent
+    // loads before any store, so the L2 latency is paid once per chunk.
     if (!zero) {
+      const cplx<T> rinv = crecip<T>(d);
       for (int i = col + 1 + tid; i < n; i += PANEL_THREADS) {
-        const cplx<T> l = A[(size_t)i + (size_t)col * ld];
-        for (int j = col + 1; j < jend; ++j) {
-          cplx<T>& a = A[(size_t)i + (size_t)j * ld];
-          a = csub<T>(a, cmul<T>(l, s_u[j - k0]));
+        cplx<T>* row = A + (size_t)i;
+        const cplx<T> l = cmul<T>(row[(size_t)col * ld], rinv);
+        row[(size_t)col * ld] = l;
+        for (int j0 = col + 1; j0 < jend; j0 += 8) {
+          cplx<T> v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (j0 + u < jend) v[u] = row[(size_t)(j0 + u) * ld];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (j0 + u < jend) row[(size_t)(j0 + u) * ld] = csub<T>(v[u], cmul<T>(l, s_u[j0 + u - k0]));
         }
       }
     }
@@ -312,8 +320,18 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
     feast_count_launch();
     k_trsm_diag<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, X, ldx, sx, k0, w, m, mode);
   };
-  auto update = [&](int M, int K, const cplx<T>* Aop, int opA, int row_out, int row_in) {
+  // X[row_out : row_out+M] -= op(A) X[row_in : row_in+K], A the factor block at
+  // (ar0, ac0): op N rows ar0.., columns ac0..; op C the conjugate transpose of
+  // the block at rows ac0.., columns ar0..
+  auto update = [&](int M, int K, int ar0, int ac0, int opA, int row_out, int row_in) {
     if (M <= 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+      if (lu.tc) {
+        cudaError_t err = cudaSuccess;
+        if (tc_solve_update(lu, X, m, M, K, ar0, ac0, opA, row_out, row_in, s, &err)) return err;
+      }
+    }
+    const cplx<T>* Aop = opA == OP_N ? lu.S + (size_t)ar0 + (size_t)ac0 * lu.ld : lu.S + (size_t)ac0 + (size_t)ar0 * lu.ld;
     GemmArgs<T> g;
     g.M = M; g.N = m; g.K = K; g.batch = lu.q;
     g.alpha = mk<T>(T(-1), T(0));
@@ -323,20 +341,18 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
     g.C = X + row_out; g.ldc = ldx; g.strideC = sx;
     return gemm_batched<T>(g, s);
   };
-  const cplx<T>* F = lu.S;
-  const long long ld = lu.ld;
   if (side == 0) {
     for (int k0 = 0; k0 < n; k0 += nbs) {  // L y = P r
       const int w = min(nbs, n - k0);
       diag(k0, w, D_LOWER_UNIT);
-      e = update(n - k0 - w, w, F + (size_t)(k0 + w) + (size_t)k0 * ld, OP_N, k0 + w, k0);
+      e = update(n - k0 - w, w, k0 + w, k0, OP_N, k0 + w, k0);
       if (e != cudaSuccess) return e;
     }
     const int last = ((n - 1) / nbs) * nbs;
     for (int k0 = last; k0 >= 0; k0 -= nbs) {  // U x = y
       const int w = min(nbs, n - k0);
       diag(k0, w, D_UPPER);
-      e = update(k0, w, F + (size_t)(k0) * ld, OP_N, 0, k0);
+      e = update(k0, w, 0, k0, OP_N, 0, k0);
       if (e != cudaSuccess) return e;
     }
   } else {
@@ -344,7 +360,7 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
       const int w = min(nbs, n - k0);
       diag(k0, w, D_UPPER_H);
       // rows k0+w.. of op(A) = (U[k0:k0+w, k0+w:])^H
-      e = update(n - k0 - w, w, F + (size_t)k0 + (size_t)(k0 + w) * ld, OP_C, k0 + w, k0);
+      e = update(n - k0 - w, w, k0 + w, k0, OP_C, k0 + w, k0);
       if (e != cudaSuccess) return e;
     }
     const int last = ((n - 1) / nbs) * nbs;
@@ -352,7 +368,7 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
       const int w = min(nbs, n - k0);
       diag(k0, w, D_LOWER_H);
       // rows 0..k0 of op(A) = (L[k0:k0+w, 0:k0])^H
-      e = update(k0, w, F + (size_t)k0, OP_C, 0, k0);
+      e = update(k0, w, 0, k0, OP_C, 0, k0);
       if (e != cudaSuccess) return e;
     }
   }

@@ -15,6 +15,7 @@ struct LuBatch {
   int32_t* pinv = nullptr;  // q x n, inverse permutation: pinv[perm[i]] = i
   int* info = nullptr;      // q ints: 0 or 1 + first column with an exact zero pivot
   unsigned* flags = nullptr;
+  void* tc = nullptr;       // tensor-core staging (complex64 path), or nullptr
 };
 
 // Trailing-update hook: C -= L21 * U12 for all shifts of one panel step.

@@ -1,0 +1,397 @@
+// The dense m0 x m0 eigenproblem of the Rayleigh-Ritz step (Algorithm
+// R-FEAST step 5, Algorithm Bi-FEAST step 7).
+//
+// Scalar FP64 issues at about 1/64 of the FP32 rate on GB300, and the
+// Hessenberg QR iteration is a long chain of dependent scalar work (one Givens
+// rotation after another).  So the Schur form is computed in FP32 (one block,
+// the matrix packed in shared memory, the sweep run by one warp, the rotations
+// logged and applied to Z by a second kernel), and FP64 accuracy is recovered
+// afterwards by refinement sweeps built from FP64 tensor-core products
+// (eig_refine_step; see feast.cu).  The same kernels instantiated for double
+// give a plain FP64 Schur form.
+#include <float.h>
+
+#include "small.cuh"
+
+namespace {
+
+template <typename T> struct Lim;
+template <> struct Lim<float> {
+  static constexpr float ulp = FLT_EPSILON * 0.5f;
+  static constexpr float safe_min = FLT_MIN;
+  static constexpr float big = 1e30f;
+  static constexpr float tiny_scale = 1e-30f;
+};
+template <> struct Lim<double> {
+  static constexpr double ulp = DBL_EPSILON * 0.5;
+  static constexpr double safe_min = DBL_MIN;
+  static constexpr double big = 1e150;
+  static constexpr double tiny_scale = 1e-150;
+};
+
+constexpr int SCHUR_THREADS = 256;
+constexpr int SCHUR_MAX_M = 160;
+
+template <typename T>
+__device__ T block_sum_t(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = T(0);
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> csqrt_t(cplx<T> z) {
+  const T r = hypot(z.x, z.y);
+  if (r == T(0)) return mk<T>(T(0), T(0));
+  const T re = sqrt(T(0.5) * (r + fabs(z.x)));
+  const T other = z.y / (T(2) * re);
+  if (z.x >= T(0)) return mk<T>(re, other);
+  return mk<T>(fabs(other), z.y >= T(0) ? re : -re);
+}
+
+// packed storage: column j keeps rows 0 .. j+2 (Hessenberg plus the bulge diagonal)
+__device__ __forceinline__ int hp_off(int i, int j) { return j * (j + 5) / 2 + i; }
+
+// Givens rotation G = [c s; -conj(s) c] with G [x; y] = [r; 0], c real.
+template <typename T>
+__device__ void givens(cplx<T> x, cplx<T> y, T& c, cplx<T>& s) {
+  const T ax = sqrt(cnorm2<T>(x)), ay = sqrt(cnorm2<T>(y));
+  if (ay == T(0)) { c = T(1); s = mk<T>(T(0), T(0)); return; }
+  if (ax == T(0)) { c = T(0); s = mk<T>(T(1), T(0)); return; }
+  const T nu = sqrt(ax * ax + ay * ay);
+  c = ax / nu;
+  const cplx<T> ph = mk<T>(x.x / ax, x.y / ax);
+  s = cscale<T>(cmul<T>(ph, cconj<T>(y)), T(1) / nu);
+}
+
+// Householder reduction to Hessenberg form (C, Z in global memory), then the
+// shifted QR iteration by warp 0 on the packed shared-memory copy.  The
+// rotations (c, Re s, Im s, k) go to rot_log; k_apply_rotations folds them into Z.
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS)
+k_small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags, double4* rot_log, int rot_cap,
+              int* rot_count) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* H = reinterpret_cast<cplx<T>*>(smem_raw);
+  __shared__ cplx<T> s_u[SCHUR_MAX_M];
+  __shared__ T red[SCHUR_THREADS / 32];
+  __shared__ cplx<T> s_beta;
+  __shared__ int s_skip;
+  const int tid = threadIdx.x;
+  auto Cg = [&](int i, int j) -> cplx<T>& { return C[i + (size_t)j * m]; };
+  for (int idx = tid; idx < m * m; idx += SCHUR_THREADS)
+    Z[idx] = mk<T>((idx % m) == (idx / m) ? T(1) : T(0), T(0));
+  __syncthreads();
+  // ---- Householder reduction to upper Hessenberg form, Z <- Z H_k
+  for (int k = 0; k + 2 < m; ++k) {
+    const int len = m - k - 1;
+    T loc = T(0);
+    for (int i = 1 + tid; i < len; i += SCHUR_THREADS) loc += cnorm2<T>(Cg(k + 1 + i, k));
+    const T tail = block_sum_t<T>(loc, red);
+    if (tid == 0) {
+      const cplx<T> x0 = Cg(k + 1, k);
+      const T a0 = hypot(x0.x, x0.y);
+      s_skip = (tail == T(0));
+      const T alpha = sqrt(tail + a0 * a0);
+      const cplx<T> beta = a0 > T(0) ? mk<T>(-x0.x / a0 * alpha, -x0.y / a0 * alpha) : mk<T>(-alpha, T(0));
+      s_beta = beta;
+      s_u[0] = csub<T>(x0, beta);
+    }
+    __syncthreads();
+    if (s_skip) { __syncthreads(); continue; }
+    for (int i = 1 + tid; i < len; i += SCHUR_THREADS) s_u[i] = Cg(k + 1 + i, k);
+    __syncthreads();
+    T uu_loc = T(0);
+    for (int i = tid; i < len; i += SCHUR_THREADS) uu_loc += cnorm2<T>(s_u[i]);
+    const T uu = block_sum_t<T>(uu_loc, red);
+    const T t = T(2) / uu;
+    for (int c = k + tid; c < m; c += SCHUR_THREADS) {
+      cplx<T> s = mk<T>(T(0), T(0));
+      for (int i = 0; i < len; ++i) s = cadd<T>(s, cmulc<T>(s_u[i], Cg(k + 1 + i, c)));
+      s = cscale<T>(s, t);
+      for (int i = 0; i < len; ++i) Cg(k + 1 + i, c) = csub<T>(Cg(k + 1 + i, c), cmul<T>(s_u[i], s));
+    }
+    __syncthreads();
+    for (int r = tid; r < 2 * m; r += SCHUR_THREADS) {
+      cplx<T>* P = r < m ? C : Z;
+      const int rr = r < m ? r : r - m;
+      cplx<T> s = mk<T>(T(0), T(0));
+      for (int i = 0; i < len; ++i) s = cadd<T>(s, cmul<T>(P[rr + (size_t)(k + 1 + i) * m], s_u[i]));
+      s = cscale<T>(s, t);
+      for (int i = 0; i < len; ++i) {
+        cplx<T>& e = P[rr + (size_t)(k + 1 + i) * m];
+        e = csub<T>(e, cmul<T>(s, cconj<T>(s_u[i])));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) Cg(k + 1, k) = s_beta;
+    for (int i = 1 + tid; i < len; i += SCHUR_THREADS) Cg(k + 1 + i, k) = mk<T>(T(0), T(0));
+    __syncthreads();
+  }
+  for (int j = 0; j < m; ++j)
+    for (int i = tid; i <= j + 2; i += SCHUR_THREADS)
+      H[hp_off(i, j)] = (i < m && i <= j + 1) ? Cg(i, j) : mk<T>(T(0), T(0));
+  __syncthreads();
+  // ---- shifted QR iterations (warp 0)
+  if (tid < 32) {
+    const int lane = tid;
+    int ihi = m - 1, its = 0, total = 0, nrot = 0;
+    const int max_total = 30 * m + 100;
+    while (ihi >= 0) {
+      int l = 0;
+      if (lane == 0) {
+        for (int k = ihi; k >= 1; --k) {
+          T tst = cabs1<T>(H[hp_off(k - 1, k - 1)]) + cabs1<T>(H[hp_off(k, k)]);
+          if (tst == T(0)) tst = T(1);
+          if (cabs1<T>(H[hp_off(k, k - 1)]) <= fmax(Lim<T>::ulp * tst, Lim<T>::safe_min * (m / Lim<T>::ulp))) {
+            H[hp_off(k, k - 1)] = mk<T>(T(0), T(0));
+            l = k;
+            break;
+          }
+        }
+      }
+      l = __shfl_sync(0xffffffffu, l, 0);
+      __syncwarp();
+      if (l == ihi) {
+        if (lane == 0) lam[ihi] = H[hp_off(ihi, ihi)];
+        --ihi;
+        its = 0;
+        __syncwarp();
+        continue;
+      }
+      ++its;
+      if (++total > max_total) {
+        if (lane == 0) {
+          atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
+          for (int i = 0; i <= ihi; ++i) lam[i] = H[hp_off(i, i)];
+        }
+        break;
+      }
+      for (int k = l; k < ihi; ++k) {
+        T c = T(0);
+        cplx<T> s = mk<T>(T(0), T(0));
+        if (lane == 0) {
+          cplx<T> x, y;
+          if (k == l) {
+            cplx<T> sh;
+            const cplx<T> a = H[hp_off(ihi - 1, ihi - 1)], b = H[hp_off(ihi - 1, ihi)];
+            const cplx<T> cc = H[hp_off(ihi, ihi - 1)], d = H[hp_off(ihi, ihi)];
+            if (its % 10 == 0) {
+              sh = mk<T>(d.x + T(0.75) * fabs(cc.x), d.y);
+            } else {
+              const cplx<T> p = cscale<T>(csub<T>(a, d), T(0.5));
+              const cplx<T> bc = cmul<T>(b, cc);
+              const cplx<T> disc = csqrt_t<T>(cadd<T>(cmul<T>(p, p), bc));
+              const cplx<T> d1 = cadd<T>(p, disc), d2 = csub<T>(p, disc);
+              const cplx<T> den = cabs1<T>(d1) >= cabs1<T>(d2) ? d1 : d2;
+              sh = (den.x == T(0) && den.y == T(0)) ? d : csub<T>(d, cdiv<T>(bc, den));
+            }
+            x = csub<T>(H[hp_off(l, l)], sh);
+            y = H[hp_off(l + 1, l)];
+          } else {
+            x = H[hp_off(k, k - 1)];
+            y = H[hp_off(k + 1, k - 1)];
+          }
+          givens<T>(x, y, c, s);
+          if (nrot < rot_cap) rot_log[nrot] = make_double4((double)c, (double)s.x, (double)s.y, (double)k);
+        }
+        ++nrot;
+        c = __shfl_sync(0xffffffffu, c, 0);
+        s.x = __shfl_sync(0xffffffffu, s.x, 0);
+        s.y = __shfl_sync(0xffffffffu, s.y, 0);
+        const cplx<T> ms = mk<T>(-s.x, s.y);  // -conj(s)
+        const int j0 = (k == l) ? l : k - 1;
+        for (int j = j0 + lane; j < m; j += 32) {
+          const cplx<T> a = H[hp_off(k, j)], b = H[hp_off(k + 1, j)];
+          H[hp_off(k, j)] = cadd<T>(cscale<T>(a, c), cmul<T>(s, b));
+          H[hp_off(k + 1, j)] = cadd<T>(cmul<T>(ms, a), cscale<T>(b, c));
+        }
+        __syncwarp();
+        const int imax = min(k + 2, ihi);
+        const cplx<T> sc = cconj<T>(s), nsv = mk<T>(-s.x, -s.y);
+        for (int i = lane; i <= imax; i += 32) {
+          const cplx<T> a = H[hp_off(i, k)], b = H[hp_off(i, k + 1)];
+          H[hp_off(i, k)] = cadd<T>(cscale<T>(a, c), cmul<T>(b, sc));
+          H[hp_off(i, k + 1)] = cadd<T>(cmul<T>(a, nsv), cscale<T>(b, c));
+        }
+        __syncwarp();
+        if (k > l && lane == 0) H[hp_off(k + 1, k - 1)] = mk<T>(T(0), T(0));
+        __syncwarp();
+      }
+    }
+    if (lane == 0) {
+      if (nrot > rot_cap) atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
+      *rot_count = nrot < rot_cap ? nrot : rot_cap;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * m; idx += SCHUR_THREADS) {
+    const int i = idx % m, j = idx / m;
+    C[idx] = (i <= j) ? H[hp_off(i, j)] : mk<T>(T(0), T(0));
+  }
+}
+
+// Z <- Z G_1^H G_2^H ... for the logged rotations, in order.  One warp per block,
+// one row of Z per lane, the rows held in shared memory (row-major, padded).
+template <typename T>
+__global__ void __launch_bounds__(32) k_apply_rotations(cplx<T>* Z, int m, const double4* rot_log, const int* rot_count) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* rows = reinterpret_cast<cplx<T>*>(smem_raw);  // [32][m + 1]
+  __shared__ double4 recs[32];
+  const int lane = threadIdx.x;
+  const int r = blockIdx.x * 32 + lane;
+  const int ld = m + 1;
+  for (int j = 0; j < m; ++j) rows[lane * ld + j] = r < m ? Z[r + (size_t)j * m] : mk<T>(T(0), T(0));
+  const int nrot = *rot_count;
+  for (int base = 0; base < nrot; base += 32) {
+    if (base + lane < nrot) recs[lane] = rot_log[base + lane];
+    __syncwarp();
+    const int cnt = min(32, nrot - base);
+    for (int t = 0; t < cnt; ++t) {
+      const double4 g = recs[t];
+      const int k = (int)g.w;
+      const T c = (T)g.x;
+      const cplx<T> sc = mk<T>((T)g.y, (T)-g.z), nsv = mk<T>((T)-g.y, (T)-g.z);
+      const cplx<T> a = rows[lane * ld + k], b = rows[lane * ld + k + 1];
+      rows[lane * ld + k] = cadd<T>(cscale<T>(a, c), cmul<T>(b, sc));
+      rows[lane * ld + k + 1] = cadd<T>(cmul<T>(a, nsv), cscale<T>(b, c));
+    }
+    __syncwarp();
+  }
+  if (r < m)
+    for (int j = 0; j < m; ++j) Z[r + (size_t)j * m] = rows[lane * ld + j];
+}
+
+// Eigenvectors of the upper triangular T by back substitution, one per thread.
+template <typename T>
+__global__ void k_small_trevc(const cplx<T>* Tm, cplx<T>* V, int m) {
+  __shared__ T red[32];
+  const int k = threadIdx.x;
+  T loc = T(0);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    if (i <= j) loc = fmax(loc, cabs1<T>(Tm[idx]));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) loc = fmax(loc, __shfl_down_sync(0xffffffffu, loc, off));
+  if (lane == 0) red[wid] = loc;
+  __syncthreads();
+  T tnorm = T(0);
+  for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) tnorm = fmax(tnorm, red[w]);
+  const T smin = fmax(Lim<T>::ulp * tnorm, Lim<T>::safe_min * (m / Lim<T>::ulp));
+  if (k >= m) return;
+  cplx<T>* v = V + (size_t)k * m;
+  for (int i = k + 1; i < m; ++i) v[i] = mk<T>(T(0), T(0));
+  v[k] = mk<T>(T(1), T(0));
+  const cplx<T> lk = Tm[k + (size_t)k * m];
+  for (int i = k - 1; i >= 0; --i) {
+    cplx<T> s = mk<T>(T(0), T(0));
+    for (int j = i + 1; j <= k; ++j) s = cadd<T>(s, cmul<T>(Tm[i + (size_t)j * m], v[j]));
+    cplx<T> d = csub<T>(Tm[i + (size_t)i * m], lk);
+    if (cabs1<T>(d) < smin) d = mk<T>(smin, T(0));
+    const cplx<T> vi = cdiv<T>(s, d);
+    v[i] = mk<T>(-vi.x, -vi.y);
+    if (cabs1<T>(v[i]) > Lim<T>::big)  // keep the partial column representable
+      for (int j = i; j <= k; ++j) v[j] = cscale<T>(v[j], Lim<T>::tiny_scale);
+  }
+}
+
+// lam = diag(E); D = I + Delta, Delta_ij = E_ij / (E_jj - E_ii) for well-separated pairs.
+__global__ void k_refine_step(const double2* E, double2* D, double2* lam, int m) {
+  __shared__ double red[32];
+  double loc = 0.0;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) loc = fmax(loc, cabs1<double>(E[idx]));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) loc = fmax(loc, __shfl_down_sync(0xffffffffu, loc, off));
+  if (lane == 0) red[wid] = loc;
+  __syncthreads();
+  double enorm = 0.0;
+  for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) enorm = fmax(enorm, red[w]);
+  const double gap_min = 1e-9 * enorm;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    if (i == j) {
+      D[idx] = make_double2(1.0, 0.0);
+      lam[i] = E[idx];
+    } else {
+      const double2 gap = csub<double>(E[j + (size_t)j * m], E[i + (size_t)i * m]);
+      D[idx] = cabs1<double>(gap) > gap_min ? cdiv<double>(E[idx], gap) : make_double2(0.0, 0.0);
+    }
+  }
+}
+
+__global__ void k_to_c64(const double2* src, float2* dst, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = make_float2((float)src[e].x, (float)src[e].y);
+}
+
+__global__ void k_to_c128(const float2* src, double2* dst, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = make_double2(src[e].x, src[e].y);
+}
+
+unsigned grid1(size_t count) {
+  size_t g = (count + 255) / 256;
+  return (unsigned)(g < 1 ? 1 : (g > 1216 ? 1216 : g));
+}
+
+}  // namespace
+
+size_t schur_log_bytes(int m) { return (size_t)(30 * m + 100) * (size_t)m * sizeof(double4) + 256; }
+
+template <typename T>
+cudaError_t small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags, void* log, cudaStream_t s) {
+  if (m < 1 || m > SCHUR_MAX_M) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(m * (m + 5) / 2 + 8) * sizeof(cplx<T>);
+  cudaError_t e = cudaFuncSetAttribute(k_small_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int* count = reinterpret_cast<int*>(log);
+  double4* recs = reinterpret_cast<double4*>(reinterpret_cast<char*>(log) + 256);
+  const int cap = (30 * m + 100) * m;
+  feast_count_launch();
+  k_small_schur<T><<<1, SCHUR_THREADS, smem, s>>>(C, Z, lam, m, flags, recs, cap, count);
+  const size_t smem2 = (size_t)32 * (m + 1) * sizeof(cplx<T>);
+  e = cudaFuncSetAttribute(k_apply_rotations<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  if (e != cudaSuccess) return e;
+  feast_count_launch();
+  k_apply_rotations<T><<<(m + 31) / 32, 32, smem2, s>>>(Z, m, recs, count);
+  return cudaGetLastError();
+}
+template cudaError_t small_schur<float>(float2*, float2*, float2*, int, unsigned*, void*, cudaStream_t);
+template cudaError_t small_schur<double>(double2*, double2*, double2*, int, unsigned*, void*, cudaStream_t);
+
+template <typename T>
+cudaError_t small_trevc(const cplx<T>* Tm, cplx<T>* V, int m, cudaStream_t s) {
+  const int threads = ((m + 31) / 32) * 32;
+  feast_count_launch();
+  k_small_trevc<T><<<1, threads, 0, s>>>(Tm, V, m);
+  return cudaGetLastError();
+}
+template cudaError_t small_trevc<float>(const float2*, float2*, int, cudaStream_t);
+template cudaError_t small_trevc<double>(const double2*, double2*, int, cudaStream_t);
+
+cudaError_t eig_refine_step(const double2* E, double2* D, double2* lam, int m, cudaStream_t s) {
+  feast_count_launch();
+  k_refine_step<<<1, 1024, 0, s>>>(E, D, lam, m);
+  return cudaGetLastError();
+}
+
+cudaError_t to_c64(const double2* src, float2* dst, size_t count, cudaStream_t s) {
+  feast_count_launch();
+  k_to_c64<<<grid1(count), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t to_c128(const float2* src, double2* dst, size_t count, cudaStream_t s) {
+  feast_count_launch();
+  k_to_c128<<<grid1(count), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}

@@ -18,6 +18,19 @@ cudaError_t small_lu_solve(const double2* LU, const int* piv, int m, double2* X,
 // Schur form of the m x m matrix C (overwritten by the upper triangular T) by
 // Householder reduction to Hessenberg form and shifted complex QR iterations;
 // Z (m x m) receives the unitary Schur vectors (C = Z T Z^H); lam the diagonal of T.
-cudaError_t small_schur(double2* C, double2* Z, double2* lam, int m, unsigned* flags, cudaStream_t s);
+// log: device scratch of schur_log_bytes(m) for the rotation record.  T is
+// float (the fast path, refined afterwards in FP64) or double.
+size_t schur_log_bytes(int m);
+template <typename T>
+cudaError_t small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags, void* log, cudaStream_t s);
 // Eigenvectors of the upper triangular T (V, m x m, unit diagonal entry, back substitution).
-cudaError_t small_trevc(const double2* T, double2* V, int m, cudaStream_t s);
+template <typename T>
+cudaError_t small_trevc(const cplx<T>* Tm, cplx<T>* V, int m, cudaStream_t s);
+// One refinement sweep of an approximate eigendecomposition C ~ W Lambda W^{-1}:
+// from E = W^{-1} C W, lam = diag(E) and D = I + Delta with
+// Delta_ij = E_ij / (E_jj - E_ii) (i != j; 0 where |E_jj - E_ii| <= tiny * ||E||),
+// so that W D is the first-order corrected eigenvector matrix.
+cudaError_t eig_refine_step(const double2* E, double2* D, double2* lam, int m, cudaStream_t s);
+// Element-wise precision conversions.
+cudaError_t to_c64(const double2* src, float2* dst, size_t count, cudaStream_t s);
+cudaError_t to_c128(const float2* src, double2* dst, size_t count, cudaStream_t s);

@@ -148,25 +148,47 @@ __device__ __forceinline__ __nv_bfloat162 pair(__nv_bfloat16 a, __nv_bfloat16 b)
 // coalesced 4-byte (bf16 pair) stores of the staged rows.
 constexpr int ST_ROWS = 32;
 
+// Operand description of one batched block product C -= A B (all complex64):
+//   A (M x K): opA = OP_N: A(i,k) = SA_b[ar0 + i, ac0 + k];  OP_C: A(i,k) = conj(SA_b[ac0 + k, ar0 + i])
+//   B (K x N): B(k,j) = SB_b[br0 + k, bc0 + j]
+//   C (M x N): C(i,j) = SC_b[cr0 + i, cc0 + j]
+struct TcGemm {
+  const float2* SA; long long lda, sa; int ar0, ac0, opA;
+  const float2* SB; long long ldb, sb; int br0, bc0;
+  float2* SC; long long ldc, sc; int cr0, cc0;
+  int M, N, K, q;
+};
+
 __global__ void __launch_bounds__(256)
-k_stage_operands(const float2* S, long long ld, long long stride, int k0, int w, int rest, __nv_bfloat16* Ast,
-                 __nv_bfloat16* Bst, long long rows_max, long long cols_max) {
+k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max) {
   __shared__ float2 tile[ST_ROWS][TC_KP / 2 + 1];  // [row or column][k]
   const int b = blockIdx.y, tid = threadIdx.x;
-  const float2* Sb = S + (size_t)b * stride;
   const int base = blockIdx.x * ST_ROWS;
   const bool isA = blockIdx.z == 0;
-  if (isA) {
+  const int rest = isA ? g.M : g.N;
+  const int w = g.K;
+  if (isA && g.opA == OP_N) {
+    const float2* Sb = g.SA + (size_t)b * g.sa;
     const int r = tid & 31;
     for (int k = tid >> 5; k < TC_KP / 2; k += 8) {
       const int i = base + r;
-      tile[r][k] = (i < rest && k < w) ? Sb[(size_t)(k0 + w + i) + (size_t)(k0 + k) * ld] : make_float2(0.f, 0.f);
+      tile[r][k] = (i < rest && k < w) ? Sb[(size_t)(g.ar0 + i) + (size_t)(g.ac0 + k) * g.lda] : make_float2(0.f, 0.f);
+    }
+  } else if (isA) {
+    const float2* Sb = g.SA + (size_t)b * g.sa;
+    const int k = tid & 63;
+    for (int c = tid >> 6; c < ST_ROWS; c += 4) {
+      const int i = base + c;
+      float2 v = (i < rest && k < w) ? Sb[(size_t)(g.ac0 + k) + (size_t)(g.ar0 + i) * g.lda] : make_float2(0.f, 0.f);
+      v.y = -v.y;
+      tile[c][k] = v;
     }
   } else {
+    const float2* Sb = g.SB + (size_t)b * g.sb;
     const int k = tid & 63;
     for (int c = tid >> 6; c < ST_ROWS; c += 4) {
       const int j = base + c;
-      tile[c][k] = (j < rest && k < w) ? Sb[(size_t)(k0 + k) + (size_t)(k0 + w + j) * ld] : make_float2(0.f, 0.f);
+      tile[c][k] = (j < rest && k < w) ? Sb[(size_t)(g.br0 + k) + (size_t)(g.bc0 + j) * g.ldb] : make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
@@ -208,11 +230,11 @@ k_stage_operands(const float2* S, long long ld, long long stride, int k0, int w,
 
 // ---------------------------------------------------------------- the GEMM
 struct TcArgs {
-  float* S;            // q matrices, complex64 interleaved, as floats
+  float* S;            // q output matrices, complex64 interleaved, as floats
   long long ld2;       // 2 * ld (floats per column)
   long long stride2;   // 2 * stride (floats per matrix)
-  long long c_off;     // float offset of C~ (row 2*(k0+w), column k0+w) inside a matrix
-  int rest;            // complex rows/columns of the trailing block
+  long long c_off;     // float offset of C~ (its first Re row, first column) inside a matrix
+  int M, N;            // complex rows and columns of the C block
   int kbox;            // number of 64-wide K boxes actually staged (1 or 2)
   unsigned* flags;
 };
@@ -234,7 +256,7 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int stripe = blockIdx.x, shift = blockIdx.y;
-  const int ntiles = (a.rest + TC_BN - 1) / TC_BN;
+  const int ntiles = (a.N + TC_BN - 1) / TC_BN;
   const int row0 = stripe * TC_BM;  // first row of C~ in this stripe
 
   if (threadIdx.x == 0) {
@@ -326,7 +348,7 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     const int r = quarter * 32 + lane;  // row within the stripe
     const long long R = row0 + r;       // row of C~
     float* Cb = a.S + (size_t)shift * a.stride2 + a.c_off;
-    const bool row_ok = R < 2LL * a.rest;
+    const bool row_ok = R < 2LL * a.M;
     for (int t = 0; t < ntiles; ++t) {
       const int s = t & 1;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&d_full[s], (t >> 1) & 1));  // warp-uniform
@@ -342,7 +364,7 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
           const int col = cbase + u;
-          cv[u] = (row_ok && col < a.rest) ? __ldcs(Cb + R + (size_t)col * a.ld2) : 0.f;
+          cv[u] = (row_ok && col < a.N) ? __ldcs(Cb + R + (size_t)col * a.ld2) : 0.f;
         }
         const unsigned taddr = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(s * TC_BN + c * 32);
         tmem_ld16(taddr, *reinterpret_cast<float(*)[16]>(&v[0]));
@@ -350,7 +372,7 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
           const int col = cbase + u;
-          if (row_ok && col < a.rest) __stcs(Cb + R + (size_t)col * a.ld2, cv[u] - v[u]);
+          if (row_ok && col < a.N) __stcs(Cb + R + (size_t)col * a.ld2, cv[u] - v[u]);
         }
       }
       fence_before();
@@ -396,40 +418,59 @@ bool encode_stage_map(CUtensorMap* m, void* base, long long rows, long long rows
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, void* vctx, cudaStream_t s) {
-  const int rest = lu.n - k0 - w;
-  if (rest <= 0) return cudaSuccess;
-  TcStaging* ctx = reinterpret_cast<TcStaging*>(vctx);
-  if (w > TC_KP / 2 || !ctx || !ctx->Ast || ctx->rows_max < 2LL * lu.n || ctx->q < lu.q)
-    return default_trailing_update<float>(lu, k0, w, nullptr, s);
+// C -= A B for all q shifts on the tensor cores (K <= 64); false if the staging
+// cannot hold the operands (the caller then uses the FP32 GEMM).
+bool tc_gemm_fits(const TcGemm& g, const TcStaging* ctx) {
+  return ctx && ctx->Ast && g.K >= 1 && g.K <= TC_KP / 2 && 2LL * g.M <= ctx->rows_max && g.N <= ctx->cols_max &&
+         g.q <= ctx->q;
+}
+
+cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   {
-    dim3 grid(ceil_div((size_t)rest, ST_ROWS), lu.q, 2);
+    const int blocks = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), ST_ROWS);
+    dim3 grid(blocks, g.q, 2);
     feast_count_launch();
-    k_stage_operands<<<grid, 256, 0, s>>>(reinterpret_cast<const float2*>(lu.S), lu.ld, lu.stride, k0, w, rest,
-                                          reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
+    k_stage_operands<<<grid, 256, 0, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
                                           reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max, ctx->cols_max);
   }
   CUtensorMap mA, mB;
-  if (!encode_stage_map(&mA, ctx->Ast, 2LL * rest, ctx->rows_max, 2 * lu.q, TC_BM)) return cudaErrorInvalidValue;
-  if (!encode_stage_map(&mB, ctx->Bst, rest, ctx->cols_max, 2 * lu.q, TC_BN)) return cudaErrorInvalidValue;
+  if (!encode_stage_map(&mA, ctx->Ast, 2LL * g.M, ctx->rows_max, 2 * g.q, TC_BM)) return cudaErrorInvalidValue;
+  if (!encode_stage_map(&mB, ctx->Bst, g.N, ctx->cols_max, 2 * g.q, TC_BN)) return cudaErrorInvalidValue;
   TcArgs a;
-  a.S = reinterpret_cast<float*>(lu.S);
-  a.ld2 = 2 * lu.ld;
-  a.stride2 = 2 * lu.stride;
-  a.c_off = 2LL * (k0 + w) + (long long)(k0 + w) * a.ld2;
-  a.rest = rest;
-  a.kbox = (2 * w + TC_BOX_K - 1) / TC_BOX_K;
-  a.flags = lu.flags;
+  a.S = reinterpret_cast<float*>(g.SC);
+  a.ld2 = 2 * g.ldc;
+  a.stride2 = 2 * g.sc;
+  a.c_off = 2LL * g.cr0 + (long long)g.cc0 * a.ld2;
+  a.M = g.M;
+  a.N = g.N;
+  a.kbox = (2 * g.K + TC_BOX_K - 1) / TC_BOX_K;
+  a.flags = flags;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(ceil_div(2 * (size_t)rest, TC_BM), lu.q);
+  dim3 grid(ceil_div(2 * (size_t)g.M, TC_BM), g.q);
   feast_count_launch();
   k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
+}
+
+// LU trailing update: C = S[k0+w:, k0+w:], A = L21 = S[k0+w:, k0:k0+w], B = U12 = S[k0:k0+w, k0+w:].
+cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, void* vctx, cudaStream_t s) {
+  const int rest = lu.n - k0 - w;
+  if (rest <= 0) return cudaSuccess;
+  const TcStaging* ctx = reinterpret_cast<const TcStaging*>(vctx);
+  TcGemm g;
+  const float2* S = reinterpret_cast<const float2*>(lu.S);
+  g.SA = S; g.lda = lu.ld; g.sa = lu.stride; g.ar0 = k0 + w; g.ac0 = k0; g.opA = OP_N;
+  g.SB = S; g.ldb = lu.ld; g.sb = lu.stride; g.br0 = k0; g.bc0 = k0 + w;
+  g.SC = reinterpret_cast<float2*>(lu.S); g.ldc = lu.ld; g.sc = lu.stride; g.cr0 = k0 + w; g.cc0 = k0 + w;
+  g.M = rest; g.N = rest; g.K = w; g.q = lu.q;
+  if (!tc_gemm_fits(g, ctx)) return default_trailing_update<float>(lu, k0, w, nullptr, s);
+  return tc_gemm(g, ctx, lu.flags, s);
 }
 
 }  // namespace
@@ -447,4 +488,19 @@ template <>
 void select_trailing_update<float>(TrailingUpdateFn<float>* fn, void** ctx, TcStaging* staging) {
   *fn = tc_trailing_update;
   *ctx = staging;
+}
+
+bool tc_solve_update(const LuBatch<float>& lu, float2* X, int m, int M, int K, int ar0, int ac0, int opA,
+                     int row_out, int row_in, cudaStream_t s, cudaError_t* err) {
+  const TcStaging* ctx = reinterpret_cast<const TcStaging*>(lu.tc);
+  TcGemm g;
+  const float2* S = reinterpret_cast<const float2*>(lu.S);
+  const long long n = lu.n, sx = (long long)lu.n * m;
+  g.SA = S; g.lda = lu.ld; g.sa = lu.stride; g.ar0 = ar0; g.ac0 = ac0; g.opA = opA;
+  g.SB = X; g.ldb = n; g.sb = sx; g.br0 = row_in; g.bc0 = 0;
+  g.SC = X; g.ldc = n; g.sc = sx; g.cr0 = row_out; g.cc0 = 0;
+  g.M = M; g.N = m; g.K = K; g.q = lu.q;
+  if (!tc_gemm_fits(g, ctx)) return false;
+  *err = tc_gemm(g, ctx, lu.flags, s);
+  return true;
 }

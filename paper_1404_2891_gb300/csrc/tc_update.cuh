@@ -19,3 +19,11 @@ size_t tc_staging_bytes_B(long long n, int q);
 // kernel, with ctx pointing at the handle's TcStaging.
 template <typename T>
 void select_trailing_update(TrailingUpdateFn<T>* fn, void** ctx, TcStaging* staging);
+
+// Off-diagonal update of a blocked triangular solve on the tensor cores:
+// X[row_out : row_out + M, :] -= op(A) X[row_in : row_in + K, :] for every shift,
+// A the factor block at (ar0, ac0) (opA = OP_N) or its conjugate transpose
+// (OP_C: A(i,k) = conj(S[ac0 + k, ar0 + i])).  Returns false (nothing done)
+// when the handle has no staging (lu.tc == nullptr) or K > 64.
+bool tc_solve_update(const LuBatch<float>& lu, float2* X, int m, int M, int K, int ar0, int ac0, int opA,
+                     int row_out, int row_in, cudaStream_t s, cudaError_t* err);
