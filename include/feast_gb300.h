@@ -175,6 +175,15 @@ feast_status feast_solve_shift(feast_handle* h, int k, int side, const feast_z* 
 feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat,
                           const feast_z* theta, feast_z* Q, feast_z* Qhat);
 
+/* Stochastic moments of the filter for counting eigenvalues (the count
+ * estimation of Sec. 6, in its plain stochastic-trace form):
+ *   mu_k = (1/S) sum_s v_s^H [ sum_j sigma_j t_j^k (phi_j B - A)^{-1} B ] v_s,
+ *   t_j = (phi_j - c) / R,  k = 0 .. kmax (kmax <= 31),
+ * with the stored factorisations.  mu_0 estimates tr rho(M) = sum_i rho(lambda_i),
+ * close to the number of eigenvalues inside C.  V: n x S probe block (entries
+ * +-1 for the usual estimator), 1 <= S <= m0; mu: kmax + 1 complex values. */
+feast_status feast_moments(feast_handle* h, const feast_z* V, int S, int kmax, feast_z* mu);
+
 /* Rayleigh-Ritz (R-FEAST steps 4-5 / Bi-FEAST steps 6-7) on the filtered blocks.
  * Q (and Qhat for Bi-FEAST; NULL selects R-FEAST's one-sided projection) are
  * replaced in FP64 by orthonormal bases of their spans, the reduced pencil
@@ -203,6 +212,34 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
 /* Timings of the last factorisation and of the last feast_solve on this handle
  * (filled when options.timing != 0; normA always).  stats must not be NULL. */
 feast_status feast_get_stats(const feast_handle* h, feast_stats* stats);
+
+/* ---- Learned choice of the subspace size m0 --------------------------------
+ * The paper leaves p (m0) to experience or to a count estimate (Sec. 6).  This
+ * network predicts the eigenvalue count from the pencil's parameter and the
+ * stochastic moments of feast_moments; m0 is then chosen from the prediction.
+ * Architecture: d_in -> width -> width -> 1, GELU after the two hidden layers,
+ * inputs standardised as (x - mean) / scale, BF16 weights in every product with
+ * FP32 accumulation, FP32 master weights, Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8), mean-squared-error loss.
+ * Parameters are one FP32 vector in the order W1 (width x d_in, row-major),
+ * b1 (width), W2 (width x width), b2, W3 (1 x width), b3 (1);
+ * feast_mlp_param_count gives its length.  Feature, label and index arrays
+ * given to predict/grad/train are row-major FP32 / int32 in DEVICE memory
+ * (FEAST_ERR_ARG otherwise); params, mean, scale, outputs may be host or device. */
+typedef struct feast_mlp feast_mlp;
+size_t feast_mlp_param_count(int d_in, int width);
+feast_status feast_mlp_create(feast_mlp** net, int d_in, int width, int max_batch, const float* params,
+                              const float* mean, const float* scale, void* stream);
+void feast_mlp_destroy(feast_mlp* net);
+feast_status feast_mlp_get_params(feast_mlp* net, float* params);
+/* y[b] = network(X[b, :]) for b < B (B <= max_batch). */
+feast_status feast_mlp_predict(feast_mlp* net, const float* X, int B, float* y);
+/* Loss (1/B) sum_b (net(X[b]) - y[b])^2 and its gradient w.r.t. every parameter. */
+feast_status feast_mlp_grad(feast_mlp* net, const float* X, const float* y, int B, float* loss, float* grads);
+/* `steps` Adam steps with learning rate lr; step s uses the B rows
+ * batches[s*B .. s*B+B) of (X, y) (n_rows rows; indices are clamped). */
+feast_status feast_mlp_train(feast_mlp* net, const float* X, const float* y, int n_rows, const int* batches,
+                             int steps, int B, float lr, float* last_loss);
 
 /* ||A||_2 estimate for callers that cannot allocate device memory (the paper
  * has no counterpart: it is the norm that scales the residual gate).

@@ -76,7 +76,9 @@ _lib = None
 SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_status_str",
            "feast_get_quadrature", "feast_factor", "feast_get_factor", "feast_solve_shift",
            "feast_filter", "feast_rayleigh_ritz", "feast_solve", "feast_kernel_launches",
-           "feast_get_stats", "feast_norm2_estimate_static")
+           "feast_get_stats", "feast_norm2_estimate_static", "feast_moments",
+           "feast_mlp_param_count", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_get_params",
+           "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train")
 
 
 def load(path=LIB_PATH):
@@ -118,6 +120,23 @@ def load(path=LIB_PATH):
     lib.feast_norm2_estimate_static.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), P]
     lib.feast_norm2_estimate_static.restype = ctypes.c_int
+    lib.feast_moments.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
+    lib.feast_moments.restype = ctypes.c_int
+    I = ctypes.c_int
+    lib.feast_mlp_param_count.argtypes = [I, I]
+    lib.feast_mlp_param_count.restype = ctypes.c_size_t
+    lib.feast_mlp_create.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, P]
+    lib.feast_mlp_create.restype = I
+    lib.feast_mlp_destroy.argtypes = [P]
+    lib.feast_mlp_destroy.restype = None
+    lib.feast_mlp_get_params.argtypes = [P, P]
+    lib.feast_mlp_get_params.restype = I
+    lib.feast_mlp_predict.argtypes = [P, P, I, P]
+    lib.feast_mlp_predict.restype = I
+    lib.feast_mlp_grad.argtypes = [P, P, P, I, P, P]
+    lib.feast_mlp_grad.restype = I
+    lib.feast_mlp_train.argtypes = [P, P, P, I, P, I, I, ctypes.c_float, P]
+    lib.feast_mlp_train.restype = I
     _lib = lib
     return lib
 
@@ -301,6 +320,15 @@ def feast_solve_shift(h, k, side, R, out_device=False):
     return _finish(X, out_device)
 
 
+def feast_moments(h, V, kmax):
+    """mu_0 .. mu_kmax of the filter from the probe block V (n x S)."""
+    pv, kv = _colmajor(V)
+    S = V.shape[1] if V.ndim == 2 else 1
+    mu = np.zeros(kmax + 1, dtype=np.complex128)
+    _check(load().feast_moments(h.ptr, pv, S, int(kmax), mu.ctypes.data), "feast_moments")
+    return mu
+
+
 def feast_filter(h, Y, Yhat=None, theta=None, out_device=False):
     py, ky = _colmajor(Y)
     pyh, kyh = _colmajor(Yhat)
@@ -347,3 +375,67 @@ def feast_solve(h, Y0, Vrand=None, out_device=False, allow_noconv=True):
     if Xl is not None:
         out["Xl"] = _finish(Xl, out_device)[:, :k]
     return out
+
+
+# ---------------------------------------------------------------- count predictor (m0)
+class MLP:
+    """Owns a feast_mlp* (d_in -> width -> width -> 1).  Features and labels are
+    moved to the GPU as float32 torch tensors before the kernels read them."""
+
+    def __init__(self, d_in, width, max_batch, params, mean, scale, stream=None):
+        import torch
+        self.d_in, self.width, self.max_batch = d_in, width, max_batch
+        self.nparam = int(load().feast_mlp_param_count(d_in, width))
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.nparam
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(scale, dtype=np.float32)
+        self.ptr = ctypes.c_void_p()
+        sp = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check(load().feast_mlp_create(ctypes.byref(self.ptr), d_in, width, max_batch, p.ctypes.data, m.ctypes.data,
+                                       s.ctypes.data, sp), "feast_mlp_create")
+        self._torch = torch
+
+    def _dev(self, a, dtype):
+        t = self._torch
+        if isinstance(a, t.Tensor):
+            return a.to(device="cuda", dtype=dtype).contiguous()
+        return t.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+    def params(self):
+        out = np.zeros(self.nparam, dtype=np.float32)
+        _check(load().feast_mlp_get_params(self.ptr, out.ctypes.data), "feast_mlp_get_params")
+        return out
+
+    def predict(self, X):
+        Xd = self._dev(X, self._torch.float32)
+        B = Xd.shape[0]
+        y = np.zeros(B, dtype=np.float32)
+        _check(load().feast_mlp_predict(self.ptr, Xd.data_ptr(), B, y.ctypes.data), "feast_mlp_predict")
+        return y
+
+    def grad(self, X, y):
+        Xd, yd = self._dev(X, self._torch.float32), self._dev(y, self._torch.float32)
+        loss = ctypes.c_float()
+        g = np.zeros(self.nparam, dtype=np.float32)
+        _check(load().feast_mlp_grad(self.ptr, Xd.data_ptr(), yd.data_ptr(), Xd.shape[0], ctypes.byref(loss),
+                                     g.ctypes.data), "feast_mlp_grad")
+        return loss.value, g
+
+    def train(self, X, y, batches, lr):
+        """batches: (steps, B) int32 row indices; returns the last mini-batch loss."""
+        Xd, yd = self._dev(X, self._torch.float32), self._dev(y, self._torch.float32)
+        bd = self._dev(np.asarray(batches, dtype=np.int32), self._torch.int32)
+        steps, B = bd.shape
+        loss = ctypes.c_float()
+        _check(load().feast_mlp_train(self.ptr, Xd.data_ptr(), yd.data_ptr(), Xd.shape[0], bd.data_ptr(), steps, B,
+                                      float(lr), ctypes.byref(loss)), "feast_mlp_train")
+        return loss.value
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                load().feast_mlp_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass

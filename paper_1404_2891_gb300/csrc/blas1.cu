@@ -169,6 +169,30 @@ __global__ void k_check_finite(const double2* X, size_t count, unsigned* flags) 
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, (unsigned)DEVFLAG_NONFINITE);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_probe_dots(const double2* V, const cplx<T>* X, int n, int S, double2* d) {
+  const size_t total = (size_t)n * S;
+  const cplx<T>* Xb = X + (size_t)blockIdx.x * total;
+  double2 acc = make_double2(0.0, 0.0);
+  for (size_t e = threadIdx.x; e < total; e += 256) acc = cadd<double>(acc, cmulc<double>(V[e], cconv<double, T>(Xb[e])));
+  acc = block_csum256(acc);
+  if (threadIdx.x == 0) d[blockIdx.x] = acc;
+}
+
+__global__ void k_moments_combine(const double2* d, const double2* z, const double2* w, double2 c, double R, int q,
+                                  int kmax, int S, double2* mu) {
+  const int k = threadIdx.x;
+  if (k > kmax) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = 0; b < q; ++b) {
+    const double2 t = cscale<double>(csub<double>(z[b], c), 1.0 / R);
+    double2 tk = make_double2(1.0, 0.0);
+    for (int e = 0; e < k; ++e) tk = cmul<double>(tk, t);
+    acc = cadd<double>(acc, cmul<double>(cmul<double>(w[b], tk), d[b]));
+  }
+  mu[k] = cscale<double>(acc, 1.0 / S);
+}
+
 unsigned grid_for(size_t total) {
   size_t g = (total + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -251,6 +275,22 @@ cudaError_t gather_columns(const double2* src, const int* idx, int k, int n, int
 cudaError_t normalize_vector(double2* x, int n, double* nrm, cudaStream_t s) {
   feast_count_launch();
   k_normalize_vec<<<1, 256, 0, s>>>(x, n, nrm);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t probe_dots(const double2* V, const cplx<T>* X, int n, int S, int q, double2* d, cudaStream_t s) {
+  feast_count_launch();
+  k_probe_dots<T><<<q, 256, 0, s>>>(V, X, n, S, d);
+  return cudaGetLastError();
+}
+template cudaError_t probe_dots<double>(const double2*, const double2*, int, int, int, double2*, cudaStream_t);
+template cudaError_t probe_dots<float>(const double2*, const float2*, int, int, int, double2*, cudaStream_t);
+
+cudaError_t moments_combine(const double2* d, const double2* z, const double2* w, double2 c, double R, int q,
+                            int kmax, int S, double2* mu, cudaStream_t s) {
+  feast_count_launch();
+  k_moments_combine<<<1, 32, 0, s>>>(d, z, w, c, R, q, kmax, S, mu);
   return cudaGetLastError();
 }
 

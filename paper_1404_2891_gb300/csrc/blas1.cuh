@@ -45,5 +45,14 @@ cudaError_t gather_columns(const double2* src, const int* idx, int k, int n, int
 // x <- x / ||x||, *nrm = ||x|| (single vector of length n)
 cudaError_t normalize_vector(double2* x, int n, double* nrm, cudaStream_t s);
 
+// d[b] = sum_{i,s} conj(V[i,s]) X_b[i,s] for each of the q solution blocks X_b (n x S),
+// summed in a fixed order (one block per shift).
+template <typename T>
+cudaError_t probe_dots(const double2* V, const cplx<T>* X, int n, int S, int q, double2* d, cudaStream_t s);
+
+// mu[k] = (1/S) sum_b w[b] ((z[b] - c)/R)^k d[b], k = 0..kmax
+cudaError_t moments_combine(const double2* d, const double2* z, const double2* w, double2 c, double R, int q,
+                            int kmax, int S, double2* mu, cudaStream_t s);
+
 // flags |= NONFINITE if any entry of X (count complex values) is NaN or Inf
 cudaError_t check_finite(const double2* X, size_t count, unsigned* flags, cudaStream_t s);

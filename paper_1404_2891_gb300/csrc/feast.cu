@@ -151,7 +151,7 @@ struct feast_handle {
   feast_status factor_status = FEAST_OK;
   int nb = 64, nbs = 64;
   // device data
-  double2 *A = nullptr, *B = nullptr, *dz = nullptr;
+  double2 *A = nullptr, *B = nullptr, *dz = nullptr, *dw = nullptr, *dmu = nullptr;
   void* S = nullptr;
   int32_t *piv = nullptr, *perm = nullptr, *pinv = nullptr;
   int* info = nullptr;
@@ -352,7 +352,7 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
 }
 
 // Host-side coefficients.  Plain form: coef_k = sigma_k.  Residual form for
-// column i (Ritz value theta_i not within 5 % of R of any node):
+// column i (Ritz value theta_i not on a node):
 //   S_k^{-1} B x = x / (phi_k - theta) + S_k^{-1} (A x - theta B x) / (phi_k - theta)
 // so coef_k,i = sigma_k / (phi_k - theta_i) and c0_i = sum_k coef_k,i = rho(theta_i).
 feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* use_out) {
@@ -364,7 +364,11 @@ feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* us
     if (theta && std::isfinite(theta[i].real()) && std::isfinite(theta[i].imag())) {
       double dmin = 1e300;
       for (int k = 0; k < q; ++k) dmin = std::min(dmin, std::abs(h->z[k] - theta[i]));
-      u = dmin >= 0.05 * h->R;
+      // The identity holds for every theta != phi_k; for a converged pair the
+      // initial iterate x / (phi_k - theta) is already close to the solution, so
+      // a Ritz value next to a node brings no cancellation.  Only a value on top
+      // of a node (division by ~0) takes the plain right-hand side.
+      u = dmin >= 1e-10 * h->R;
     }
     use[i] = u;
     zc acc = 0.0;
@@ -625,6 +629,8 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->A, nn * sizeof(double2));
   if (h->hasB) AL(h->B, nn * sizeof(double2));
   AL(h->dz, h->q * sizeof(double2));
+  AL(h->dw, h->q * sizeof(double2));
+  AL(h->dmu, (size_t)(h->q + 64) * sizeof(double2));
   AL(h->S, nn * h->q * esz);
   AL(h->piv, (size_t)h->q * n * sizeof(int32_t));
   AL(h->perm, (size_t)h->q * n * sizeof(int32_t));
@@ -673,6 +679,9 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   std::vector<double2> zd(h->q);
   for (int k = 0; k < h->q; ++k) zd[k] = d2(h->z[k]);
   if ((e = cudaMemcpyAsync(h->dz, zd.data(), h->q * sizeof(double2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
+  std::vector<double2> wd(h->q);
+  for (int k = 0; k < h->q; ++k) wd[k] = d2(h->w[k]);
+  if ((e = cudaMemcpyAsync(h->dw, wd.data(), h->q * sizeof(double2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemsetAsync(h->flags, 0, 64, h->st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpy2DAsync(h->A, n * sizeof(double2), A, lda * sizeof(double2), n * sizeof(double2), n,
                              cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
@@ -784,6 +793,42 @@ feast_status feast_solve_shift(feast_handle* h, int k, int side, const feast_z* 
   if ((s = copy_out(h, X, h->tmp, cnt)) != FEAST_OK) return s;
   CK(cudaStreamSynchronize(h->st));
   return FEAST_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+feast_status moments_impl(feast_handle* h, const double2* BV, int S, int kmax) {
+  LuBatch<T> lu = lu_view<T>(h);
+  cplx<T>* Xs = reinterpret_cast<cplx<T>*>(h->Xs);
+  CK(rows_gather<T>(lu, BV, Xs, S, true, h->st));
+  CK(lu_solve_batched<T>(lu, 0, Xs, S, h->nbs, h->st));
+  CK(probe_dots<T>(h->Y, Xs, (int)h->n, S, h->q, h->dmu + 64, h->st));
+  CK(moments_combine(h->dmu + 64, h->dz, h->dw, d2(h->center), h->R, h->q, kmax, S, h->dmu, h->st));
+  return FEAST_OK;
+}
+}  // namespace
+
+extern "C" {
+
+feast_status feast_moments(feast_handle* h, const feast_z* V, int S, int kmax, feast_z* mu) {
+  if (!h || !V || !mu || S < 1 || S > h->m0 || kmax < 0 || kmax > 31) return FEAST_ERR_ARG;
+  feast_status s = ensure_factored(h);
+  if (s != FEAST_OK) return s;
+  const int n = (int)h->n;
+  const size_t cnt = (size_t)n * S;
+  if ((s = copy_in(h, h->Y, V, cnt)) != FEAST_OK) return s;
+  const double2* BV = h->Y;
+  if (h->hasB) {
+    CK(zg(h, OP_N, OP_N, n, S, n, zc(1.0), h->B, n, h->Y, n, zc(0.0), h->BX, n));
+    BV = h->BX;
+  }
+  s = mixed(h) ? moments_impl<float>(h, BV, S, kmax) : moments_impl<double>(h, BV, S, kmax);
+  if (s != FEAST_OK) return s;
+  CK(cudaMemcpyAsync(mu, h->dmu, (kmax + 1) * sizeof(double2), cudaMemcpyDefault, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return read_flags(h);
 }
 
 feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat, const feast_z* theta, feast_z* Q,

@@ -214,3 +214,20 @@ def test_bifeast_generalized_vs_brute_force(precision):
     assert r.max() <= 1e-10, r.max()
     X, Y = out["X"], out["Xl"]
     assert np.allclose(Y.conj().T @ B @ X, np.eye(len(ref)), atol=1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_moments_match_oracle(precision):
+    from oracle import moments
+    fg = lib()
+    cfg = small_pencil()
+    A, B = cfg["A"], cfg["B"]
+    h = make(fg, cfg, precision, B=B)
+    z, w = fg.feast_get_quadrature(h)
+    rng = np.random.default_rng(17)
+    V = rng.choice([-1.0, 1.0], size=(A.shape[0], 20)).astype(np.complex128)
+    mu = fg.feast_moments(h, V, 7)
+    c = cfg["contour"]
+    ref = moments.moments(A, B, z, w, c["c"], c["R"], V, 7)
+    tol = 1e-11 if precision == "fp64" else MIXED_TOL
+    assert np.linalg.norm(mu - ref) <= tol * np.linalg.norm(ref), (mu, ref)

@@ -94,3 +94,46 @@ def gaussian_pencil(n=4096, seed=2, m0=128, K=16, zero_block=None, b_eps=0.05):
 def random_block(n, m, seed):
     """A seeded complex Gaussian n x m block."""
     return cgauss(np.random.default_rng(seed), n, m)
+
+
+def parametric_family(n=256, seed=5, n_train=2000, n_test=200):
+    """A(p) = A0 + p A1 with A0, A1 complex Gaussian / sqrt(n), p ~ U[0, 1]
+    (training and held-out draws), circle c = 0.3, r = 0.5, 8 midpoint nodes.
+    By the circular law the spectrum of A(p) fills the disk of radius
+    sqrt(1 + p^2), so about n / (4 (1 + p^2)) eigenvalues lie inside."""
+    rng = np.random.default_rng(seed)
+    A0 = cgauss(rng, n, n) / np.sqrt(n)
+    A1 = cgauss(rng, n, n) / np.sqrt(n)
+    p_train = rng.uniform(0.0, 1.0, n_train)
+    p_test = rng.uniform(0.0, 1.0, n_test)
+    return dict(A0=A0, A1=A1, p_train=p_train, p_test=p_test,
+                contour=dict(c=0.3 + 0j, R=0.5, a=1.0, rule="trap_mid"), N_e=8, seed=seed)
+
+
+def rademacher(n, S, seed):
+    """n x S block of independent +-1 entries (complex128)."""
+    return np.random.default_rng(seed).choice([-1.0, 1.0], size=(n, S)).astype(np.complex128)
+
+
+def mlp_init(d_in, width, seed):
+    """Initial parameters of the count predictor (He-style normal weights, zero
+    biases) in the layout W1, b1, W2, b2, W3, b3."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((width, d_in)) * np.sqrt(2.0 / d_in)
+    W2 = rng.standard_normal((width, width)) * np.sqrt(2.0 / width)
+    W3 = rng.standard_normal((1, width)) * np.sqrt(1.0 / width)
+    return np.concatenate([W1.ravel(), np.zeros(width), W2.ravel(), np.zeros(width), W3.ravel(),
+                           np.zeros(1)]).astype(np.float32)
+
+
+def batch_schedule(n_rows, batch, steps, seed):
+    """Mini-batch row indices for `steps` Adam steps (epochs of shuffled rows)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < steps:
+        perm = rng.permutation(n_rows)
+        for k in range(0, n_rows - batch + 1, batch):
+            out.append(perm[k:k + batch])
+            if len(out) == steps:
+                break
+    return np.array(out, dtype=np.int32)
