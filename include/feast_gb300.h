@@ -101,6 +101,10 @@ typedef struct {
                         (Sec. 5, default 1e-4)                                 */
   int panel;         /* LU panel width (0 = library default)                   */
   int timing;        /* nonzero: record per-phase CUDA-event times in stats    */
+  int symmetric;     /* nonzero: A = A^T and B = B^T (complex symmetric pencil).
+                        Then (phi B - A)^{-H} conj(V) = conj((phi B - A)^{-1} V),
+                        so Bi-FEAST takes the left block as conj(right block):
+                        no left solves, Qhat = conj(Q), Vk = conj(Uk).        */
 } feast_options;
 
 typedef struct {

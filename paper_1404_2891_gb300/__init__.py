@@ -52,7 +52,7 @@ class feast_contour(ctypes.Structure):
 class feast_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("cand_tol", ctypes.c_double), ("panel", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("symmetric", ctypes.c_int)]
 
 
 class feast_stats(ctypes.Structure):
@@ -226,12 +226,14 @@ def make_contour(center=0.0, R=1.0, aspect=1.0, rule="trap_mid", N_e=8, nodes=No
     return c
 
 
-def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False):
+def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False,
+                 symmetric=False):
     o = feast_options()
     load().feast_default_options(ctypes.byref(o))
     o.algo = ALGOS[algo]
     o.precision = PRECISIONS[precision]
     o.tol, o.max_iter, o.cand_tol, o.panel, o.timing = float(tol), int(max_iter), float(cand_tol), int(panel), int(timing)
+    o.symmetric = int(symmetric)
     return o
 
 

@@ -135,6 +135,11 @@ __global__ void k_conj_transpose(const double2* src, int n, int m, double2* dst)
   }
 }
 
+__global__ void k_conj_copy(const double2* src, double2* dst, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = cconj<double>(src[e]);
+}
+
 __global__ void k_identity(double2* M, int m) {
   const size_t total = (size_t)m * m;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -257,6 +262,12 @@ cudaError_t column_dots(const double2* X, const double2* Y, int n, int m, double
 cudaError_t conj_transpose(const double2* src, int n, int m, double2* dst, cudaStream_t s) {
   feast_count_launch();
   k_conj_transpose<<<grid_for((size_t)n * m), 256, 0, s>>>(src, n, m, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t conj_copy(const double2* src, double2* dst, size_t count, cudaStream_t s) {
+  feast_count_launch();
+  k_conj_copy<<<grid_for(count), 256, 0, s>>>(src, dst, count);
   return cudaGetLastError();
 }
 

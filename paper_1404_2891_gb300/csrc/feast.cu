@@ -341,7 +341,11 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   CK(rows_gather<T>(lu, R, Xs, m, true, h->st));
   CK(lu_solve_batched<T>(lu, 0, Xs, m, h->nbs, h->st));
   CK(accumulate<T>(Xs, h->q, n, m, h->coef, use_c0 ? h->c0 : nullptr, use_c0 ? Yc0 : nullptr, nullptr, Qout, h->st));
-  if (Rh) {
+  if (Rh && h->opt.symmetric) {
+    // complex symmetric pencil: (phi B - A)^{-H} conj(V) = conj((phi B - A)^{-1} V),
+    // and the left inputs are the conjugates of the right ones
+    CK(conj_copy(Qout, Qhout, (size_t)n * m, h->st));
+  } else if (Rh) {
     cplx<T>* Xsh = reinterpret_cast<cplx<T>*>(h->Xsh);
     CK(rows_gather<T>(lu, Rh, Xsh, m, false, h->st));
     CK(lu_solve_batched<T>(lu, 1, Xsh, m, h->nbs, h->st));
@@ -468,11 +472,20 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   CK(scale_columns_inv(h->X, h->AX, h->hasB ? h->BX : nullptr, n, m, h->xn, nullptr, h->st));
   CK(residual_columns(h->AX, BXp, h->lam, 0, n, m, h->E, h->res, nullptr, h->st));
   if (bi) {
-    CK(zg(h, OP_C, OP_N, n, m, n, one, h->A, n, h->Qho, n, zero, h->AhQ, n));
     const double2* BhQp = h->Qho;
-    if (h->hasB) {
-      CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Qho, n, zero, h->BhQ, n));
-      BhQp = h->BhQ;
+    if (h->opt.symmetric) {
+      // Qho = conj(Qo) and A = A^T: A^H conj(Qo) = conj(A Qo), likewise for B
+      CK(conj_copy(h->AQ, h->AhQ, (size_t)n * m, h->st));
+      if (h->hasB) {
+        CK(conj_copy(h->BQ, h->BhQ, (size_t)n * m, h->st));
+        BhQp = h->BhQ;
+      }
+    } else {
+      CK(zg(h, OP_C, OP_N, n, m, n, one, h->A, n, h->Qho, n, zero, h->AhQ, n));
+      if (h->hasB) {
+        CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Qho, n, zero, h->BhQ, n));
+        BhQp = h->BhQ;
+      }
     }
     CK(cudaMemcpyAsync(h->LUW, h->W, sm, cudaMemcpyDeviceToDevice, h->st));
     CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
@@ -919,7 +932,10 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
   st.t_factor_ms = h->t_factor;
   if (s != FEAST_OK) return s;
   if ((s = copy_in(h, h->Y, Y0, cnt)) != FEAST_OK) return s;
-  if (bi) {
+  if (bi && h->opt.symmetric) {
+    // complex symmetric pencil: the left block is the conjugate of the right one
+    CK(conj_copy(h->Y, h->Yh, cnt, h->st));
+  } else if (bi) {
     // Bi-FEAST step 2: V0 = Vr (Vr^H B Y0)^{-H}
     if ((s = copy_in(h, h->Yh, Vrand ? Vrand : Y0, cnt)) != FEAST_OK) return s;
     const double2* BY0 = h->Y;

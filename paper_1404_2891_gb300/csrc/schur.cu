@@ -322,8 +322,12 @@ __global__ void k_refine_step(const double2* E, double2* D, double2* lam, int m)
       D[idx] = make_double2(1.0, 0.0);
       lam[i] = E[idx];
     } else {
+      // first-order correction only where it is small: pairs inside a cluster
+      // (|E_ij| comparable to the gap, e.g. a multiple eigenvalue) keep their
+      // common invariant subspace as it is
       const double2 gap = csub<double>(E[j + (size_t)j * m], E[i + (size_t)i * m]);
-      D[idx] = cabs1<double>(gap) > gap_min ? cdiv<double>(E[idx], gap) : make_double2(0.0, 0.0);
+      const bool sep = cabs1<double>(gap) > gap_min && cabs1<double>(gap) > 10.0 * cabs1<double>(E[idx]);
+      D[idx] = sep ? cdiv<double>(E[idx], gap) : make_double2(0.0, 0.0);
     }
   }
 }

@@ -91,6 +91,43 @@ def gaussian_pencil(n=4096, seed=2, m0=128, K=16, zero_block=None, b_eps=0.05):
                 N_e=K, m0=m0, seed=seed)
 
 
+def pml_laplacian(nx=90, layer=10, sigma_max=50.0, m_low=60):
+    """Complex symmetric A = h^-2 (5-point Dirichlet Laplacian on an nx x nx grid,
+    h = 1/(nx+1)) - i sigma, with the absorbing profile
+    sigma(i, j) = sigma_max ((d(i)/L)^2 + (d(j)/L)^2), d(i) = max(0, L - i, i - (nx-1-L)),
+    stored dense; B = I.  The circle is placed from the closed-form spectrum of
+    the Laplacian without absorption (lambda_jk = h^-2 (4 - 2 cos(j pi h) - 2 cos(k pi h))):
+    it spans the m_low lowest levels, its rightmost point half way to the next
+    distinct level, centred on the real axis."""
+    n = nx * nx
+    h = 1.0 / (nx + 1)
+    idx = np.arange(nx)
+    d = np.maximum(0, np.maximum(layer - idx, idx - (nx - 1 - layer))) / float(layer)
+    sig = sigma_max * (d[:, None] ** 2 + d[None, :] ** 2)  # [i, j]
+    A = np.zeros((n, n), dtype=np.complex128)
+    for j in range(nx):
+        for i in range(nx):
+            r = i + nx * j
+            A[r, r] = 4.0 / h ** 2 - 1j * sig[i, j]
+            if i > 0:
+                A[r, r - 1] = -1.0 / h ** 2
+            if i < nx - 1:
+                A[r, r + 1] = -1.0 / h ** 2
+            if j > 0:
+                A[r, r - nx] = -1.0 / h ** 2
+            if j < nx - 1:
+                A[r, r + nx] = -1.0 / h ** 2
+    k = np.arange(1, nx + 1)
+    lev = np.sort((4.0 - 2.0 * np.cos(k[:, None] * np.pi * h) - 2.0 * np.cos(k[None, :] * np.pi * h)).ravel()) / h ** 2
+    top = lev[m_low - 1]
+    nxt = lev[lev > top * (1 + 1e-12)][0]
+    right = 0.5 * (top + nxt)
+    left = lev[0] - (right - lev[0]) * 0.05
+    c = 0.5 * (left + right)
+    return dict(A=A, B=None, levels=lev, contour=dict(c=complex(c), R=0.5 * (right - left), a=1.0, rule="trap_mid"),
+                N_e=16, m0=96, sigma=sig)
+
+
 def random_block(n, m, seed):
     """A seeded complex Gaussian n x m block."""
     return cgauss(np.random.default_rng(seed), n, m)
