@@ -268,6 +268,81 @@ feast_status feast_mlp_train(feast_mlp* net, const float* X, const float* y, int
 feast_status feast_norm2_estimate_static(const feast_z* A, int64_t n, int64_t lda, int iters,
                                          double* norm, void* stream);
 
+/* ---- Batched path: many independent standard pencils (B = I) at once.
+ * Sec. 6 notes that FEAST's systems are independent across quadrature nodes
+ * and across search intervals; the batched path uses that independence
+ * across pencils too.  Every pencil p has its own order n[p], subspace size
+ * m0[p] and contour, and the pencils are iterated together with Algorithm
+ * R-FEAST (Q^ = Q) in mixed precision.
+ *
+ * On the device, ONE persistent launch factors all sum_p q_p shifted matrices
+ * z I - A_p with partial pivoting (complex64, padded to a multiple of 64) and
+ * solves them for their pencil's right-hand sides.  A device task queue in an
+ * order planned on the host drives it: critical path first, largest pencils
+ * first.  The Rayleigh-Ritz steps run as grouped kernels (one launch per step
+ * for all pencils), and the steady iterations replay one CUDA graph.
+ *
+ *   n        : count orders, 1 <= n[p] <= 4096.
+ *   A        : count pointers to n[p] x n[p] column-major matrices (host or
+ *              device), leading dimensions lda[p] >= n[p] (lda NULL: lda = n);
+ *              copied.
+ *   contours : count contours (any rule; q_p <= 256 nodes).
+ *   m0       : count subspace sizes, 1 <= m0[p] <= min(n[p], 160).
+ *   opts     : algo must be FEAST_ALGO_R and precision FEAST_PREC_MIXED
+ *              (FEAST_ERR_ARG otherwise); tol, max_iter, cand_tol and timing
+ *              as for a handle.
+ * The batch owns all device memory until feast_batch_destroy. */
+typedef struct feast_batch feast_batch;
+
+typedef struct {
+  int iters;                /* lockstep iterations                                  */
+  int converged;            /* pencils that met the Sec. 5 test                     */
+  int tasks_factor;         /* tasks of the persistent factorisation launch         */
+  int grid;                 /* CTAs of the persistent launch                        */
+  int graph;                /* 1 if the steady iterations replayed a CUDA graph     */
+  double plan_makespan_us;  /* makespan of the host schedule's cost model           */
+  double t_factor_ms;       /* first launch (factorisations + first solves), timing */
+  double t_iter_ms[64];     /* wall time of each iteration, timing option           */
+} feast_batch_stats;
+
+feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, const feast_z* const* A,
+                                const int64_t* lda, const feast_contour* contours, const int* m0,
+                                const feast_options* opts, void* stream);
+void feast_batch_destroy(feast_batch* b);
+/* Factor every shifted matrix (one persistent launch of the factorisation
+ * tasks only).  A later call forms and factors them again.
+ * FEAST_ERR_SINGULAR_SHIFT if some pivot is exactly zero. */
+feast_status feast_batch_factor(feast_batch* b);
+/* Q[p] = sum_k w_k (z_k I - A_p)^{-1} Y[p] for every pencil (Eq. Rasp with
+ * B = I); Y[p], Q[p] are n[p] x m0[p] (host or device).  Factors first if
+ * needed, in the same launch as the solves. */
+feast_status feast_batch_filter(feast_batch* b, const feast_z* const* Y, feast_z* const* Q);
+/* Iterate every pencil from its starting block Y0[p] (n[p] x m0[p]) until all
+ * converge or max_iter.  Per pencil: lambda[p] (m0[p] values, the first
+ * m_found[p] valid, sorted by (Re, Im)), X[p] (n[p] x m0[p], unit columns;
+ * nullable), res[p] (normalised residuals, nullable).  FEAST_ERR_NOCONV if
+ * some pencil did not converge (its outputs are those of the last iteration). */
+feast_status feast_batch_solve(feast_batch* b, const feast_z* const* Y0, feast_z* const* lambda, feast_z* const* X,
+                               double* const* res, int* m_found, feast_batch_stats* stats);
+/* Factor of shift k of pencil p after factorisation: LU (n x n, host or
+ * device; L unit lower below the diagonal, U on and above), and the row
+ * permutation perm (n entries) with (P S)[r, :] = S[perm[r], :]. */
+feast_status feast_batch_get_factor(feast_batch* b, int pencil, int shift, feast_z* LU, int32_t* perm);
+/* Shape of the batch: pencils, shifted matrices, CTAs of the persistent
+ * launch, tasks of the factorisation, the schedule's model makespan (us), and
+ * the algorithmic LU flops sum_i 8/3 n_i^3. Any output may be NULL. */
+feast_status feast_batch_info(const feast_batch* b, int* count, int* nmat, int* grid, int* tasks_factor,
+                              double* plan_makespan_us, double* lu_flops);
+/* The host scheduler alone (no GPU): the task order of the persistent launch
+ * for nmat matrices with nb[i] = ceil(n_i / 64) block columns and m[i]
+ * right-hand sides on `workers` CTAs, with factorisation tasks (with_lu) and/or
+ * solve tasks (with_solve).  tasks receives 4 ints per task {kind, matrix, k, j}
+ * with kind 0 = panel k, 1 = update of block column j by step k,
+ * 2 = interchange fix-up of block column j, 3 = solve of 32-column chunk j.
+ * capacity is in tasks; tasks may be NULL to query ntasks. */
+feast_status feast_batch_plan(int nmat, const int* nb, const int* m, int with_lu, int with_solve, int workers,
+                              int* tasks, int capacity, int* ntasks, double* makespan_us);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; no paper counterpart). */
 uint64_t feast_kernel_launches(void);

@@ -78,7 +78,15 @@ SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_stat
            "feast_filter", "feast_rayleigh_ritz", "feast_solve", "feast_kernel_launches",
            "feast_get_stats", "feast_norm2_estimate_static", "feast_moments",
            "feast_mlp_param_count", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_get_params",
-           "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train")
+           "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train",
+           "feast_batch_create", "feast_batch_destroy", "feast_batch_factor", "feast_batch_filter",
+           "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_plan")
+
+
+class feast_batch_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("tasks_factor", ctypes.c_int),
+                ("grid", ctypes.c_int), ("graph", ctypes.c_int), ("plan_makespan_us", ctypes.c_double),
+                ("t_factor_ms", ctypes.c_double), ("t_iter_ms", ctypes.c_double * 64)]
 
 
 def load(path=LIB_PATH):
@@ -137,6 +145,22 @@ def load(path=LIB_PATH):
     lib.feast_mlp_grad.restype = I
     lib.feast_mlp_train.argtypes = [P, P, P, I, P, I, I, ctypes.c_float, P]
     lib.feast_mlp_train.restype = I
+    lib.feast_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P, P, ctypes.POINTER(feast_options), P]
+    lib.feast_batch_create.restype = I
+    lib.feast_batch_destroy.argtypes = [P]
+    lib.feast_batch_destroy.restype = None
+    lib.feast_batch_factor.argtypes = [P]
+    lib.feast_batch_factor.restype = I
+    lib.feast_batch_filter.argtypes = [P, P, P]
+    lib.feast_batch_filter.restype = I
+    lib.feast_batch_solve.argtypes = [P, P, P, P, P, P, ctypes.POINTER(feast_batch_stats)]
+    lib.feast_batch_solve.restype = I
+    lib.feast_batch_get_factor.argtypes = [P, I, I, P, P]
+    lib.feast_batch_get_factor.restype = I
+    lib.feast_batch_info.argtypes = [P, P, P, P, P, P, P]
+    lib.feast_batch_info.restype = I
+    lib.feast_batch_plan.argtypes = [I, P, P, I, I, I, P, I, P, P]
+    lib.feast_batch_plan.restype = I
     _lib = lib
     return lib
 
@@ -377,6 +401,121 @@ def feast_solve(h, Y0, Vrand=None, out_device=False, allow_noconv=True):
     if Xl is not None:
         out["Xl"] = _finish(Xl, out_device)[:, :k]
     return out
+
+
+# ---------------------------------------------------------------- batched path
+class Batch:
+    """Owns a feast_batch* (many standard pencils, R-FEAST, mixed precision)."""
+
+    def __init__(self, ptr, n, m0, keep):
+        self.ptr, self.n, self.m0, self._keep = ptr, list(n), list(m0), keep
+
+    def __del__(self):
+        try:
+            feast_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(p) if p else None for p in ptrs])
+    return arr
+
+
+def feast_batch_create(As, contours, m0, options, stream=None):
+    """As: list of n_p x n_p complex128 matrices (numpy or torch CUDA); contours:
+    list of make_contour results; m0: list of subspace sizes; options from
+    make_options(algo="R", precision="mixed", ...)."""
+    lib = load()
+    count = len(As)
+    keep = [_colmajor(A) for A in As]
+    n = np.array([A.shape[0] for A in As], dtype=np.int64)
+    lda = n.copy()
+    ptrs = _ptr_array([k[0] for k in keep])
+    cons = (feast_contour * count)(*contours)
+    m = np.array(m0, dtype=np.int32)
+    b = ctypes.c_void_p()
+    sp = None
+    if stream is not None:
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.feast_batch_create(ctypes.byref(b), count, n.ctypes.data, ptrs, lda.ctypes.data, cons, m.ctypes.data,
+                                  ctypes.byref(options), sp), "feast_batch_create")
+    return Batch(b, n.tolist(), m.tolist(), (keep, contours))
+
+
+def feast_batch_destroy(b):
+    if b is not None and b.ptr:
+        load().feast_batch_destroy(b.ptr)
+        b.ptr = None
+
+
+def feast_batch_factor(b, allow_singular=False):
+    allow = (FEAST_ERR_SINGULAR_SHIFT,) if allow_singular else ()
+    return _check(load().feast_batch_factor(b.ptr), "feast_batch_factor", allow)
+
+
+def feast_batch_filter(b, Ys):
+    """Plain filter Q_p = sum_k w_k (z_k I - A_p)^{-1} Y_p for every pencil."""
+    keep = [_colmajor(Y) for Y in Ys]
+    outs = [np.zeros((n, m), dtype=np.complex128, order="F") for n, m in zip(b.n, b.m0)]
+    _check(load().feast_batch_filter(b.ptr, _ptr_array([k[0] for k in keep]),
+                                     _ptr_array([o.ctypes.data for o in outs])), "feast_batch_filter")
+    return outs
+
+
+def feast_batch_solve(b, Y0s, allow_noconv=True):
+    keep = [_colmajor(Y) for Y in Y0s]
+    lams = [np.zeros(m, dtype=np.complex128) for m in b.m0]
+    ress = [np.zeros(m, dtype=np.float64) for m in b.m0]
+    Xs = [np.zeros((n, m), dtype=np.complex128, order="F") for n, m in zip(b.n, b.m0)]
+    mf = np.zeros(len(b.n), dtype=np.int32)
+    st = feast_batch_stats()
+    s = load().feast_batch_solve(b.ptr, _ptr_array([k[0] for k in keep]), _ptr_array([l.ctypes.data for l in lams]),
+                                 _ptr_array([x.ctypes.data for x in Xs]), _ptr_array([r.ctypes.data for r in ress]),
+                                 mf.ctypes.data, ctypes.byref(st))
+    _check(s, "feast_batch_solve", (FEAST_ERR_NOCONV,) if allow_noconv else ())
+    out = []
+    for p in range(len(b.n)):
+        k = int(mf[p])
+        out.append(dict(m_found=k, lam=lams[p][:k], res=ress[p][:k], X=Xs[p][:, :k]))
+    stats = dict(status=s, converged=st.converged, iters=st.iters, tasks_factor=st.tasks_factor, grid=st.grid,
+                 graph=st.graph, plan_makespan_us=st.plan_makespan_us, t_factor_ms=st.t_factor_ms,
+                 t_iter_ms=list(st.t_iter_ms[:st.iters]))
+    return out, stats
+
+
+def feast_batch_get_factor(b, p, k):
+    n = b.n[p]
+    LU = np.zeros((n, n), dtype=np.complex128, order="F")
+    perm = np.zeros(n, dtype=np.int32)
+    _check(load().feast_batch_get_factor(b.ptr, int(p), int(k), LU.ctypes.data, perm.ctypes.data),
+           "feast_batch_get_factor")
+    return LU, perm
+
+
+def feast_batch_info(b):
+    c, nm, g, t = (ctypes.c_int() for _ in range(4))
+    mk, fl = ctypes.c_double(), ctypes.c_double()
+    _check(load().feast_batch_info(b.ptr, ctypes.byref(c), ctypes.byref(nm), ctypes.byref(g), ctypes.byref(t),
+                                   ctypes.byref(mk), ctypes.byref(fl)), "feast_batch_info")
+    return dict(count=c.value, nmat=nm.value, grid=g.value, tasks_factor=t.value, plan_makespan_us=mk.value,
+                lu_flops=fl.value)
+
+
+def feast_batch_plan(nb, m, with_lu=True, with_solve=True, workers=152):
+    """The host scheduler alone: (tasks as an (ntasks, 4) int array, model makespan in us)."""
+    lib = load()
+    nbv = np.ascontiguousarray(nb, dtype=np.int32)
+    mv = np.ascontiguousarray(m, dtype=np.int32)
+    nt = ctypes.c_int()
+    mk = ctypes.c_double()
+    _check(lib.feast_batch_plan(len(nbv), nbv.ctypes.data, mv.ctypes.data, int(with_lu), int(with_solve),
+                                int(workers), None, 0, ctypes.byref(nt), ctypes.byref(mk)), "feast_batch_plan")
+    out = np.zeros((nt.value, 4), dtype=np.int32)
+    _check(lib.feast_batch_plan(len(nbv), nbv.ctypes.data, mv.ctypes.data, int(with_lu), int(with_solve),
+                                int(workers), out.ctypes.data, nt.value, ctypes.byref(nt), ctypes.byref(mk)),
+           "feast_batch_plan")
+    return out, mk.value
 
 
 # ---------------------------------------------------------------- count predictor (m0)

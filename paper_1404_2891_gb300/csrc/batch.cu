@@ -1,0 +1,999 @@
+// The batched path of include/feast_gb300.h: many independent standard
+// pencils (B = I), each with its own order, subspace size and contour,
+// iterated together with Algorithm R-FEAST in mixed precision.
+//
+// Per iteration, for every active pencil at once:
+//   1. right-hand sides: Y (first iteration) or the residual form
+//      select(E, X) with its coefficients (one grouped kernel);
+//   2. ONE persistent launch factors every shifted matrix (first call only)
+//      and solves every (matrix, 32-column chunk) -- batch_lu.cu;
+//   3. Q = c0 .* X + sum_k coef_k .* S_k^{-1} R (grouped accumulation);
+//   4. Rayleigh-Ritz as grouped kernels: CGS2 (one cooperative launch for all
+//      blocks), the FP64 projections on DMMA, the reduced problem (FP32 Schur
+//      + two FP64 refinement sweeps), Ritz vectors and residuals.
+// Steps 1-4 of the steady iterations are captured once into a CUDA graph and
+// replayed; the host reads ~m0 eigenvalues and residuals per pencil per
+// iteration and takes the Sec. 5 decisions per pencil.  Converged pencils are
+// switched off through a device flag array, so the graph never changes.
+//
+// The task order of the persistent launch comes from a list-scheduling
+// simulation on the host (plan_order): each task's priority is its bottom
+// level (longest cost path to the end of its matrix's DAG), so the largest
+// pencils start first and their panels run ahead of their updates.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <queue>
+#include <vector>
+
+#include "../../include/feast_gb300.h"
+#include "batch.cuh"
+#include "blas1.cuh"
+#include "gemm.cuh"
+#include "norm2.cuh"
+#include "small.cuh"
+
+using zc = std::complex<double>;
+
+bool feast_quadrature_host(const feast_contour& c, std::vector<zc>& z, std::vector<zc>& w);
+
+namespace {
+
+inline double2 d2(zc v) { return make_double2(v.real(), v.imag()); }
+inline zc zz(double2 v) { return zc(v.x, v.y); }
+
+// ---------------------------------------------------------------- scheduling
+// Model costs in microseconds of one SM (only their ratios matter).
+double cost_panel(int rows) { return 8.0 + 0.06 * rows; }
+double cost_update(int tiles) { return 3.0 + 4.5 * tiles; }
+double cost_lswap(int panels) { return 1.0 + 1.0 * panels; }
+double cost_solve(int nb, int w) { return 6.0 * nb + 2.2 * nb * (nb - 1) * (w / 32.0); }
+
+struct Plan {
+  std::vector<int> nb, m;
+  bool lu = true, solve = true;
+  std::vector<long long> base;
+  long long count_of(int i) const {
+    const long long n = nb[i];
+    return (lu ? n + n * (n - 1) / 2 + (n - 1) : 0) + (solve ? (m[i] + BATCH_SOLVE_W - 1) / BATCH_SOLVE_W : 0);
+  }
+  long long P(int i, int k) const { return base[i] + k; }
+  long long U(int i, int k, int j) const {
+    const long long n = nb[i];
+    return base[i] + n + (long long)k * (2 * n - k - 1) / 2 + (j - k - 1);
+  }
+  long long L(int i, int j) const {
+    const long long n = nb[i];
+    return base[i] + n + n * (n - 1) / 2 + j;
+  }
+  long long S(int i, int c) const {
+    const long long n = nb[i];
+    return base[i] + (lu ? n + n * (n - 1) / 2 + (n - 1) : 0) + c;
+  }
+  int nch(int i) const { return solve ? (m[i] + BATCH_SOLVE_W - 1) / BATCH_SOLVE_W : 0; }
+};
+
+// Topological task order by list scheduling on `workers` identical workers.
+std::vector<int4> plan_order(const std::vector<int>& nbv, const std::vector<int>& mv, bool lu, bool solve,
+                             int workers, double* makespan) {
+  Plan pl;
+  pl.nb = nbv;
+  pl.m = mv;
+  pl.lu = lu;
+  pl.solve = solve;
+  const int nm = (int)nbv.size();
+  pl.base.assign(nm + 1, 0);
+  for (int i = 0; i < nm; ++i) pl.base[i + 1] = pl.base[i] + pl.count_of(i);
+  const long long T = pl.base[nm];
+  std::vector<int4> task(T);
+  std::vector<double> cost(T), bl(T);
+  std::vector<int> pend(T, 0);
+  for (int i = 0; i < nm; ++i) {
+    const int nb = nbv[i], ch = pl.nch(i);
+    if (lu) {
+      for (int k = 0; k < nb; ++k) {
+        task[pl.P(i, k)] = make_int4(BT_PANEL, i, k, k);
+        cost[pl.P(i, k)] = cost_panel(BATCH_TILE * (nb - k));
+        pend[pl.P(i, k)] = k > 0 ? 1 : 0;
+        for (int j = k + 1; j < nb; ++j) {
+          task[pl.U(i, k, j)] = make_int4(BT_UPDATE, i, k, j);
+          cost[pl.U(i, k, j)] = cost_update(nb - k - 1);
+          pend[pl.U(i, k, j)] = 1 + (k > 0 ? 1 : 0);
+        }
+      }
+      for (int j = 0; j + 1 < nb; ++j) {
+        task[pl.L(i, j)] = make_int4(BT_LSWAP, i, 0, j);
+        cost[pl.L(i, j)] = cost_lswap(nb - 1 - j);
+        pend[pl.L(i, j)] = 1;
+      }
+    }
+    double maxS = 0.0;
+    for (int c = 0; c < ch; ++c) {
+      const int w = std::min(BATCH_SOLVE_W, mv[i] - BATCH_SOLVE_W * c);
+      task[pl.S(i, c)] = make_int4(BT_SOLVE, i, 0, c);
+      cost[pl.S(i, c)] = cost_solve(nb, w);
+      pend[pl.S(i, c)] = lu ? nb : 0;  // the last panel and the nb - 1 fix-ups
+      bl[pl.S(i, c)] = cost[pl.S(i, c)];
+      maxS = std::max(maxS, bl[pl.S(i, c)]);
+    }
+    if (!lu) continue;
+    double maxL = 0.0;
+    for (int j = 0; j + 1 < nb; ++j) {
+      bl[pl.L(i, j)] = cost[pl.L(i, j)] + maxS;
+      maxL = std::max(maxL, bl[pl.L(i, j)]);
+    }
+    bl[pl.P(i, nb - 1)] = cost[pl.P(i, nb - 1)] + std::max(maxL, maxS);
+    for (int k = nb - 2; k >= 0; --k) {
+      double mx = 0.0;
+      for (int j = k + 1; j < nb; ++j) {
+        const double nxt = j == k + 1 ? bl[pl.P(i, k + 1)] : bl[pl.U(i, k + 1, j)];
+        bl[pl.U(i, k, j)] = cost[pl.U(i, k, j)] + nxt;
+        mx = std::max(mx, bl[pl.U(i, k, j)]);
+      }
+      bl[pl.P(i, k)] = cost[pl.P(i, k)] + mx;
+    }
+  }
+  auto for_succ = [&](long long id, const std::function<void(long long)>& fn) {
+    const int4 t = task[id];
+    const int i = t.y, nb = nbv[i];
+    switch (t.x) {
+      case BT_PANEL:
+        for (int j = t.z + 1; j < nb; ++j) fn(pl.U(i, t.z, j));
+        if (t.z == nb - 1) {
+          for (int j = 0; j + 1 < nb; ++j) fn(pl.L(i, j));
+          for (int c = 0; c < pl.nch(i); ++c) fn(pl.S(i, c));
+        }
+        break;
+      case BT_UPDATE: fn(t.w == t.z + 1 ? pl.P(i, t.z + 1) : pl.U(i, t.z + 1, t.w)); break;
+      case BT_LSWAP:
+        for (int c = 0; c < pl.nch(i); ++c) fn(pl.S(i, c));
+        break;
+      default: break;
+    }
+  };
+  std::priority_queue<std::pair<double, long long>> ready;  // (bottom level, -id)
+  for (long long id = 0; id < T; ++id)
+    if (pend[id] == 0) ready.push({bl[id], -id});
+  using Ev = std::pair<double, long long>;
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> run;
+  std::vector<int4> order;
+  order.reserve(T);
+  double now = 0.0;
+  int free = std::max(1, workers);
+  while ((long long)order.size() < T) {
+    while (free > 0 && !ready.empty()) {
+      const long long id = -ready.top().second;
+      ready.pop();
+      order.push_back(task[id]);
+      run.push({now + cost[id], id});
+      --free;
+    }
+    if (run.empty()) break;
+    const Ev e = run.top();
+    run.pop();
+    now = e.first;
+    ++free;
+    for_succ(e.second, [&](long long s) {
+      if (--pend[s] == 0) ready.push({bl[s], -s});
+    });
+  }
+  while (!run.empty()) {
+    now = std::max(now, run.top().first);
+    run.pop();
+  }
+  if (makespan) *makespan = now;
+  return order;
+}
+
+feast_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FEAST_OK;
+  if (e == cudaErrorMemoryAllocation) return FEAST_ERR_ALLOC;
+  return FEAST_ERR_CUDA;
+}
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+#define FS(expr)                       \
+  do {                                 \
+    feast_status s_ = (expr);          \
+    if (s_ != FEAST_OK) return s_;     \
+  } while (0)
+
+struct GG {  // one grouped GEMM call site
+  void* tab = nullptr;
+  int* tstart = nullptr;
+  int total = 0;
+  bool f32 = false;
+};
+
+}  // namespace
+
+struct feast_batch {
+  int np = 0, nmat = 0, Nmax = 0, nmax = 0, mmax = 0;
+  feast_options opt;
+  cudaStream_t st = nullptr;
+  std::vector<GrpDesc> pd;
+  std::vector<BMat> mats;
+  std::vector<std::vector<zc>> z, w;
+  std::vector<zc> center;
+  std::vector<double> R, aspect, normA;
+  size_t snn = 0, snm = 0, smm = 0, sm = 0, sqm = 0, slog = 0, sS = 0, sX = 0, sN = 0, snb = 0;
+  // device
+  GrpDesc* d_pd = nullptr;
+  BMat* d_mats = nullptr;
+  double2 *A = nullptr, *Y = nullptr, *Q = nullptr, *AQ = nullptr, *X = nullptr, *AX = nullptr, *E = nullptr,
+          *Rhs = nullptr;
+  double2 *Ahat = nullptr, *Bhat = nullptr, *LUB = nullptr, *Cm = nullptr, *Zs = nullptr, *V = nullptr,
+          *W = nullptr, *LUW = nullptr, *Minv = nullptr;
+  float2 *C32 = nullptr, *Z32 = nullptr, *V32 = nullptr, *W32 = nullptr, *lam32 = nullptr;
+  double2 *lam = nullptr, *coef = nullptr, *c0 = nullptr, *dz = nullptr;
+  int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *active = nullptr;
+  double *res = nullptr, *xn = nullptr, *scal = nullptr;
+  char* logs = nullptr;
+  void* pw_scratch = nullptr;
+  float2 *S = nullptr, *Xs = nullptr;
+  int *head = nullptr, *cver = nullptr, *pdone = nullptr, *fcnt = nullptr, *mv = nullptr, *perm = nullptr,
+      *piv = nullptr, *info = nullptr;
+  unsigned* flags = nullptr;
+  int4 *t_factor = nullptr, *t_first = nullptr, *t_solve = nullptr;
+  int n_factor = 0, n_first = 0, n_solve = 0;
+  double makespan = 0.0;
+  int grid = 0;
+  GG g_AQ, g_Ahat, g_Bhat, g_W32, g_V, g_Zs, g_LUW, g_X, g_AX;
+  int* orth_cta0 = nullptr;
+  int orth_total = 0;
+  double2* orth_part = nullptr;
+  unsigned* orth_bars = nullptr;
+  bool factored = false;
+  std::vector<void*> allocs;
+  // pinned host staging (graph-capturable copies)
+  double2 *h_coef = nullptr, *h_c0 = nullptr, *h_lam = nullptr;
+  int *h_use = nullptr, *h_active = nullptr;
+  double* h_res = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_failed = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+template <typename P>
+cudaError_t dalloc(feast_batch* b, P** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  b->allocs.push_back(v);
+  *p = reinterpret_cast<P*>(v);
+  return cudaSuccess;
+}
+
+BatchLuArgs lu_args(feast_batch* b, const int4* tasks, int ntasks) {
+  BatchLuArgs a;
+  a.S = b->S;
+  a.mats = b->d_mats;
+  a.tasks = tasks;
+  a.ntasks = ntasks;
+  a.head = b->head;
+  a.cver = b->cver;
+  a.pdone = b->pdone;
+  a.fcnt = b->fcnt;
+  a.mv = b->mv;
+  a.perm = b->perm;
+  a.piv = b->piv;
+  a.info = b->info;
+  a.R = b->Rhs;
+  a.X = b->Xs;
+  a.active = b->active;
+  a.flags = b->flags;
+  return a;
+}
+
+template <typename T>
+feast_status make_gg(feast_batch* b, GG& g, const std::function<GemmArgs<T>(const GrpDesc&)>& f) {
+  std::vector<GemmArgs<T>> tab(b->np);
+  std::vector<int> ts(b->np + 1, 0);
+  for (int p = 0; p < b->np; ++p) {
+    tab[p] = f(b->pd[p]);
+    tab[p].batch = 1;
+    tab[p].splitk = 1;
+    ts[p + 1] = ts[p] + gemm_tiles(tab[p].M, tab[p].N);
+  }
+  CK(dalloc(b, &g.tab, tab.size() * sizeof(GemmArgs<T>)));
+  CK(dalloc(b, &g.tstart, ts.size() * sizeof(int)));
+  CK(cudaMemcpyAsync(g.tab, tab.data(), tab.size() * sizeof(GemmArgs<T>), cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(g.tstart, ts.data(), ts.size() * sizeof(int), cudaMemcpyHostToDevice, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  g.total = ts[b->np];
+  g.f32 = std::is_same<T, float>::value;
+  return FEAST_OK;
+}
+
+cudaError_t run_gg(feast_batch* b, const GG& g) {
+  if (g.f32)
+    return gemm_grouped<float>(reinterpret_cast<const GemmArgs<float>*>(g.tab), g.tstart, b->np, g.total, b->active,
+                               b->st);
+  return gemm_grouped<double>(reinterpret_cast<const GemmArgs<double>*>(g.tab), g.tstart, b->np, g.total, b->active,
+                              b->st);
+}
+
+GemmArgs<double> zargs(int M, int N, int K, const double2* A, long long lda, int opA, const double2* B, long long ldb,
+                       int opB, double2* C, long long ldc) {
+  GemmArgs<double> g;
+  g.M = M; g.N = N; g.K = K;
+  g.alpha = make_double2(1.0, 0.0);
+  g.beta = make_double2(0.0, 0.0);
+  g.A = A; g.lda = lda; g.opA = opA;
+  g.B = B; g.ldb = ldb; g.opB = opB;
+  g.C = C; g.ldc = ldc;
+  return g;
+}
+
+feast_status read_flags(feast_batch* b) {
+  unsigned f = 0;
+  CK(cudaMemcpyAsync(&f, b->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  if (f & DEVFLAG_TIMEOUT) return FEAST_ERR_DEVICE_TIMEOUT;
+  if (f & DEVFLAG_NONFINITE) return FEAST_ERR_NONFINITE;
+  if (f & DEVFLAG_BADARG) return FEAST_ERR_CUDA;
+  return FEAST_OK;
+}
+
+// Persistent launch over one of the task lists.
+cudaError_t launch_lu(feast_batch* b, const int4* tasks, int n) {
+  if (tasks == b->t_factor || tasks == b->t_first) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->cver, 0, b->snb * sizeof(int), b->st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->pdone, 0, b->snb * sizeof(int), b->st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->fcnt, 0, b->nmat * sizeof(int), b->st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->info, 0, b->nmat * sizeof(int), b->st)) != cudaSuccess) return e;
+  }
+  return batch_lu_launch(lu_args(b, tasks, n), b->Nmax, b->grid, b->st);
+}
+
+// Rayleigh-Ritz for every active pencil (Algorithm R-FEAST steps 4-5 with Q^ = Q).
+cudaError_t enqueue_rr(feast_batch* b) {
+  cudaError_t e;
+  const size_t mmb = b->smm * sizeof(double2);
+#define CE(x) if ((e = (x)) != cudaSuccess) return e
+  CE(orth_cgs2_grp(b->Q, b->d_pd, b->orth_cta0, b->np, b->orth_total, b->orth_part, b->orth_bars, b->active,
+                   b->flags, b->st));
+  CE(run_gg(b, b->g_AQ));
+  CE(run_gg(b, b->g_Ahat));
+  CE(run_gg(b, b->g_Bhat));
+  CE(cudaMemcpyAsync(b->LUB, b->Bhat, mmb, cudaMemcpyDeviceToDevice, b->st));
+  CE(small_lu_grp(b->LUB, b->d_pd, b->np, b->active, b->pivB, b->flags, b->st));
+  CE(cudaMemcpyAsync(b->Cm, b->Ahat, mmb, cudaMemcpyDeviceToDevice, b->st));
+  CE(small_lu_solve_grp(b->LUB, b->pivB, b->d_pd, b->np, b->mmax, b->active, b->Cm, 0, b->st));
+  CE(to_c64(b->Cm, b->C32, b->smm, b->st));
+  CE(small_schur_grp(b->C32, b->Z32, b->lam32, b->d_pd, b->np, b->mmax, b->active, b->flags, b->logs, b->st));
+  CE(small_trevc_grp(b->C32, b->V32, b->d_pd, b->np, b->mmax, b->active, b->st));
+  CE(run_gg(b, b->g_W32));
+  CE(to_c128(b->W32, b->W, b->smm, b->st));
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    CE(cudaMemcpyAsync(b->LUW, b->W, mmb, cudaMemcpyDeviceToDevice, b->st));
+    CE(small_lu_grp(b->LUW, b->d_pd, b->np, b->active, b->pivW, b->flags, b->st));
+    CE(batch_identity(b->Minv, b->d_pd, b->np, b->mmax, b->active, b->st));
+    CE(small_lu_solve_grp(b->LUW, b->pivW, b->d_pd, b->np, b->mmax, b->active, b->Minv, 0, b->st));
+    CE(run_gg(b, b->g_V));
+    CE(run_gg(b, b->g_Zs));
+    CE(eig_refine_step_grp(b->Zs, b->Ahat, b->lam, b->d_pd, b->np, b->active, b->st));
+    CE(run_gg(b, b->g_LUW));
+    CE(cudaMemcpyAsync(b->W, b->LUW, mmb, cudaMemcpyDeviceToDevice, b->st));
+  }
+  CE(run_gg(b, b->g_X));
+  CE(run_gg(b, b->g_AX));
+  CE(batch_normalize(b->X, b->AX, b->d_pd, b->np, b->mmax, b->active, b->xn, b->st));
+  CE(batch_residual(b->AX, b->X, b->lam, b->d_pd, b->np, b->mmax, b->active, b->E, b->res, b->st));
+  CE(cudaMemcpyAsync(b->h_lam, b->lam, b->sm * sizeof(double2), cudaMemcpyDeviceToHost, b->st));
+  CE(cudaMemcpyAsync(b->h_res, b->res, b->sm * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+#undef CE
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_inputs(feast_batch* b) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b->coef, b->h_coef, b->sqm * sizeof(double2), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b->c0, b->h_c0, b->sm * sizeof(double2), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b->useres, b->h_use, b->sm * sizeof(int), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(b->active, b->h_active, b->np * sizeof(int), cudaMemcpyHostToDevice, b->st);
+}
+
+// A steady iteration: residual-form right-hand sides, solves, accumulation, Rayleigh-Ritz.
+cudaError_t enqueue_steady(feast_batch* b) {
+  cudaError_t e;
+  if ((e = enqueue_inputs(b)) != cudaSuccess) return e;
+  if ((e = batch_select(b->E, b->X, b->useres, b->d_pd, b->np, b->nmax, b->mmax, b->active, b->Rhs, b->st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = launch_lu(b, b->t_solve, b->n_solve)) != cudaSuccess) return e;
+  if ((e = batch_accumulate(b->Xs, b->d_mats, b->d_pd, b->np, b->nmax, b->mmax, b->coef, b->c0, b->X, b->active,
+                            b->Q, b->st)) != cudaSuccess)
+    return e;
+  return enqueue_rr(b);
+}
+
+// Host: coefficients of pencil p for Ritz values theta (or the plain filter when null).
+void host_coefs(feast_batch* b, int p, const double2* theta) {
+  const GrpDesc& d = b->pd[p];
+  for (int i = 0; i < d.m; ++i) {
+    bool u = false;
+    zc th(0.0);
+    if (theta) {
+      th = zz(theta[d.om + i]);
+      if (std::isfinite(th.real()) && std::isfinite(th.imag())) {
+        double dmin = 1e300;
+        for (int k = 0; k < d.q; ++k) dmin = std::min(dmin, std::abs(b->z[p][k] - th));
+        u = dmin >= 1e-10 * b->R[p];
+      }
+    }
+    zc acc = 0.0;
+    for (int k = 0; k < d.q; ++k) {
+      const zc g = u ? b->w[p][k] / (b->z[p][k] - th) : b->w[p][k];
+      acc += g;
+      b->h_coef[d.oqm + (size_t)k * d.m + i] = d2(g);
+    }
+    b->h_c0[d.om + i] = d2(u ? acc : zc(0.0));
+    b->h_use[d.om + i] = u ? 1 : 0;
+  }
+}
+
+bool inside(const feast_batch* b, int p, zc l) {
+  const double x = (l.real() - b->center[p].real()) / b->R[p];
+  const double y = (l.imag() - b->center[p].imag()) / (b->R[p] * b->aspect[p]);
+  return x * x + y * y < 1.0;
+}
+
+std::vector<int> candidates(const feast_batch* b, int p) {
+  const GrpDesc& d = b->pd[p];
+  std::vector<int> idx;
+  for (int i = 0; i < d.m; ++i) {
+    const zc l = zz(b->h_lam[d.om + i]);
+    const double r = b->h_res[d.om + i];
+    if (!std::isfinite(l.real()) || !std::isfinite(l.imag()) || !std::isfinite(r)) continue;
+    if (inside(b, p, l) && r <= b->opt.cand_tol) idx.push_back(i);
+  }
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) {
+    const zc a = zz(b->h_lam[d.om + x]), c = zz(b->h_lam[d.om + y]);
+    if (a.real() != c.real()) return a.real() < c.real();
+    return a.imag() < c.imag();
+  });
+  return idx;
+}
+
+feast_status ensure_factored_first(feast_batch* b, bool with_solve) {
+  // with_solve: the first launch also solves the current right-hand sides
+  const int4* t = with_solve ? (b->factored ? b->t_solve : b->t_first) : (b->factored ? nullptr : b->t_factor);
+  const int n = with_solve ? (b->factored ? b->n_solve : b->n_first) : (b->factored ? 0 : b->n_factor);
+  if (!t) return FEAST_OK;
+  const bool timing = b->opt.timing && !b->factored;
+  if (timing) CK(cudaEventRecord(b->ev[0], b->st));
+  CK(launch_lu(b, t, n));
+  if (timing) CK(cudaEventRecord(b->ev[1], b->st));
+  if (!b->factored) {
+    FS(read_flags(b));
+    std::vector<int> info(b->nmat);
+    CK(cudaMemcpyAsync(info.data(), b->info, b->nmat * sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    CK(cudaStreamSynchronize(b->st));
+    b->factored = true;
+    for (int v : info)
+      if (v != 0) return FEAST_ERR_SINGULAR_SHIFT;
+  }
+  return FEAST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void feast_batch_destroy(feast_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (void* p : b->allocs) cudaFree(p);
+  for (void* p : {(void*)b->h_coef, (void*)b->h_c0, (void*)b->h_lam, (void*)b->h_use, (void*)b->h_active,
+                  (void*)b->h_res})
+    if (p) cudaFreeHost(p);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+
+feast_status feast_batch_plan(int nmat, const int* nb, const int* m, int with_lu, int with_solve, int workers,
+                              int* tasks, int capacity, int* ntasks, double* makespan_us) {
+  if (nmat < 1 || !nb || !m || !ntasks || workers < 1) return FEAST_ERR_ARG;
+  std::vector<int> nbv(nb, nb + nmat), mv(m, m + nmat);
+  for (int i = 0; i < nmat; ++i)
+    if (nbv[i] < 1 || mv[i] < 0) return FEAST_ERR_ARG;
+  double ms = 0.0;
+  const std::vector<int4> order = plan_order(nbv, mv, with_lu != 0, with_solve != 0, workers, &ms);
+  *ntasks = (int)order.size();
+  if (makespan_us) *makespan_us = ms;
+  if (tasks) {
+    if (capacity < (int)order.size()) return FEAST_ERR_ARG;
+    for (size_t t = 0; t < order.size(); ++t) {
+      tasks[4 * t] = order[t].x;
+      tasks[4 * t + 1] = order[t].y;
+      tasks[4 * t + 2] = order[t].z;
+      tasks[4 * t + 3] = order[t].w;
+    }
+  }
+  return FEAST_OK;
+}
+
+feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, const feast_z* const* A,
+                                const int64_t* lda, const feast_contour* contours, const int* m0,
+                                const feast_options* o, void* stream) {
+  if (!out) return FEAST_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || count > 4096 || !n || !A || !contours || !m0) return FEAST_ERR_ARG;
+  feast_batch* b = new (std::nothrow) feast_batch();
+  if (!b) return FEAST_ERR_ALLOC;
+  if (o) b->opt = *o; else feast_default_options(&b->opt);
+  if (b->opt.tol <= 0) b->opt.tol = 1e-10;
+  if (b->opt.max_iter < 1) b->opt.max_iter = 20;
+  if (b->opt.max_iter > 64) b->opt.max_iter = 64;
+  if (b->opt.cand_tol <= 0) b->opt.cand_tol = 1e-4;
+  auto bad = [&](feast_status s) { feast_batch_destroy(b); return s; };
+  if (b->opt.algo != FEAST_ALGO_R || b->opt.precision != FEAST_PREC_MIXED) return bad(FEAST_ERR_ARG);
+  b->st = reinterpret_cast<cudaStream_t>(stream);
+  b->np = count;
+  b->pd.resize(count);
+  b->z.resize(count);
+  b->w.resize(count);
+  for (int p = 0; p < count; ++p) {
+    const int64_t np_ = n[p];
+    const int64_t ld = lda ? lda[p] : np_;
+    if (np_ < 1 || np_ > BATCH_MAX_N || m0[p] < 1 || m0[p] > np_ || m0[p] > 160 || !A[p] || ld < np_)
+      return bad(FEAST_ERR_ARG);
+    const feast_contour& c = contours[p];
+    if (c.R <= 0.0 || c.aspect <= 0.0) return bad(FEAST_ERR_ARG);
+    if (!feast_quadrature_host(c, b->z[p], b->w[p]) || b->z[p].size() > 256) return bad(FEAST_ERR_ARG);
+    b->center.push_back(zc(c.center.re, c.center.im));
+    b->R.push_back(c.R);
+    b->aspect.push_back(c.aspect);
+    GrpDesc& d = b->pd[p];
+    d.n = (int)np_;
+    d.m = m0[p];
+    d.q = (int)b->z[p].size();
+    d.mat0 = b->nmat;
+    d.onn = (long long)b->snn;
+    d.onm = (long long)b->snm;
+    d.omm = (long long)b->smm;
+    d.om = (long long)b->sm;
+    d.oqm = (long long)b->sqm;
+    d.olog = (long long)b->slog;
+    b->snn += (size_t)d.n * d.n;
+    b->snm += (size_t)d.n * d.m;
+    b->smm += (size_t)d.m * d.m;
+    b->sm += (size_t)d.m;
+    b->sqm += (size_t)d.q * d.m;
+    b->slog += (schur_log_bytes(d.m) + 255) / 256 * 256;
+    const int N = (d.n + BATCH_TILE - 1) / BATCH_TILE * BATCH_TILE;
+    b->Nmax = std::max(b->Nmax, N);
+    b->nmax = std::max(b->nmax, d.n);
+    b->mmax = std::max(b->mmax, d.m);
+    for (int k = 0; k < d.q; ++k) {
+      BMat M;
+      M.soff = (long long)b->sS;
+      M.xoff = (long long)b->sX;
+      M.roff = d.onm;
+      M.N = N;
+      M.n = d.n;
+      M.m = d.m;
+      M.nb = N / BATCH_TILE;
+      M.coff = (int)b->snb;
+      M.poff = (int)b->sN;
+      M.pencil = p;
+      M.shift = k;
+      b->sS += (size_t)N * N;
+      b->sX += (size_t)N * d.m;
+      b->snb += (size_t)M.nb;
+      b->sN += (size_t)N;
+      b->mats.push_back(M);
+      ++b->nmat;
+    }
+  }
+  cudaError_t e;
+#define AL(p, bytes) if ((e = dalloc(b, &(p), (bytes))) != cudaSuccess) return bad(cuda_status(e))
+  AL(b->d_pd, b->np * sizeof(GrpDesc));
+  AL(b->d_mats, b->nmat * sizeof(BMat));
+  AL(b->A, b->snn * sizeof(double2));
+  double2** nms[] = {&b->Y, &b->Q, &b->AQ, &b->X, &b->AX, &b->E, &b->Rhs};
+  for (double2** p : nms) AL(*p, b->snm * sizeof(double2));
+  double2** mms[] = {&b->Ahat, &b->Bhat, &b->LUB, &b->Cm, &b->Zs, &b->V, &b->W, &b->LUW, &b->Minv};
+  for (double2** p : mms) AL(*p, b->smm * sizeof(double2));
+  float2** m32[] = {&b->C32, &b->Z32, &b->V32, &b->W32};
+  for (float2** p : m32) AL(*p, b->smm * sizeof(float2));
+  AL(b->lam32, b->sm * sizeof(float2));
+  AL(b->lam, b->sm * sizeof(double2));
+  AL(b->c0, b->sm * sizeof(double2));
+  AL(b->coef, b->sqm * sizeof(double2));
+  AL(b->dz, b->nmat * sizeof(double2));
+  AL(b->pivB, b->sm * sizeof(int));
+  AL(b->pivW, b->sm * sizeof(int));
+  AL(b->useres, b->sm * sizeof(int));
+  AL(b->active, b->np * sizeof(int));
+  AL(b->res, b->sm * sizeof(double));
+  AL(b->xn, b->sm * sizeof(double));
+  AL(b->scal, 64);
+  AL(b->logs, b->slog);
+  AL(b->pw_scratch, norm2_scratch_bytes(b->nmax));
+  AL(b->S, b->sS * sizeof(float2));
+  AL(b->Xs, b->sX * sizeof(float2));
+  AL(b->head, 64);
+  AL(b->cver, b->snb * sizeof(int));
+  AL(b->pdone, b->snb * sizeof(int));
+  AL(b->fcnt, b->nmat * sizeof(int));
+  AL(b->info, b->nmat * sizeof(int));
+  AL(b->mv, b->snb * BATCH_MVSTRIDE * sizeof(int));
+  AL(b->perm, b->sN * sizeof(int));
+  AL(b->piv, b->sN * sizeof(int));
+  AL(b->flags, 64);
+  for (void** hp : {(void**)&b->h_coef, (void**)&b->h_c0, (void**)&b->h_lam}) {
+    if ((e = cudaMallocHost(hp, (hp == (void**)&b->h_coef ? b->sqm : b->sm) * sizeof(double2))) != cudaSuccess)
+      return bad(cuda_status(e));
+  }
+  if ((e = cudaMallocHost((void**)&b->h_use, b->sm * sizeof(int))) != cudaSuccess) return bad(cuda_status(e));
+  if ((e = cudaMallocHost((void**)&b->h_active, b->np * sizeof(int))) != cudaSuccess) return bad(cuda_status(e));
+  if ((e = cudaMallocHost((void**)&b->h_res, b->sm * sizeof(double))) != cudaSuccess) return bad(cuda_status(e));
+  for (auto& ev : b->ev)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bad(cuda_status(e));
+  // tables
+  std::vector<double2> zd;
+  for (int p = 0; p < b->np; ++p)
+    for (const zc& v : b->z[p]) zd.push_back(d2(v));
+  if ((e = cudaMemcpyAsync(b->d_pd, b->pd.data(), b->np * sizeof(GrpDesc), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
+    return bad(cuda_status(e));
+  if ((e = cudaMemcpyAsync(b->d_mats, b->mats.data(), b->nmat * sizeof(BMat), cudaMemcpyHostToDevice, b->st)) !=
+      cudaSuccess)
+    return bad(cuda_status(e));
+  if ((e = cudaMemcpyAsync(b->dz, zd.data(), zd.size() * sizeof(double2), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
+    return bad(cuda_status(e));
+  if ((e = cudaMemsetAsync(b->flags, 0, 64, b->st)) != cudaSuccess) return bad(cuda_status(e));
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    const int64_t ld = lda ? lda[p] : d.n;
+    if ((e = cudaMemcpy2DAsync(b->A + d.onn, d.n * sizeof(double2), A[p], ld * sizeof(double2), d.n * sizeof(double2),
+                               d.n, cudaMemcpyDefault, b->st)) != cudaSuccess)
+      return bad(cuda_status(e));
+  }
+  if ((e = check_finite(b->A, b->snn, b->flags, b->st)) != cudaSuccess) return bad(cuda_status(e));
+  {
+    feast_status s = read_flags(b);
+    if (s != FEAST_OK) return bad(s);
+  }
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    if ((e = norm2_power(b->A + d.onn, d.n, d.n, 50, b->pw_scratch, b->scal, b->flags, b->st)) != cudaSuccess)
+      return bad(cuda_status(e));
+    double s = 0.0;
+    if ((e = cudaMemcpyAsync(&s, b->scal, sizeof(double), cudaMemcpyDeviceToHost, b->st)) != cudaSuccess)
+      return bad(cuda_status(e));
+    if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess) return bad(cuda_status(e));
+    b->normA.push_back(s);
+  }
+  // persistent launch: resident CTAs and the three task lists
+  b->grid = batch_lu_grid(b->Nmax);
+  if (b->grid < 1) return bad(FEAST_ERR_CUDA);
+  {
+    std::vector<int> nbv, mv;
+    for (const BMat& M : b->mats) {
+      nbv.push_back(M.nb);
+      mv.push_back(M.m);
+    }
+    auto upload = [&](bool lu, bool solve, int4** dst, int* cnt, double* mk) -> cudaError_t {
+      const std::vector<int4> ord = plan_order(nbv, mv, lu, solve, b->grid, mk);
+      *cnt = (int)ord.size();
+      cudaError_t ee = dalloc(b, dst, ord.size() * sizeof(int4));
+      if (ee != cudaSuccess) return ee;
+      ee = cudaMemcpyAsync(*dst, ord.data(), ord.size() * sizeof(int4), cudaMemcpyHostToDevice, b->st);
+      if (ee != cudaSuccess) return ee;
+      return cudaStreamSynchronize(b->st);
+    };
+    double mk = 0.0;
+    if ((e = upload(true, false, &b->t_factor, &b->n_factor, &b->makespan)) != cudaSuccess) return bad(cuda_status(e));
+    if ((e = upload(true, true, &b->t_first, &b->n_first, &mk)) != cudaSuccess) return bad(cuda_status(e));
+    if ((e = upload(false, true, &b->t_solve, &b->n_solve, &mk)) != cudaSuccess) return bad(cuda_status(e));
+  }
+  // S_i = z_i I - A_p
+  if ((e = batch_form_shifted(b->A, b->d_pd, b->d_mats, b->dz, b->nmat, b->Nmax, b->S, b->st)) != cudaSuccess)
+    return bad(cuda_status(e));
+  // grouped CGS2: CTAs per block in proportion to n, within the resident limit
+  {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int cap = nsm * std::max(1, orth_grp_ctas_per_sm());
+    std::vector<int> G(b->np);
+    long long tot = 0;
+    for (int p = 0; p < b->np; ++p) {
+      G[p] = std::max(1, std::min(16, (b->pd[p].n + 127) / 128));
+      tot += G[p];
+    }
+    while (tot > cap) {
+      tot = 0;
+      for (int p = 0; p < b->np; ++p) {
+        G[p] = std::max(1, G[p] / 2);
+        tot += G[p];
+      }
+      if (tot > cap && *std::max_element(G.begin(), G.end()) == 1) return bad(FEAST_ERR_ARG);
+    }
+    std::vector<int> c0(b->np + 1, 0);
+    for (int p = 0; p < b->np; ++p) c0[p + 1] = c0[p] + G[p];
+    b->orth_total = c0[b->np];
+    AL(b->orth_cta0, c0.size() * sizeof(int));
+    AL(b->orth_part, (size_t)2 * b->orth_total * 256 * sizeof(double2));
+    AL(b->orth_bars, (size_t)2 * b->np * sizeof(unsigned));
+    if ((e = cudaMemcpyAsync(b->orth_cta0, c0.data(), c0.size() * sizeof(int), cudaMemcpyHostToDevice, b->st)) !=
+        cudaSuccess)
+      return bad(cuda_status(e));
+  }
+#undef AL
+  // grouped GEMM call sites
+  {
+    feast_batch* B = b;
+    feast_status s;
+    if ((s = make_gg<double>(b, b->g_AQ, [B](const GrpDesc& d) {
+           return zargs(d.n, d.m, d.n, B->A + d.onn, d.n, OP_N, B->Q + d.onm, d.n, OP_N, B->AQ + d.onm, d.n);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_Ahat, [B](const GrpDesc& d) {
+           return zargs(d.m, d.m, d.n, B->Q + d.onm, d.n, OP_C, B->AQ + d.onm, d.n, OP_N, B->Ahat + d.omm, d.m);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_Bhat, [B](const GrpDesc& d) {
+           return zargs(d.m, d.m, d.n, B->Q + d.onm, d.n, OP_C, B->Q + d.onm, d.n, OP_N, B->Bhat + d.omm, d.m);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<float>(b, b->g_W32, [B](const GrpDesc& d) {
+           GemmArgs<float> g;
+           g.M = d.m; g.N = d.m; g.K = d.m;
+           g.alpha = make_float2(1.f, 0.f);
+           g.beta = make_float2(0.f, 0.f);
+           g.A = B->Z32 + d.omm; g.lda = d.m;
+           g.B = B->V32 + d.omm; g.ldb = d.m;
+           g.C = B->W32 + d.omm; g.ldc = d.m;
+           return g;
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_V, [B](const GrpDesc& d) {
+           return zargs(d.m, d.m, d.m, B->Cm + d.omm, d.m, OP_N, B->W + d.omm, d.m, OP_N, B->V + d.omm, d.m);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_Zs, [B](const GrpDesc& d) {
+           return zargs(d.m, d.m, d.m, B->Minv + d.omm, d.m, OP_N, B->V + d.omm, d.m, OP_N, B->Zs + d.omm, d.m);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_LUW, [B](const GrpDesc& d) {
+           return zargs(d.m, d.m, d.m, B->W + d.omm, d.m, OP_N, B->Ahat + d.omm, d.m, OP_N, B->LUW + d.omm, d.m);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_X, [B](const GrpDesc& d) {
+           return zargs(d.n, d.m, d.m, B->Q + d.onm, d.n, OP_N, B->W + d.omm, d.m, OP_N, B->X + d.onm, d.n);
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_AX, [B](const GrpDesc& d) {
+           return zargs(d.n, d.m, d.m, B->AQ + d.onm, d.n, OP_N, B->W + d.omm, d.m, OP_N, B->AX + d.onm, d.n);
+         })) != FEAST_OK) return bad(s);
+  }
+  for (int p = 0; p < b->np; ++p) b->h_active[p] = 1;
+  if ((e = cudaMemcpyAsync(b->active, b->h_active, b->np * sizeof(int), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
+    return bad(cuda_status(e));
+  if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess) return bad(cuda_status(e));
+  *out = b;
+  return FEAST_OK;
+}
+
+feast_status feast_batch_factor(feast_batch* b) {
+  if (!b) return FEAST_ERR_ARG;
+  if (b->factored) {  // an explicit call factors again
+    CK(batch_form_shifted(b->A, b->d_pd, b->d_mats, b->dz, b->nmat, b->Nmax, b->S, b->st));
+    b->factored = false;
+  }
+  return ensure_factored_first(b, false);
+}
+
+feast_status feast_batch_filter(feast_batch* b, const feast_z* const* Y, feast_z* const* Q) {
+  if (!b || !Y || !Q) return FEAST_ERR_ARG;
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    if (!Y[p]) return FEAST_ERR_ARG;
+    CK(cudaMemcpyAsync(b->Y + d.onm, Y[p], (size_t)d.n * d.m * sizeof(double2), cudaMemcpyDefault, b->st));
+    host_coefs(b, p, nullptr);
+    b->h_active[p] = 1;
+  }
+  CK(enqueue_inputs(b));
+  CK(cudaMemcpyAsync(b->Rhs, b->Y, b->snm * sizeof(double2), cudaMemcpyDeviceToDevice, b->st));
+  FS(ensure_factored_first(b, true));
+  CK(batch_accumulate(b->Xs, b->d_mats, b->d_pd, b->np, b->nmax, b->mmax, b->coef, nullptr, nullptr, b->active, b->Q,
+                      b->st));
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    if (Q[p]) CK(cudaMemcpyAsync(Q[p], b->Q + d.onm, (size_t)d.n * d.m * sizeof(double2), cudaMemcpyDefault, b->st));
+  }
+  CK(cudaStreamSynchronize(b->st));
+  return read_flags(b);
+}
+
+feast_status feast_batch_solve(feast_batch* b, const feast_z* const* Y0, feast_z* const* lambda, feast_z* const* X,
+                               double* const* res, int* m_found, feast_batch_stats* stats) {
+  if (!b || !Y0 || !lambda) return FEAST_ERR_ARG;
+  feast_batch_stats st;
+  std::memset(&st, 0, sizeof(st));
+  st.grid = b->grid;
+  st.tasks_factor = b->n_factor;
+  st.plan_makespan_us = b->makespan;
+  const bool was_factored = b->factored;
+  // iteration 1: plain filter of Y0
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    if (!Y0[p] || !lambda[p]) return FEAST_ERR_ARG;
+    CK(cudaMemcpyAsync(b->Y + d.onm, Y0[p], (size_t)d.n * d.m * sizeof(double2), cudaMemcpyDefault, b->st));
+    host_coefs(b, p, nullptr);
+    b->h_active[p] = 1;
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (b->opt.timing) {
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    CK(cudaEventRecord(t0, b->st));
+  }
+  CK(cudaMemsetAsync(b->flags, 0, sizeof(unsigned), b->st));
+  CK(enqueue_inputs(b));
+  CK(cudaMemcpyAsync(b->Rhs, b->Y, b->snm * sizeof(double2), cudaMemcpyDeviceToDevice, b->st));
+  feast_status fs = ensure_factored_first(b, true);
+  if (fs != FEAST_OK) return fs;
+  if (b->opt.timing && !was_factored) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+    st.t_factor_ms = ms;
+  }
+  CK(batch_accumulate(b->Xs, b->d_mats, b->d_pd, b->np, b->nmax, b->mmax, b->coef, nullptr, nullptr, b->active, b->Q,
+                      b->st));
+  CK(enqueue_rr(b));
+  CK(cudaStreamSynchronize(b->st));
+  FS(read_flags(b));
+  if (b->opt.timing) {
+    CK(cudaEventRecord(t1, b->st));
+    CK(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    st.t_iter_ms[0] = ms;
+  }
+  std::vector<int> prev(b->np, -1), conv(b->np, 0);
+  std::vector<std::vector<int>> cand(b->np);
+  int it = 1;
+  for (;; ++it) {
+    int nconv = 0;
+    for (int p = 0; p < b->np; ++p) {
+      if (conv[p]) { ++nconv; continue; }
+      cand[p] = candidates(b, p);
+      const int count = (int)cand[p].size();
+      double mx = count ? 0.0 : INFINITY;
+      for (int i : cand[p]) mx = std::max(mx, b->h_res[b->pd[p].om + i] / b->normA[p]);
+      if (count > 0 && count == prev[p] && mx <= b->opt.tol) {
+        conv[p] = 1;
+        ++nconv;
+      }
+      prev[p] = count;
+    }
+    st.iters = it;
+    st.converged = nconv;
+    if (nconv == b->np || it >= b->opt.max_iter) break;
+    // next iteration: residual form for the pencils still active
+    for (int p = 0; p < b->np; ++p) {
+      b->h_active[p] = conv[p] ? 0 : 1;
+      if (!conv[p]) host_coefs(b, p, b->h_lam);
+    }
+    if (b->opt.timing) CK(cudaEventRecord(t0, b->st));
+    bool done = false;
+    if (!b->graph_failed) {
+      if (!b->gexec) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+          cudaError_t e2 = enqueue_steady(b);
+          e = cudaStreamEndCapture(b->st, &g);
+          if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          if (b->gexec) cudaGraphExecDestroy(b->gexec);
+          b->gexec = nullptr;
+          b->graph_failed = true;
+        }
+      }
+      if (b->gexec) {
+        CK(cudaGraphLaunch(b->gexec, b->st));
+        done = true;
+        st.graph = 1;
+      }
+    }
+    if (!done) CK(enqueue_steady(b));
+    CK(cudaStreamSynchronize(b->st));
+    FS(read_flags(b));
+    if (b->opt.timing) {
+      CK(cudaEventRecord(t1, b->st));
+      CK(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (it < 64) st.t_iter_ms[it] = ms;
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  // outputs: candidates first, sorted by (Re, Im)
+  int nconv = 0;
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    const int k = (int)cand[p].size();
+    std::vector<double2> lam(d.m, make_double2(0.0, 0.0));
+    std::vector<double> r(d.m, 0.0);
+    for (int j = 0; j < k; ++j) {
+      lam[j] = b->h_lam[d.om + cand[p][j]];
+      r[j] = b->h_res[d.om + cand[p][j]] / b->normA[p];
+    }
+    CK(cudaMemcpyAsync(lambda[p], lam.data(), d.m * sizeof(double2), cudaMemcpyDefault, b->st));
+    if (res && res[p]) CK(cudaMemcpyAsync(res[p], r.data(), d.m * sizeof(double), cudaMemcpyDefault, b->st));
+    if (X && X[p]) {  // gather through the (now free) AQ arena, then one copy out
+      double2* tmp = b->AQ + d.onm;
+      for (int j = 0; j < d.m; ++j) {
+        if (j < k)
+          CK(cudaMemcpyAsync(tmp + (size_t)j * d.n, b->X + d.onm + (size_t)cand[p][j] * d.n, d.n * sizeof(double2),
+                             cudaMemcpyDeviceToDevice, b->st));
+        else
+          CK(cudaMemsetAsync(tmp + (size_t)j * d.n, 0, d.n * sizeof(double2), b->st));
+      }
+      CK(cudaMemcpyAsync(X[p], tmp, (size_t)d.n * d.m * sizeof(double2), cudaMemcpyDefault, b->st));
+    }
+    if (m_found) m_found[p] = k;
+    nconv += conv[p];
+    CK(cudaStreamSynchronize(b->st));  // the host vectors go out of scope
+  }
+  if (stats) *stats = st;
+  return nconv == b->np ? FEAST_OK : FEAST_ERR_NOCONV;
+}
+
+feast_status feast_batch_get_factor(feast_batch* b, int pencil, int shift, feast_z* LU, int32_t* perm) {
+  if (!b || pencil < 0 || pencil >= b->np || shift < 0 || shift >= b->pd[pencil].q) return FEAST_ERR_ARG;
+  if (!b->factored) return FEAST_ERR_STATE;
+  const BMat& M = b->mats[b->pd[pencil].mat0 + shift];
+  if (LU) {
+    std::vector<float2> f((size_t)M.N * M.N);
+    CK(cudaMemcpyAsync(f.data(), b->S + M.soff, f.size() * sizeof(float2), cudaMemcpyDeviceToHost, b->st));
+    CK(cudaStreamSynchronize(b->st));
+    std::vector<double2> d((size_t)M.n * M.n);
+    for (int c = 0; c < M.n; ++c)
+      for (int r = 0; r < M.n; ++r) {
+        const float2 v = f[(size_t)r + (size_t)c * M.N];
+        d[(size_t)r + (size_t)c * M.n] = make_double2(v.x, v.y);
+      }
+    CK(cudaMemcpyAsync(LU, d.data(), d.size() * sizeof(double2), cudaMemcpyDefault, b->st));
+    CK(cudaStreamSynchronize(b->st));
+  }
+  if (perm) {
+    CK(cudaMemcpyAsync(perm, b->perm + M.poff, M.n * sizeof(int32_t), cudaMemcpyDefault, b->st));
+    CK(cudaStreamSynchronize(b->st));
+  }
+  return FEAST_OK;
+}
+
+feast_status feast_batch_info(const feast_batch* b, int* count, int* nmat, int* grid, int* tasks_factor,
+                              double* plan_makespan_us, double* lu_flops) {
+  if (!b) return FEAST_ERR_ARG;
+  if (count) *count = b->np;
+  if (nmat) *nmat = b->nmat;
+  if (grid) *grid = b->grid;
+  if (tasks_factor) *tasks_factor = b->n_factor;
+  if (plan_makespan_us) *plan_makespan_us = b->makespan;
+  if (lu_flops) {
+    double f = 0.0;
+    for (const BMat& M : b->mats) f += 8.0 / 3.0 * (double)M.n * M.n * M.n;
+    *lu_flops = f;
+  }
+  return FEAST_OK;
+}
+
+}  // extern "C"

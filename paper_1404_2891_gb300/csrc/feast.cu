@@ -136,6 +136,11 @@ bool build_quadrature(const feast_contour& c, std::vector<zc>& z, std::vector<zc
 
 }  // namespace
 
+// Nodes and weights for the batched path (same rules as the handle).
+bool feast_quadrature_host(const feast_contour& c, std::vector<zc>& z, std::vector<zc>& w) {
+  return build_quadrature(c, z, w);
+}
+
 // ---------------------------------------------------------------- the handle
 struct feast_handle {
   int64_t n = 0;

@@ -36,14 +36,14 @@ __device__ __forceinline__ void dmma16n8k8(double (&c)[4], const double (&a)[4],
 
 // 256 threads = 8 warps as 4 (M) x 2 (N); each warp owns 16 x 32 of the 64 x 64 tile,
 // i.e. one m16 row block and four n8 column blocks, with separate re/im accumulators.
-__global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
+__device__ __forceinline__ void zgemm_body(const GemmArgs<double>& g, const int bx, const int by, const int bz) {
   __shared__ double As[2][2][BK64][BM + 1];  // [buf][re/im][k][m]
   __shared__ double Bs[2][2][BK64][BN + 1];  // [buf][re/im][k][n]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int split = (int)(blockIdx.z % g.splitk);
-  const size_t b = blockIdx.z / g.splitk;
+  const int m0 = bx * BM, n0 = by * BN;
+  const int split = bz % g.splitk;
+  const size_t b = bz / g.splitk;
   const double2* A = g.A + b * g.strideA;
   const double2* B = g.B + b * g.strideB;
   double2* C = g.C + b * g.strideC;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
   }
   // epilogue: C fragment c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
   const bool beta_zero = (g.beta.x == 0.0 && g.beta.y == 0.0);
-  double2* part = g.splitk > 1 ? g.ws + (size_t)blockIdx.z * g.M * g.N : nullptr;
+  double2* part = g.splitk > 1 ? g.ws + (size_t)bz * g.M * g.N : nullptr;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
 #pragma unroll
@@ -143,17 +143,32 @@ __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) { zgemm_body(g, blockIdx.x, blockIdx.y, blockIdx.z); }
+
+// Grouped form: tiles [tstart[p], tstart[p+1]) of the grid belong to problem p
+// (one M x N product per pencil, no split-K).
+__global__ void __launch_bounds__(256)
+k_zgemm_dmma_grp(const GemmArgs<double>* tab, const int* tstart, int np, const int* active) {
+  const int t = blockIdx.x;
+  int p = 0;
+  while (p + 1 < np && tstart[p + 1] <= t) ++p;
+  if (!active[p]) return;
+  const GemmArgs<double> g = tab[p];
+  const int local = t - tstart[p], tm = (g.M + BM - 1) / BM;
+  zgemm_body(g, local % tm, local / tm, 0);
+}
+
 // ---------------------------------------------------------------- FP32 SIMT
 constexpr int BK32 = 16;
 
 // 256 threads, each computing a 4 x 4 block of the 64 x 64 tile.
-__global__ void __launch_bounds__(256) k_cgemm_simt(GemmArgs<float> g) {
+__device__ __forceinline__ void cgemm_body(const GemmArgs<float>& g, const int bx, const int by, const int bz) {
   __shared__ float2 As[BK32][BM + 1];
   __shared__ float2 Bs[BK32][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const size_t b = blockIdx.z;
+  const int m0 = bx * BM, n0 = by * BN;
+  const size_t b = bz;
   const float2* A = g.A + b * g.strideA;
   const float2* B = g.B + b * g.strideB;
   float2* C = g.C + b * g.strideC;
@@ -202,6 +217,19 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(GemmArgs<float> g) {
         *p = out;
       }
     }
+}
+
+__global__ void __launch_bounds__(256) k_cgemm_simt(GemmArgs<float> g) { cgemm_body(g, blockIdx.x, blockIdx.y, blockIdx.z); }
+
+__global__ void __launch_bounds__(256)
+k_cgemm_simt_grp(const GemmArgs<float>* tab, const int* tstart, int np, const int* active) {
+  const int t = blockIdx.x;
+  int p = 0;
+  while (p + 1 < np && tstart[p + 1] <= t) ++p;
+  if (!active[p]) return;
+  const GemmArgs<float> g = tab[p];
+  const int local = t - tstart[p], tm = (g.M + BM - 1) / BM;
+  cgemm_body(g, local % tm, local / tm, 0);
 }
 
 }  // namespace
@@ -260,3 +288,23 @@ cudaError_t gemm_batched<float>(const GemmArgs<float>& g, cudaStream_t s) {
   k_cgemm_simt<<<grid, 256, 0, s>>>(g);
   return cudaGetLastError();
 }
+
+template <>
+cudaError_t gemm_grouped<double>(const GemmArgs<double>* tab, const int* tstart, int np, int total_tiles,
+                                 const int* active, cudaStream_t s) {
+  if (np < 1 || total_tiles < 1) return cudaSuccess;
+  feast_count_launch();
+  k_zgemm_dmma_grp<<<total_tiles, 256, 0, s>>>(tab, tstart, np, active);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t gemm_grouped<float>(const GemmArgs<float>* tab, const int* tstart, int np, int total_tiles,
+                                const int* active, cudaStream_t s) {
+  if (np < 1 || total_tiles < 1) return cudaSuccess;
+  feast_count_launch();
+  k_cgemm_simt_grp<<<total_tiles, 256, 0, s>>>(tab, tstart, np, active);
+  return cudaGetLastError();
+}
+
+int gemm_tiles(int M, int N) { return (int)(ceil_div(M, BM) * ceil_div(N, BN)); }

@@ -27,3 +27,11 @@ struct GemmArgs {
 
 template <typename T>
 cudaError_t gemm_batched(const GemmArgs<T>& g, cudaStream_t s);
+
+// Grouped GEMM: problem p (tab[p] in device memory, batch = 1) owns grid tiles
+// [tstart[p], tstart[p+1]) with tstart[p+1] - tstart[p] = gemm_tiles(M_p, N_p);
+// problems with active[p] == 0 are skipped.
+template <typename T>
+cudaError_t gemm_grouped(const GemmArgs<T>* tab, const int* tstart, int np, int total_tiles, const int* active,
+                         cudaStream_t s);
+int gemm_tiles(int M, int N);

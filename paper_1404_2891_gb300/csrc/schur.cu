@@ -74,9 +74,8 @@ __device__ void givens(cplx<T> x, cplx<T> y, T& c, cplx<T>& s) {
 // shifted QR iteration by warp 0 on the packed shared-memory copy.  The
 // rotations (c, Re s, Im s, k) go to rot_log; k_apply_rotations folds them into Z.
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS)
-k_small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags, double4* rot_log, int rot_cap,
-              int* rot_count) {
+__device__ __forceinline__ void small_schur_body(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags,
+                                                 double4* rot_log, int rot_cap, int* rot_count) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* H = reinterpret_cast<cplx<T>*>(smem_raw);
   __shared__ cplx<T> s_u[SCHUR_MAX_M];
@@ -237,15 +236,34 @@ k_small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags, doub
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS)
+k_small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* flags, double4* rot_log, int rot_cap,
+              int* rot_count) {
+  small_schur_body<T>(C, Z, lam, m, flags, rot_log, rot_cap, rot_count);
+}
+
+__global__ void __launch_bounds__(SCHUR_THREADS)
+k_small_schur_grp(float2* C, float2* Z, float2* lam, const GrpDesc* pd, const int* active, unsigned* flags,
+                  char* logs) {
+  const int p = blockIdx.x;
+  if (!active[p]) return;
+  const GrpDesc d = pd[p];
+  char* log = logs + d.olog;
+  small_schur_body<float>(C + d.omm, Z + d.omm, lam + d.om, d.m, flags, reinterpret_cast<double4*>(log + 256),
+                          (30 * d.m + 100) * d.m, reinterpret_cast<int*>(log));
+}
+
 // Z <- Z G_1^H G_2^H ... for the logged rotations, in order.  One warp per block,
 // one row of Z per lane, the rows held in shared memory (row-major, padded).
 template <typename T>
-__global__ void __launch_bounds__(32) k_apply_rotations(cplx<T>* Z, int m, const double4* rot_log, const int* rot_count) {
+__device__ __forceinline__ void apply_rotations_body(cplx<T>* Z, int m, const double4* rot_log, const int* rot_count,
+                                                     int bx) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* rows = reinterpret_cast<cplx<T>*>(smem_raw);  // [32][m + 1]
   __shared__ double4 recs[32];
   const int lane = threadIdx.x;
-  const int r = blockIdx.x * 32 + lane;
+  const int r = bx * 32 + lane;
   const int ld = m + 1;
   for (int j = 0; j < m; ++j) rows[lane * ld + j] = r < m ? Z[r + (size_t)j * m] : mk<T>(T(0), T(0));
   const int nrot = *rot_count;
@@ -268,9 +286,24 @@ __global__ void __launch_bounds__(32) k_apply_rotations(cplx<T>* Z, int m, const
     for (int j = 0; j < m; ++j) Z[r + (size_t)j * m] = rows[lane * ld + j];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32) k_apply_rotations(cplx<T>* Z, int m, const double4* rot_log, const int* rot_count) {
+  apply_rotations_body<T>(Z, m, rot_log, rot_count, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32)
+k_apply_rotations_grp(float2* Z, const GrpDesc* pd, const int* active, const char* logs) {
+  const int p = blockIdx.y;
+  if (!active[p] || (int)blockIdx.x * 32 >= pd[p].m) return;
+  const GrpDesc d = pd[p];
+  const char* log = logs + d.olog;
+  apply_rotations_body<float>(Z + d.omm, d.m, reinterpret_cast<const double4*>(log + 256),
+                              reinterpret_cast<const int*>(log), blockIdx.x);
+}
+
 // Eigenvectors of the upper triangular T by back substitution, one per thread.
 template <typename T>
-__global__ void k_small_trevc(const cplx<T>* Tm, cplx<T>* V, int m) {
+__device__ __forceinline__ void small_trevc_body(const cplx<T>* Tm, cplx<T>* V, int m) {
   __shared__ T red[32];
   const int k = threadIdx.x;
   T loc = T(0);
@@ -303,8 +336,19 @@ __global__ void k_small_trevc(const cplx<T>* Tm, cplx<T>* V, int m) {
   }
 }
 
+template <typename T>
+__global__ void k_small_trevc(const cplx<T>* Tm, cplx<T>* V, int m) {
+  small_trevc_body<T>(Tm, V, m);
+}
+
+__global__ void k_small_trevc_grp(const float2* Tm, float2* V, const GrpDesc* pd, const int* active) {
+  const int p = blockIdx.x;
+  if (!active[p]) return;
+  small_trevc_body<float>(Tm + pd[p].omm, V + pd[p].omm, pd[p].m);
+}
+
 // lam = diag(E); D = I + Delta, Delta_ij = E_ij / (E_jj - E_ii) for well-separated pairs.
-__global__ void k_refine_step(const double2* E, double2* D, double2* lam, int m) {
+__device__ __forceinline__ void refine_step_body(const double2* E, double2* D, double2* lam, int m) {
   __shared__ double red[32];
   double loc = 0.0;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) loc = fmax(loc, cabs1<double>(E[idx]));
@@ -330,6 +374,15 @@ __global__ void k_refine_step(const double2* E, double2* D, double2* lam, int m)
       D[idx] = sep ? cdiv<double>(E[idx], gap) : make_double2(0.0, 0.0);
     }
   }
+}
+
+__global__ void k_refine_step(const double2* E, double2* D, double2* lam, int m) { refine_step_body(E, D, lam, m); }
+
+__global__ void k_refine_step_grp(const double2* E, double2* D, double2* lam, const GrpDesc* pd, const int* active) {
+  const int p = blockIdx.x;
+  if (!active[p]) return;
+  const GrpDesc d = pd[p];
+  refine_step_body(E + d.omm, D + d.omm, lam + d.om, d.m);
 }
 
 __global__ void k_to_c64(const double2* src, float2* dst, size_t count) {
@@ -397,5 +450,39 @@ cudaError_t to_c64(const double2* src, float2* dst, size_t count, cudaStream_t s
 cudaError_t to_c128(const float2* src, double2* dst, size_t count, cudaStream_t s) {
   feast_count_launch();
   k_to_c128<<<grid1(count), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- grouped forms
+cudaError_t small_schur_grp(float2* C, float2* Z, float2* lam, const GrpDesc* pd, int np, int mmax,
+                            const int* active, unsigned* flags, void* logs, cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  if (mmax < 1 || mmax > SCHUR_MAX_M) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(mmax * (mmax + 5) / 2 + 8) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_small_schur_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  feast_count_launch();
+  k_small_schur_grp<<<np, SCHUR_THREADS, smem, s>>>(C, Z, lam, pd, active, flags, reinterpret_cast<char*>(logs));
+  const size_t smem2 = (size_t)32 * (mmax + 1) * sizeof(float2);
+  e = cudaFuncSetAttribute(k_apply_rotations_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  if (e != cudaSuccess) return e;
+  feast_count_launch();
+  k_apply_rotations_grp<<<dim3((mmax + 31) / 32, np), 32, smem2, s>>>(Z, pd, active, reinterpret_cast<const char*>(logs));
+  return cudaGetLastError();
+}
+
+cudaError_t small_trevc_grp(const float2* Tm, float2* V, const GrpDesc* pd, int np, int mmax, const int* active,
+                            cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_small_trevc_grp<<<np, ((mmax + 31) / 32) * 32, 0, s>>>(Tm, V, pd, active);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_refine_step_grp(const double2* E, double2* D, double2* lam, const GrpDesc* pd, int np,
+                                const int* active, cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_refine_step_grp<<<np, 1024, 0, s>>>(E, D, lam, pd, active);
   return cudaGetLastError();
 }

@@ -69,11 +69,12 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
-__global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2(OrthArgs a) {
+// CTA g of the G that share one block Q.
+__device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const int G) {
   __shared__ double2 s_r[ORTH_MAX_M];
   __shared__ double red[ORTH_THREADS / 32];
   __shared__ int s_ok;
-  const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int n = a.n, m = a.m;
   const int r0 = min(n, g * a.rows_per), r1 = min(n, r0 + a.rows_per);
   double2* Q = a.Q;
@@ -118,10 +119,33 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2(OrthArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2(OrthArgs a) { orth_body(a, blockIdx.x, gridDim.x); }
+
+// Many blocks at once: CTAs [cta0[p], cta0[p+1]) orthonormalise pencil p's
+// block, with a grid barrier of their own (bars + 2 p).
+__global__ void __launch_bounds__(ORTH_THREADS)
+k_orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, double2* part, unsigned* bars,
+                const int* active, unsigned* flags) {
+  int p = 0;
+  while (p + 1 < np && cta0[p + 1] <= (int)blockIdx.x) ++p;
+  if (!active[p]) return;  // the whole group leaves together
+  const GrpDesc d = pd[p];
+  const int G = cta0[p + 1] - cta0[p];
+  OrthArgs a;
+  a.Q = Q + d.onm;
+  a.n = d.n;
+  a.m = d.m;
+  a.rows_per = (d.n + G - 1) / G;
+  a.part = part + (size_t)2 * cta0[p] * ORTH_MAX_M;
+  a.bar = bars + 2 * p;
+  a.flags = flags;
+  orth_body(a, blockIdx.x - cta0[p], G);
+}
+
 // ---------------------------------------------------------------- small LU
 constexpr int SMALL_THREADS = 1024;
 
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_lu(double2* M, int m, int* piv, unsigned* flags) {
+__device__ __forceinline__ void small_lu_body(double2* M, int m, int* piv, unsigned* flags) {
   __shared__ int s_p;
   const int tid = threadIdx.x;
   for (int k = 0; k < m; ++k) {
@@ -171,14 +195,26 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_lu(double2* M, int m, i
   }
 }
 
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_lu(double2* M, int m, int* piv, unsigned* flags) {
+  small_lu_body(M, m, piv, flags);
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_small_lu_grp(double2* M, const GrpDesc* pd, const int* active, int* piv, unsigned* flags) {
+  const int p = blockIdx.x;
+  if (!active[p]) return;
+  small_lu_body(M + pd[p].omm, pd[p].m, piv + pd[p].om, flags);
+}
+
 // One block per group of SOLVE_COLS right-hand sides (the factors are shared).
 constexpr int SOLVE_COLS = 8;
 
-__global__ void __launch_bounds__(SMALL_THREADS)
-k_small_lu_solve(const double2* LU, const int* piv, int m, double2* X, int nrhs, int trans) {
+__device__ __forceinline__ void small_lu_solve_body(const double2* LU, const int* piv, int m, double2* X, int nrhs,
+                                                    int trans, int bx) {
   const int tid = threadIdx.x;
-  X += (size_t)blockIdx.x * SOLVE_COLS * m;
-  nrhs = min(SOLVE_COLS, nrhs - (int)blockIdx.x * SOLVE_COLS);
+  X += (size_t)bx * SOLVE_COLS * m;
+  nrhs = min(SOLVE_COLS, nrhs - bx * SOLVE_COLS);
+  if (nrhs <= 0) return;
   auto Lx = [&](int i, int j) { return LU[i + (size_t)j * m]; };
   auto Xr = [&](int i, int c) -> double2& { return X[i + (size_t)c * m]; };
   if (trans == 0) {
@@ -231,6 +267,20 @@ k_small_lu_solve(const double2* LU, const int* piv, int m, double2* X, int nrhs,
   }
 }
 
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_small_lu_solve(const double2* LU, const int* piv, int m, double2* X, int nrhs, int trans) {
+  small_lu_solve_body(LU, piv, m, X, nrhs, trans, blockIdx.x);
+}
+
+// Square right-hand side per pencil (nrhs = m); grid (chunks of the largest m, pencils).
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_small_lu_solve_grp(const double2* LU, const int* piv, const GrpDesc* pd, const int* active, double2* X, int trans) {
+  const int p = blockIdx.y;
+  if (!active[p]) return;
+  const GrpDesc d = pd[p];
+  small_lu_solve_body(LU + d.omm, piv + d.om, d.m, X + d.omm, d.m, trans, blockIdx.x);
+}
+
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
@@ -269,6 +319,40 @@ cudaError_t small_lu_solve(const double2* LU, const int* piv, int m, double2* X,
                            cudaStream_t s) {
   feast_count_launch();
   k_small_lu_solve<<<(nrhs + SOLVE_COLS - 1) / SOLVE_COLS, SMALL_THREADS, 0, s>>>(LU, piv, m, X, nrhs, trans);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- grouped forms
+int orth_grp_ctas_per_sm() {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_orth_cgs2_grp, ORTH_THREADS, 0);
+  return per;
+}
+
+cudaError_t orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, int total_ctas, double2* part,
+                          unsigned* bars, const int* active, unsigned* flags, cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(bars, 0, sizeof(unsigned) * 2 * np, s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&Q, &pd, &cta0, &np, &part, &bars, &active, &flags};
+  feast_count_launch();
+  return cudaLaunchCooperativeKernel((void*)k_orth_cgs2_grp, dim3(total_ctas), dim3(ORTH_THREADS), args, 0, s);
+}
+
+cudaError_t small_lu_grp(double2* M, const GrpDesc* pd, int np, const int* active, int* piv, unsigned* flags,
+                         cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_small_lu_grp<<<np, SMALL_THREADS, 0, s>>>(M, pd, active, piv, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t small_lu_solve_grp(const double2* LU, const int* piv, const GrpDesc* pd, int np, int mmax,
+                               const int* active, double2* X, int trans, cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_small_lu_solve_grp<<<dim3((mmax + SOLVE_COLS - 1) / SOLVE_COLS, np), SMALL_THREADS, 0, s>>>(LU, piv, pd, active,
+                                                                                                 X, trans);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // for the orthonormal bases of the filtered blocks.
 #pragma once
 #include "common.cuh"
+#include "batch.cuh"
 
 // In-place orthonormalisation of the n x m block Q (ld n) by classical
 // Gram-Schmidt applied twice, one cooperative launch with bounded grid barriers.
@@ -34,3 +35,25 @@ cudaError_t eig_refine_step(const double2* E, double2* D, double2* lam, int m, c
 // Element-wise precision conversions.
 cudaError_t to_c64(const double2* src, float2* dst, size_t count, cudaStream_t s);
 cudaError_t to_c128(const float2* src, double2* dst, size_t count, cudaStream_t s);
+
+// ---- grouped forms: one launch for every active pencil of a batch (GrpDesc
+// offsets into the n x m, m x m and length-m arenas).
+// CTAs [cta0[p], cta0[p+1]) orthonormalise pencil p's block of the n x m arena;
+// a cooperative launch of total_ctas = cta0[np] CTAs (at most the resident
+// count: orth_grp_ctas_per_sm() per SM).  part: 2 * total_ctas * 256 double2;
+// bars: 2 * np unsigned.
+int orth_grp_ctas_per_sm();
+cudaError_t orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, int total_ctas, double2* part,
+                          unsigned* bars, const int* active, unsigned* flags, cudaStream_t s);
+cudaError_t small_lu_grp(double2* M, const GrpDesc* pd, int np, const int* active, int* piv, unsigned* flags,
+                         cudaStream_t s);
+// X_p (m x m) <- M_p^{-1} X_p (trans 0) or M_p^{-H} X_p (trans 1)
+cudaError_t small_lu_solve_grp(const double2* LU, const int* piv, const GrpDesc* pd, int np, int mmax,
+                               const int* active, double2* X, int trans, cudaStream_t s);
+// Schur form of C_p (FP32), Schur vectors Z_p, eigenvalues lam_p; rotation logs at olog.
+cudaError_t small_schur_grp(float2* C, float2* Z, float2* lam, const GrpDesc* pd, int np, int mmax,
+                            const int* active, unsigned* flags, void* logs, cudaStream_t s);
+cudaError_t small_trevc_grp(const float2* Tm, float2* V, const GrpDesc* pd, int np, int mmax, const int* active,
+                            cudaStream_t s);
+cudaError_t eig_refine_step_grp(const double2* E, double2* D, double2* lam, const GrpDesc* pd, int np,
+                                const int* active, cudaStream_t s);

@@ -128,6 +128,29 @@ def pml_laplacian(nx=90, layer=10, sigma_max=50.0, m_low=60):
                 N_e=16, m0=96, sigma=sig)
 
 
+def batch_sizes(count=64, n_lo=256, n_hi=2048, m_lo=20, m_hi=80, seed=41):
+    """Orders n_p log-uniform in [n_lo, n_hi], inside counts m_p uniform in
+    {m_lo..m_hi} and subspace sizes m0_p = clamp(8 ceil(1.6 m_p / 8), 32, 128)."""
+    rng = np.random.default_rng(seed)
+    n = np.rint(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count))).astype(int)
+    m_in = rng.integers(m_lo, m_hi + 1, count)
+    m0 = np.clip(8 * np.ceil(1.6 * m_in / 8), 32, 128).astype(int)
+    centers = rng.uniform(-2.0, 2.0, count) + 1j * rng.uniform(-2.0, 2.0, count)
+    radii = rng.uniform(0.5, 2.0, count)
+    return n, m_in, m0, centers, radii
+
+
+def batch_prescribed(count=64, n_lo=256, n_hi=2048, m_lo=20, m_hi=80, seed=41, cond=100.0):
+    """Many independent standard pencils (the batched workload): pencil p is
+    prescribed(n_p, m_in_p, cond) around its own circle (centre c_p uniform in
+    [-2, 2] + i[-2, 2], radius r_p uniform in [0.5, 2]) with 8 midpoint
+    trapezoid nodes, sizes from batch_sizes.  Returns a list of prescribed()
+    dictionaries."""
+    n, m_in, m0, centers, radii = batch_sizes(count, n_lo, n_hi, m_lo, m_hi, seed)
+    return [prescribed(n=int(n[p]), m_in=int(m_in[p]), cond=cond, seed=seed * 1000 + p, m0=int(m0[p]),
+                       center=complex(centers[p]), radius=float(radii[p])) for p in range(count)]
+
+
 def random_block(n, m, seed):
     """A seeded complex Gaussian n x m block."""
     return cgauss(np.random.default_rng(seed), n, m)
