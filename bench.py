@@ -46,11 +46,31 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     p.add_argument("--solve-iters", type=int, default=20)
+    p.add_argument("--no-batch", action="store_true", help="skip the batched 64-pencil workload")
+    p.add_argument("--batch-count", type=int, default=64)
+    p.add_argument("--batch-only", action="store_true", help="run only the batched workload (prints its object)")
     return p.parse_args()
 
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values (every rank gets it); identity at N = 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seeds(rank):
+    """Per-rank workload seeds: every rank gets its own pencil and its own batch
+    (independent problems, weak scaling, no data-path collective)."""
+    return {"pencil": 2 + rank, "batch": 41 + 1000 * rank}
 
 
 # ---------------------------------------------------------------- clocks
@@ -185,6 +205,83 @@ def trailing_update_flops(n, q, nb):
     return q * tot
 
 
+def trailing_update_bytes(n, q, nb):
+    """Algorithmic HBM bytes of all trailing updates: the complex64 C block read
+    and written once, the L21 and U12 panels read once (8 bytes per entry)."""
+    tot = 0.0
+    for k0 in range(0, n, nb):
+        w = min(nb, n - k0)
+        rest = n - k0 - w
+        tot += 8.0 * (2 * rest * rest + 2 * rest * w)
+    return q * tot
+
+
+def profiled_traffic_ratio():
+    """DRAM bytes per algorithmic byte of the trailing-update kernel, from the
+    committed ncu summary (None when absent)."""
+    import re
+    path = os.path.join(ROOT, "profiles", "k_tc_update_bifeast_n2048_mixed.md")
+    try:
+        m = re.search(r"traffic_per_algorithmic_byte:\s*([0-9.]+)", open(path).read())
+        return float(m.group(1)) if m else None
+    except OSError:
+        return None
+
+
+def run_batch(fg, torch, args, barrier):
+    """The batched workload: 64 standard pencils, n log-uniform in [256, 2048],
+    20-80 eigenvalues inside each circle, 8 midpoint nodes each (512 shifted
+    matrices), R-FEAST in mixed precision, the factorisations and solves in
+    one persistent launch."""
+    import workloads
+    rank = dist_env()[0]
+    cfgs = workloads.batch_prescribed(count=args.batch_count, seed=rank_seeds(rank)["batch"])
+    cons = [fg.make_contour(center=c["contour"]["c"], R=c["contour"]["R"], aspect=c["contour"]["a"],
+                            rule=c["contour"]["rule"], N_e=c["N_e"]) for c in cfgs]
+    opts = fg.make_options(algo="R", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True)
+    A_d = [colmajor_device(torch, c["A"]) for c in cfgs]
+    Y_d = [colmajor_device(torch, c["U0"]) for c in cfgs]
+    b = fg.feast_batch_create(A_d, cons, [c["m0"] for c in cfgs], opts)
+    info = fg.feast_batch_info(b)
+    for _ in range(max(1, args.warmup)):
+        fg.feast_batch_factor(b)
+    lu = []
+    for _ in range(max(1, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        fg.feast_batch_factor(b)
+        e1.record()
+        barrier()
+        lu.append(e0.elapsed_time(e1))
+    out, st = fg.feast_batch_solve(b, Y_d)
+    barrier()
+    t0 = time.perf_counter()
+    out, st = fg.feast_batch_solve(b, Y_d)
+    barrier()
+    solve_ms = (time.perf_counter() - t0) * 1e3
+    worst, count_ok = 0.0, 0
+    for c, o in zip(cfgs, out):
+        if o["m_found"]:
+            X = o["X"]
+            nA = np.linalg.norm(c["A"], 2)
+            r = np.linalg.norm(c["A"] @ X - X * o["lam"][None, :], axis=0) / (nA * np.linalg.norm(X, axis=0))
+            worst = max(worst, float(r.max()))
+        count_ok += int(o["m_found"] == len(c["lam_inside"]))
+    lu_ms = float(np.median(lu))
+    it = st["t_iter_ms"]
+    fg.feast_batch_destroy(b)
+    return {"workload": (f"{args.batch_count} standard pencils A_p = V diag(lam) V^-1 (cond(V)=100), n log-uniform in "
+                         "[256, 2048], 20-80 eigenvalues inside each circle, 8 midpoint nodes, m0 in 32..128, "
+                         "R-FEAST mixed"),
+            "pencils": info["count"], "shifted_matrices": info["nmat"], "persistent_ctas": info["grid"],
+            "factor_tasks": info["tasks_factor"], "lu_ms": lu_ms,
+            "lu_tflops": info["lu_flops"] / (lu_ms * 1e-3) / 1e12,
+            "iter1_ms": it[0] if it else None, "steady_iter_ms": float(np.median(it[1:])) if len(it) > 1 else None,
+            "iters": st["iters"], "converged": st["converged"], "counts_exact": count_ok,
+            "max_res": worst, "solve_ms": solve_ms, "graph": st["graph"]}
+
+
 def run_ours(args):
     import torch
     import paper_1404_2891_gb300 as fg
@@ -199,9 +296,16 @@ def run_ours(args):
     build.build()
     fg.load()
 
+    if args.batch_only:
+        def sync():
+            torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"batched": run_batch(fg, torch, args, sync)}))
+        return
+
     n, m0, K = args.n, args.m0, args.K
     q = 2 * K
-    cfg = workloads.gaussian_pencil(n=n, seed=2 + rank, m0=m0, K=K)
+    cfg = workloads.gaussian_pencil(n=n, seed=rank_seeds(rank)["pencil"], m0=m0, K=K)
     c = cfg["contour"]
     contour = fg.make_contour(center=c["c"], R=c["R"], aspect=c["a"], rule=c["rule"], N_e=K)
     stream = torch.cuda.Stream()
@@ -215,13 +319,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     def step(h):
         fg.feast_factor(h)
@@ -277,7 +374,7 @@ def run_ours(args):
     barrier()
     launches = fg.feast_kernel_launches() - launches0
     clk = clocks.stop()
-    iter_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    iter_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     steady_ms = timed(steady, h, max(1, args.steps))
     lu_mean = float(np.mean(lu_ms))
     nb = 64
@@ -321,7 +418,7 @@ def run_ours(args):
         for _ in range(ne):
             e2e_step()
         barrier()
-        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / ne)
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / ne, world)
         h2d = (2 * n * n + 2 * n * m0) * 16 * 2 + 2 * n * m0 * 16  # A, B, Y, V in; Q, Qhat back in for RR
         d2h = 2 * n * m0 * 16 * 2 + m0 * (16 + 8)  # Q, Qhat out; X, Xl, lambda, res out
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -332,19 +429,31 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         _, cpu = cpu_baseline_sample(n, q, m0)
 
+    batched = None
+    if not args.no_batch:
+        batched = run_batch(fg, torch, args, barrier)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    bf16_sust = peaks.get("bf16_tflops_sustained", 1700.0)
-    achieved = upd_flops / (upd_time * 1e-3) / 1e12 if upd_time > 0 else 0.0
-    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
-    roofline = {"kernel": "LU trailing update A22 -= L21 U12 (complex64)", "bound": "alu", "achieved": achieved,
-                "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
-                "launches": upd_n, "avg_launch_ms": upd_time / max(upd_n, 1),
-                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)",
-                "bf16_sustained_measured": bf16_sust}
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    if hbm is None:
+        hbm, peak_note = 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
+    # dominant kernel: the tcgen05 trailing update, HBM-bound (C streamed once per launch)
+    upd_n = max(upd_n, 1)
+    avg_launch_s = upd_time * 1e-3 / upd_n
+    bytes_per_launch = trailing_update_bytes(n, q, nb) / upd_n
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if upd_time > 0 else 0.0
+    ratio = profiled_traffic_ratio()
+    roofline = {"kernel": "k_tc_update: LU trailing update A22 -= L21 U12 (complex64 C, split-BF16 tcgen05)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": (ratio * bytes_per_launch) if ratio else None,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "launches": upd_n,
+                "avg_launch_ms": avg_launch_s * 1e3, "peak_note": peak_note,
+                "tensor_tflops_algorithmic": upd_flops / (upd_time * 1e-3) / 1e12 if upd_time > 0 else 0.0}
     if rank == 0:
         line = {
             "metric": METRIC, "value": iter_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -362,7 +471,7 @@ def run_ours(args):
                       "converged": sol["converged"], "max_res": float(np.max(resid)),
                       "res_hist": sol["res_hist"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches), "batched": batched,
         }
         print(json.dumps(line))
     if world > 1:

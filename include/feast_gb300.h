@@ -299,7 +299,9 @@ typedef struct {
   int converged;            /* pencils that met the Sec. 5 test                     */
   int tasks_factor;         /* tasks of the persistent factorisation launch         */
   int grid;                 /* CTAs of the persistent launch                        */
-  int graph;                /* 1 if the steady iterations replayed a CUDA graph     */
+  int graph;                /* 1 if the steady iterations replayed a CUDA graph;
+                               -e if capturing them failed with cudaError_t e and
+                               they ran as ordinary launches                         */
   double plan_makespan_us;  /* makespan of the host schedule's cost model           */
   double t_factor_ms;       /* first launch (factorisations + first solves), timing */
   double t_iter_ms[64];     /* wall time of each iteration, timing option           */

@@ -208,6 +208,7 @@ struct GG {  // one grouped GEMM call site
   void* tab = nullptr;
   int* tstart = nullptr;
   int total = 0;
+  size_t split_mn = 0;
   bool f32 = false;
 };
 
@@ -217,6 +218,7 @@ struct feast_batch {
   int np = 0, nmat = 0, Nmax = 0, nmax = 0, mmax = 0;
   feast_options opt;
   cudaStream_t st = nullptr;
+  cudaStream_t own_stream = nullptr;  // created when the caller passes no stream (the legacy stream cannot be captured)
   std::vector<GrpDesc> pd;
   std::vector<BMat> mats;
   std::vector<std::vector<zc>> z, w;
@@ -257,6 +259,7 @@ struct feast_batch {
   double* h_res = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool graph_failed = false;
+  int graph_err = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
@@ -293,16 +296,42 @@ BatchLuArgs lu_args(feast_batch* b, const int4* tasks, int ntasks) {
   return a;
 }
 
+// One grouped GEMM call site: entries ordered by per-tile work (longest first,
+// so the long-K tiles do not form the tail), complex128 products with few
+// output tiles and a long K cut into K-chunks of at least 256.
 template <typename T>
 feast_status make_gg(feast_batch* b, GG& g, const std::function<GemmArgs<T>(const GrpDesc&)>& f) {
   std::vector<GemmArgs<T>> tab(b->np);
-  std::vector<int> ts(b->np + 1, 0);
+  size_t ws_total = 0;
   for (int p = 0; p < b->np; ++p) {
     tab[p] = f(b->pd[p]);
     tab[p].batch = 1;
-    tab[p].splitk = 1;
-    ts[p + 1] = ts[p] + gemm_tiles(tab[p].M, tab[p].N);
+    tab[p].tag = p;
+    int sk = 1;
+    if (!std::is_same<T, float>::value && gemm_tiles(tab[p].M, tab[p].N) <= 4 && tab[p].K >= 512)
+      sk = std::min(8, tab[p].K / 256);
+    tab[p].splitk = sk;
+    if (sk > 1) {
+      ws_total += (size_t)sk * tab[p].M * tab[p].N;
+      g.split_mn = std::max(g.split_mn, (size_t)tab[p].M * tab[p].N);
+    }
   }
+  std::stable_sort(tab.begin(), tab.end(), [](const GemmArgs<T>& x, const GemmArgs<T>& y) {
+    return (long long)x.K / x.splitk > (long long)y.K / y.splitk;
+  });
+  if (ws_total) {
+    cplx<T>* ws = nullptr;
+    CK(dalloc(b, &ws, ws_total * sizeof(cplx<T>)));
+    size_t off = 0;
+    for (auto& e : tab)
+      if (e.splitk > 1) {
+        e.ws = ws + off;
+        e.ws_elems = (size_t)e.splitk * e.M * e.N;
+        off += e.ws_elems;
+      }
+  }
+  std::vector<int> ts(b->np + 1, 0);
+  for (int p = 0; p < b->np; ++p) ts[p + 1] = ts[p] + gemm_tiles(tab[p].M, tab[p].N) * tab[p].splitk;
   CK(dalloc(b, &g.tab, tab.size() * sizeof(GemmArgs<T>)));
   CK(dalloc(b, &g.tstart, ts.size() * sizeof(int)));
   CK(cudaMemcpyAsync(g.tab, tab.data(), tab.size() * sizeof(GemmArgs<T>), cudaMemcpyHostToDevice, b->st));
@@ -316,9 +345,9 @@ feast_status make_gg(feast_batch* b, GG& g, const std::function<GemmArgs<T>(cons
 cudaError_t run_gg(feast_batch* b, const GG& g) {
   if (g.f32)
     return gemm_grouped<float>(reinterpret_cast<const GemmArgs<float>*>(g.tab), g.tstart, b->np, g.total, b->active,
-                               b->st);
+                               0, b->st);
   return gemm_grouped<double>(reinterpret_cast<const GemmArgs<double>*>(g.tab), g.tstart, b->np, g.total, b->active,
-                              b->st);
+                              g.split_mn, b->st);
 }
 
 GemmArgs<double> zargs(int M, int N, int K, const double2* A, long long lda, int opA, const double2* B, long long ldb,
@@ -503,6 +532,7 @@ void feast_batch_destroy(feast_batch* b) {
     if (p) cudaFreeHost(p);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
   delete b;
 }
 
@@ -544,6 +574,11 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
   auto bad = [&](feast_status s) { feast_batch_destroy(b); return s; };
   if (b->opt.algo != FEAST_ALGO_R || b->opt.precision != FEAST_PREC_MIXED) return bad(FEAST_ERR_ARG);
   b->st = reinterpret_cast<cudaStream_t>(stream);
+  if (!b->st) {
+    // a blocking stream: it stays ordered with the legacy default stream
+    if (cudaStreamCreate(&b->own_stream) != cudaSuccess) return bad(FEAST_ERR_CUDA);
+    b->st = b->own_stream;
+  }
   b->np = count;
   b->pd.resize(count);
   b->z.resize(count);
@@ -900,6 +935,7 @@ feast_status feast_batch_solve(feast_batch* b, const feast_z* const* Y0, feast_z
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
           cudaGetLastError();
+          b->graph_err = (int)e;
           if (b->gexec) cudaGraphExecDestroy(b->gexec);
           b->gexec = nullptr;
           b->graph_failed = true;
@@ -911,7 +947,10 @@ feast_status feast_batch_solve(feast_batch* b, const feast_z* const* Y0, feast_z
         st.graph = 1;
       }
     }
-    if (!done) CK(enqueue_steady(b));
+    if (!done) {
+      st.graph = -b->graph_err;  // the capture's CUDA error, negated
+      CK(enqueue_steady(b));
+    }
     CK(cudaStreamSynchronize(b->st));
     FS(read_flags(b));
     if (b->opt.timing) {

@@ -145,17 +145,35 @@ __device__ __forceinline__ void zgemm_body(const GemmArgs<double>& g, const int 
 
 __global__ void __launch_bounds__(256) k_zgemm_dmma(GemmArgs<double> g) { zgemm_body(g, blockIdx.x, blockIdx.y, blockIdx.z); }
 
-// Grouped form: tiles [tstart[p], tstart[p+1]) of the grid belong to problem p
-// (one M x N product per pencil, no split-K).
+// Grouped form: tiles [tstart[p], tstart[p+1]) of the grid belong to entry p
+// of the table (tm x tn x splitk tiles; split-K partials go to the entry's ws).
 __global__ void __launch_bounds__(256)
 k_zgemm_dmma_grp(const GemmArgs<double>* tab, const int* tstart, int np, const int* active) {
   const int t = blockIdx.x;
   int p = 0;
   while (p + 1 < np && tstart[p + 1] <= t) ++p;
-  if (!active[p]) return;
   const GemmArgs<double> g = tab[p];
-  const int local = t - tstart[p], tm = (g.M + BM - 1) / BM;
-  zgemm_body(g, local % tm, local / tm, 0);
+  if (!active[g.tag]) return;
+  const int local = t - tstart[p], tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
+  const int rest = local / tm;
+  zgemm_body(g, local % tm, rest % tn, rest / tn);
+}
+
+// C = alpha * sum_s P_s + beta * C for the split entries of a grouped call (fixed order in s).
+__global__ void k_splitk_reduce_grp(const GemmArgs<double>* tab, const int* active) {
+  const GemmArgs<double> g = tab[blockIdx.y];
+  if (g.splitk < 2 || !active[g.tag]) return;
+  const size_t mn = (size_t)g.M * g.N;
+  const bool beta_zero = (g.beta.x == 0.0 && g.beta.y == 0.0);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mn; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % g.M), c = (int)(e / g.M);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int sp = 0; sp < g.splitk; ++sp) acc = cadd<double>(acc, g.ws[sp * mn + e]);
+    double2* q = g.C + (size_t)r + (size_t)c * g.ldc;
+    double2 out = cmul<double>(g.alpha, acc);
+    if (!beta_zero) out = cadd<double>(out, cmul<double>(g.beta, *q));
+    *q = out;
+  }
 }
 
 // ---------------------------------------------------------------- FP32 SIMT
@@ -226,8 +244,8 @@ k_cgemm_simt_grp(const GemmArgs<float>* tab, const int* tstart, int np, const in
   const int t = blockIdx.x;
   int p = 0;
   while (p + 1 < np && tstart[p + 1] <= t) ++p;
-  if (!active[p]) return;
   const GemmArgs<float> g = tab[p];
+  if (!active[g.tag]) return;
   const int local = t - tstart[p], tm = (g.M + BM - 1) / BM;
   cgemm_body(g, local % tm, local / tm, 0);
 }
@@ -291,16 +309,22 @@ cudaError_t gemm_batched<float>(const GemmArgs<float>& g, cudaStream_t s) {
 
 template <>
 cudaError_t gemm_grouped<double>(const GemmArgs<double>* tab, const int* tstart, int np, int total_tiles,
-                                 const int* active, cudaStream_t s) {
+                                 const int* active, size_t split_mn, cudaStream_t s) {
   if (np < 1 || total_tiles < 1) return cudaSuccess;
   feast_count_launch();
   k_zgemm_dmma_grp<<<total_tiles, 256, 0, s>>>(tab, tstart, np, active);
+  if (split_mn > 0) {
+    const size_t want = (split_mn + 255) / 256;
+    feast_count_launch();
+    k_splitk_reduce_grp<<<dim3((unsigned)(want < 64 ? want : 64), np), 256, 0, s>>>(tab, active);
+  }
   return cudaGetLastError();
 }
 
 template <>
 cudaError_t gemm_grouped<float>(const GemmArgs<float>* tab, const int* tstart, int np, int total_tiles,
-                                const int* active, cudaStream_t s) {
+                                const int* active, size_t split_mn, cudaStream_t s) {
+  (void)split_mn;
   if (np < 1 || total_tiles < 1) return cudaSuccess;
   feast_count_launch();
   k_cgemm_simt_grp<<<total_tiles, 256, 0, s>>>(tab, tstart, np, active);

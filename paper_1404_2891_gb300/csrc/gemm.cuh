@@ -22,16 +22,21 @@ struct GemmArgs {
   // summed in a fixed order by a second kernel (deterministic).
   cplx<T>* ws = nullptr;
   size_t ws_elems = 0;
-  int splitk = 1;  // set by gemm_batched
+  int splitk = 1;  // set by gemm_batched; chosen by the caller for gemm_grouped
+  int tag = 0;     // gemm_grouped: the problem's index into `active`
 };
 
 template <typename T>
 cudaError_t gemm_batched(const GemmArgs<T>& g, cudaStream_t s);
 
-// Grouped GEMM: problem p (tab[p] in device memory, batch = 1) owns grid tiles
-// [tstart[p], tstart[p+1]) with tstart[p+1] - tstart[p] = gemm_tiles(M_p, N_p);
-// problems with active[p] == 0 are skipped.
+// Grouped GEMM: table entry p (tab[p] in device memory, batch = 1) owns grid
+// tiles [tstart[p], tstart[p+1]), tstart[p+1] - tstart[p] =
+// gemm_tiles(M_p, N_p) * splitk_p; entries with active[tag_p] == 0 are skipped.
+// complex128 entries with splitk_p > 1 write K-chunk partials to their ws
+// (splitk_p * M_p * N_p elements) and a second kernel sums them in a fixed
+// order; split_mn = the largest M_p * N_p among such entries (0: none).
+// complex64 entries must have splitk_p = 1.
 template <typename T>
 cudaError_t gemm_grouped(const GemmArgs<T>* tab, const int* tstart, int np, int total_tiles, const int* active,
-                         cudaStream_t s);
+                         size_t split_mn, cudaStream_t s);
 int gemm_tiles(int M, int N);
