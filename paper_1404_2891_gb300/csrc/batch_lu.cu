@@ -26,6 +26,7 @@
 // the output tile, and the 64 x 64 triangular solves run one warp per 8 (or 4)
 // columns with shuffles and no block barriers.
 #include "batch.cuh"
+#include "panel_ll.cuh"
 
 namespace {
 
@@ -34,10 +35,9 @@ constexpr int TT = BATCH_TILE * BATCH_TILE;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 struct Shared {
-  int task, ok, piv, cnt;
-  float wv[NT / 32];
-  int wi[NT / 32];
-  int mvd[BATCH_MAXMV], mvs[BATCH_MAXMV], tmp[BATCH_MAXMV];
+  int task, ok;
+  int tmp[BATCH_MAXMV];
+  PanelShared ps;
 };
 
 __device__ __forceinline__ unsigned long long gtime() {
@@ -212,162 +212,23 @@ __device__ void apply_moves(float2* A, int N, int r0, int c0, const int* mvp, fl
 }
 
 // ---------------------------------------------------------------- PANEL
-// Left-looking within the panel, GW columns at a time: the group is gathered
-// in logical row order into shared memory, brought up to date with the
-// panel's earlier columns (unit-lower solve for its U rows, then a product
-// with the earlier L columns for the rest), and factored there with a
-// block-wide pivot search per column.  Rows are never moved in memory while
-// the panel is factored; `pl` maps logical to physical rows, and the moved
-// rows are written in logical order at the end.
+// The shared left-looking panel (panel_ll.cuh), then the batch bookkeeping:
+// the moved-row list for the update and fix-up tasks, the release of the
+// panel, and after the last panel the composed row permutation.
 template <int GW>
 __device__ void panel_task(const BatchLuArgs& a, const BMat& M, int mat, int k, char* smem, int gcap, Shared& sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int N = M.N, r0 = k * 64, R = N - r0;
+  const int tid = threadIdx.x;
+  const int N = M.N, r0 = k * 64;
   float2* A = a.S + M.soff;
   float2* Lt = reinterpret_cast<float2*>(smem);
   float2* G = Lt + TT;
   int* pl = reinterpret_cast<int*>(G + gcap);
-  for (int r = tid; r < R; r += NT) pl[r] = r;
-  __syncthreads();
-  for (int g0 = 0; g0 < 64; g0 += GW) {
-    for (int idx = tid; idx < R * GW; idx += NT) {
-      const int c = idx / R, r = idx - c * R;
-      G[idx] = __ldcg(A + (size_t)(r0 + pl[r]) + (size_t)(r0 + g0 + c) * N);
-    }
-    for (int idx = tid; idx < 64 * g0; idx += NT) {
-      const int t = idx >> 6, r = idx & 63;
-      Lt[idx] = __ldcg(A + (size_t)(r0 + pl[r]) + (size_t)(r0 + t) * N);
-    }
-    __syncthreads();
-    if (g0 > 0) {
-      // U rows of the group: forward substitution with L[0:g0, 0:g0]
-      if (warp < GW) {
-        float2* Gc = G + warp * R;
-        float2 x0 = lane < g0 ? Gc[lane] : make_float2(0.f, 0.f);
-        float2 x1 = lane + 32 < g0 ? Gc[lane + 32] : make_float2(0.f, 0.f);
-        for (int t = 0; t < g0 - 1; ++t) {
-          const float2 xt = shfl2(t < 32 ? x0 : x1, t & 31);
-          const float2 l0 = Lt[t * 64 + lane], l1 = Lt[t * 64 + lane + 32];
-          if (lane > t && lane < g0) x0 = csub<float>(x0, cmul<float>(l0, xt));
-          if (lane + 32 > t && lane + 32 < g0) x1 = csub<float>(x1, cmul<float>(l1, xt));
-        }
-        if (lane < g0) Gc[lane] = x0;
-        if (lane + 32 < g0) Gc[lane + 32] = x1;
-      }
-      __syncthreads();
-      // remaining rows: G[r, c] -= sum_{t < g0} L[r, t] U[t, c]
-      for (int r = g0 + tid; r < R; r += NT) {
-        float2 acc[GW];
-#pragma unroll
-        for (int c = 0; c < GW; ++c) acc[c] = make_float2(0.f, 0.f);
-        const float2* Lrow = A + (size_t)(r0 + pl[r]) + (size_t)r0 * N;
-#pragma unroll 8
-        for (int t = 0; t < g0; ++t) {
-          const float2 l = __ldcg(Lrow + (size_t)t * N);
-#pragma unroll
-          for (int c = 0; c < GW; ++c) cfma<float>(acc[c], l, G[c * R + t]);
-        }
-#pragma unroll
-        for (int c = 0; c < GW; ++c) G[c * R + r] = csub<float>(G[c * R + r], acc[c]);
-      }
-      __syncthreads();
-    }
-    // factor the group's columns
-    for (int c = 0; c < GW; ++c) {
-      const int col = g0 + c;
-      float2* Gc = G + c * R;
-      float best = -1.f;
-      int bi = R;
-      for (int r = col + tid; r < R; r += NT) {
-        const float v = cabs1<float>(Gc[r]);
-        if (v > best) { best = v; bi = r; }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float v2 = __shfl_down_sync(0xffffffffu, best, off);
-        const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
-        if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
-      }
-      if (lane == 0) { sh.wv[warp] = best; sh.wi[warp] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        float b = sh.wv[0];
-        int p = sh.wi[0];
-        for (int w = 1; w < NT / 32; ++w)
-          if (sh.wv[w] > b || (sh.wv[w] == b && sh.wi[w] < p)) { b = sh.wv[w]; p = sh.wi[w]; }
-        if (p >= R) { p = col; atomicOr(a.flags, (unsigned)DEVFLAG_NONFINITE); }
-        sh.piv = p;
-        a.piv[M.poff + r0 + col] = r0 + p;
-      }
-      __syncthreads();
-      const int p = sh.piv;
-      if (p != col) {
-        if (tid < GW) {
-          const float2 t0 = G[tid * R + col];
-          G[tid * R + col] = G[tid * R + p];
-          G[tid * R + p] = t0;
-        }
-        if (tid == 0) {
-          const int t1 = pl[col];
-          pl[col] = pl[p];
-          pl[p] = t1;
-        }
-        __syncthreads();
-      }
-      const float2 d = Gc[col];
-      if (d.x == 0.f && d.y == 0.f) {
-        if (tid == 0) {
-          atomicCAS(a.info + mat, 0, r0 + col + 1);
-          atomicOr(a.flags, (unsigned)DEVFLAG_SINGULAR);
-        }
-      } else {
-        const float2 inv = crecip<float>(d);
-        for (int r = col + 1 + tid; r < R; r += NT) {
-          const float2 l = cmul<float>(Gc[r], inv);
-          Gc[r] = l;
-#pragma unroll
-          for (int c2 = c + 1; c2 < GW; ++c2) G[c2 * R + r] = csub<float>(G[c2 * R + r], cmul<float>(l, G[c2 * R + col]));
-        }
-      }
-      __syncthreads();
-    }
-    for (int idx = tid; idx < R * GW; idx += NT) {
-      const int c = idx / R, r = idx - c * R;
-      A[(size_t)(r0 + pl[r]) + (size_t)(r0 + g0 + c) * N] = G[idx];
-    }
-    __syncthreads();
-  }
-  // moved rows: logical row dst takes physical row src
-  if (tid == 0) sh.cnt = 0;
-  __syncthreads();
-  for (int r = tid; r < R; r += NT)
-    if (pl[r] != r) {
-      const int e = atomicAdd(&sh.cnt, 1);
-      if (e < BATCH_MAXMV) { sh.mvd[e] = r; sh.mvs[e] = pl[r]; }
-    }
-  __syncthreads();
-  int cnt = sh.cnt;
-  if (cnt > BATCH_MAXMV) {  // cannot happen: 64 interchanges move at most 128 rows
-    if (tid == 0) atomicOr(a.flags, (unsigned)DEVFLAG_BADARG);
-    cnt = BATCH_MAXMV;
-  }
-  // put the panel's own columns in logical order (32 columns at a time through Lt)
-  for (int half = 0; half < 2; ++half) {
-    for (int idx = tid; idx < cnt * 32; idx += NT) {
-      const int e = idx % cnt, c = idx / cnt;
-      Lt[idx] = __ldcg(A + (size_t)(r0 + sh.mvs[e]) + (size_t)(r0 + 32 * half + c) * N);
-    }
-    __syncthreads();
-    for (int idx = tid; idx < cnt * 32; idx += NT) {
-      const int e = idx % cnt, c = idx / cnt;
-      A[(size_t)(r0 + sh.mvd[e]) + (size_t)(r0 + 32 * half + c) * N] = Lt[idx];
-    }
-    __syncthreads();
-  }
+  panel_ll<GW, NT>(A, N, N, r0, 64, a.piv + M.poff + r0, a.info + mat, a.flags, Lt, G, pl, sh.ps);
+  const int cnt = sh.ps.cnt;
   int* mvp = a.mv + (size_t)(M.coff + k) * BATCH_MVSTRIDE;
   for (int e = tid; e < cnt; e += NT) {
-    mvp[1 + 2 * e] = sh.mvd[e];
-    mvp[2 + 2 * e] = sh.mvs[e];
+    mvp[1 + 2 * e] = sh.ps.mvd[e];
+    mvp[2 + 2 * e] = sh.ps.mvs[e];
   }
   if (tid == 0) mvp[0] = cnt;
   __syncthreads();
@@ -572,8 +433,12 @@ __global__ void __launch_bounds__(NT, 1) k_batch_lu(BatchLuArgs a, int gcap) {
     if (!sh.ok) return;
     switch (tk.x) {
       case BT_PANEL:
-        if (M.N - 64 * tk.z <= 2048) panel_task<8>(a, M, tk.y, tk.z, smem, gcap, sh);
-        else panel_task<4>(a, M, tk.y, tk.z, smem, gcap, sh);
+        switch (panel_group_width(M.N - 64 * tk.z, gcap)) {
+          case 8: panel_task<8>(a, M, tk.y, tk.z, smem, gcap, sh); break;
+          case 4: panel_task<4>(a, M, tk.y, tk.z, smem, gcap, sh); break;
+          case 2: panel_task<2>(a, M, tk.y, tk.z, smem, gcap, sh); break;
+          default: panel_task<1>(a, M, tk.y, tk.z, smem, gcap, sh); break;
+        }
         break;
       case BT_UPDATE: update_task(a, M, tk.z, tk.w, smem); break;
       case BT_LSWAP: lswap_task(a, M, tk.y, tk.w, smem); break;

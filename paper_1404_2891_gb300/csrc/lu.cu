@@ -11,6 +11,7 @@
 
 #include <type_traits>
 
+#include "panel_ll.cuh"
 #include "tc_update.cuh"
 
 namespace {
@@ -278,6 +279,55 @@ __global__ void k_rows_scatter(const cplx<T>* V, const int32_t* perm, cplx<T>* O
 template <typename T>
 size_t diag_smem(int w) { return (size_t)(w * w + w * 32) * sizeof(cplx<T>); }
 
+// complex64 panels: the left-looking group form of panel_ll.cuh, one CTA per shift.
+constexpr int PLL_THREADS = 512;
+constexpr int PLL_GCAP = 16384;  // group buffer: 128 KB of complex64
+
+template <int GW>
+__global__ void __launch_bounds__(PLL_THREADS)
+k_panel_ll(float2* S, long long ld, long long stride, int n, int k0, int w, int32_t* piv, int* info, unsigned* flags,
+           int gcap) {
+  extern __shared__ __align__(16) unsigned char pll_smem[];
+  __shared__ PanelShared sh;
+  const int b = blockIdx.x;
+  float2* Lt = reinterpret_cast<float2*>(pll_smem);
+  float2* G = Lt + 64 * 64;
+  int* pl = reinterpret_cast<int*>(G + gcap);
+  panel_ll<GW, PLL_THREADS>(S + (size_t)b * stride, ld, n, k0, w, piv + (size_t)b * n + k0, info + b, flags, Lt, G,
+                            pl, sh);
+}
+
+size_t pll_smem_bytes(int n, int gcap) { return (size_t)64 * 64 * sizeof(float2) + (size_t)gcap * sizeof(float2) + (size_t)n * sizeof(int); }
+
+template <int GW>
+cudaError_t launch_panel_ll(const LuBatch<float>& lu, int k0, int w, int gcap, cudaStream_t s) {
+  const size_t smem = pll_smem_bytes(lu.n, gcap);
+  cudaError_t e = cudaFuncSetAttribute(k_panel_ll<GW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  feast_count_launch();
+  k_panel_ll<GW><<<lu.q, PLL_THREADS, smem, s>>>(reinterpret_cast<float2*>(lu.S), lu.ld, lu.stride, lu.n, k0, w,
+                                                 lu.piv, lu.info, lu.flags, gcap);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_panel(const LuBatch<T>& lu, int k0, int w, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (w <= 64 && lu.n <= PLL_GCAP) {
+      const int gcap = min(PLL_GCAP, 8 * lu.n);
+      switch (panel_group_width(lu.n - k0, gcap)) {
+        case 8: return launch_panel_ll<8>(lu, k0, w, gcap, s);
+        case 4: return launch_panel_ll<4>(lu, k0, w, gcap, s);
+        case 2: return launch_panel_ll<2>(lu, k0, w, gcap, s);
+        default: return launch_panel_ll<1>(lu, k0, w, gcap, s);
+      }
+    }
+  }
+  feast_count_launch();
+  k_panel<T><<<lu.q, PANEL_THREADS, 0, s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv, lu.info, lu.flags);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename T>
@@ -291,8 +341,8 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
   cudaMemsetAsync(lu.info, 0, sizeof(int) * lu.q, s);
   for (int k0 = 0; k0 < lu.n; k0 += nb) {
     const int w = min(nb, lu.n - k0);
-    feast_count_launch();
-    k_panel<T><<<lu.q, PANEL_THREADS, 0, s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv, lu.info, lu.flags);
+    e = launch_panel<T>(lu, k0, w, s);
+    if (e != cudaSuccess) return e;
     const int nother = lu.n - w;
     if (nother > 0) {
       dim3 grid(ceil_div(nother, 32), lu.q);
