@@ -277,11 +277,11 @@ struct UpdateTimer {
 };
 
 template <typename T>
-cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, void* c, cudaStream_t s) {
+cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bool stage, void* c, cudaStream_t s) {
   auto* t = reinterpret_cast<UpdateTimer<T>*>(c);
-  if (lu.n - k0 - w <= 0) return cudaSuccess;
+  if (lu.n - k0 - w <= 0 || nc <= 0) return cudaSuccess;
   cudaEventRecord(t->h->upd_ev[2 * t->used], s);
-  cudaError_t e = t->inner(lu, k0, w, t->ctx, s);
+  cudaError_t e = t->inner(lu, k0, w, c0, nc, stage, t->ctx, s);
   cudaEventRecord(t->h->upd_ev[2 * t->used + 1], s);
   ++t->used;
   return e;
@@ -298,7 +298,7 @@ feast_status factor_impl(feast_handle* h) {
   UpdateTimer<T> timer{upd, ctx, h, 0, 0.0};
   if (h->opt.timing) {
     const int panels = (int)((h->n + h->nb - 1) / h->nb);
-    while ((int)h->upd_ev.size() < 2 * panels) {
+    while ((int)h->upd_ev.size() < 4 * panels) {  // two update launches per step
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
       h->upd_ev.push_back(e);

@@ -176,20 +176,22 @@ __global__ void k_piv_to_perm(const int32_t* piv, int32_t* perm, int32_t* pinv, 
 }  // namespace
 
 template <typename T>
-cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, void*, cudaStream_t s) {
+cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bool, void*, cudaStream_t s) {
   const int rest = lu.n - k0 - w;
-  if (rest <= 0) return cudaSuccess;
+  if (rest <= 0 || nc <= 0) return cudaSuccess;
   GemmArgs<T> g;
-  g.M = rest; g.N = rest; g.K = w; g.batch = lu.q;
+  g.M = rest; g.N = nc; g.K = w; g.batch = lu.q;
   g.alpha = mk<T>(T(-1), T(0));
   g.beta = mk<T>(T(1), T(0));
-  g.A = lu.S + (size_t)(k0 + w) + (size_t)k0 * lu.ld;        g.lda = lu.ld; g.strideA = lu.stride; g.opA = OP_N;
-  g.B = lu.S + (size_t)k0 + (size_t)(k0 + w) * lu.ld;        g.ldb = lu.ld; g.strideB = lu.stride; g.opB = OP_N;
-  g.C = lu.S + (size_t)(k0 + w) + (size_t)(k0 + w) * lu.ld;  g.ldc = lu.ld; g.strideC = lu.stride;
+  g.A = lu.S + (size_t)(k0 + w) + (size_t)k0 * lu.ld;  g.lda = lu.ld; g.strideA = lu.stride; g.opA = OP_N;
+  g.B = lu.S + (size_t)k0 + (size_t)c0 * lu.ld;        g.ldb = lu.ld; g.strideB = lu.stride; g.opB = OP_N;
+  g.C = lu.S + (size_t)(k0 + w) + (size_t)c0 * lu.ld;  g.ldc = lu.ld; g.strideC = lu.stride;
   return gemm_batched<T>(g, s);
 }
-template cudaError_t default_trailing_update<double>(const LuBatch<double>&, int, int, void*, cudaStream_t);
-template cudaError_t default_trailing_update<float>(const LuBatch<float>&, int, int, void*, cudaStream_t);
+template cudaError_t default_trailing_update<double>(const LuBatch<double>&, int, int, int, int, bool, void*,
+                                                     cudaStream_t);
+template cudaError_t default_trailing_update<float>(const LuBatch<float>&, int, int, int, int, bool, void*,
+                                                    cudaStream_t);
 
 namespace {
 
@@ -339,22 +341,49 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
                                        (int)diag_smem<T>(nb));
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(lu.info, 0, sizeof(int) * lu.q, s);
+  // side stream (highest priority, so that the panel's CTAs are dispatched as
+  // soon as SMs free up) and the two events of each step
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
+  if ((e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
+  auto cleanup = [&](cudaError_t r) {
+    if (ev_next) cudaEventDestroy(ev_next);
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    cudaStreamDestroy(side);
+    return r;
+  };
+  if ((e = cudaEventCreateWithFlags(&ev_next, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  auto laswp = [&](int k0, int w) -> cudaError_t {
+    const int nother = lu.n - w;
+    if (nother <= 0) return cudaSuccess;
+    dim3 grid(ceil_div(nother, 32), lu.q);
+    feast_count_launch();
+    k_laswp_trsm<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv);
+    return cudaGetLastError();
+  };
+  if ((e = launch_panel<T>(lu, 0, min(nb, lu.n), s)) != cudaSuccess) return cleanup(e);
+  if ((e = laswp(0, min(nb, lu.n))) != cudaSuccess) return cleanup(e);
   for (int k0 = 0; k0 < lu.n; k0 += nb) {
     const int w = min(nb, lu.n - k0);
-    e = launch_panel<T>(lu, k0, w, s);
-    if (e != cudaSuccess) return e;
-    const int nother = lu.n - w;
-    if (nother > 0) {
-      dim3 grid(ceil_div(nother, 32), lu.q);
-      feast_count_launch();
-      k_laswp_trsm<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv);
-    }
-    e = upd(lu, k0, w, ctx, s);
-    if (e != cudaSuccess) return e;
+    const int rest = lu.n - k0 - w;
+    if (rest <= 0) break;
+    const int k1 = k0 + w, w1 = min(nb, rest);
+    // block column k+1 first, then panel k+1 beside the rest of the update
+    if ((e = upd(lu, k0, w, k1, w1, true, ctx, s)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaStreamWaitEvent(side, ev_next, 0)) != cudaSuccess) return cleanup(e);
+    if ((e = launch_panel<T>(lu, k1, w1, side)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaEventRecord(ev_panel, side)) != cudaSuccess) return cleanup(e);
+    if (rest > w1 && (e = upd(lu, k0, w, k1 + w1, rest - w1, false, ctx, s)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaStreamWaitEvent(s, ev_panel, 0)) != cudaSuccess) return cleanup(e);
+    if ((e = laswp(k1, w1)) != cudaSuccess) return cleanup(e);
   }
   feast_count_launch();
   k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
-  return cudaGetLastError();
+  return cleanup(cudaGetLastError());
 }
 
 template <typename T>

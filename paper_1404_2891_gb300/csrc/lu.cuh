@@ -18,15 +18,23 @@ struct LuBatch {
   void* tc = nullptr;       // tensor-core staging (complex64 path), or nullptr
 };
 
-// Trailing-update hook: C -= L21 * U12 for all shifts of one panel step.
+// Trailing-update hook of panel step (k0, w): the columns c0 .. c0+nc-1 of
+// the trailing block, C = S[k0+w:, c0:c0+nc] -= L21 U12[:, c0 - (k0+w) ...],
+// for all shifts.  `stage` is true on the first call of a step (an
+// implementation that prepares the step's operands once does it then).
 // Defaults to gemm_batched<T>; the mixed path installs its tensor-core kernel.
 template <typename T>
-using TrailingUpdateFn = cudaError_t (*)(const LuBatch<T>& lu, int k0, int w, void* ctx, cudaStream_t s);
+using TrailingUpdateFn = cudaError_t (*)(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bool stage, void* ctx,
+                                         cudaStream_t s);
 
 // The batched-GEMM trailing update (used when no other kernel is installed).
 template <typename T>
-cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, void* ctx, cudaStream_t s);
+cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bool stage, void* ctx,
+                                    cudaStream_t s);
 
+// Look-ahead: after panel k, the trailing update of block column k+1 runs
+// first; panel k+1 then factors on a high-priority side stream while the rest
+// of step k's trailing update runs on `s` (joined through events).
 template <typename T>
 cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> upd, void* ctx,
                               cudaStream_t s);

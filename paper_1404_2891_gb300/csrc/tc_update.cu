@@ -235,6 +235,7 @@ struct TcArgs {
   long long stride2;   // 2 * stride (floats per matrix)
   long long c_off;     // float offset of C~ (its first Re row, first column) inside a matrix
   int M, N;            // complex rows and columns of the C block
+  int b_col0;          // first staged B row (column of the B operand) used by this launch
   int kbox;            // number of 64-wide K boxes actually staged (1 or 2)
   unsigned* flags;
 };
@@ -300,7 +301,8 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         unsigned char* dst = sB + s * B_STAGE_BYTES;
         for (int h = 0; h < 2; ++h)
           for (int kb = 0; kb < a.kbox; ++kb)
-            tma_load_3d(dst + (h * 2 + kb) * (TC_BN * 128), &mapB, &b_full[s], kb * TC_BOX_K, t * TC_BN, shift * 2 + h);
+            tma_load_3d(dst + (h * 2 + kb) * (TC_BN * 128), &mapB, &b_full[s], kb * TC_BOX_K, a.b_col0 + t * TC_BN,
+                        shift * 2 + h);
         last[s] = t;
       }
       // no copy may still be writing shared memory when the block exits
@@ -425,15 +427,19 @@ bool tc_gemm_fits(const TcGemm& g, const TcStaging* ctx) {
          g.q <= ctx->q;
 }
 
-cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  {
-    const int blocks = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), ST_ROWS);
-    dim3 grid(blocks, g.q, 2);
-    feast_count_launch();
-    k_stage_operands<<<grid, 256, 0, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
-                                          reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max, ctx->cols_max);
-  }
+// Stage the operands of g (all of A and all N columns of B) as split-BF16.
+cudaError_t tc_stage(const TcGemm& g, const TcStaging* ctx, cudaStream_t s) {
+  const int blocks = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), ST_ROWS);
+  dim3 grid(blocks, g.q, 2);
+  feast_count_launch();
+  k_stage_operands<<<grid, 256, 0, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
+                                        reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max, ctx->cols_max);
+  return cudaGetLastError();
+}
+
+// C[:, c0 : c0 + nc] -= A B[:, c0 : c0 + nc] from the staged operands of g.
+cudaError_t tc_run(const TcGemm& g, int c0, int nc, const TcStaging* ctx, unsigned* flags, cudaStream_t s) {
+  if (g.M <= 0 || nc <= 0) return cudaSuccess;
   CUtensorMap mA, mB;
   if (!encode_stage_map(&mA, ctx->Ast, 2LL * g.M, ctx->rows_max, 2 * g.q, TC_BM)) return cudaErrorInvalidValue;
   if (!encode_stage_map(&mB, ctx->Bst, g.N, ctx->cols_max, 2 * g.q, TC_BN)) return cudaErrorInvalidValue;
@@ -441,9 +447,10 @@ cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cuda
   a.S = reinterpret_cast<float*>(g.SC);
   a.ld2 = 2 * g.ldc;
   a.stride2 = 2 * g.sc;
-  a.c_off = 2LL * g.cr0 + (long long)g.cc0 * a.ld2;
+  a.c_off = 2LL * g.cr0 + (long long)(g.cc0 + c0) * a.ld2;
   a.M = g.M;
-  a.N = g.N;
+  a.N = nc;
+  a.b_col0 = c0;
   a.kbox = (2 * g.K + TC_BOX_K - 1) / TC_BOX_K;
   a.flags = flags;
   static bool attr = false;
@@ -458,10 +465,20 @@ cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cuda
   return cudaGetLastError();
 }
 
-// LU trailing update: C = S[k0+w:, k0+w:], A = L21 = S[k0+w:, k0:k0+w], B = U12 = S[k0:k0+w, k0+w:].
-cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, void* vctx, cudaStream_t s) {
+cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  cudaError_t e = tc_stage(g, ctx, s);
+  if (e != cudaSuccess) return e;
+  return tc_run(g, 0, g.N, ctx, flags, s);
+}
+
+// LU trailing update of step (k0, w): C = S[k0+w:, k0+w:], A = L21 = S[k0+w:, k0:k0+w],
+// B = U12 = S[k0:k0+w, k0+w:]; this call updates the columns c0 .. c0+nc-1 of S
+// (staging the whole step's operands when `stage`).
+cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, int c0, int nc, bool stage, void* vctx,
+                               cudaStream_t s) {
   const int rest = lu.n - k0 - w;
-  if (rest <= 0) return cudaSuccess;
+  if (rest <= 0 || nc <= 0) return cudaSuccess;
   const TcStaging* ctx = reinterpret_cast<const TcStaging*>(vctx);
   TcGemm g;
   const float2* S = reinterpret_cast<const float2*>(lu.S);
@@ -469,8 +486,12 @@ cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, void* vc
   g.SB = S; g.ldb = lu.ld; g.sb = lu.stride; g.br0 = k0; g.bc0 = k0 + w;
   g.SC = reinterpret_cast<float2*>(lu.S); g.ldc = lu.ld; g.sc = lu.stride; g.cr0 = k0 + w; g.cc0 = k0 + w;
   g.M = rest; g.N = rest; g.K = w; g.q = lu.q;
-  if (!tc_gemm_fits(g, ctx)) return default_trailing_update<float>(lu, k0, w, nullptr, s);
-  return tc_gemm(g, ctx, lu.flags, s);
+  if (!tc_gemm_fits(g, ctx)) return default_trailing_update<float>(lu, k0, w, c0, nc, stage, nullptr, s);
+  if (stage) {
+    cudaError_t e = tc_stage(g, ctx, s);
+    if (e != cudaSuccess) return e;
+  }
+  return tc_run(g, c0 - (k0 + w), nc, ctx, lu.flags, s);
 }
 
 }  // namespace
