@@ -34,7 +34,7 @@ constexpr int TC_BM = 128;      // rows of C~ per stripe (= 64 complex rows)
 constexpr int TC_BN = 128;      // columns per tile
 constexpr int TC_KP = 128;      // staged K width (2 * nb, nb <= 64), bf16 elements
 constexpr int TC_BOX_K = 64;    // 64 bf16 = 128 bytes = one swizzle row
-constexpr int TC_THREADS = 192; // 6 warps
+constexpr int TC_THREADS = 320; // 10 warps: TMA, MMA, 8 epilogue (two per TMEM lane quarter)
 constexpr int A_BYTES = 2 * 2 * TC_BM * TC_BOX_K * 2;        // hi/lo x 2 k-boxes x 128 rows x 128 B = 64 KB
 constexpr int B_STAGE_BYTES = 2 * 2 * TC_BN * TC_BOX_K * 2;  // 64 KB
 constexpr int TC_SMEM = 1024 + A_BYTES + 2 * B_STAGE_BYTES + 256;  // 197,888 bytes
@@ -266,7 +266,7 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
       mbar_init(&d_full[s], 1);
-      mbar_init(&d_empty[s], 4);
+      mbar_init(&d_empty[s], 8);
     }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -346,7 +346,8 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     }
   } else {
     // epilogue warps 2..5: TMEM lane quarter (warp % 4)
-    const int quarter = warp & 3;
+    const int quarter = warp & 3;        // the TMEM lane quarter this warp may read
+    const int half = (warp - 2) >> 2;    // which of the tile's 32-column chunks it takes
     const int r = quarter * 32 + lane;  // row within the stripe
     const long long R = row0 + r;       // row of C~
     float* Cb = a.S + (size_t)shift * a.stride2 + a.c_off;
@@ -360,7 +361,7 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
       }
       fence_after();
       const int col0 = t * TC_BN;
-      for (int c = 0; c < TC_BN / 32; ++c) {
+      for (int c = half; c < TC_BN / 32; c += 2) {
         float cv[32], v[32];
         const int cbase = col0 + c * 32;
 #pragma unroll
