@@ -345,6 +345,19 @@ feast_status feast_batch_info(const feast_batch* b, int* count, int* nmat, int* 
 feast_status feast_batch_plan(int nmat, const int* nb, const int* m, int with_lu, int with_solve, int workers,
                               int* tasks, int capacity, int* ntasks, double* makespan_us);
 
+/* Diagnostic: C = op(A) X by the emulated-FP64 tensor-core product that the
+ * mixed path uses for its n x n x m0 Rayleigh-Ritz products (no paper
+ * counterpart).  Each row of the real form of op(A) and each column of X is
+ * scaled by a power of two and cut into signed integer digits of beta bits,
+ * stored exactly in bfloat16, with n 2^(2 beta + 1) <= 2^24.  Every digit-pair
+ * product is then exact in the tensor cores' FP32 accumulators, and the pairs
+ * are summed with their weights in FP64 (about 50 significant bits kept).
+ *   A : n x n, lda >= n;  X : n x m (1 <= m <= 4096), ldx >= n;  C : n x m, ldc >= n;
+ *   column-major complex128, host or device; op = 0 (A) or 2 (A^H).
+ * Allocates its own scratch (freed before return); returns after the stream has drained. */
+feast_status feast_emulated_zgemm(int64_t n, int64_t m, const feast_z* A, int64_t lda, int op, const feast_z* X,
+                                  int64_t ldx, feast_z* C, int64_t ldc, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; no paper counterpart). */
 uint64_t feast_kernel_launches(void);

@@ -80,7 +80,8 @@ SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_stat
            "feast_mlp_param_count", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_get_params",
            "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train",
            "feast_batch_create", "feast_batch_destroy", "feast_batch_factor", "feast_batch_filter",
-           "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_plan")
+           "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_plan",
+           "feast_emulated_zgemm")
 
 
 class feast_batch_stats(ctypes.Structure):
@@ -161,6 +162,9 @@ def load(path=LIB_PATH):
     lib.feast_batch_info.restype = I
     lib.feast_batch_plan.argtypes = [I, P, P, I, I, I, P, I, P, P]
     lib.feast_batch_plan.restype = I
+    I64 = ctypes.c_int64
+    lib.feast_emulated_zgemm.argtypes = [I64, I64, P, I64, I, P, I64, P, I64, P]
+    lib.feast_emulated_zgemm.restype = I
     _lib = lib
     return lib
 
@@ -516,6 +520,18 @@ def feast_batch_plan(nb, m, with_lu=True, with_solve=True, workers=152):
                                 int(workers), out.ctypes.data, nt.value, ctypes.byref(nt), ctypes.byref(mk)),
            "feast_batch_plan")
     return out, mk.value
+
+
+def feast_emulated_zgemm(A, X, op="N"):
+    """op(A) X (op "N" or "C") by the emulated-FP64 tensor-core product (diagnostic)."""
+    pa, ka = _colmajor(A)
+    px, kx = _colmajor(X)
+    n = A.shape[0]
+    m = X.shape[1] if X.ndim == 2 else 1
+    C = np.zeros((n, m), dtype=np.complex128, order="F")
+    _check(load().feast_emulated_zgemm(n, m, pa, n, {"N": 0, "C": 2}[op], px, n, C.ctypes.data, n, None),
+           "feast_emulated_zgemm")
+    return C
 
 
 # ---------------------------------------------------------------- count predictor (m0)

@@ -19,6 +19,7 @@
 #include "lu.cuh"
 #include "norm2.cuh"
 #include "small.cuh"
+#include "ozaki.cuh"
 #include "tc_update.cuh"
 
 using zc = std::complex<double>;
@@ -176,6 +177,12 @@ struct feast_handle {
   TcStaging staging;
   void* schur_log = nullptr;
   double2* gemm_ws = nullptr;  // split-K partial products
+  // mixed path: FP64-accurate n x n x m0 products on the BF16 tensor cores
+  // (digits of A, A^H, B, B^H made on first use)
+  bool use_oz = false;
+  OzOperator oz[4];
+  bool oz_ready[4] = {false, false, false, false};
+  OzWork ozw;
   float2* s32 = nullptr;       // FP32 Schur work: C, Z, V, W, lambda (m0 x m0 each)
   size_t gemm_ws_elems = 0;
   std::vector<void*> allocs;
@@ -243,6 +250,26 @@ cudaError_t zg(feast_handle* h, int opA, int opB, int M, int N, int K, zc alpha,
   g.ws = h->gemm_ws;
   g.ws_elems = h->gemm_ws_elems;
   return gemm_batched<double>(g, h->st);
+}
+
+// C (n x m0) = op(M) X for M = A (which = 0) or B (which = 1), op = OP_N or OP_C:
+// on the emulated-FP64 tensor-core path when the handle uses it (the digits of
+// op(M) are made on first use), else the DMMA GEMM.
+cudaError_t big_product(feast_handle* h, int which, int op, const double2* X, double2* C) {
+  const int n = (int)h->n, m = h->m0;
+  const double2* Mx = which == 0 ? h->A : h->B;
+  if (!h->use_oz) return zg(h, op, OP_N, n, m, n, zc(1.0), Mx, n, X, n, zc(0.0), C, n);
+  const int slot = which * 2 + (op == OP_C ? 1 : 0);
+  if (!h->oz_ready[slot]) {
+    void* base = nullptr;
+    cudaError_t e = dalloc(h, &base, oz_operator_bytes(n));
+    if (e != cudaSuccess) return e;
+    oz_operator_layout(base, n, &h->oz[slot]);
+    e = oz_make_operator(Mx, n, op, h->oz[slot], h->st);
+    if (e != cudaSuccess) return e;
+    h->oz_ready[slot] = true;
+  }
+  return oz_apply(h->oz[slot], X, n, m, C, n, h->ozw, h->flags, h->st);
 }
 
 feast_status read_flags(feast_handle* h) {
@@ -420,10 +447,10 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
   }
   const double2* Vb = bi ? h->Qho : h->Qo;
-  CK(zg(h, OP_N, OP_N, n, m, n, one, h->A, n, h->Qo, n, zero, h->AQ, n));
+  CK(big_product(h, 0, OP_N, h->Qo, h->AQ));
   const double2* BQp = h->Qo;
   if (h->hasB) {
-    CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Qo, n, zero, h->BQ, n));
+    CK(big_product(h, 1, OP_N, h->Qo, h->BQ));
     BQp = h->BQ;
   }
   CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, h->AQ, n, zero, h->Ahat, m));
@@ -486,9 +513,9 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
         BhQp = h->BhQ;
       }
     } else {
-      CK(zg(h, OP_C, OP_N, n, m, n, one, h->A, n, h->Qho, n, zero, h->AhQ, n));
+      CK(big_product(h, 0, OP_C, h->Qho, h->AhQ));
       if (h->hasB) {
-        CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Qho, n, zero, h->BhQ, n));
+        CK(big_product(h, 1, OP_C, h->Qho, h->BhQ));
         BhQp = h->BhQ;
       }
     }
@@ -684,6 +711,12 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   h->gemm_ws_elems = (size_t)64 * 160 * 160;
   AL(h->gemm_ws, h->gemm_ws_elems * sizeof(double2));
   AL(h->s32, (size_t)5 * m0 * m0 * sizeof(float2));
+  if (mx && n >= 256) {  // FP64-accurate Rayleigh-Ritz products on the BF16 tensor cores
+    void* ozbase = nullptr;
+    AL(ozbase, oz_work_bytes((int)n, m0));
+    oz_work_layout(ozbase, (int)n, m0, &h->ozw);
+    h->use_oz = true;
+  }
   if (mx) {
     AL(h->staging.Ast, tc_staging_bytes_A(n, h->q));
     AL(h->staging.Bst, tc_staging_bytes_B(n, h->q));
@@ -1045,6 +1078,56 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
   }
   if (stats) *stats = st;
   return converged ? FEAST_OK : FEAST_ERR_NOCONV;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+feast_status feast_emulated_zgemm(int64_t n, int64_t m, const feast_z* A, int64_t lda, int op, const feast_z* X,
+                                  int64_t ldx, feast_z* C, int64_t ldc, void* stream) {
+  if (n < 1 || m < 1 || m > 4096 || !A || !X || !C || lda < n || ldx < n || ldc < n || (op != OP_N && op != OP_C))
+    return FEAST_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<void*> mem;
+  auto release = [&](feast_status s) {
+    cudaStreamSynchronize(st);
+    for (void* p : mem) cudaFree(p);
+    return s;
+  };
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    mem.push_back(p);
+    return p;
+  };
+  double2* dA = static_cast<double2*>(alloc((size_t)n * n * sizeof(double2)));
+  double2* dX = static_cast<double2*>(alloc((size_t)n * m * sizeof(double2)));
+  double2* dC = static_cast<double2*>(alloc((size_t)n * m * sizeof(double2)));
+  void* opb = alloc(oz_operator_bytes((int)n));
+  void* wb = alloc(oz_work_bytes((int)n, (int)m));
+  unsigned* flags = static_cast<unsigned*>(alloc(64));
+  if (!dA || !dX || !dC || !opb || !wb || !flags) return release(FEAST_ERR_ALLOC);
+  if (cudaMemcpy2DAsync(dA, n * sizeof(double2), A, lda * sizeof(double2), n * sizeof(double2), n, cudaMemcpyDefault,
+                        st) != cudaSuccess ||
+      cudaMemcpy2DAsync(dX, n * sizeof(double2), X, ldx * sizeof(double2), n * sizeof(double2), m, cudaMemcpyDefault,
+                        st) != cudaSuccess ||
+      cudaMemsetAsync(flags, 0, 64, st) != cudaSuccess)
+    return release(FEAST_ERR_CUDA);
+  OzOperator L;
+  OzWork w;
+  oz_operator_layout(opb, (int)n, &L);
+  oz_work_layout(wb, (int)n, (int)m, &w);
+  if (oz_make_operator(dA, n, op, L, st) != cudaSuccess) return release(FEAST_ERR_CUDA);
+  if (oz_apply(L, dX, n, (int)m, dC, n, w, flags, st) != cudaSuccess) return release(FEAST_ERR_CUDA);
+  if (cudaMemcpy2DAsync(C, ldc * sizeof(double2), dC, n * sizeof(double2), n * sizeof(double2), m, cudaMemcpyDefault,
+                        st) != cudaSuccess)
+    return release(FEAST_ERR_CUDA);
+  unsigned f = 0;
+  if (cudaMemcpyAsync(&f, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return release(FEAST_ERR_CUDA);
+  return release(f & DEVFLAG_TIMEOUT ? FEAST_ERR_DEVICE_TIMEOUT : FEAST_OK);
 }
 
 }  // extern "C"
