@@ -34,6 +34,7 @@
 #include "blas1.cuh"
 #include "gemm.cuh"
 #include "norm2.cuh"
+#include "ozaki.cuh"
 #include "small.cuh"
 
 using zc = std::complex<double>;
@@ -247,6 +248,10 @@ struct feast_batch {
   double makespan = 0.0;
   int grid = 0;
   GG g_AQ, g_Ahat, g_Bhat, g_W32, g_V, g_Zs, g_LUW, g_X, g_AX;
+  // A_p Q_p, FP64-accurate on the BF16 tensor cores: digits of every A_p (made at
+  // creation) and one work area that the pencils' products use in turn
+  std::vector<OzOperator> ozop;
+  void* oz_work = nullptr;
   int* orth_cta0 = nullptr;
   int orth_total = 0;
   double2* orth_part = nullptr;
@@ -391,7 +396,12 @@ cudaError_t enqueue_rr(feast_batch* b) {
 #define CE(x) if ((e = (x)) != cudaSuccess) return e
   CE(orth_cgs2_grp(b->Q, b->d_pd, b->orth_cta0, b->np, b->orth_total, b->orth_part, b->orth_bars, b->active,
                    b->flags, b->st));
-  CE(run_gg(b, b->g_AQ));
+  for (int p = 0; p < b->np; ++p) {
+    const GrpDesc& d = b->pd[p];
+    OzWork w;
+    oz_work_layout(b->oz_work, d.n, d.m, &w);
+    CE(oz_apply(b->ozop[p], b->Q + d.onm, d.n, d.m, b->AQ + d.onm, d.n, w, b->flags, b->st, b->active + p));
+  }
   CE(run_gg(b, b->g_Ahat));
   CE(run_gg(b, b->g_Bhat));
   CE(cudaMemcpyAsync(b->LUB, b->Bhat, mmb, cudaMemcpyDeviceToDevice, b->st));
@@ -714,6 +724,20 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
       return bad(cuda_status(e));
     if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess) return bad(cuda_status(e));
     b->normA.push_back(s);
+  }
+  // digits of every A_p for the emulated-FP64 products A_p Q_p
+  {
+    size_t wmax = 0;
+    b->ozop.resize(b->np);
+    for (int p = 0; p < b->np; ++p) {
+      const GrpDesc& d = b->pd[p];
+      void* base = nullptr;
+      if ((e = dalloc(b, &base, oz_operator_bytes(d.n))) != cudaSuccess) return bad(cuda_status(e));
+      oz_operator_layout(base, d.n, &b->ozop[p]);
+      if ((e = oz_make_operator(b->A + d.onn, d.n, OP_N, b->ozop[p], b->st)) != cudaSuccess) return bad(cuda_status(e));
+      wmax = std::max(wmax, oz_work_bytes(d.n, d.m));
+    }
+    if ((e = dalloc(b, &b->oz_work, wmax)) != cudaSuccess) return bad(cuda_status(e));
   }
   // persistent launch: resident CTAs and the three task lists
   b->grid = batch_lu_grid(b->Nmax);

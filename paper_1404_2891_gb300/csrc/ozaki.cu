@@ -123,7 +123,9 @@ k_oz_split_L(const double2* A, long long lda, int n, int opA, const int* e, int 
 
 // Column exponents and digits of X (n x m): row c of E_sl holds (Re, Im) of X[:, c].
 __global__ void __launch_bounds__(256)
-k_oz_split_X(const double2* X, long long ldx, int n, int m, int s, int beta, int Kp, __nv_bfloat16* E, int* f) {
+k_oz_split_X(const double2* X, long long ldx, int n, int m, int s, int beta, int Kp, __nv_bfloat16* E, int* f,
+             const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double red[8];
   __shared__ int s_ex;
   const int c = blockIdx.x;
@@ -160,6 +162,7 @@ struct OzGemmArgs {
   long long M;
   int m, s, NP, nkb;
   unsigned* flags;
+  const int* gate;  // nullable: the product is skipped when *gate == 0
 };
 
 // CTA (x, y, z): tile x of the stacked columns of slice z's products, 128-row stripe y.
@@ -169,6 +172,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
   const int ncols = (a.s - i) * a.m;  // slice i pairs with E_0 .. E_{s-1-i}
   const int col0 = blockIdx.x * OZ_BN;
   if (col0 >= ncols) return;  // whole CTA, before any barrier or allocation
+  if (a.gate && *a.gate == 0) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sA = smem;
@@ -269,7 +273,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
 // ---------------------------------------------------------------- recombination
 // C[i, c] = (C~[2i, c], C~[2i+1, c]); pairs summed from the smallest weight up.
 __global__ void k_oz_combine(const float* P, const int* e, const int* f, long long M, int m, int s, int NP, int beta,
-                             int n, double2* C, long long ldc) {
+                             int n, double2* C, long long ldc, const int* gate) {
+  if (gate && *gate == 0) return;
   const size_t total = (size_t)n * m;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx % m), i = (int)(idx / m);
@@ -392,11 +397,11 @@ cudaError_t oz_make_operator(const double2* A, long long lda, int opA, OzOperato
 }
 
 cudaError_t oz_apply(const OzOperator& L, const double2* X, long long ldx, int m, double2* C, long long ldc,
-                     const OzWork& w, unsigned* flags, cudaStream_t s) {
+                     const OzWork& w, unsigned* flags, cudaStream_t s, const int* gate) {
   if (m < 1) return cudaSuccess;
   const int NP = work_np(L.s, m);
   feast_count_launch();
-  k_oz_split_X<<<m, 256, 0, s>>>(X, ldx, L.n, m, L.s, L.beta, L.Kp, w.E, w.f);
+  k_oz_split_X<<<m, 256, 0, s>>>(X, ldx, L.n, m, L.s, L.beta, L.Kp, w.E, w.f, gate);
   CUtensorMap mD, mE;
   if (!encode_digits(&mD, L.D, L.Kp, L.M, L.s)) return cudaErrorInvalidValue;
   if (!encode_digits(&mE, w.E, L.Kp, (long long)L.s * m, 1)) return cudaErrorInvalidValue;
@@ -414,12 +419,13 @@ cudaError_t oz_apply(const OzOperator& L, const double2* X, long long ldx, int m
   a.NP = NP;
   a.nkb = L.Kp / OZ_BK;
   a.flags = flags;
+  a.gate = gate;
   dim3 grid((unsigned)((L.s * m + OZ_BN - 1) / OZ_BN), (unsigned)((L.M + OZ_BM - 1) / OZ_BM), (unsigned)L.s);
   feast_count_launch();
   k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mD, mE, a);
   const size_t total = (size_t)L.n * m;
   const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 8 ? (total + 255) / 256 : 152 * 8);
   feast_count_launch();
-  k_oz_combine<<<blocks, 256, 0, s>>>(w.P, L.e, w.f, L.M, m, L.s, NP, L.beta, L.n, C, ldc);
+  k_oz_combine<<<blocks, 256, 0, s>>>(w.P, L.e, w.f, L.M, m, L.s, NP, L.beta, L.n, C, ldc, gate);
   return cudaGetLastError();
 }

@@ -45,6 +45,7 @@ void oz_work_layout(void* base, int n, int m, OzWork* w);
 // Digits of op(A) (opA = OP_N or OP_C); A complex128 column-major n x n (lda).
 cudaError_t oz_make_operator(const double2* A, long long lda, int opA, OzOperator& L, cudaStream_t s);
 // C (n x m, ldc) = op(A) X (X n x m, ldx), FP64-accurate.  flags: DEVFLAG_TIMEOUT on a
-// bounded-wait expiry in the tensor-core kernel.
+// bounded-wait expiry in the tensor-core kernel.  gate (device, nullable): when
+// *gate == 0 every kernel of the product returns at once (C untouched).
 cudaError_t oz_apply(const OzOperator& L, const double2* X, long long ldx, int m, double2* C, long long ldc,
-                     const OzWork& w, unsigned* flags, cudaStream_t s);
+                     const OzWork& w, unsigned* flags, cudaStream_t s, const int* gate = nullptr);
