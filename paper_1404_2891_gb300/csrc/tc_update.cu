@@ -310,6 +310,181 @@ k_tc_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
   }
 }
 
+// The same update with C streamed by TMA: a 64-column variant in which warp 0
+// also loads each 128 x 64 tile of C~ into a two-stage shared-memory ring as
+// soon as the ring has room (independently of the MMAs), so that the HBM reads
+// of C are in flight in bulk while the previous tile is written back; the
+// epilogue reads C from shared memory (conflict-free: lane r reads row r).
+// Used when the C block's first float row is 16-byte aligned and the column
+// stride is a multiple of 16 bytes.
+constexpr int TCC_BN = 64;
+constexpr int TCC_B_STAGE = 2 * 2 * TCC_BN * TC_BOX_K * 2;      // 32 KB
+constexpr int TCC_C_STAGE = TC_BM * TCC_BN * 4;                 // 32 KB
+constexpr int TCC_SMEM = 1024 + A_BYTES + 2 * TCC_B_STAGE + 2 * TCC_C_STAGE + 256;
+constexpr unsigned IDESC_C = bf16_idesc(TC_BM, TCC_BN);
+
+struct TcCArgs {
+  int c_row0;   // float row of the C block's first Re row (multiple of 4)
+  int c_col0;   // matrix column of the C block's first column
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_update_c(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const __grid_constant__ CUtensorMap mapC, TcArgs a, TcCArgs cc) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = smem;                                 // [hi k0, hi k1, lo k0, lo k1] x 16 KB
+  unsigned char* sB = smem + A_BYTES;                       // 2 stages x [hi k0, hi k1, lo k0, lo k1] x 8 KB
+  float* sC = reinterpret_cast<float*>(smem + A_BYTES + 2 * TCC_B_STAGE);  // 2 stages x [64 cols][128 rows]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + A_BYTES + 2 * TCC_B_STAGE + 2 * TCC_C_STAGE);
+  uint64_t* a_full = bars + 0;
+  uint64_t* b_full = bars + 1;   // [2]
+  uint64_t* b_empty = bars + 3;  // [2]
+  uint64_t* d_full = bars + 5;   // [2]
+  uint64_t* d_empty = bars + 7;  // [2]
+  uint64_t* c_full = bars + 9;   // [2]
+  uint64_t* c_empty = bars + 11; // [2]
+  uint64_t* mma_done = bars + 13;
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 14);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stripe = blockIdx.x, shift = blockIdx.y;
+  const int ntiles = (a.N + TCC_BN - 1) / TCC_BN;
+  const int row0 = stripe * TC_BM;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+      mbar_init(&d_full[s], 1);
+      mbar_init(&d_empty[s], 8);
+      mbar_init(&c_full[s], 1);
+      mbar_init(&c_empty[s], 8);
+    }
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * TCC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const unsigned tmem_base = *tmem_slot;
+  const unsigned a_bytes = (unsigned)(2 * a.kbox * TC_BM * TC_BOX_K * 2);
+  const unsigned b_bytes = (unsigned)(2 * a.kbox * TCC_BN * TC_BOX_K * 2);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_expect_tx(a_full, a_bytes);
+      for (int h = 0; h < 2; ++h)
+        for (int kb = 0; kb < a.kbox; ++kb)
+          tma_load_3d(sA + (h * 2 + kb) * (TC_BM * 128), &mapA, a_full, kb * TC_BOX_K, row0, shift * 2 + h);
+      int lastb[2] = {-1, -1}, lastc[2] = {-1, -1};
+      bool ok = true;
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int s = t & 1;
+        if (t >= 2 && !mbar_wait(&c_empty[s], ((t >> 1) - 1) & 1)) { ok = false; break; }
+        mbar_expect_tx(&c_full[s], TCC_C_STAGE);
+        tma_load_3d(sC + s * (TC_BM * TCC_BN), &mapC, &c_full[s], cc.c_row0 + row0, cc.c_col0 + t * TCC_BN, shift);
+        lastc[s] = t;
+        if (t >= 2 && !mbar_wait(&b_empty[s], ((t >> 1) - 1) & 1)) { ok = false; break; }
+        mbar_expect_tx(&b_full[s], b_bytes);
+        unsigned char* dst = sB + s * TCC_B_STAGE;
+        for (int h = 0; h < 2; ++h)
+          for (int kb = 0; kb < a.kbox; ++kb)
+            tma_load_3d(dst + (h * 2 + kb) * (TCC_BN * 128), &mapB, &b_full[s], kb * TC_BOX_K, a.b_col0 + t * TCC_BN,
+                        shift * 2 + h);
+        lastb[s] = t;
+      }
+      if (!ok) atomicOr(a.flags, (unsigned)DEVFLAG_TIMEOUT);
+      // no copy may still be writing shared memory when the block exits
+      mbar_wait(a_full, 0);
+      for (int s = 0; s < 2; ++s) {
+        if (lastb[s] >= 0) mbar_wait(&b_full[s], (lastb[s] >> 1) & 1);
+        if (lastc[s] >= 0) mbar_wait(&c_full[s], (lastc[s] >> 1) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(a_full, 0);
+      fence_after();
+      bool issued = false;
+      for (int t = 0; ok && t < ntiles; ++t) {
+        const int s = t & 1;
+        if (!mbar_wait(&b_full[s], (t >> 1) & 1)) { ok = false; break; }
+        if (t >= 2 && !mbar_wait(&d_empty[s], ((t >> 1) - 1) & 1)) { ok = false; break; }
+        fence_after();
+        const unsigned d = tmem_base + (unsigned)(s * TCC_BN);
+        const unsigned aBase = smem_u32(sA), bBase = smem_u32(sB + s * TCC_B_STAGE);
+        unsigned acc = 0;
+        for (int term = 0; term < 3; ++term) {  // hi*hi, hi*lo, lo*hi
+          const int ha = term == 2 ? 1 : 0, hb = term == 1 ? 1 : 0;
+          for (int kk = 0; kk < a.kbox * 4; ++kk) {
+            const int kb = kk >> 2, ko = (kk & 3) * 32;
+            const uint64_t ad = sw128_desc(aBase + (ha * 2 + kb) * (TC_BM * 128) + ko);
+            const uint64_t bd = sw128_desc(bBase + (hb * 2 + kb) * (TCC_BN * 128) + ko);
+            mma_bf16_idesc(d, ad, bd, IDESC_C, acc);
+            acc = 1;
+          }
+        }
+        mma_commit(&b_empty[s]);
+        mma_commit(&d_full[s]);
+        issued = true;
+      }
+      if (!ok) atomicOr(a.flags, (unsigned)DEVFLAG_TIMEOUT);
+      if (issued) {  // every MMA of this block has completed before TMEM is freed
+        mma_commit(mma_done);
+        mbar_wait(mma_done, 0);
+      }
+    }
+  } else {
+    const int quarter = warp & 3;      // TMEM lane quarter of this warp
+    const int c = (warp - 2) >> 2;     // the tile's 32-column chunk it takes
+    const int r = quarter * 32 + lane; // row within the stripe
+    const long long R = row0 + r;
+    float* Cb = a.S + (size_t)shift * a.stride2 + a.c_off;
+    const bool row_ok = R < 2LL * a.M;
+    for (int t = 0; t < ntiles; ++t) {
+      const int s = t & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&c_full[s], (t >> 1) & 1) && mbar_wait(&d_full[s], (t >> 1) & 1));
+      if (!ok) {
+        if (lane == 0) atomicOr(a.flags, (unsigned)DEVFLAG_TIMEOUT);
+        break;
+      }
+      fence_after();
+      const float* tile = sC + s * (TC_BM * TCC_BN);
+      const int cbase = t * TCC_BN + c * 32;
+      float cv[32], v[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) cv[u] = tile[(c * 32 + u) * TC_BM + r];
+      const unsigned taddr = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(s * TCC_BN + c * 32);
+      tmem_ld16(taddr, *reinterpret_cast<float(*)[16]>(&v[0]));
+      tmem_ld16(taddr + 16, *reinterpret_cast<float(*)[16]>(&v[16]));
+      fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&d_empty[s]);
+        mbar_arrive(&c_empty[s]);
+      }
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int col = cbase + u;
+        if (row_ok && col < a.N) __stcs(Cb + R + (size_t)col * a.ld2, cv[u] - v[u]);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * TCC_BN));
+  }
+}
+
 // ---------------------------------------------------------------- host side
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -373,13 +548,42 @@ cudaError_t tc_run(const TcGemm& g, int c0, int nc, const TcStaging* ctx, unsign
   a.b_col0 = c0;
   a.kbox = (2 * g.K + TC_BOX_K - 1) / TC_BOX_K;
   a.flags = flags;
+  dim3 grid(ceil_div(2 * (size_t)g.M, TC_BM), g.q);
+  // C streamed by TMA when its rows start on a 16-byte boundary and the
+  // column and matrix strides are multiples of 16 bytes
+  const long long c_row0 = 2LL * g.cr0;
+  if (c_row0 % 4 == 0 && (2 * g.ldc) % 4 == 0 && (2 * g.sc) % 4 == 0) {
+    CUtensorMap mBc, mC;
+    EncodeFn enc = get_encode();
+    if (enc && encode_stage_map(&mBc, ctx->Bst, g.N, ctx->cols_max, 2 * g.q, TCC_BN)) {
+      cuuint64_t dims[3] = {(cuuint64_t)(c_row0 + 2LL * g.M), (cuuint64_t)(g.cc0 + c0 + nc), (cuuint64_t)g.q};
+      cuuint64_t strides[2] = {(cuuint64_t)(2 * g.ldc) * 4, (cuuint64_t)(2 * g.sc) * 4};
+      cuuint32_t box[3] = {(cuuint32_t)TC_BM, (cuuint32_t)TCC_BN, 1};
+      cuuint32_t estr[3] = {1, 1, 1};
+      if (enc(&mC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g.SC, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+          CUDA_SUCCESS) {
+        static bool attr_c = false;
+        if (!attr_c) {
+          cudaError_t e = cudaFuncSetAttribute(k_tc_update_c, cudaFuncAttributeMaxDynamicSharedMemorySize, TCC_SMEM);
+          if (e != cudaSuccess) return e;
+          attr_c = true;
+        }
+        TcCArgs cc;
+        cc.c_row0 = (int)c_row0;
+        cc.c_col0 = g.cc0 + c0;
+        feast_count_launch();
+        k_tc_update_c<<<grid, TC_THREADS, TCC_SMEM, s>>>(mA, mBc, mC, a, cc);
+        return cudaGetLastError();
+      }
+    }
+  }
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(ceil_div(2 * (size_t)g.M, TC_BM), g.q);
   feast_count_launch();
   k_tc_update<<<grid, TC_THREADS, TC_SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
