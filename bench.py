@@ -220,7 +220,7 @@ def profiled_traffic_ratio():
     """DRAM bytes per algorithmic byte of the trailing-update kernel, from the
     committed ncu summary (None when absent)."""
     import re
-    path = os.path.join(ROOT, "profiles", "k_tc_update_bifeast_n2048_mixed.md")
+    path = os.path.join(ROOT, "profiles", "k_tc_update_c_bifeast_n2048_mixed.md")
     try:
         m = re.search(r"traffic_per_algorithmic_byte:\s*([0-9.]+)", open(path).read())
         return float(m.group(1)) if m else None
@@ -448,7 +448,8 @@ def run_ours(args):
     bytes_per_launch = trailing_update_bytes(n, q, nb) / upd_n
     achieved = bytes_per_launch / avg_launch_s / 1e9 if upd_time > 0 else 0.0
     ratio = profiled_traffic_ratio()
-    roofline = {"kernel": "k_tc_update: LU trailing update A22 -= L21 U12 (complex64 C, split-BF16 tcgen05)",
+    roofline = {"kernel": "k_tc_update_c: LU trailing update A22 -= L21 U12 (complex64 C streamed by TMA, "
+                          "split-BF16 tcgen05)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (ratio * bytes_per_launch) if ratio else None,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "launches": upd_n,
