@@ -175,6 +175,9 @@ struct feast_handle {
   void* orth_scratch = nullptr;
   void* pw_scratch = nullptr;
   TcStaging staging;
+  TcStaging staging_left;              // the left solves' own staging (they run beside the right ones)
+  cudaStream_t side = nullptr;         // stream of the left solves
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   void* schur_log = nullptr;
   double2* gemm_ws = nullptr;  // split-K partial products
   // mixed path: FP64-accurate n x n x m0 products on the BF16 tensor cores
@@ -370,6 +373,8 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   LuBatch<T> lu = lu_view<T>(h);
   const int n = (int)h->n, m = h->m0;
   cplx<T>* Xs = reinterpret_cast<cplx<T>*>(h->Xs);
+  const bool split = Rh && !h->opt.symmetric && h->side;
+  if (split) CK(cudaEventRecord(h->fork_ev, h->st));  // the left solves start from here
   CK(rows_gather<T>(lu, R, Xs, m, true, h->st));
   CK(lu_solve_batched<T>(lu, 0, Xs, m, h->nbs, h->st));
   CK(accumulate<T>(Xs, h->q, n, m, h->coef, use_c0 ? h->c0 : nullptr, use_c0 ? Yc0 : nullptr, nullptr, Qout, h->st));
@@ -378,11 +383,21 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
     // and the left inputs are the conjugates of the right ones
     CK(conj_copy(Qout, Qhout, (size_t)n * m, h->st));
   } else if (Rh) {
+    // the left solves (U^H, then L^H) run on the side stream, beside the right
+    // ones: both are chains of small block steps that leave most SMs idle
     cplx<T>* Xsh = reinterpret_cast<cplx<T>*>(h->Xsh);
-    CK(rows_gather<T>(lu, Rh, Xsh, m, false, h->st));
-    CK(lu_solve_batched<T>(lu, 1, Xsh, m, h->nbs, h->st));
+    LuBatch<T> lul = lu;
+    if (std::is_same<T, float>::value) lul.tc = h->staging_left.Ast ? &h->staging_left : nullptr;
+    cudaStream_t ls = split ? h->side : h->st;
+    if (split) CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    CK(rows_gather<T>(lul, Rh, Xsh, m, false, ls));
+    CK(lu_solve_batched<T>(lul, 1, Xsh, m, h->nbs, ls));
     CK(accumulate<T>(Xsh, h->q, n, m, h->coefh, use_c0 ? h->c0h : nullptr, use_c0 ? Yhc0 : nullptr, lu.pinv,
-                     Qhout, h->st));
+                     Qhout, ls));
+    if (split) {
+      CK(cudaEventRecord(h->join_ev, h->side));
+      CK(cudaStreamWaitEvent(h->st, h->join_ev, 0));
+    }
   }
   return FEAST_OK;
 }
@@ -636,6 +651,12 @@ void feast_destroy(feast_handle* h) {
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->upd_ev) cudaEventDestroy(e);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   delete h;
 }
 
@@ -723,6 +744,18 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     h->staging.rows_max = 2 * n;
     h->staging.cols_max = n;
     h->staging.q = h->q;
+    if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
+      AL(h->staging_left.Ast, tc_staging_bytes_A(n, h->q));
+      AL(h->staging_left.Bst, tc_staging_bytes_B(n, h->q));
+      h->staging_left.rows_max = 2 * n;
+      h->staging_left.cols_max = n;
+      h->staging_left.q = h->q;
+    }
+  }
+  if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
+    if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   }
 #undef AL
   if (h->opt.timing)
