@@ -470,7 +470,8 @@ def run_ours(args):
             "speedup_vs_fp64_steady": (fp64["steady_iter_ms"] / steady_ms) if fp64 else None,
             "solve": {"ms": solve_ms, "iters": sol["iters"], "m_found": sol["m_found"],
                       "converged": sol["converged"], "max_res": float(np.max(resid)),
-                      "res_hist": sol["res_hist"]},
+                      "res_hist": sol["res_hist"], "t_factor_ms": sol["t_factor_ms"],
+                      "t_filter_ms": sol["t_filter_ms"], "t_rr_ms": sol["t_rr_ms"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches), "batched": batched,
         }

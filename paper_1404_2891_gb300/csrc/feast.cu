@@ -171,6 +171,7 @@ struct feast_handle {
   double2 *W = nullptr, *LUW = nullptr, *Minv = nullptr, *Zl = nullptr, *lam = nullptr, *dd = nullptr;
   double2 *coef = nullptr, *coefh = nullptr, *c0 = nullptr, *c0h = nullptr;
   int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *useresh = nullptr, *colidx = nullptr;
+  int* gate = nullptr;  // device flag: the Newton-Schulz inverse of W missed its tolerance
   double *res = nullptr, *resl = nullptr, *xn = nullptr, *xln = nullptr, *scal = nullptr;
   void* orth_scratch = nullptr;
   void* pw_scratch = nullptr;
@@ -495,16 +496,41 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     g32.A = Z32; g32.lda = m; g32.B = V32; g32.ldb = m; g32.C = W32; g32.ldc = m;
     CK(gemm_batched<float>(g32, h->st));
     CK(to_c128(W32, h->W, mm, h->st));
+    // W^{-1} = V^{-1} Z^H from the Schur factors (FP32), made FP64-accurate by
+    // Newton-Schulz steps X <- X (2I - W X) (quadratic convergence, DMMA products)
+    CK(small_triu_inv<float>(V32, C32, m, h->st));
+    GemmArgs<float> gi = g32;
+    gi.A = C32; gi.B = Z32; gi.opB = OP_C; gi.C = W32;
+    CK(gemm_batched<float>(gi, h->st));
+    CK(to_c128(W32, h->Minv, mm, h->st));
+    auto newton_schulz = [&](int steps) -> cudaError_t {
+      for (int it = 0; it < steps; ++it) {
+        cudaError_t e = set_identity(h->LUW, m, h->st);
+        if (e == cudaSuccess) e = zg(h, OP_N, OP_N, m, m, m, zc(-1.0), h->W, m, h->Minv, m, zc(2.0), h->LUW, m);
+        if (e == cudaSuccess) e = zg(h, OP_N, OP_N, m, m, m, one, h->Minv, m, h->LUW, m, zero, h->Zs, m);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->Minv, h->Zs, sm, cudaMemcpyDeviceToDevice, h->st);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    };
+    // guard: when ||W X - I|| > 1e-12 (an ill-conditioned W, or a start too far
+    // off for the iteration) the inverse is recomputed by LU on the device
+    auto inverse_guard = [&]() -> cudaError_t {
+      cudaError_t e = zg(h, OP_N, OP_N, m, m, m, one, h->W, m, h->Minv, m, zero, h->Zs, m);
+      if (e == cudaSuccess) e = inverse_check(h->Zs, m, 1e-12, h->gate, h->st);
+      if (e == cudaSuccess) e = small_inverse_gated(h->W, h->LUW, h->pivW, h->Minv, m, h->flags, h->gate, h->st);
+      return e;
+    };
+    CK(newton_schulz(3));
+    CK(inverse_guard());
     for (int sweep = 0; sweep < 2; ++sweep) {
-      CK(cudaMemcpyAsync(h->LUW, h->W, sm, cudaMemcpyDeviceToDevice, h->st));
-      CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
-      CK(set_identity(h->Minv, m, h->st));
-      CK(small_lu_solve(h->LUW, h->pivW, m, h->Minv, m, 0, h->st));
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->Cm, m, h->W, m, zero, h->V, m));
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->Minv, m, h->V, m, zero, h->Zs, m));
       CK(eig_refine_step(h->Zs, h->Ahat, h->lam, m, h->st));
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->W, m, h->Ahat, m, zero, h->LUW, m));
       CK(cudaMemcpyAsync(h->W, h->LUW, sm, cudaMemcpyDeviceToDevice, h->st));
+      CK(newton_schulz(2 - sweep));  // W changed by O(Delta): quadratic steps from the old inverse
+      CK(inverse_guard());
     }
   }
   // Ritz vectors and residuals
@@ -534,10 +560,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
         BhQp = h->BhQ;
       }
     }
-    CK(cudaMemcpyAsync(h->LUW, h->W, sm, cudaMemcpyDeviceToDevice, h->st));
-    CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
-    CK(set_identity(h->Minv, m, h->st));
-    CK(small_lu_solve(h->LUW, h->pivW, m, h->Minv, m, 0, h->st));
+    // Minv holds W^{-1} (Newton-Schulz above)
     CK(conj_transpose(h->Minv, m, m, h->Zl, h->st));
     CK(small_lu_solve(h->LUB, h->pivB, m, h->Zl, m, 1, h->st));
     CK(zg(h, OP_N, OP_N, n, m, m, one, h->Qho, n, h->Zl, m, zero, h->Xl, n));
@@ -721,6 +744,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->useres, m0 * sizeof(int));
   AL(h->useresh, m0 * sizeof(int));
   AL(h->colidx, m0 * sizeof(int));
+  AL(h->gate, 64);
   AL(h->res, m0 * sizeof(double));
   AL(h->resl, m0 * sizeof(double));
   AL(h->xn, m0 * sizeof(double));

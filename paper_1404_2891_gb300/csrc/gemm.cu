@@ -279,9 +279,9 @@ cudaError_t gemm_batched<double>(const GemmArgs<double>& g0, cudaStream_t s) {
   int S = 1;
   // split only when the tiles fill less than half of the 152 SMs, and keep the
   // split grid within one wave (one 256-thread block per SM)
-  if (g.ws && tiles < 76 && g.K >= 8 * BK64 * 4) {
+  if (g.ws && tiles < 76 && g.K >= 4 * BK64 * 2) {
     S = (int)(152 / tiles);
-    S = min(S, g.K / (BK64 * 4));
+    S = min(S, g.K / (BK64 * 2));  // chunks of at least 16
     while (S > 1 && (size_t)S * g.M * g.N * g.batch > g.ws_elems) --S;
   }
   g.splitk = S;

@@ -435,6 +435,50 @@ cudaError_t small_trevc(const cplx<T>* Tm, cplx<T>* V, int m, cudaStream_t s) {
 template cudaError_t small_trevc<float>(const float2*, float2*, int, cudaStream_t);
 template cudaError_t small_trevc<double>(const double2*, double2*, int, cudaStream_t);
 
+namespace {
+// Inverse of an upper triangular m x m matrix, one column per thread (back
+// substitution for V x = e_j); one block per matrix (grid y = problem index).
+template <typename T>
+__global__ void k_triu_inv(const cplx<T>* V, cplx<T>* Vi, int m, long long stride, const GrpDesc* pd,
+                           const int* active) {
+  int mm = m;
+  size_t off = (size_t)blockIdx.y * stride;
+  if (pd) {
+    if (!active[blockIdx.y]) return;
+    mm = pd[blockIdx.y].m;
+    off = (size_t)pd[blockIdx.y].omm;
+  }
+  const cplx<T>* Vb = V + off;
+  cplx<T>* X = Vi + off;
+  for (int j = threadIdx.x; j < mm; j += blockDim.x) {
+    cplx<T>* x = X + (size_t)j * mm;
+    for (int i = j + 1; i < mm; ++i) x[i] = mk<T>(T(0), T(0));
+    x[j] = crecip<T>(Vb[j + (size_t)j * mm]);
+    for (int i = j - 1; i >= 0; --i) {
+      cplx<T> acc = mk<T>(T(0), T(0));
+      for (int k = i + 1; k <= j; ++k) acc = cadd<T>(acc, cmul<T>(Vb[i + (size_t)k * mm], x[k]));
+      x[i] = cmul<T>(mk<T>(-acc.x, -acc.y), crecip<T>(Vb[i + (size_t)i * mm]));
+    }
+  }
+}
+}  // namespace
+
+template <typename T>
+cudaError_t small_triu_inv(const cplx<T>* V, cplx<T>* Vi, int m, cudaStream_t s) {
+  feast_count_launch();
+  k_triu_inv<T><<<1, ((m + 31) / 32) * 32, 0, s>>>(V, Vi, m, 0, nullptr, nullptr);
+  return cudaGetLastError();
+}
+template cudaError_t small_triu_inv<float>(const float2*, float2*, int, cudaStream_t);
+
+cudaError_t small_triu_inv_grp(const float2* V, float2* Vi, const GrpDesc* pd, int np, int mmax, const int* active,
+                               cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_triu_inv<float><<<dim3(1, np), ((mmax + 31) / 32) * 32, 0, s>>>(V, Vi, 0, 0, pd, active);
+  return cudaGetLastError();
+}
+
 cudaError_t eig_refine_step(const double2* E, double2* D, double2* lam, int m, cudaStream_t s) {
   feast_count_launch();
   k_refine_step<<<1, 1024, 0, s>>>(E, D, lam, m);

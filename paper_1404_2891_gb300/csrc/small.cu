@@ -86,18 +86,28 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
       for (int i = tid; i < j; i += ORTH_THREADS) {
         const double2* qi = Q + (size_t)i * n;
         double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 8
         for (int r = r0; r < r1; ++r) acc = cadd<double>(acc, cmulc<double>(qi[r], qj[r]));
         part[(size_t)g * m + i] = acc;
       }
       if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
-      for (int i = tid; i < j; i += ORTH_THREADS) {
+      // one warp per coefficient: the G partial dot products are read in
+      // parallel and summed by shuffles (a fixed order)
+      for (int i = tid >> 5; i < j; i += ORTH_THREADS / 32) {
+        const int lane = tid & 31;
         double2 acc = make_double2(0.0, 0.0);
-        for (int gg = 0; gg < G; ++gg) acc = cadd<double>(acc, part[(size_t)gg * m + i]);
-        s_r[i] = acc;
+        for (int gg = lane; gg < G; gg += 32) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * m + i));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) s_r[i] = acc;
       }
       __syncthreads();
       for (int r = r0 + tid; r < r1; r += ORTH_THREADS) {
         double2 acc = qj[r];
+#pragma unroll 8
         for (int i = 0; i < j; ++i) acc = csub<double>(acc, cmul<double>(Q[(size_t)i * n + r], s_r[i]));
         qj[r] = acc;
       }
@@ -111,7 +121,8 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
     if (tid == 0) part[(size_t)g * m] = make_double2(loc, 0.0);
     if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
     double tot = 0.0;
-    for (int gg = 0; gg < G; ++gg) tot += part[(size_t)gg * m].x;
+    for (int gg = tid; gg < G; gg += ORTH_THREADS) tot += __ldcg(&part[(size_t)gg * m].x);
+    tot = block_sum(tot, red);
     const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
     for (int r = r0 + tid; r < r1; r += ORTH_THREADS) qj[r] = cscale<double>(qj[r], inv);
     __syncthreads();
@@ -281,6 +292,46 @@ k_small_lu_solve_grp(const double2* LU, const int* piv, const GrpDesc* pd, const
   small_lu_solve_body(LU + d.omm, piv + d.om, d.m, X + d.omm, d.m, trans, blockIdx.x);
 }
 
+// gate = (max_ij |T_ij - delta_ij| > tol): T = W X checks an approximate inverse X of W.
+__global__ void __launch_bounds__(256) k_inv_check(const double2* T, int m, double tol, int* gate) {
+  __shared__ double red[8];
+  double mx = 0.0;
+  for (int idx = threadIdx.x; idx < m * m; idx += 256) {
+    double2 v = T[idx];
+    if (idx % m == idx / m) v.x -= 1.0;
+    const double a = cabs1<double>(v);
+    mx = (a > mx || a != a) ? a : mx;  // a NaN entry fails the check too
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, mx, off);
+    mx = (o > mx || o != o) ? o : mx;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) mx = (red[w] > mx || red[w] != red[w]) ? red[w] : mx;
+    *gate = (mx > tol || mx != mx) ? 1 : 0;
+  }
+}
+
+// When *gate != 0: X = W^{-1} by LU with partial pivoting (LU, piv scratch); else nothing.
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_small_inv_gated(const double2* W, double2* LU, int* piv, double2* X, int m, unsigned* flags, const int* gate) {
+  if (*gate == 0) return;
+  for (int idx = threadIdx.x; idx < m * m; idx += SMALL_THREADS) LU[idx] = W[idx];
+  __syncthreads();
+  small_lu_body(LU, m, piv, flags);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += SMALL_THREADS)
+    X[idx] = make_double2((idx % m) == (idx / m) ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int bx = 0; bx * SOLVE_COLS < m; ++bx) {
+    small_lu_solve_body(LU, piv, m, X, m, 0, bx);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
@@ -356,3 +407,16 @@ cudaError_t small_lu_solve_grp(const double2* LU, const int* piv, const GrpDesc*
   return cudaGetLastError();
 }
 
+
+cudaError_t inverse_check(const double2* T, int m, double tol, int* gate, cudaStream_t s) {
+  feast_count_launch();
+  k_inv_check<<<1, 256, 0, s>>>(T, m, tol, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t small_inverse_gated(const double2* W, double2* LU, int* piv, double2* X, int m, unsigned* flags,
+                                const int* gate, cudaStream_t s) {
+  feast_count_launch();
+  k_small_inv_gated<<<1, SMALL_THREADS, 0, s>>>(W, LU, piv, X, m, flags, gate);
+  return cudaGetLastError();
+}

@@ -27,6 +27,11 @@ cudaError_t small_schur(cplx<T>* C, cplx<T>* Z, cplx<T>* lam, int m, unsigned* f
 // Eigenvectors of the upper triangular T (V, m x m, unit diagonal entry, back substitution).
 template <typename T>
 cudaError_t small_trevc(const cplx<T>* Tm, cplx<T>* V, int m, cudaStream_t s);
+// Vi = V^{-1} for an upper triangular m x m V (back substitution, one column per thread).
+template <typename T>
+cudaError_t small_triu_inv(const cplx<T>* V, cplx<T>* Vi, int m, cudaStream_t s);
+cudaError_t small_triu_inv_grp(const float2* V, float2* Vi, const GrpDesc* pd, int np, int mmax, const int* active,
+                               cudaStream_t s);
 // One refinement sweep of an approximate eigendecomposition C ~ W Lambda W^{-1}:
 // from E = W^{-1} C W, lam = diag(E) and D = I + Delta with
 // Delta_ij = E_ij / (E_jj - E_ii) (i != j; 0 where |E_jj - E_ii| <= tiny * ||E||),
@@ -57,3 +62,10 @@ cudaError_t small_trevc_grp(const float2* Tm, float2* V, const GrpDesc* pd, int 
                             cudaStream_t s);
 cudaError_t eig_refine_step_grp(const double2* E, double2* D, double2* lam, const GrpDesc* pd, int np,
                                 const int* active, cudaStream_t s);
+
+// gate = 1 when max |T - I| > tol (or T holds a NaN), else 0 (T = W X checks X ~ W^{-1}).
+cudaError_t inverse_check(const double2* T, int m, double tol, int* gate, cudaStream_t s);
+// When *gate != 0: X = W^{-1} by LU with partial pivoting (LU, piv: scratch); otherwise
+// the kernel returns at once.
+cudaError_t small_inverse_gated(const double2* W, double2* LU, int* piv, double2* X, int m, unsigned* flags,
+                                const int* gate, cudaStream_t s);
