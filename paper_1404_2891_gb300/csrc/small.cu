@@ -91,8 +91,15 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
         part[(size_t)g * m + i] = acc;
       }
       if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
-      // one warp per coefficient: the G partial dot products are read in
-      // parallel and summed by shuffles (a fixed order)
+      // the G partial dot products of each coefficient: few partials are summed
+      // by one thread each; many by one warp (parallel reads, shuffle sums)
+      if (G <= 16) {
+        for (int i = tid; i < j; i += ORTH_THREADS) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int gg = 0; gg < G; ++gg) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * m + i));
+          s_r[i] = acc;
+        }
+      } else
       for (int i = tid >> 5; i < j; i += ORTH_THREADS / 32) {
         const int lane = tid & 31;
         double2 acc = make_double2(0.0, 0.0);
