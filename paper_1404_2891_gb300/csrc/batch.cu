@@ -232,10 +232,10 @@ struct feast_batch {
   double2 *A = nullptr, *Y = nullptr, *Q = nullptr, *AQ = nullptr, *X = nullptr, *AX = nullptr, *E = nullptr,
           *Rhs = nullptr;
   double2 *Ahat = nullptr, *Bhat = nullptr, *LUB = nullptr, *Cm = nullptr, *Zs = nullptr, *V = nullptr,
-          *W = nullptr, *LUW = nullptr, *Minv = nullptr;
+          *W = nullptr, *LUW = nullptr, *Minv = nullptr, *Binv = nullptr;
   float2 *C32 = nullptr, *Z32 = nullptr, *V32 = nullptr, *W32 = nullptr, *lam32 = nullptr;
   double2 *lam = nullptr, *coef = nullptr, *c0 = nullptr, *dz = nullptr;
-  int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *active = nullptr;
+  int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *active = nullptr, *gate = nullptr;
   double *res = nullptr, *xn = nullptr, *scal = nullptr;
   char* logs = nullptr;
   void* pw_scratch = nullptr;
@@ -247,7 +247,7 @@ struct feast_batch {
   int n_factor = 0, n_first = 0, n_solve = 0;
   double makespan = 0.0;
   int grid = 0;
-  GG g_AQ, g_Ahat, g_Bhat, g_W32, g_V, g_Zs, g_LUW, g_X, g_AX;
+  GG g_AQ, g_Ahat, g_Bhat, g_W32, g_Cm, g_V, g_Zs, g_LUW, g_X, g_AX;
   // A_p Q_p, FP64-accurate on the BF16 tensor cores: digits of every A_p (made at
   // creation) and one work area that the pencils' products use in turn
   std::vector<OzOperator> ozop;
@@ -404,15 +404,20 @@ cudaError_t enqueue_rr(feast_batch* b) {
   }
   CE(run_gg(b, b->g_Ahat));
   CE(run_gg(b, b->g_Bhat));
-  CE(cudaMemcpyAsync(b->LUB, b->Bhat, mmb, cudaMemcpyDeviceToDevice, b->st));
-  CE(small_lu_grp(b->LUB, b->d_pd, b->np, b->active, b->pivB, b->flags, b->st));
-  CE(cudaMemcpyAsync(b->Cm, b->Ahat, mmb, cudaMemcpyDeviceToDevice, b->st));
-  CE(small_lu_solve_grp(b->LUB, b->pivB, b->d_pd, b->np, b->mmax, b->active, b->Cm, 0, b->st));
+  // C = B^^{-1} A^.  Q is orthonormal, so B^ = I + E with E at rounding level:
+  // B^^{-1} = 2I - B^ to O(|E|^2) while max |E_ij| <= 1e-10 (for m <= 128 the
+  // dropped terms stay below 2e-16); a pencil past that gets B^^{-1} by LU.
+  CE(inverse_check_grp(b->Bhat, b->d_pd, b->np, b->active, 1e-10, b->gate, b->Binv, b->st));
+  CE(small_inverse_gated_grp(b->Bhat, b->LUB, b->pivB, b->Binv, b->d_pd, b->np, b->flags, b->gate, b->st));
+  CE(run_gg(b, b->g_Cm));
   CE(to_c64(b->Cm, b->C32, b->smm, b->st));
   CE(small_schur_grp(b->C32, b->Z32, b->lam32, b->d_pd, b->np, b->mmax, b->active, b->flags, b->logs, b->st));
   CE(small_trevc_grp(b->C32, b->V32, b->d_pd, b->np, b->mmax, b->active, b->st));
   CE(run_gg(b, b->g_W32));
   CE(to_c128(b->W32, b->W, b->smm, b->st));
+  // Two refinement sweeps E = W^{-1} C W, lam = diag(E), W <- W (I + Delta); W^{-1}
+  // by one LU per pencil (a CTA each: at m <= 128 this beats Newton-Schulz on the
+  // FP64 tensor cores, whose m x m products leave most SMs idle)
   for (int sweep = 0; sweep < 2; ++sweep) {
     CE(cudaMemcpyAsync(b->LUW, b->W, mmb, cudaMemcpyDeviceToDevice, b->st));
     CE(small_lu_grp(b->LUW, b->d_pd, b->np, b->active, b->pivW, b->flags, b->st));
@@ -653,7 +658,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
   AL(b->A, b->snn * sizeof(double2));
   double2** nms[] = {&b->Y, &b->Q, &b->AQ, &b->X, &b->AX, &b->E, &b->Rhs};
   for (double2** p : nms) AL(*p, b->snm * sizeof(double2));
-  double2** mms[] = {&b->Ahat, &b->Bhat, &b->LUB, &b->Cm, &b->Zs, &b->V, &b->W, &b->LUW, &b->Minv};
+  double2** mms[] = {&b->Ahat, &b->Bhat, &b->LUB, &b->Cm, &b->Zs, &b->V, &b->W, &b->LUW, &b->Minv, &b->Binv};
   for (double2** p : mms) AL(*p, b->smm * sizeof(double2));
   float2** m32[] = {&b->C32, &b->Z32, &b->V32, &b->W32};
   for (float2** p : m32) AL(*p, b->smm * sizeof(float2));
@@ -666,6 +671,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
   AL(b->pivW, b->sm * sizeof(int));
   AL(b->useres, b->sm * sizeof(int));
   AL(b->active, b->np * sizeof(int));
+  AL(b->gate, b->np * sizeof(int));
   AL(b->res, b->sm * sizeof(double));
   AL(b->xn, b->sm * sizeof(double));
   AL(b->scal, 64);
@@ -818,6 +824,9 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
            g.B = B->V32 + d.omm; g.ldb = d.m;
            g.C = B->W32 + d.omm; g.ldc = d.m;
            return g;
+         })) != FEAST_OK) return bad(s);
+    if ((s = make_gg<double>(b, b->g_Cm, [B](const GrpDesc& d) {
+           return zargs(d.m, d.m, d.m, B->Binv + d.omm, d.m, OP_N, B->Ahat + d.omm, d.m, OP_N, B->Cm + d.omm, d.m);
          })) != FEAST_OK) return bad(s);
     if ((s = make_gg<double>(b, b->g_V, [B](const GrpDesc& d) {
            return zargs(d.m, d.m, d.m, B->Cm + d.omm, d.m, OP_N, B->W + d.omm, d.m, OP_N, B->V + d.omm, d.m);

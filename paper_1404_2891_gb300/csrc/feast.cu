@@ -256,11 +256,11 @@ cudaError_t zg(feast_handle* h, int opA, int opB, int M, int N, int K, zc alpha,
   return gemm_batched<double>(g, h->st);
 }
 
-// C (n x m0) = op(M) X for M = A (which = 0) or B (which = 1), op = OP_N or OP_C:
+// C (n x cols, cols <= m0; default m0) = op(M) X for M = A (which = 0) or B (which = 1), op = OP_N or OP_C:
 // on the emulated-FP64 tensor-core path when the handle uses it (the digits of
 // op(M) are made on first use), else the DMMA GEMM.
-cudaError_t big_product(feast_handle* h, int which, int op, const double2* X, double2* C) {
-  const int n = (int)h->n, m = h->m0;
+cudaError_t big_product(feast_handle* h, int which, int op, const double2* X, double2* C, int cols = -1) {
+  const int n = (int)h->n, m = cols < 0 ? h->m0 : cols;
   const double2* Mx = which == 0 ? h->A : h->B;
   if (!h->use_oz) return zg(h, op, OP_N, n, m, n, zc(1.0), Mx, n, X, n, zc(0.0), C, n);
   const int slot = which * 2 + (op == OP_C ? 1 : 0);
@@ -929,7 +929,7 @@ feast_status feast_moments(feast_handle* h, const feast_z* V, int S, int kmax, f
   if ((s = copy_in(h, h->Y, V, cnt)) != FEAST_OK) return s;
   const double2* BV = h->Y;
   if (h->hasB) {
-    CK(zg(h, OP_N, OP_N, n, S, n, zc(1.0), h->B, n, h->Y, n, zc(0.0), h->BX, n));
+    CK(big_product(h, 1, OP_N, h->Y, h->BX, S));
     BV = h->BX;
   }
   s = mixed(h) ? moments_impl<float>(h, BV, S, kmax) : moments_impl<double>(h, BV, S, kmax);
@@ -961,11 +961,11 @@ feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat
   if ((s = upload_coefs(h, resform ? th.data() : nullptr, nullptr)) != FEAST_OK) return s;
   // right-hand sides: B Y (plain) or (A Y - B Y Theta) per column (residual form)
   double2* BY = h->Y;
-  if (h->hasB) { CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Y, n, zero, h->BX, n)); BY = h->BX; }
+  if (h->hasB) { CK(big_product(h, 1, OP_N, h->Y, h->BX)); BY = h->BX; }
   const double2* R = BY;
   if (resform) {
     CK(cudaMemcpyAsync(h->lam, theta, m * sizeof(double2), cudaMemcpyDefault, h->st));
-    CK(zg(h, OP_N, OP_N, n, m, n, one, h->A, n, h->Y, n, zero, h->AX, n));
+    CK(big_product(h, 0, OP_N, h->Y, h->AX));
     CK(residual_columns(h->AX, BY, h->lam, 0, n, m, h->E, h->res, nullptr, h->st));
     CK(select_columns(h->E, BY, h->useres, n, m, h->Rr, h->st));
     R = h->Rr;
@@ -973,10 +973,10 @@ feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat
   const double2* Rh = nullptr;
   if (Yhat) {
     double2* BhY = h->Yh;
-    if (h->hasB) { CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Yh, n, zero, h->BhX, n)); BhY = h->BhX; }
+    if (h->hasB) { CK(big_product(h, 1, OP_C, h->Yh, h->BhX)); BhY = h->BhX; }
     Rh = BhY;
     if (resform) {
-      CK(zg(h, OP_C, OP_N, n, m, n, one, h->A, n, h->Yh, n, zero, h->AhX, n));
+      CK(big_product(h, 0, OP_C, h->Yh, h->AhX));
       CK(residual_columns(h->AhX, BhY, h->lam, 1, n, m, h->Eh, h->resl, nullptr, h->st));
       CK(select_columns(h->Eh, BhY, h->useres, n, m, h->Rl, h->st));
       Rh = h->Rl;
@@ -1034,7 +1034,7 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
     // Bi-FEAST step 2: V0 = Vr (Vr^H B Y0)^{-H}
     if ((s = copy_in(h, h->Yh, Vrand ? Vrand : Y0, cnt)) != FEAST_OK) return s;
     const double2* BY0 = h->Y;
-    if (h->hasB) { CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Y, n, zero, h->BX, n)); BY0 = h->BX; }
+    if (h->hasB) { CK(big_product(h, 1, OP_N, h->Y, h->BX)); BY0 = h->BX; }
     CK(zg(h, OP_C, OP_N, m, m, n, one, h->Yh, n, BY0, n, zero, h->LUW, m));
     CK(small_lu(h->LUW, m, h->pivW, h->flags, h->st));
     CK(set_identity(h->Minv, m, h->st));
@@ -1054,11 +1054,11 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
     if (it == 1) {
       if ((s = upload_coefs(h, nullptr, nullptr)) != FEAST_OK) return s;
       double2* BY = h->Y;
-      if (h->hasB) { CK(zg(h, OP_N, OP_N, n, m, n, one, h->B, n, h->Y, n, zero, h->BX, n)); BY = h->BX; }
+      if (h->hasB) { CK(big_product(h, 1, OP_N, h->Y, h->BX)); BY = h->BX; }
       R = BY;
       if (bi) {
         double2* BhY = h->Yh;
-        if (h->hasB) { CK(zg(h, OP_C, OP_N, n, m, n, one, h->B, n, h->Yh, n, zero, h->BhX, n)); BhY = h->BhX; }
+        if (h->hasB) { CK(big_product(h, 1, OP_C, h->Yh, h->BhX)); BhY = h->BhX; }
         Rh = BhY;
       }
     } else if (!resform) {

@@ -39,18 +39,27 @@ __device__ __forceinline__ int exponent_of(double mx) {
 }
 
 // e[2i] = e[2i+1] = exponent of max |Re|, |Im| over row i of op(A).
-__global__ void k_oz_rowexp(const double2* A, long long lda, int n, int opA, int* e) {
+// OP_N: a block takes 32 rows, its 8 warps stride over the columns (each warp
+// reads 32 consecutive entries of a column), the warps' maxima meet in shared
+// memory.  OP_C: row i of A^H is column i of A, one block per column.
+__global__ void __launch_bounds__(256) k_oz_rowexp(const double2* A, long long lda, int n, int opA, int* e) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (opA == OP_N) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int i = blockIdx.x * 32 + lane;
     double mx = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double2 v = A[(size_t)i + (size_t)j * lda];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    if (i < n)
+      for (int j = warp; j < n; j += 8) {
+        const double2 v = A[(size_t)i + (size_t)j * lda];
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      }
+    red[warp][lane] = mx;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+      for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w][lane]);
+      e[2 * i] = e[2 * i + 1] = exponent_of(mx);
     }
-    e[2 * i] = e[2 * i + 1] = exponent_of(mx);
-  } else {  // row i of A^H is column i of A
-    __shared__ double red[8];
+  } else {
     const int i = blockIdx.x;
     if (i >= n) return;
     double mx = 0.0;
@@ -60,13 +69,42 @@ __global__ void k_oz_rowexp(const double2* A, long long lda, int n, int opA, int
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    if (lane == 0) red[warp][0] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+      for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w][0]);
       e[2 * i] = e[2 * i + 1] = exponent_of(mx);
     }
   }
+}
+
+// |v| 2^(sb - ex) rounded to the nearest integer (halves up), with v's sign, for
+// |v| < 2^ex and sb = s beta <= 59: the 53-bit significand of v shifted by
+// integer operations (a shift left of at most sb - 53 bits, so |N| <= 2^sb).
+__device__ __forceinline__ long long scaled_int(double v, int ex, int sb) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const bool neg = (bits >> 63) != 0;
+  int E = (int)((bits >> 52) & 0x7ff);
+  unsigned long long mant = bits & ((1ULL << 52) - 1);
+  if (E == 0) E = 1;  // subnormal: no hidden bit
+  else mant |= 1ULL << 52;
+  // |v| = mant 2^(E - 1075)
+  const int sh = E - 1075 + sb - ex;
+  unsigned long long N;
+  if (sh >= 0) N = mant << sh;
+  else if (sh < -54) N = 0;
+  else N = ((mant >> (-sh - 1)) + 1) >> 1;
+  return neg ? -(long long)N : (long long)N;
+}
+
+// Digit sl of N = sum_i d_i 2^((s-1-i) beta): d_0 = |N| >> (s-1) beta (at most
+// 2^beta), the others beta-bit fields; every digit carries N's sign.
+__device__ __forceinline__ float int_digit(long long N, int sl, int s, int beta) {
+  const unsigned long long u = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
+  unsigned long long q = u >> ((s - 1 - sl) * beta);
+  if (sl > 0) q &= (1ULL << beta) - 1;
+  const float f = (float)q;
+  return N < 0 ? -f : f;
 }
 
 // Two digits streams at once: t <- t 2^beta, d = rint(t), t <- t - d (all exact in FP64).
@@ -112,10 +150,12 @@ k_oz_split_L(const double2* A, long long lda, int n, int opA, const int* e, int 
     double t1 = (r & 1) ? a.x : -a.y;
     const long long row = 2LL * i + (r & 1);
     const int ex = e[row];
-    t0 = ldexp(t0, -ex);
-    t1 = ldexp(t1, -ex);
+    // t = sum_i d_i 2^(ex - (i+1) beta) + O(2^(ex - s beta)) by integer digits
+    const long long N0 = scaled_int(t0, ex, s * beta), N1 = scaled_int(t1, ex, s * beta);
     for (int sl = 0; sl < s; ++sl) {
-      __nv_bfloat162 d = next_digits(t0, t1, beta);
+      __nv_bfloat162 d;
+      d.x = __float2bfloat16_rn(int_digit(N0, sl, s, beta));  // |d| <= 2^beta <= 256: exact
+      d.y = __float2bfloat16_rn(int_digit(N1, sl, s, beta));
       reinterpret_cast<__nv_bfloat162*>(D + ((size_t)sl * M + row) * Kp)[j] = d;
     }
   }
@@ -383,11 +423,13 @@ void oz_work_layout(void* base, int n, int m, OzWork* w) {
 }
 
 cudaError_t oz_make_operator(const double2* A, long long lda, int opA, OzOperator& L, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(L.D, 0, (size_t)L.s * L.M * L.Kp * 2, s);
-  if (e != cudaSuccess) return e;
+  if (L.Kp > L.K) {  // zero the padding columns K..Kp-1 of every digit row (the rest is written below)
+    cudaError_t e = cudaMemset2DAsync(L.D + L.K, (size_t)L.Kp * 2, 0, (size_t)(L.Kp - L.K) * 2, (size_t)L.s * L.M, s);
+    if (e != cudaSuccess) return e;
+  }
   feast_count_launch();
   if (opA == OP_N)
-    k_oz_rowexp<<<(L.n + 255) / 256, 256, 0, s>>>(A, lda, L.n, opA, L.e);
+    k_oz_rowexp<<<(L.n + 31) / 32, 256, 0, s>>>(A, lda, L.n, opA, L.e);
   else
     k_oz_rowexp<<<L.n, 256, 0, s>>>(A, lda, L.n, opA, L.e);
   dim3 grid((L.n + 31) / 32, (L.n + 31) / 32);

@@ -7,8 +7,11 @@
 // C~'s rows 2i, 2i+1 are Re and Im of C's row i.
 //
 // Every row r of L is scaled by 2^-e_r (|L[r, :]| < 2^e_r) and cut into s
-// signed integer digits of beta bits: L[r, k] = 2^e_r sum_i d_i[r, k] 2^(-i beta)
-// + remainder; likewise every column of U~ with its own exponent f_c.  With
+// signed integer digits of beta bits: L[r, k] = 2^e_r sum_i d_i[r, k] 2^(-(i+1) beta)
+// + remainder (the digits of L are bit fields of the significand shifted to
+// s beta bits, rounded at the last one; those of U~ come from repeated
+// rounding, t <- 2^beta t - rint(2^beta t)); likewise every column of U~ with
+// its own exponent f_c.  With
 // K 2^(2 beta) <= 2^24 every digit product P_ij = D_i E_j (a BF16 tensor-core
 // GEMM with FP32 accumulation) is exact, and
 //     C~[r, c] = 2^(e_r + f_c) sum_{i + j <= s + 1} 2^(-(i + j) beta) P_ij[r, c]

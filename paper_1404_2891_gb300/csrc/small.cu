@@ -339,6 +339,62 @@ k_small_inv_gated(const double2* W, double2* LU, int* piv, double2* X, int m, un
   }
 }
 
+// Grouped check: gate[p] = active[p] && max_ij |T_ij - delta_ij| > tol (NaN fails);
+// with X non-null, X = 2I - T as well (the first-order inverse of a near-identity T).
+__global__ void __launch_bounds__(256)
+k_inv_check_grp(const double2* T, const GrpDesc* pd, const int* active, double tol, int* gate, double2* X) {
+  __shared__ double red[8];
+  const int p = blockIdx.x;
+  if (!active[p]) {
+    if (threadIdx.x == 0) gate[p] = 0;
+    return;
+  }
+  const GrpDesc d = pd[p];
+  const int m = d.m;
+  double mx = 0.0;
+  for (int idx = threadIdx.x; idx < m * m; idx += 256) {
+    const double2 t = T[d.omm + idx];
+    double2 v = t;
+    const bool diag = idx % m == idx / m;
+    if (diag) v.x -= 1.0;
+    if (X) X[d.omm + idx] = make_double2((diag ? 2.0 : 0.0) - t.x, -t.y);
+    const double a = cabs1<double>(v);
+    mx = (a > mx || a != a) ? a : mx;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, mx, off);
+    mx = (o > mx || o != o) ? o : mx;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) mx = (red[w] > mx || red[w] != red[w]) ? red[w] : mx;
+    gate[p] = (mx > tol || mx != mx) ? 1 : 0;
+  }
+}
+
+// Grouped fallback: X_p = W_p^{-1} by LU with partial pivoting where gate[p] != 0.
+__global__ void __launch_bounds__(SMALL_THREADS)
+k_small_inv_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const GrpDesc* pd, unsigned* flags,
+                      const int* gate) {
+  const int p = blockIdx.x;
+  if (gate[p] == 0) return;
+  const GrpDesc d = pd[p];
+  const int m = d.m;
+  for (int idx = threadIdx.x; idx < m * m; idx += SMALL_THREADS) LU[d.omm + idx] = W[d.omm + idx];
+  __syncthreads();
+  small_lu_body(LU + d.omm, m, piv + d.om, flags);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += SMALL_THREADS)
+    X[d.omm + idx] = make_double2((idx % m) == (idx / m) ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int bx = 0; bx * SOLVE_COLS < m; ++bx) {
+    small_lu_solve_body(LU + d.omm, piv + d.om, m, X + d.omm, m, 0, bx);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
@@ -425,5 +481,21 @@ cudaError_t small_inverse_gated(const double2* W, double2* LU, int* piv, double2
                                 const int* gate, cudaStream_t s) {
   feast_count_launch();
   k_small_inv_gated<<<1, SMALL_THREADS, 0, s>>>(W, LU, piv, X, m, flags, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t inverse_check_grp(const double2* T, const GrpDesc* pd, int np, const int* active, double tol, int* gate,
+                              double2* X, cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_inv_check_grp<<<np, 256, 0, s>>>(T, pd, active, tol, gate, X);
+  return cudaGetLastError();
+}
+
+cudaError_t small_inverse_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const GrpDesc* pd, int np,
+                                    unsigned* flags, const int* gate, cudaStream_t s) {
+  if (np < 1) return cudaSuccess;
+  feast_count_launch();
+  k_small_inv_gated_grp<<<np, SMALL_THREADS, 0, s>>>(W, LU, piv, X, pd, flags, gate);
   return cudaGetLastError();
 }

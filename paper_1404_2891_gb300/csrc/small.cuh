@@ -69,3 +69,10 @@ cudaError_t inverse_check(const double2* T, int m, double tol, int* gate, cudaSt
 // the kernel returns at once.
 cudaError_t small_inverse_gated(const double2* W, double2* LU, int* piv, double2* X, int m, unsigned* flags,
                                 const int* gate, cudaStream_t s);
+// Grouped forms: gate[p] = active[p] && max |T_p - I| > tol; with X non-null also
+// X_p = 2I - T_p (for a near-identity T_p, its inverse to O(|T_p - I|^2)).
+cudaError_t inverse_check_grp(const double2* T, const GrpDesc* pd, int np, const int* active, double tol, int* gate,
+                              double2* X, cudaStream_t s);
+// X_p = W_p^{-1} by LU (LU, piv: arena scratch) for the pencils with gate[p] != 0.
+cudaError_t small_inverse_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const GrpDesc* pd, int np,
+                                    unsigned* flags, const int* gate, cudaStream_t s);
