@@ -358,6 +358,17 @@ feast_status feast_batch_plan(int nmat, const int* nb, const int* m, int with_lu
 feast_status feast_emulated_zgemm(int64_t n, int64_t m, const feast_z* A, int64_t lda, int op, const feast_z* X,
                                   int64_t ldx, feast_z* C, int64_t ldc, void* stream);
 
+/* Diagnostic: Q (n x m, 1 <= m <= min(n, 256), ldq >= n, column-major
+ * complex128, host or device) replaced in place by the orthonormal basis of
+ * its columns that the Rayleigh-Ritz step uses (the orthogonalisation of the
+ * filtered block recommended at the close of Sec. 4): classical Gram-Schmidt
+ * applied twice, column by column, in FP64.  For a block of full numerical
+ * rank this is the Q of the QR factorisation with a positive real diagonal in
+ * R; a column that is dependent on the earlier ones is replaced by its
+ * normalised remainder (a remainder of exactly zero stays zero).  Allocates its own scratch (freed before return);
+ * returns after the stream has drained. */
+feast_status feast_orthonormalize(int64_t n, int64_t m, feast_z* Q, int64_t ldq, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; no paper counterpart). */
 uint64_t feast_kernel_launches(void);

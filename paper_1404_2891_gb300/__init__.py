@@ -81,7 +81,7 @@ SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_stat
            "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train",
            "feast_batch_create", "feast_batch_destroy", "feast_batch_factor", "feast_batch_filter",
            "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_plan",
-           "feast_emulated_zgemm")
+           "feast_emulated_zgemm", "feast_orthonormalize")
 
 
 class feast_batch_stats(ctypes.Structure):
@@ -165,6 +165,8 @@ def load(path=LIB_PATH):
     I64 = ctypes.c_int64
     lib.feast_emulated_zgemm.argtypes = [I64, I64, P, I64, I, P, I64, P, I64, P]
     lib.feast_emulated_zgemm.restype = I
+    lib.feast_orthonormalize.argtypes = [I64, I64, P, I64, P]
+    lib.feast_orthonormalize.restype = I
     _lib = lib
     return lib
 
@@ -530,8 +532,16 @@ def feast_emulated_zgemm(A, X, op="N"):
     m = X.shape[1] if X.ndim == 2 else 1
     C = np.zeros((n, m), dtype=np.complex128, order="F")
     _check(load().feast_emulated_zgemm(n, m, pa, n, {"N": 0, "C": 2}[op], px, n, C.ctypes.data, n, None),
-           "feast_emulated_zgemm")
+           "feast_emulated_zgemm", "feast_orthonormalize")
     return C
+
+
+def feast_orthonormalize(Q):
+    """Orthonormal basis of Q's columns by the library's FP64 CGS2 (diagnostic)."""
+    Q = np.array(Q, dtype=np.complex128, order="F", copy=True)
+    n, m = Q.shape
+    _check(load().feast_orthonormalize(n, m, Q.ctypes.data, n, None), "feast_orthonormalize")
+    return Q
 
 
 # ---------------------------------------------------------------- count predictor (m0)

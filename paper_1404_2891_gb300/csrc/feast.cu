@@ -1187,4 +1187,36 @@ feast_status feast_emulated_zgemm(int64_t n, int64_t m, const feast_z* A, int64_
   return release(f & DEVFLAG_TIMEOUT ? FEAST_ERR_DEVICE_TIMEOUT : FEAST_OK);
 }
 
+feast_status feast_orthonormalize(int64_t n, int64_t m, feast_z* Q, int64_t ldq, void* stream) {
+  if (n < 1 || m < 1 || m > 256 || m > n || !Q || ldq < n) return FEAST_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double2* dQ = nullptr;
+  void* scratch = nullptr;
+  unsigned* flags = nullptr;
+  auto release = [&](feast_status s) {
+    cudaStreamSynchronize(st);
+    cudaFree(dQ);
+    cudaFree(scratch);
+    cudaFree(flags);
+    return s;
+  };
+  if (cudaMalloc(&dQ, (size_t)n * m * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&scratch, orth_scratch_bytes((int)n, (int)m)) != cudaSuccess ||
+      cudaMalloc(&flags, 64) != cudaSuccess)
+    return release(FEAST_ERR_ALLOC);
+  if (cudaMemcpy2DAsync(dQ, n * sizeof(double2), Q, ldq * sizeof(double2), n * sizeof(double2), m, cudaMemcpyDefault,
+                        st) != cudaSuccess ||
+      cudaMemsetAsync(flags, 0, 64, st) != cudaSuccess)
+    return release(FEAST_ERR_CUDA);
+  if (orth_cgs2(dQ, (int)n, (int)m, scratch, flags, st) != cudaSuccess) return release(FEAST_ERR_CUDA);
+  if (cudaMemcpy2DAsync(Q, ldq * sizeof(double2), dQ, n * sizeof(double2), n * sizeof(double2), m, cudaMemcpyDefault,
+                        st) != cudaSuccess)
+    return release(FEAST_ERR_CUDA);
+  unsigned f = 0;
+  if (cudaMemcpyAsync(&f, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return release(FEAST_ERR_CUDA);
+  return release(f & DEVFLAG_TIMEOUT ? FEAST_ERR_DEVICE_TIMEOUT : FEAST_OK);
+}
+
 }  // extern "C"

@@ -1,16 +1,17 @@
 // Power iteration for ||A||_2 as one persistent cooperative kernel.
 //
-// Phase 1, y = A x: a block owns 32 rows and sweeps all columns (column-major
-// A: each warp reads 32 consecutive rows of a column, 512 B).  Phase 2,
-// z = A^H y: one warp per column, lanes down the contiguous column.  Phase 3:
-// ||z|| from one partial sum per block, x = z / ||z||.  Three bounded grid
-// barriers per iteration; A streams from HBM twice per iteration.
+// Phase 1, y = c A x (c = 1 / ||x|| from the previous step): a block owns 16
+// rows; lane l of a warp reads row l % 16 of column 2w + l / 16, 16 columns
+// per sweep over the 8 warps (256-byte segments).  Phase 2, x <- A^H y: one warp
+// per column, lanes down the contiguous column; one partial sum of |x|^2 per
+// block.  Two bounded grid barriers per iteration; A streams from HBM twice per
+// iteration, eight loads in flight per thread.
 #include "norm2.cuh"
 
 namespace {
 
 constexpr int PW_THREADS = 256;
-constexpr int PW_ROWS = 32;
+constexpr int PW_ROWS = 16;
 
 struct PowArgs {
   const double2* A;
@@ -57,37 +58,39 @@ __device__ bool pw_barrier(unsigned* bar, unsigned nblocks, unsigned* flags, int
 }
 
 __global__ void __launch_bounds__(PW_THREADS) k_norm2_power(PowArgs a) {
-  __shared__ double2 sacc[PW_THREADS / 32][PW_ROWS];
+  __shared__ double2 sacc[2 * PW_THREADS / 32][PW_ROWS];
   __shared__ double red[PW_THREADS / 32];
   __shared__ int s_ok;
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
   const int nblk = (n + PW_ROWS - 1) / PW_ROWS;
   const double2* A = a.A;
-  const double inv0 = 1.0 / sqrt((double)n);
-  for (int i = g * PW_THREADS + tid; i < n; i += G * PW_THREADS) a.x[i] = make_double2(inv0, 0.0);
+  constexpr int NSTREAM = 2 * PW_THREADS / 32;  // column streams of phase 1
+  for (int i = g * PW_THREADS + tid; i < n; i += G * PW_THREADS) a.x[i] = make_double2(1.0, 0.0);
+  double xs = 1.0 / sqrt((double)n);  // x = xs * (stored x): the unit start vector
   if (!pw_barrier(a.bar, G, a.flags, &s_ok)) return;
   double s = 0.0;
   for (int it = 0; it < a.iters; ++it) {
-    // y = A x
+    // y = xs A x
     for (int blk = g; blk < nblk; blk += G) {
-      const int r = blk * PW_ROWS + lane;
+      const int r = blk * PW_ROWS + (lane & 15);
+      const int stream = 2 * warp + (lane >> 4);
       double2 acc = make_double2(0.0, 0.0);
       if (r < n) {
-#pragma unroll 4
-        for (int c = warp; c < n; c += PW_THREADS / 32) cfma<double>(acc, A[(size_t)r + (size_t)c * a.lda], a.x[c]);
+#pragma unroll 8
+        for (int c = stream; c < n; c += NSTREAM) cfma<double>(acc, A[(size_t)r + (size_t)c * a.lda], a.x[c]);
       }
-      sacc[warp][lane] = acc;
+      sacc[stream][lane & 15] = acc;
       __syncthreads();
-      if (warp == 0 && r < n) {
-        double2 t = sacc[0][lane];
-        for (int w = 1; w < PW_THREADS / 32; ++w) t = cadd<double>(t, sacc[w][lane]);
-        a.y[r] = t;
+      if (tid < PW_ROWS && blk * PW_ROWS + tid < n) {
+        double2 t = sacc[0][tid];
+        for (int w = 1; w < NSTREAM; ++w) t = cadd<double>(t, sacc[w][tid]);
+        a.y[blk * PW_ROWS + tid] = cscale<double>(t, xs);
       }
       __syncthreads();
     }
     if (!pw_barrier(a.bar, G, a.flags, &s_ok)) return;
-    // z = A^H y, kept in x until normalised
+    // x = A^H y (unnormalised; the next phase 1 applies 1 / ||x||)
     double loc = 0.0;
     for (int blk = g; blk < nblk; blk += G) {
       for (int cc = warp; cc < PW_ROWS; cc += PW_THREADS / 32) {
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_norm2_power(PowArgs a) {
         if (c >= n) continue;
         const double2* col = A + (size_t)c * a.lda;
         double2 acc = make_double2(0.0, 0.0);
-#pragma unroll 4
+#pragma unroll 8
         for (int r = lane; r < n; r += 32) acc = cadd<double>(acc, cmulc<double>(col[r], a.y[r]));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -118,14 +121,9 @@ __global__ void __launch_bounds__(PW_THREADS) k_norm2_power(PowArgs a) {
     if (!pw_barrier(a.bar, G, a.flags, &s_ok)) return;
     double tot = 0.0;
     for (int k = 0; k < G; ++k) tot += a.part[k];
-    const double nz = sqrt(tot);
+    const double nz = sqrt(tot);  // ||A^H A u|| for the unit vector u of this step
     s = sqrt(nz);
-    const double inv = nz > 0.0 ? 1.0 / nz : 0.0;
-    for (int blk = g; blk < nblk; blk += G) {
-      const int c = blk * PW_ROWS + tid;
-      if (tid < PW_ROWS && c < n) a.x[c] = cscale<double>(a.x[c], inv);
-    }
-    if (!pw_barrier(a.bar, G, a.flags, &s_ok)) return;
+    xs = nz > 0.0 ? 1.0 / nz : 0.0;
   }
   if (g == 0 && tid == 0) *a.out = s;
 }

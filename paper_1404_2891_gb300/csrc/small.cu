@@ -160,6 +160,125 @@ k_orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, double2*
   orth_body(a, blockIdx.x - cta0[p], G);
 }
 
+// CGS2 with every CTA's rows of Q resident in shared memory (rows_per x (m + 1),
+// padded so that a warp reading one row of 32 columns and a warp reading one
+// column of 32 rows both meet distinct banks).  Two grid barriers per column:
+// pass 1 of column j also carries the partial |q_{j-1}|^2, so that q_{j-1} is
+// normalised (and its coefficient rescaled) after the same reduction.  The
+// partial sums of a phase sit in part[(phase & 1)][g * (m + 1) + slot].
+constexpr int ORTH_SM_BYTES_MAX = 200 * 1024;
+
+__global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
+  extern __shared__ double2 sQ[];
+  __shared__ double2 s_r[ORTH_MAX_M + 1];
+  __shared__ double2 s_red[ORTH_THREADS + ORTH_MAX_M + 1];
+  __shared__ int s_ok;
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int n = a.n, m = a.m, ld = m + 1, S = m + 1;
+  const int r0 = min(n, g * a.rows_per), R = min(n, r0 + a.rows_per) - r0;
+  for (int idx = tid; idx < R * m; idx += ORTH_THREADS) {
+    const int rl = idx % R, c = idx / R;
+    sQ[rl * ld + c] = a.Q[(size_t)c * n + r0 + rl];
+  }
+  __syncthreads();
+  int phase = 0;
+  // s_r[0..ns) = the reduced slots of one phase: slot i < j the coefficient
+  // q_i^H q_j; slot j (when norm) the squared norm of column j - 1.
+  auto reduce_phase = [&](int j, bool norm) -> bool {
+    const int ns = j + (norm ? 1 : 0);
+    const int groups = ns <= ORTH_THREADS ? ORTH_THREADS / ns : 1;
+    for (int t = tid; t < ns * groups; t += ORTH_THREADS) {
+      const int i = t % ns, gr = t / ns;
+      double2 acc = make_double2(0.0, 0.0);
+      if (i < j) {
+#pragma unroll 4
+        for (int rl = gr; rl < R; rl += groups) acc = cadd<double>(acc, cmulc<double>(sQ[rl * ld + i], sQ[rl * ld + j]));
+      } else {
+        for (int rl = gr; rl < R; rl += groups) acc.x += cnorm2<double>(sQ[rl * ld + j - 1]);
+      }
+      s_red[t] = acc;
+    }
+    __syncthreads();
+    double2* part = a.part + (size_t)(phase & 1) * G * S;
+    for (int i = tid; i < ns; i += ORTH_THREADS) {
+      double2 acc = s_red[i];
+      for (int gr = 1; gr < groups; ++gr) acc = cadd<double>(acc, s_red[gr * ns + i]);
+      part[(size_t)g * S + i] = acc;
+    }
+    ++phase;
+    if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return false;
+    // every CTA sums the G partials of every slot: thread (slot i, group k)
+    // takes the CTAs g = k mod K, the K groups meet in shared memory
+    const int K = ns <= ORTH_THREADS ? ORTH_THREADS / ns : 1;
+    for (int t = tid; t < ns * K; t += ORTH_THREADS) {
+      const int i = t % ns, k = t / ns;
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 8
+      for (int gg = k; gg < G; gg += K) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * S + i));
+      s_red[t] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < ns; i += ORTH_THREADS) {
+      double2 acc = s_red[i];
+      for (int k = 1; k < K; ++k) acc = cadd<double>(acc, s_red[k * ns + i]);
+      s_r[i] = acc;
+    }
+    __syncthreads();
+    return true;
+  };
+  // q_j -= sum_{i<j} q_i s_r[i] on this CTA's rows: warp w takes rows w, w+8, ...,
+  // its lanes split the i range, a shuffle sums the lanes
+  auto update = [&](int j) {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int rl = warp; rl < R; rl += ORTH_THREADS / 32) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int i = lane; i < j; i += 32) acc = cadd<double>(acc, cmul<double>(sQ[rl * ld + i], s_r[i]));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+      }
+      if (lane == 0) sQ[rl * ld + j] = csub<double>(sQ[rl * ld + j], acc);
+    }
+    __syncthreads();
+  };
+  auto normalise = [&](int c, double nrm2) {
+    const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+    for (int rl = tid; rl < R; rl += ORTH_THREADS) sQ[rl * ld + c] = cscale<double>(sQ[rl * ld + c], inv);
+    return inv;
+  };
+  for (int j = 1; j < m; ++j) {
+    // pass 1 with the norm of column j - 1
+    if (!reduce_phase(j, true)) return;
+    const double inv = normalise(j - 1, s_r[j].x);
+    if (tid == 0) s_r[j - 1] = cscale<double>(s_r[j - 1], inv);
+    __syncthreads();
+    update(j);
+    // pass 2
+    if (!reduce_phase(j, false)) return;
+    update(j);
+  }
+  // the norm of the last column
+  {
+    double loc = 0.0;
+    for (int rl = tid; rl < R; rl += ORTH_THREADS) loc += cnorm2<double>(sQ[rl * ld + m - 1]);
+    double* red = reinterpret_cast<double*>(s_red);
+    loc = block_sum(loc, red);
+    double2* part = a.part + (size_t)(phase & 1) * G * S;
+    if (tid == 0) part[(size_t)g * S] = make_double2(loc, 0.0);
+    if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
+    double tot = 0.0;
+    for (int gg = tid; gg < G; gg += ORTH_THREADS) tot += __ldcg(&part[(size_t)gg * S].x);
+    tot = block_sum(tot, red + 32);
+    normalise(m - 1, tot);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < R * m; idx += ORTH_THREADS) {
+    const int rl = idx % R, c = idx / R;
+    a.Q[(size_t)c * n + r0 + rl] = sQ[rl * ld + c];
+  }
+}
+
 // ---------------------------------------------------------------- small LU
 constexpr int SMALL_THREADS = 1024;
 
@@ -398,7 +517,7 @@ k_small_inv_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
-  return (size_t)2 * 160 * m * sizeof(double2) + 64;
+  return (size_t)2 * 160 * (m + 1) * sizeof(double2) + 64;
 }
 
 cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s) {
@@ -406,18 +525,38 @@ cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, 
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  OrthArgs a;
+  a.Q = Q; a.n = n; a.m = m;
+  a.bar = reinterpret_cast<unsigned*>(scratch);
+  a.part = reinterpret_cast<double2*>(reinterpret_cast<char*>(scratch) + 64);
+  a.flags = flags;
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 64, s);
+  if (e != cudaSuccess) return e;
+  // shared-memory form: one CTA per SM, each holding its rows of Q
+  {
+    int G = min(nsm, 160);
+    G = min(G, max(1, (n + 7) / 8));
+    a.rows_per = (n + G - 1) / G;
+    G = (n + a.rows_per - 1) / a.rows_per;
+    const size_t smem = (size_t)a.rows_per * (m + 1) * sizeof(double2);
+    if (m >= 2 && smem <= (size_t)ORTH_SM_BYTES_MAX) {
+      static bool attr = false;
+      if (!attr) {
+        e = cudaFuncSetAttribute(k_orth_cgs2_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTH_SM_BYTES_MAX);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      void* args[] = {&a};
+      feast_count_launch();
+      return cudaLaunchCooperativeKernel((void*)k_orth_cgs2_sm, dim3(G), dim3(ORTH_THREADS), args, smem, s);
+    }
+  }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_orth_cgs2, ORTH_THREADS, 0);
   int G = min(nsm * max(per, 1), 128);
   G = min(G, max(1, (n + 15) / 16));
   G = min(G, 160);
-  OrthArgs a;
-  a.Q = Q; a.n = n; a.m = m;
   a.rows_per = (n + G - 1) / G;
   G = (n + a.rows_per - 1) / a.rows_per;
-  a.bar = reinterpret_cast<unsigned*>(scratch);
-  a.part = reinterpret_cast<double2*>(reinterpret_cast<char*>(scratch) + 64);
-  a.flags = flags;
-  cudaMemsetAsync(a.bar, 0, 64, s);
   void* args[] = {&a};
   feast_count_launch();
   return cudaLaunchCooperativeKernel((void*)k_orth_cgs2, dim3(G), dim3(ORTH_THREADS), args, 0, s);
