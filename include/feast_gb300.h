@@ -364,8 +364,10 @@ feast_status feast_emulated_zgemm(int64_t n, int64_t m, const feast_z* A, int64_
  * filtered block recommended at the close of Sec. 4): classical Gram-Schmidt
  * applied twice, column by column, in FP64.  For a block of full numerical
  * rank this is the Q of the QR factorisation with a positive real diagonal in
- * R; a column that is dependent on the earlier ones is replaced by its
- * normalised remainder (a remainder of exactly zero stays zero).  Allocates its own scratch (freed before return);
+ * R.  A column that lies numerically in the span of the earlier ones (the
+ * second projection takes more than 1 - 1/sqrt(2) of what the first left:
+ * Kahan's twice-is-enough test) restarts from a unit vector, so the result
+ * stays orthonormal.  Allocates its own scratch (freed before return);
  * returns after the stream has drained. */
 feast_status feast_orthonormalize(int64_t n, int64_t m, feast_z* Q, int64_t ldq, void* stream);
 

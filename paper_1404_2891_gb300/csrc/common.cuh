@@ -34,6 +34,20 @@ template <typename T> FEAST_HD void cfma(cplx<T>& acc, cplx<T> a, cplx<T> b) {
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
 }
+// acc += conj(a) * b
+template <typename T> FEAST_HD void cfmac(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc -= a * b
+template <typename T> FEAST_HD void cfms(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
 // Division with Smith's scaling (avoids overflow/underflow of |b|^2).
 template <typename T> FEAST_HD cplx<T> cdiv(cplx<T> a, cplx<T> b) {
   if (fabs(b.x) >= fabs(b.y)) {

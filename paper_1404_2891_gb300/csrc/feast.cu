@@ -174,6 +174,7 @@ struct feast_handle {
   int* gate = nullptr;  // device flag: the Newton-Schulz inverse of W missed its tolerance
   double *res = nullptr, *resl = nullptr, *xn = nullptr, *xln = nullptr, *scal = nullptr;
   void* orth_scratch = nullptr;
+  void* orth_scratch2 = nullptr;       // the left block's orthonormalisation (side stream)
   void* pw_scratch = nullptr;
   TcStaging staging;
   TcStaging staging_left;              // the left solves' own staging (they run beside the right ones)
@@ -457,11 +458,18 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   const zc one(1.0), zero(0.0);
   CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned), h->st));
   CK(cudaMemcpyAsync(h->Qo, Qin, blk, cudaMemcpyDeviceToDevice, h->st));
-  CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st));
-  if (bi) {
-    CK(cudaMemcpyAsync(h->Qho, Qhin, blk, cudaMemcpyDeviceToDevice, h->st));
-    CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
+  if (bi) CK(cudaMemcpyAsync(h->Qho, Qhin, blk, cudaMemcpyDeviceToDevice, h->st));
+  // the left block is orthonormalised on the side stream, beside the right one
+  // and the products A Q, B Q (the two latency-bound kernels share the SMs)
+  const bool par = bi && h->side && h->orth_scratch2;
+  if (par) {
+    CK(cudaEventRecord(h->fork_ev, h->st));
+    CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    CK(orth_cgs2(h->Qho, n, m, h->orth_scratch2, h->flags, h->side));
+    CK(cudaEventRecord(h->join_ev, h->side));
   }
+  CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st));
+  if (bi && !par) CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
   const double2* Vb = bi ? h->Qho : h->Qo;
   CK(big_product(h, 0, OP_N, h->Qo, h->AQ));
   const double2* BQp = h->Qo;
@@ -469,6 +477,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     CK(big_product(h, 1, OP_N, h->Qo, h->BQ));
     BQp = h->BQ;
   }
+  if (par) CK(cudaStreamWaitEvent(h->st, h->join_ev, 0));
   CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, h->AQ, n, zero, h->Ahat, m));
   CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, BQp, n, zero, h->Bhat, m));
   // reduced problem: C = B^{-1} A^, Schur form, eigenvectors
@@ -777,6 +786,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     }
   }
   if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
+    AL(h->orth_scratch2, orth_scratch_bytes((int)n, m0));
     if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);

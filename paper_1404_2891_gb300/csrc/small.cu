@@ -45,6 +45,43 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* flags, i
   return *s_ok != 0;
 }
 
+// The same barrier with the generation word on its own 128-byte line (bar + 32)
+// and the waiters polling without sleeping, bounded by the global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 32;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 32, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == gen) {
+        if (global_ns() - t0 > 1000000000ull) {
+          atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
 // ---------------------------------------------------------------- CGS2
 constexpr int ORTH_THREADS = 256;
 constexpr int ORTH_MAX_M = 256;
@@ -69,6 +106,16 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
+// A column that the second projection shrinks below 1/sqrt(2) of what the first
+// left (or to zero) lies numerically in the span of the earlier columns
+// (Kahan's criterion for 'twice is enough'); it restarts from the unit vector
+// e_r, r drawn from the column index and the attempt number.  After
+// ORTH_RETRIES attempts the column is kept as it is.
+constexpr int ORTH_RETRIES = 3;
+__device__ __forceinline__ int orth_restart_row(int c, int attempt, int n) {
+  return (int)(((long long)c * 7919 + (long long)(attempt + 1) * 104729) % n);
+}
+
 // CTA g of the G that share one block Q.
 __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const int G) {
   __shared__ double2 s_r[ORTH_MAX_M];
@@ -78,29 +125,37 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
   const int n = a.n, m = a.m;
   const int r0 = min(n, g * a.rows_per), r1 = min(n, r0 + a.rows_per);
   double2* Q = a.Q;
-  int use = 0;
-  for (int j = 0; j < m; ++j) {
+  int use = 0, retries = 0;
+  double r1sq = 0.0;  // |q_j|^2 after the first projection
+  for (int j = 0; j < m;) {
     double2* qj = Q + (size_t)j * n;
+    r1sq = 0.0;
     for (int pass = 0; pass < 2 && j > 0; ++pass) {
       double2* part = a.part + (size_t)(use & 1) * G * m;
-      for (int i = tid; i < j; i += ORTH_THREADS) {
+      // the second pass also sums |q_j|^2 (slot j)
+      const int ns = pass == 1 ? j + 1 : j;
+      for (int i = tid; i < ns; i += ORTH_THREADS) {
         const double2* qi = Q + (size_t)i * n;
         double2 acc = make_double2(0.0, 0.0);
+        if (i < j) {
 #pragma unroll 8
-        for (int r = r0; r < r1; ++r) acc = cadd<double>(acc, cmulc<double>(qi[r], qj[r]));
+          for (int r = r0; r < r1; ++r) acc = cadd<double>(acc, cmulc<double>(qi[r], qj[r]));
+        } else {
+          for (int r = r0; r < r1; ++r) acc.x += cnorm2<double>(qj[r]);
+        }
         part[(size_t)g * m + i] = acc;
       }
       if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
       // the G partial dot products of each coefficient: few partials are summed
       // by one thread each; many by one warp (parallel reads, shuffle sums)
       if (G <= 16) {
-        for (int i = tid; i < j; i += ORTH_THREADS) {
+        for (int i = tid; i < ns; i += ORTH_THREADS) {
           double2 acc = make_double2(0.0, 0.0);
           for (int gg = 0; gg < G; ++gg) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * m + i));
           s_r[i] = acc;
         }
       } else
-      for (int i = tid >> 5; i < j; i += ORTH_THREADS / 32) {
+      for (int i = tid >> 5; i < ns; i += ORTH_THREADS / 32) {
         const int lane = tid & 31;
         double2 acc = make_double2(0.0, 0.0);
         for (int gg = lane; gg < G; gg += 32) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * m + i));
@@ -112,6 +167,7 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
         if (lane == 0) s_r[i] = acc;
       }
       __syncthreads();
+      if (pass == 1) r1sq = s_r[j].x;
       for (int r = r0 + tid; r < r1; r += ORTH_THREADS) {
         double2 acc = qj[r];
 #pragma unroll 8
@@ -130,10 +186,18 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
     double tot = 0.0;
     for (int gg = tid; gg < G; gg += ORTH_THREADS) tot += __ldcg(&part[(size_t)gg * m].x);
     tot = block_sum(tot, red);
+    ++use;
+    if ((!(tot > SAFE_MIN) || tot < 0.5 * r1sq) && retries < ORTH_RETRIES) {
+      const int rr = orth_restart_row(j, retries++, n);
+      for (int r = r0 + tid; r < r1; r += ORTH_THREADS) qj[r] = make_double2(r == rr ? 1.0 : 0.0, 0.0);
+      __syncthreads();
+      continue;
+    }
     const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
     for (int r = r0 + tid; r < r1; r += ORTH_THREADS) qj[r] = cscale<double>(qj[r], inv);
     __syncthreads();
-    ++use;
+    retries = 0;
+    ++j;
   }
 }
 
@@ -182,19 +246,19 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
   }
   __syncthreads();
   int phase = 0;
-  // s_r[0..ns) = the reduced slots of one phase: slot i < j the coefficient
-  // q_i^H q_j; slot j (when norm) the squared norm of column j - 1.
-  auto reduce_phase = [&](int j, bool norm) -> bool {
-    const int ns = j + (norm ? 1 : 0);
+  // s_r[0..ns) = the reduced slots of one phase: slot i < nc the coefficient
+  // q_i^H q_j; slot nc (when nc_norm >= 0) the squared norm of column nc_norm.
+  auto reduce_phase = [&](int j, int nc, int nc_norm) -> bool {
+    const int ns = nc + (nc_norm >= 0 ? 1 : 0);
     const int groups = ns <= ORTH_THREADS ? ORTH_THREADS / ns : 1;
     for (int t = tid; t < ns * groups; t += ORTH_THREADS) {
       const int i = t % ns, gr = t / ns;
       double2 acc = make_double2(0.0, 0.0);
-      if (i < j) {
+      if (i < nc) {
 #pragma unroll 4
-        for (int rl = gr; rl < R; rl += groups) acc = cadd<double>(acc, cmulc<double>(sQ[rl * ld + i], sQ[rl * ld + j]));
+        for (int rl = gr; rl < R; rl += groups) cfmac<double>(acc, sQ[rl * ld + i], sQ[rl * ld + j]);
       } else {
-        for (int rl = gr; rl < R; rl += groups) acc.x += cnorm2<double>(sQ[rl * ld + j - 1]);
+        for (int rl = gr; rl < R; rl += groups) acc.x += cnorm2<double>(sQ[rl * ld + nc_norm]);
       }
       s_red[t] = acc;
     }
@@ -206,7 +270,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
       part[(size_t)g * S + i] = acc;
     }
     ++phase;
-    if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return false;
+    if (!grid_barrier_spin(a.bar, G, a.flags, &s_ok)) return false;
     // every CTA sums the G partials of every slot: thread (slot i, group k)
     // takes the CTAs g = k mod K, the K groups meet in shared memory
     const int K = ns <= ORTH_THREADS ? ORTH_THREADS / ns : 1;
@@ -232,7 +296,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
     const int lane = tid & 31, warp = tid >> 5;
     for (int rl = warp; rl < R; rl += ORTH_THREADS / 32) {
       double2 acc = make_double2(0.0, 0.0);
-      for (int i = lane; i < j; i += 32) acc = cadd<double>(acc, cmul<double>(sQ[rl * ld + i], s_r[i]));
+      for (int i = lane; i < j; i += 32) cfma<double>(acc, sQ[rl * ld + i], s_r[i]);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -247,30 +311,36 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
     for (int rl = tid; rl < R; rl += ORTH_THREADS) sQ[rl * ld + c] = cscale<double>(sQ[rl * ld + c], inv);
     return inv;
   };
-  for (int j = 1; j < m; ++j) {
-    // pass 1 with the norm of column j - 1
-    if (!reduce_phase(j, true)) return;
-    const double inv = normalise(j - 1, s_r[j].x);
+  // column j: pass 1 carries the squared norm of column j - 1, which is then
+  // normalised, or restarted from e_r when the second projection took more
+  // than half of what the first left (the column lies in the span of the
+  // earlier ones: Kahan's criterion for 'twice is enough'); j = m only
+  // takes the norm of the last column.  Every CTA reduces the same partials in
+  // the same order, so all take the same branch.
+  int retries = 0;
+  double r1sq = 0.0;  // |q_{j-1}|^2 after its first projection (0 for column 0)
+  for (int j = 1; j <= m;) {
+    const int nc = j < m ? j : 0;
+    if (!reduce_phase(j, nc, j - 1)) return;
+    const double nrm2 = s_r[nc].x;
+    if ((!(nrm2 > SAFE_MIN) || nrm2 < 0.5 * r1sq) && retries < ORTH_RETRIES) {
+      const int c = j - 1, rr = orth_restart_row(c, retries++, n);
+      for (int rl = tid; rl < R; rl += ORTH_THREADS) sQ[rl * ld + c] = make_double2(r0 + rl == rr ? 1.0 : 0.0, 0.0);
+      __syncthreads();
+      if (c == 0) r1sq = 0.0;
+      j = c > 0 ? c : 1;  // project the restarted column again (column 0 needs no projection)
+      continue;
+    }
+    retries = 0;
+    const double inv = normalise(j - 1, nrm2);
+    if (j == m) break;
     if (tid == 0) s_r[j - 1] = cscale<double>(s_r[j - 1], inv);
     __syncthreads();
     update(j);
-    // pass 2
-    if (!reduce_phase(j, false)) return;
+    if (!reduce_phase(j, j, j)) return;  // pass 2, with |q_j|^2 after pass 1
+    r1sq = s_r[j].x;
     update(j);
-  }
-  // the norm of the last column
-  {
-    double loc = 0.0;
-    for (int rl = tid; rl < R; rl += ORTH_THREADS) loc += cnorm2<double>(sQ[rl * ld + m - 1]);
-    double* red = reinterpret_cast<double*>(s_red);
-    loc = block_sum(loc, red);
-    double2* part = a.part + (size_t)(phase & 1) * G * S;
-    if (tid == 0) part[(size_t)g * S] = make_double2(loc, 0.0);
-    if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
-    double tot = 0.0;
-    for (int gg = tid; gg < G; gg += ORTH_THREADS) tot += __ldcg(&part[(size_t)gg * S].x);
-    tot = block_sum(tot, red + 32);
-    normalise(m - 1, tot);
+    ++j;
   }
   __syncthreads();
   for (int idx = tid; idx < R * m; idx += ORTH_THREADS) {
@@ -517,7 +587,7 @@ k_small_inv_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
-  return (size_t)2 * 160 * (m + 1) * sizeof(double2) + 64;
+  return (size_t)2 * 160 * (m + 1) * sizeof(double2) + 256;
 }
 
 cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s) {
@@ -528,9 +598,9 @@ cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, 
   OrthArgs a;
   a.Q = Q; a.n = n; a.m = m;
   a.bar = reinterpret_cast<unsigned*>(scratch);
-  a.part = reinterpret_cast<double2*>(reinterpret_cast<char*>(scratch) + 64);
+  a.part = reinterpret_cast<double2*>(reinterpret_cast<char*>(scratch) + 256);
   a.flags = flags;
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, 64, s);
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 256, s);
   if (e != cudaSuccess) return e;
   // shared-memory form: one CTA per SM, each holding its rows of Q
   {

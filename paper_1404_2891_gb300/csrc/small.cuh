@@ -6,6 +6,8 @@
 
 // In-place orthonormalisation of the n x m block Q (ld n) by classical
 // Gram-Schmidt applied twice, one cooperative launch with bounded grid barriers.
+// A column that lies numerically in the span of the earlier ones (Kahan's
+// twice-is-enough test) restarts from a unit vector.
 // scratch: >= 2 * grid * m double2 + 4 unsigned (see orth_scratch_bytes).
 size_t orth_scratch_bytes(int n, int m);
 cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s);

@@ -64,8 +64,9 @@ def test_ill_conditioned_block():
 
 
 def test_dependent_columns():
-    # columns 20..39 repeat columns 0..19 (scaled): their remainders are rounding
-    # noise, which the second pass makes orthogonal to everything before
+    # columns 20..39 repeat columns 0..19 (scaled): nothing but rounding is left
+    # of them after the first projection; the result must still be orthonormal
+    # (such columns restart from unit vectors) and span the input
     fg = lib()
     rng = np.random.default_rng(13)
     base = cg(rng, 1500, 40)
