@@ -159,7 +159,7 @@ struct feast_handle {
   // device data
   double2 *A = nullptr, *B = nullptr, *dz = nullptr, *dw = nullptr, *dmu = nullptr;
   void* S = nullptr;
-  int32_t *piv = nullptr, *perm = nullptr, *pinv = nullptr;
+  int32_t *piv = nullptr, *perm = nullptr, *pinv = nullptr, *mv = nullptr;
   int* info = nullptr;
   unsigned* flags = nullptr;
   void *Xs = nullptr, *Xsh = nullptr;
@@ -240,6 +240,7 @@ LuBatch<T> lu_view(feast_handle* h) {
   lu.pinv = h->pinv;
   lu.info = h->info;
   lu.flags = h->flags;
+  lu.mv = h->mv;
   if (std::is_same<T, float>::value && h->staging.Ast) lu.tc = &h->staging;
   return lu;
 }
@@ -733,6 +734,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->piv, (size_t)h->q * n * sizeof(int32_t));
   AL(h->perm, (size_t)h->q * n * sizeof(int32_t));
   AL(h->pinv, (size_t)h->q * n * sizeof(int32_t));
+  AL(h->mv, (size_t)h->q * LU_MV_STRIDE * sizeof(int32_t));
   AL(h->info, h->q * sizeof(int));
   AL(h->flags, 64);
   AL(h->Xs, nm * std::max(h->q, 2) * esz);

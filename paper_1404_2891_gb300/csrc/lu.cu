@@ -155,6 +155,68 @@ k_laswp_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, c
     for (int r = tid >> 5; r < w; r += 8) A[(size_t)(k0 + r) + (size_t)c * ld] = X[r * 32 + cc];
 }
 
+// The same from the panel's moved-row list (mv: count, dst[128], src[128], rows
+// relative to k0): every moved element of a column is read first, then written
+// to its new row, so the loads of a column are all in flight at once instead of
+// one interchange after another.  Then U12 = L11^{-1} A12 on the right columns.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, const int32_t* mv) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* L = reinterpret_cast<cplx<T>*>(smem_raw);  // w x w, [r * w + s]
+  cplx<T>* X = L + w * w;                              // w x 32, [r * 32 + cc]
+  __shared__ cplx<T> vals[128 * 32];
+  __shared__ int s_d[128], s_s[128], s_cnt;
+  const int b = blockIdx.y, tid = threadIdx.x;
+  cplx<T>* A = S + (size_t)b * stride;
+  const int32_t* m = mv + (size_t)b * LU_MV_STRIDE;
+  if (tid == 0) s_cnt = min(max(m[0], 0), 128);
+  for (int e = tid; e < 128; e += 256) {
+    s_d[e] = m[1 + e];
+    s_s[e] = m[129 + e];
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  const int nother = n - w;
+  for (int idx = tid; idx < cnt * 32; idx += 256) {
+    const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
+    if (o < nother) {
+      const int c = o < k0 ? o : o + w;
+      vals[idx] = A[(size_t)(k0 + s_s[e]) + (size_t)c * ld];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < cnt * 32; idx += 256) {
+    const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
+    if (o < nother) {
+      const int c = o < k0 ? o : o + w;
+      A[(size_t)(k0 + s_d[e]) + (size_t)c * ld] = vals[idx];
+    }
+  }
+  const int o = blockIdx.x * 32 + (tid & 31);
+  const bool valid = o < nother;
+  const int c = valid ? (o < k0 ? o : o + w) : 0;
+  const bool right = valid && c >= k0 + w;
+  const int o_last = min(blockIdx.x * 32 + 31, nother - 1);
+  if (o_last < k0) return;  // no column of this CTA lies right of the panel
+  __syncthreads();
+  for (int idx = tid; idx < w * w; idx += 256) {
+    const int r = idx % w, s2 = idx / w;
+    L[r * w + s2] = A[(size_t)(k0 + r) + (size_t)(k0 + s2) * ld];
+  }
+  const int cc = tid & 31;
+  for (int r = tid >> 5; r < w; r += 8) X[r * 32 + cc] = right ? A[(size_t)(k0 + r) + (size_t)c * ld] : czero<T>();
+  __syncthreads();
+  for (int s2 = 0; s2 < w - 1; ++s2) {
+    const cplx<T> xs = X[s2 * 32 + cc];
+    for (int r = s2 + 1 + (tid >> 5); r < w; r += 8)
+      X[r * 32 + cc] = csub<T>(X[r * 32 + cc], cmul<T>(L[r * w + s2], xs));
+    __syncthreads();
+  }
+  if (right)
+    for (int r = tid >> 5; r < w; r += 8) A[(size_t)(k0 + r) + (size_t)c * ld] = X[r * 32 + cc];
+}
+
 // Row permutation vector from the interchange sequence: perm = P applied to 0..n-1.
 __global__ void k_piv_to_perm(const int32_t* piv, int32_t* perm, int32_t* pinv, int n) {
   const int b = blockIdx.x;
@@ -288,7 +350,7 @@ constexpr int PLL_GCAP = 16384;  // group buffer: 128 KB of complex64
 template <int GW>
 __global__ void __launch_bounds__(PLL_THREADS)
 k_panel_ll(float2* S, long long ld, long long stride, int n, int k0, int w, int32_t* piv, int* info, unsigned* flags,
-           int gcap) {
+           int gcap, int32_t* mv) {
   extern __shared__ __align__(16) unsigned char pll_smem[];
   __shared__ PanelShared sh;
   const int b = blockIdx.x;
@@ -297,6 +359,15 @@ k_panel_ll(float2* S, long long ld, long long stride, int n, int k0, int w, int3
   int* pl = reinterpret_cast<int*>(G + gcap);
   panel_ll<GW, PLL_THREADS>(S + (size_t)b * stride, ld, n, k0, w, piv + (size_t)b * n + k0, info + b, flags, Lt, G,
                             pl, sh);
+  if (mv) {  // the moved rows, for the interchanges on the other columns
+    int32_t* o = mv + (size_t)b * LU_MV_STRIDE;
+    const int cnt = sh.cnt;
+    if (threadIdx.x == 0) o[0] = cnt;
+    for (int e = threadIdx.x; e < cnt; e += PLL_THREADS) {
+      o[1 + e] = sh.mvd[e];
+      o[129 + e] = sh.mvs[e];
+    }
+  }
 }
 
 size_t pll_smem_bytes(int n, int gcap) { return (size_t)64 * 64 * sizeof(float2) + (size_t)gcap * sizeof(float2) + (size_t)n * sizeof(int); }
@@ -308,7 +379,7 @@ cudaError_t launch_panel_ll(const LuBatch<float>& lu, int k0, int w, int gcap, c
   if (e != cudaSuccess) return e;
   feast_count_launch();
   k_panel_ll<GW><<<lu.q, PLL_THREADS, smem, s>>>(reinterpret_cast<float2*>(lu.S), lu.ld, lu.stride, lu.n, k0, w,
-                                                 lu.piv, lu.info, lu.flags, gcap);
+                                                 lu.piv, lu.info, lu.flags, gcap, lu.mv);
   return cudaGetLastError();
 }
 
@@ -356,11 +427,24 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
   };
   if ((e = cudaEventCreateWithFlags(&ev_next, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
   if ((e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  // the complex64 group panel leaves its moved-row list for the interchanges
+  const bool use_mv = std::is_same<T, float>::value && lu.mv && nb <= 64 && lu.n <= PLL_GCAP;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_mv && (e = cudaFuncSetAttribute(k_laswp_mv_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)diag_smem<float>(nb))) != cudaSuccess)
+      return e;
+  }
   auto laswp = [&](int k0, int w) -> cudaError_t {
     const int nother = lu.n - w;
     if (nother <= 0) return cudaSuccess;
     dim3 grid(ceil_div(nother, 32), lu.q);
     feast_count_launch();
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_mv) {
+        k_laswp_mv_trsm<float><<<grid, 256, diag_smem<float>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.mv);
+        return cudaGetLastError();
+      }
+    }
     k_laswp_trsm<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv);
     return cudaGetLastError();
   };

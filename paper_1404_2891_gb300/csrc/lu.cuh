@@ -16,7 +16,11 @@ struct LuBatch {
   int* info = nullptr;      // q ints: 0 or 1 + first column with an exact zero pivot
   unsigned* flags = nullptr;
   void* tc = nullptr;       // tensor-core staging (complex64 path), or nullptr
+  // q x LU_MV_STRIDE ints, or nullptr: the last panel's moved rows {count, dst[128], src[128]}
+  // (relative to the panel's first row), written by the complex64 panel for the interchanges
+  int32_t* mv = nullptr;
 };
+constexpr int LU_MV_STRIDE = 257;
 
 // Trailing-update hook of panel step (k0, w): the columns c0 .. c0+nc-1 of
 // the trailing block, C = S[k0+w:, c0:c0+nc] -= L21 U12[:, c0 - (k0+w) ...],

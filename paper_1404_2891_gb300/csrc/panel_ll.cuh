@@ -75,22 +75,51 @@ __device__ void panel_ll(float2* A, long long ld, int N, int r0, int w, int* piv
         if (lane + 32 < g0) Gc[lane + 32] = x1;
       }
       __syncthreads();
-      // the remaining rows: G[r, c] -= sum_{t < g0} L[r, t] U[t, c]
-      for (int r = g0 + tid; r < R; r += NT) {
-        float2 acc[GW];
+      // the remaining rows: G[r, c] -= sum_{t < g0} L[r, t] U[t, c].  The L
+      // entries come from L2; each thread takes two rows and loads PF entries
+      // of each before using them, so that 2 PF loads per thread are in flight.
+      constexpr int PF = GW >= 2 ? 8 : 16;
+      for (int r = g0 + tid; r < R; r += 2 * NT) {
+        const int r2 = r + NT;
+        const bool two = r2 < R;
+        float2 acc0[GW], acc1[GW];
 #pragma unroll
-        for (int c = 0; c < GW; ++c) acc[c] = make_float2(0.f, 0.f);
-        const float2* Lrow = A + (size_t)(r0 + pl[r]) + (size_t)r0 * ld;
-#pragma unroll 8
-        for (int t = 0; t < g0; ++t) {
-          const float2 l = __ldcg(Lrow + (size_t)t * ld);
+        for (int c = 0; c < GW; ++c) {
+          acc0[c] = make_float2(0.f, 0.f);
+          acc1[c] = make_float2(0.f, 0.f);
+        }
+        const float2* L0 = A + (size_t)(r0 + pl[r]) + (size_t)r0 * ld;
+        const float2* L1 = two ? A + (size_t)(r0 + pl[r2]) + (size_t)r0 * ld : L0;
+        for (int t0 = 0; t0 < g0; t0 += PF) {
+          float2 la[PF], lb[PF];
 #pragma unroll
-          for (int c = 0; c < GW; ++c)
-            if (c < gw) cfma<float>(acc[c], l, G[c * R + t]);
+          for (int u = 0; u < PF; ++u) {
+            const int t = t0 + u;
+            if (t < g0) {
+              la[u] = __ldcg(L0 + (size_t)t * ld);
+              lb[u] = __ldcg(L1 + (size_t)t * ld);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < PF; ++u) {
+            const int t = t0 + u;
+            if (t < g0) {
+#pragma unroll
+              for (int c = 0; c < GW; ++c)
+                if (c < gw) {
+                  const float2 gv = G[c * R + t];
+                  cfma<float>(acc0[c], la[u], gv);
+                  cfma<float>(acc1[c], lb[u], gv);
+                }
+            }
+          }
         }
 #pragma unroll
         for (int c = 0; c < GW; ++c)
-          if (c < gw) G[c * R + r] = csub<float>(G[c * R + r], acc[c]);
+          if (c < gw) {
+            G[c * R + r] = csub<float>(G[c * R + r], acc0[c]);
+            if (two) G[c * R + r2] = csub<float>(G[c * R + r2], acc1[c]);
+          }
       }
       __syncthreads();
     }
