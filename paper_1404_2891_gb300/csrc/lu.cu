@@ -491,7 +491,7 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
     if constexpr (std::is_same<T, float>::value) {
       if (lu.tc) {
         cudaError_t err = cudaSuccess;
-        if (tc_solve_update(lu, X, m, M, K, ar0, ac0, opA, row_out, row_in, s, &err)) return err;
+        if (tc_solve_update(lu, X, m, M, K, ar0, ac0, opA, row_out, row_in, -1, s, &err)) return err;
       }
     }
     const cplx<T>* Aop = opA == OP_N ? lu.S + (size_t)ar0 + (size_t)ac0 * lu.ld : lu.S + (size_t)ac0 + (size_t)ar0 * lu.ld;
@@ -504,35 +504,36 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
     g.C = X + row_out; g.ldc = ldx; g.strideC = sx;
     return gemm_batched<T>(g, s);
   };
+  // one block step: the diagonal solve (folded into the tensor-core staging
+  // when that path applies) and the update of the rows still to be solved
+  auto step = [&](int k0, int w, int mode, int M, int ar0, int ac0, int opA, int row_out) -> cudaError_t {
+    if constexpr (std::is_same<T, float>::value) {
+      if (lu.tc && M > 0) {
+        cudaError_t err = cudaSuccess;
+        if (tc_solve_update(lu, X, m, M, w, ar0, ac0, opA, row_out, k0, mode, s, &err)) return err;
+      }
+    }
+    diag(k0, w, mode);
+    return update(M, w, ar0, ac0, opA, row_out, k0);
+  };
+  const int last = ((n - 1) / nbs) * nbs;
   if (side == 0) {
     for (int k0 = 0; k0 < n; k0 += nbs) {  // L y = P r
       const int w = min(nbs, n - k0);
-      diag(k0, w, D_LOWER_UNIT);
-      e = update(n - k0 - w, w, k0 + w, k0, OP_N, k0 + w, k0);
-      if (e != cudaSuccess) return e;
+      if ((e = step(k0, w, D_LOWER_UNIT, n - k0 - w, k0 + w, k0, OP_N, k0 + w)) != cudaSuccess) return e;
     }
-    const int last = ((n - 1) / nbs) * nbs;
     for (int k0 = last; k0 >= 0; k0 -= nbs) {  // U x = y
       const int w = min(nbs, n - k0);
-      diag(k0, w, D_UPPER);
-      e = update(k0, w, 0, k0, OP_N, 0, k0);
-      if (e != cudaSuccess) return e;
+      if ((e = step(k0, w, D_UPPER, k0, 0, k0, OP_N, 0)) != cudaSuccess) return e;
     }
   } else {
-    for (int k0 = 0; k0 < n; k0 += nbs) {  // U^H w = r
+    for (int k0 = 0; k0 < n; k0 += nbs) {  // U^H w = r; rows k0+w.. of op(A) = (U[k0:k0+w, k0+w:])^H
       const int w = min(nbs, n - k0);
-      diag(k0, w, D_UPPER_H);
-      // rows k0+w.. of op(A) = (U[k0:k0+w, k0+w:])^H
-      e = update(n - k0 - w, w, k0 + w, k0, OP_C, k0 + w, k0);
-      if (e != cudaSuccess) return e;
+      if ((e = step(k0, w, D_UPPER_H, n - k0 - w, k0 + w, k0, OP_C, k0 + w)) != cudaSuccess) return e;
     }
-    const int last = ((n - 1) / nbs) * nbs;
-    for (int k0 = last; k0 >= 0; k0 -= nbs) {  // L^H v = w
+    for (int k0 = last; k0 >= 0; k0 -= nbs) {  // L^H v = w; rows 0..k0 of op(A) = (L[k0:k0+w, 0:k0])^H
       const int w = min(nbs, n - k0);
-      diag(k0, w, D_LOWER_H);
-      // rows 0..k0 of op(A) = (L[k0:k0+w, 0:k0])^H
-      e = update(k0, w, 0, k0, OP_C, 0, k0);
-      if (e != cudaSuccess) return e;
+      if ((e = step(k0, w, D_LOWER_H, k0, 0, k0, OP_C, 0)) != cudaSuccess) return e;
     }
   }
   return cudaGetLastError();

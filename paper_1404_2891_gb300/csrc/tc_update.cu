@@ -78,12 +78,12 @@ struct TcGemm {
   int M, N, K, q;
 };
 
-__global__ void __launch_bounds__(256)
-k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max) {
-  __shared__ float2 tile[ST_ROWS][TC_KP / 2 + 1];  // [row or column][k]
-  const int b = blockIdx.y, tid = threadIdx.x;
-  const int base = blockIdx.x * ST_ROWS;
-  const bool isA = blockIdx.z == 0;
+typedef float2 StageTile[TC_KP / 2 + 1];
+
+// Load the block's 32 rows of A (blockIdx.z = 0) or 32 columns of B (z = 1)
+// into tile[row or column][k], zero-padded.
+__device__ __forceinline__ void stage_load(const TcGemm& g, StageTile* tile, bool isA, int b, int base) {
+  const int tid = threadIdx.x;
   const int rest = isA ? g.M : g.N;
   const int w = g.K;
   if (isA && g.opA == OP_N) {
@@ -110,7 +110,14 @@ k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long row
       tile[c][k] = (j < rest && k < w) ? Sb[(size_t)(g.br0 + k) + (size_t)(g.bc0 + j) * g.ldb] : make_float2(0.f, 0.f);
     }
   }
-  __syncthreads();
+}
+
+// Write the tile as split-BF16 staging rows.
+__device__ __forceinline__ void stage_store(const TcGemm& g, StageTile* tile, bool isA, int b, int base,
+                                            __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max,
+                                            long long cols_max) {
+  const int tid = threadIdx.x;
+  const int rest = isA ? g.M : g.N;
   constexpr int WORDS = TC_KP / 2;  // bf16 pairs per staged row
   if (isA) {
     // per complex row i: A' rows 2i ([Re, -Im] pairs) and 2i+1 ([Im, Re] pairs), hi and lo
@@ -145,6 +152,87 @@ k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long row
       dst[k] = h ? pair(lr, lim) : pair(hr, him);
     }
   }
+}
+
+__global__ void __launch_bounds__(256)
+k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max) {
+  __shared__ StageTile tile[ST_ROWS];  // [row or column][k]
+  const int b = blockIdx.y;
+  const int base = blockIdx.x * ST_ROWS;
+  const bool isA = blockIdx.z == 0;
+  stage_load(g, tile, isA, b, base);
+  __syncthreads();
+  stage_store(g, tile, isA, b, base, Ast, Bst, rows_max, cols_max);
+}
+
+// The staging of one block step of a triangular solve, with the step's
+// diagonal solve folded into the B part: B = X[k0 : k0 + w, :] (k0 = br0,
+// w = K) is first solved with the w x w diagonal block D = S[k0 : k0 + w,
+// k0 : k0 + w] of the same shift (mode: 0 L_kk unit lower, 1 U_kk, 2 U_kk^H,
+// 3 L_kk^H unit upper), written back to X, and then staged.  Dynamic shared
+// memory: D (64 x 64 complex64) and the reciprocals of its diagonal.
+__global__ void __launch_bounds__(256)
+k_stage_solve(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max, int mode) {
+  __shared__ StageTile tile[ST_ROWS];
+  extern __shared__ __align__(16) unsigned char stage_smem[];
+  float2* D = reinterpret_cast<float2*>(stage_smem);  // [r * 64 + s] = S[k0 + r, k0 + s]
+  float2* rinv = D + 64 * 64;
+  const int b = blockIdx.y, tid = threadIdx.x;
+  const int base = blockIdx.x * ST_ROWS;
+  const bool isA = blockIdx.z == 0;
+  if (!isA && base >= g.N) return;  // no columns of X here (uniform per block)
+  stage_load(g, tile, isA, b, base);
+  if (!isA) {
+    const int w = g.K, k0 = g.br0;
+    const float2* Sd = g.SA + (size_t)b * g.sa;
+    for (int idx = tid; idx < w * w; idx += 256) {
+      const int r = idx % w, s2 = idx / w;
+      D[r * 64 + s2] = Sd[(size_t)(k0 + r) + (size_t)(k0 + s2) * g.lda];
+    }
+    __syncthreads();
+    if (mode == 1 || mode == 2)
+      for (int s2 = tid; s2 < w; s2 += 256) {
+        const float2 d = D[s2 * 64 + s2];
+        rinv[s2] = crecip<float>(mode == 1 ? d : cconj<float>(d));
+      }
+    __syncthreads();
+    const int cc = tid & 31, rg = tid >> 5;
+    // column cc of the block; each step's pivot value xs is read by every
+    // thread before the barrier and written back (scaled) after it
+    if (mode == 0 || mode == 2) {
+      for (int s2 = 0; s2 < w; ++s2) {
+        float2 xs = tile[cc][s2];
+        if (mode == 2) xs = cmul<float>(xs, rinv[s2]);
+        for (int r = s2 + 1 + rg; r < w; r += 8) {
+          const float2 l = mode == 0 ? D[r * 64 + s2] : cconj<float>(D[s2 * 64 + r]);
+          tile[cc][r] = csub<float>(tile[cc][r], cmul<float>(l, xs));
+        }
+        __syncthreads();
+        if (mode == 2 && rg == 0) tile[cc][s2] = xs;
+      }
+    } else {
+      for (int s2 = w - 1; s2 >= 0; --s2) {
+        float2 xs = tile[cc][s2];
+        if (mode == 1) xs = cmul<float>(xs, rinv[s2]);
+        for (int r = rg; r < s2; r += 8) {
+          const float2 u = mode == 1 ? D[r * 64 + s2] : cconj<float>(D[s2 * 64 + r]);
+          tile[cc][r] = csub<float>(tile[cc][r], cmul<float>(u, xs));
+        }
+        __syncthreads();
+        if (mode == 1 && rg == 0) tile[cc][s2] = xs;
+      }
+    }
+    __syncthreads();
+    // the solved rows back to X
+    float2* Xb = const_cast<float2*>(g.SB) + (size_t)b * g.sb;
+    const int k = tid & 63;
+    for (int c = tid >> 6; c < ST_ROWS; c += 4) {
+      const int j = base + c;
+      if (j < g.N && k < w) Xb[(size_t)(g.br0 + k) + (size_t)(g.bc0 + j) * g.ldb] = tile[c][k];
+    }
+  }
+  __syncthreads();
+  stage_store(g, tile, isA, b, base, Ast, Bst, rows_max, cols_max);
 }
 
 // ---------------------------------------------------------------- the GEMM
@@ -636,7 +724,7 @@ void select_trailing_update<float>(TrailingUpdateFn<float>* fn, void** ctx, TcSt
 }
 
 bool tc_solve_update(const LuBatch<float>& lu, float2* X, int m, int M, int K, int ar0, int ac0, int opA,
-                     int row_out, int row_in, cudaStream_t s, cudaError_t* err) {
+                     int row_out, int row_in, int diag_mode, cudaStream_t s, cudaError_t* err) {
   const TcStaging* ctx = reinterpret_cast<const TcStaging*>(lu.tc);
   TcGemm g;
   const float2* S = reinterpret_cast<const float2*>(lu.S);
@@ -646,6 +734,27 @@ bool tc_solve_update(const LuBatch<float>& lu, float2* X, int m, int M, int K, i
   g.SC = X; g.ldc = n; g.sc = sx; g.cr0 = row_out; g.cc0 = 0;
   g.M = M; g.N = m; g.K = K; g.q = lu.q;
   if (!tc_gemm_fits(g, ctx)) return false;
-  *err = tc_gemm(g, ctx, lu.flags, s);
+  if (diag_mode < 0) {
+    *err = tc_gemm(g, ctx, lu.flags, s);
+    return true;
+  }
+  if (M <= 0 || m <= 0) return false;
+  constexpr int smem = (64 * 64 + 64) * (int)sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) {
+      *err = e;
+      return true;
+    }
+    attr = true;
+  }
+  const int blocks = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), ST_ROWS);
+  feast_count_launch();
+  k_stage_solve<<<dim3(blocks, g.q, 2), 256, smem, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
+                                                        reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max,
+                                                        ctx->cols_max, diag_mode);
+  cudaError_t e = cudaGetLastError();
+  *err = e != cudaSuccess ? e : tc_run(g, 0, g.N, ctx, lu.flags, s);
   return true;
 }

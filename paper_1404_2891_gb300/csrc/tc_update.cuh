@@ -23,7 +23,11 @@ void select_trailing_update(TrailingUpdateFn<T>* fn, void** ctx, TcStaging* stag
 // Off-diagonal update of a blocked triangular solve on the tensor cores:
 // X[row_out : row_out + M, :] -= op(A) X[row_in : row_in + K, :] for every shift,
 // A the factor block at (ar0, ac0) (opA = OP_N) or its conjugate transpose
-// (OP_C: A(i,k) = conj(S[ac0 + k, ar0 + i])).  Returns false (nothing done)
-// when the handle has no staging (lu.tc == nullptr) or K > 64.
+// (OP_C: A(i,k) = conj(S[ac0 + k, ar0 + i])).  With diag_mode >= 0 the block
+// X[row_in : row_in + K, :] is first solved with the diagonal block
+// S[row_in : row_in + K, row_in : row_in + K] (0: unit lower L, 1: upper U,
+// 2: U^H, 3: unit upper L^H) inside the staging kernel.  Returns false
+// (nothing done) when the handle has no staging (lu.tc == nullptr), K > 64, or
+// (with a diagonal solve) M == 0.
 bool tc_solve_update(const LuBatch<float>& lu, float2* X, int m, int M, int K, int ar0, int ac0, int opA,
-                     int row_out, int row_in, cudaStream_t s, cudaError_t* err);
+                     int row_out, int row_in, int diag_mode, cudaStream_t s, cudaError_t* err);
