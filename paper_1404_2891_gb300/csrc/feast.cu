@@ -168,7 +168,7 @@ struct feast_handle {
   double2 *X = nullptr, *Xl = nullptr, *AX = nullptr, *BX = nullptr, *AhX = nullptr, *BhX = nullptr;
   double2 *E = nullptr, *Eh = nullptr, *tmp = nullptr;
   double2 *Ahat = nullptr, *Bhat = nullptr, *LUB = nullptr, *Cm = nullptr, *Zs = nullptr, *V = nullptr;
-  double2 *W = nullptr, *LUW = nullptr, *Minv = nullptr, *Zl = nullptr, *lam = nullptr, *dd = nullptr;
+  double2 *W = nullptr, *LUW = nullptr, *Minv = nullptr, *Binv = nullptr, *Zl = nullptr, *lam = nullptr, *dd = nullptr;
   double2 *coef = nullptr, *coefh = nullptr, *c0 = nullptr, *c0h = nullptr;
   int *pivB = nullptr, *pivW = nullptr, *useres = nullptr, *useresh = nullptr, *colidx = nullptr;
   int* gate = nullptr;  // device flag: the Newton-Schulz inverse of W missed its tolerance
@@ -483,10 +483,30 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, BQp, n, zero, h->Bhat, m));
   // reduced problem: C = B^{-1} A^, Schur form, eigenvectors
   const size_t sm = (size_t)m * m * sizeof(double2);
-  CK(cudaMemcpyAsync(h->LUB, h->Bhat, sm, cudaMemcpyDeviceToDevice, h->st));
-  CK(small_lu(h->LUB, m, h->pivB, h->flags, h->st));
-  CK(cudaMemcpyAsync(h->Cm, h->Ahat, sm, cudaMemcpyDeviceToDevice, h->st));
-  CK(small_lu_solve(h->LUB, h->pivB, m, h->Cm, m, 0, h->st));
+  // X <- X (2I - M X): quadratic convergence to M^{-1} (DMMA products; LUW, Zs scratch)
+  auto newton_schulz = [&](const double2* Mx, double2* X, int steps) -> cudaError_t {
+    for (int it = 0; it < steps; ++it) {
+      cudaError_t e = set_identity(h->LUW, m, h->st);
+      if (e == cudaSuccess) e = zg(h, OP_N, OP_N, m, m, m, zc(-1.0), Mx, m, X, m, zc(2.0), h->LUW, m);
+      if (e == cudaSuccess) e = zg(h, OP_N, OP_N, m, m, m, one, X, m, h->LUW, m, zero, h->Zs, m);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(X, h->Zs, sm, cudaMemcpyDeviceToDevice, h->st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // guard: when ||M X - I|| > 1e-12 (an ill-conditioned M, or a start too far
+  // off for the iteration) the inverse is recomputed by LU on the device
+  auto inverse_guard = [&](const double2* Mx, double2* X, double2* LU, int* piv) -> cudaError_t {
+    cudaError_t e = zg(h, OP_N, OP_N, m, m, m, one, Mx, m, X, m, zero, h->Zs, m);
+    if (e == cudaSuccess) e = inverse_check(h->Zs, m, 1e-12, h->gate, h->st);
+    if (e == cudaSuccess) e = small_inverse_gated(Mx, LU, piv, X, m, h->flags, h->gate, h->st);
+    return e;
+  };
+  // B^^{-1}: FP32 Gauss-Jordan start, three Newton-Schulz steps, checked
+  CK(gj_inverse32(h->Bhat, m, h->Binv, h->st));
+  CK(newton_schulz(h->Bhat, h->Binv, 3));
+  CK(inverse_guard(h->Bhat, h->Binv, h->LUB, h->pivB));
+  CK(zg(h, OP_N, OP_N, m, m, m, one, h->Binv, m, h->Ahat, m, zero, h->Cm, m));
   // Schur form and eigenvectors in FP32, then two FP64 refinement sweeps:
   // E = W^{-1} C W (DMMA products), lam = diag(E), W <- W (I + Delta).
   {
@@ -513,34 +533,16 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     gi.A = C32; gi.B = Z32; gi.opB = OP_C; gi.C = W32;
     CK(gemm_batched<float>(gi, h->st));
     CK(to_c128(W32, h->Minv, mm, h->st));
-    auto newton_schulz = [&](int steps) -> cudaError_t {
-      for (int it = 0; it < steps; ++it) {
-        cudaError_t e = set_identity(h->LUW, m, h->st);
-        if (e == cudaSuccess) e = zg(h, OP_N, OP_N, m, m, m, zc(-1.0), h->W, m, h->Minv, m, zc(2.0), h->LUW, m);
-        if (e == cudaSuccess) e = zg(h, OP_N, OP_N, m, m, m, one, h->Minv, m, h->LUW, m, zero, h->Zs, m);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->Minv, h->Zs, sm, cudaMemcpyDeviceToDevice, h->st);
-        if (e != cudaSuccess) return e;
-      }
-      return cudaSuccess;
-    };
-    // guard: when ||W X - I|| > 1e-12 (an ill-conditioned W, or a start too far
-    // off for the iteration) the inverse is recomputed by LU on the device
-    auto inverse_guard = [&]() -> cudaError_t {
-      cudaError_t e = zg(h, OP_N, OP_N, m, m, m, one, h->W, m, h->Minv, m, zero, h->Zs, m);
-      if (e == cudaSuccess) e = inverse_check(h->Zs, m, 1e-12, h->gate, h->st);
-      if (e == cudaSuccess) e = small_inverse_gated(h->W, h->LUW, h->pivW, h->Minv, m, h->flags, h->gate, h->st);
-      return e;
-    };
-    CK(newton_schulz(3));
-    CK(inverse_guard());
+    CK(newton_schulz(h->W, h->Minv, 3));
+    CK(inverse_guard(h->W, h->Minv, h->LUW, h->pivW));
     for (int sweep = 0; sweep < 2; ++sweep) {
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->Cm, m, h->W, m, zero, h->V, m));
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->Minv, m, h->V, m, zero, h->Zs, m));
       CK(eig_refine_step(h->Zs, h->Ahat, h->lam, m, h->st));
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->W, m, h->Ahat, m, zero, h->LUW, m));
       CK(cudaMemcpyAsync(h->W, h->LUW, sm, cudaMemcpyDeviceToDevice, h->st));
-      CK(newton_schulz(2 - sweep));  // W changed by O(Delta): quadratic steps from the old inverse
-      CK(inverse_guard());
+      CK(newton_schulz(h->W, h->Minv, 2 - sweep));  // W changed by O(Delta): quadratic steps from the old inverse
+      CK(inverse_guard(h->W, h->Minv, h->LUW, h->pivW));
     }
   }
   // Ritz vectors and residuals
@@ -570,9 +572,8 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
         BhQp = h->BhQ;
       }
     }
-    // Minv holds W^{-1} (Newton-Schulz above)
-    CK(conj_transpose(h->Minv, m, m, h->Zl, h->st));
-    CK(small_lu_solve(h->LUB, h->pivB, m, h->Zl, m, 1, h->st));
+    // Zl = (W^{-1} B^^{-1})^H from the two inverses above
+    CK(zg(h, OP_C, OP_C, m, m, m, one, h->Binv, m, h->Minv, m, zero, h->Zl, m));
     CK(zg(h, OP_N, OP_N, n, m, m, one, h->Qho, n, h->Zl, m, zero, h->Xl, n));
     CK(zg(h, OP_N, OP_N, n, m, m, one, h->AhQ, n, h->Zl, m, zero, h->AhX, n));
     double2* BhXp = h->Xl;
@@ -742,7 +743,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   double2** blocks[] = {&h->Y, &h->Yh, &h->Rr, &h->Rl, &h->Q, &h->Qh, &h->Qo, &h->Qho, &h->AQ, &h->BQ,
                         &h->AhQ, &h->BhQ, &h->X, &h->Xl, &h->AX, &h->BX, &h->AhX, &h->BhX, &h->E, &h->Eh, &h->tmp};
   for (double2** p : blocks) AL(*p, nm * sizeof(double2) + 2 * n * sizeof(double2));
-  double2** smalls[] = {&h->Ahat, &h->Bhat, &h->LUB, &h->Cm, &h->Zs, &h->V, &h->W, &h->LUW, &h->Minv, &h->Zl};
+  double2** smalls[] = {&h->Ahat, &h->Bhat, &h->LUB, &h->Cm, &h->Zs, &h->V, &h->W, &h->LUW, &h->Minv, &h->Binv, &h->Zl};
   for (double2** p : smalls) AL(*p, mm * sizeof(double2));
   AL(h->lam, m0 * sizeof(double2));
   AL(h->dd, m0 * sizeof(double2));

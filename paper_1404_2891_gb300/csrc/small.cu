@@ -584,6 +584,84 @@ k_small_inv_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const
   }
 }
 
+// X ~ M^{-1} (m x m, m <= GJ_MAX_M) by Gauss-Jordan elimination with partial
+// pivoting in FP32 on one CTA, the matrix in shared memory (ld m + 1): the
+// start of a Newton-Schulz refinement in FP64.  Row k is scaled by 1 / A_kk
+// (the pivot position then holds 1 / A_kk), column k is eliminated from every
+// other row, and the column interchanges undo the row interchanges in reverse
+// order at the end.  A zero pivot leaves a non-finite X, which the following
+// check rejects.
+constexpr int GJ_THREADS = 1024;
+constexpr int GJ_MAX_M = 160;
+
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_inverse32(const double2* M, int m, double2* X) {
+  extern __shared__ float2 gjA[];  // [i + j * (m + 1)]
+  __shared__ float2 f[GJ_MAX_M];
+  __shared__ int s_piv[GJ_MAX_M];
+  const int tid = threadIdx.x, ld = m + 1;
+  for (int idx = tid; idx < m * m; idx += GJ_THREADS) {
+    const int i = idx % m, j = idx / m;
+    const double2 v = M[idx];
+    gjA[i + j * ld] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (tid < 32) {
+      float best = -1.f;
+      int bi = m;
+      for (int i = k + tid; i < m; i += 32) {
+        const float v = cabs1<float>(gjA[i + k * ld]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float v2 = __shfl_down_sync(0xffffffffu, best, off);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+        if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+      }
+      if (tid == 0) s_piv[k] = bi < m ? bi : k;
+    }
+    __syncthreads();
+    const int p = s_piv[k];
+    if (p != k)
+      for (int j = tid; j < m; j += GJ_THREADS) {
+        const float2 a = gjA[k + j * ld];
+        gjA[k + j * ld] = gjA[p + j * ld];
+        gjA[p + j * ld] = a;
+      }
+    __syncthreads();
+    const float2 rd = crecip<float>(gjA[k + k * ld]);
+    for (int i = tid; i < m; i += GJ_THREADS) f[i] = i == k ? make_float2(0.f, 0.f) : gjA[i + k * ld];
+    __syncthreads();
+    for (int j = tid; j < m; j += GJ_THREADS)
+      gjA[k + j * ld] = j == k ? rd : cmul<float>(gjA[k + j * ld], rd);
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += GJ_THREADS) {
+      const int i = idx % m, j = idx / m;
+      if (i != k) {
+        const float2 a = j == k ? make_float2(0.f, 0.f) : gjA[i + j * ld];
+        gjA[i + j * ld] = csub<float>(a, cmul<float>(f[i], gjA[k + j * ld]));
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    const int p = s_piv[k];
+    if (p != k)
+      for (int i = tid; i < m; i += GJ_THREADS) {
+        const float2 a = gjA[i + k * ld];
+        gjA[i + k * ld] = gjA[i + p * ld];
+        gjA[i + p * ld] = a;
+      }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < m * m; idx += GJ_THREADS) {
+    const int i = idx % m, j = idx / m;
+    const float2 v = gjA[i + j * ld];
+    X[idx] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
@@ -706,5 +784,20 @@ cudaError_t small_inverse_gated_grp(const double2* W, double2* LU, int* piv, dou
   if (np < 1) return cudaSuccess;
   feast_count_launch();
   k_small_inv_gated_grp<<<np, SMALL_THREADS, 0, s>>>(W, LU, piv, X, pd, flags, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t gj_inverse32(const double2* M, int m, double2* X, cudaStream_t s) {
+  if (m < 1 || m > GJ_MAX_M) return cudaErrorInvalidValue;
+  const int smem = m * (m + 1) * (int)sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gj_inverse32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         GJ_MAX_M * (GJ_MAX_M + 1) * (int)sizeof(float2));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  feast_count_launch();
+  k_gj_inverse32<<<1, GJ_THREADS, smem, s>>>(M, m, X);
   return cudaGetLastError();
 }

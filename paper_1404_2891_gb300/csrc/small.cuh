@@ -78,3 +78,6 @@ cudaError_t inverse_check_grp(const double2* T, const GrpDesc* pd, int np, const
 // X_p = W_p^{-1} by LU (LU, piv: arena scratch) for the pencils with gate[p] != 0.
 cudaError_t small_inverse_gated_grp(const double2* W, double2* LU, int* piv, double2* X, const GrpDesc* pd, int np,
                                     unsigned* flags, const int* gate, cudaStream_t s);
+// X ~ M^{-1} (FP32 accuracy, m <= 160) by Gauss-Jordan elimination with partial
+// pivoting on one CTA: the start of a Newton-Schulz refinement.
+cudaError_t gj_inverse32(const double2* M, int m, double2* X, cudaStream_t s);
