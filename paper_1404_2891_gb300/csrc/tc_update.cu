@@ -167,15 +167,18 @@ k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long row
 
 // The staging of one block step of a triangular solve, with the step's
 // diagonal solve folded into the B part: B = X[k0 : k0 + w, :] (k0 = br0,
-// w = K) is first solved with the w x w diagonal block D = S[k0 : k0 + w,
-// k0 : k0 + w] of the same shift (mode: 0 L_kk unit lower, 1 U_kk, 2 U_kk^H,
-// 3 L_kk^H unit upper), written back to X, and then staged.  Dynamic shared
-// memory: D (64 x 64 complex64) and the reciprocals of its diagonal.
+// w = K) is first solved with the w x w diagonal block of the same shift
+// (mode: 0 L_kk unit lower, 1 U_kk, 2 U_kk^H, 3 L_kk^H unit upper), written
+// back to X, and then staged.  Each warp solves four of the block's 32 columns
+// on its own (lanes hold rows lane and lane + 32, pivots broadcast by
+// shuffles), so the 64 substitution steps need no block barrier.  D is kept in
+// shared memory with the entries a step reads (one column of the triangle)
+// contiguous: as stored for modes 0 and 1, transposed for 2 and 3.
 __global__ void __launch_bounds__(256)
 k_stage_solve(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max, int mode) {
   __shared__ StageTile tile[ST_ROWS];
   extern __shared__ __align__(16) unsigned char stage_smem[];
-  float2* D = reinterpret_cast<float2*>(stage_smem);  // [r * 64 + s] = S[k0 + r, k0 + s]
+  float2* D = reinterpret_cast<float2*>(stage_smem);  // [s * 64 + r]: the entry that step s applies to row r
   float2* rinv = D + 64 * 64;
   const int b = blockIdx.y, tid = threadIdx.x;
   const int base = blockIdx.x * ST_ROWS;
@@ -185,42 +188,50 @@ k_stage_solve(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_m
   if (!isA) {
     const int w = g.K, k0 = g.br0;
     const float2* Sd = g.SA + (size_t)b * g.sa;
+    const bool transposed = mode >= 2;
     for (int idx = tid; idx < w * w; idx += 256) {
       const int r = idx % w, s2 = idx / w;
-      D[r * 64 + s2] = Sd[(size_t)(k0 + r) + (size_t)(k0 + s2) * g.lda];
+      const float2 v = Sd[(size_t)(k0 + r) + (size_t)(k0 + s2) * g.lda];  // S[k0 + r, k0 + s2]
+      if (transposed)
+        D[r * 64 + s2] = cconj<float>(v);  // step r, row s2: conj(S[k0 + r, k0 + s2])
+      else
+        D[s2 * 64 + r] = v;  // step s2, row r
     }
     __syncthreads();
     if (mode == 1 || mode == 2)
-      for (int s2 = tid; s2 < w; s2 += 256) {
-        const float2 d = D[s2 * 64 + s2];
-        rinv[s2] = crecip<float>(mode == 1 ? d : cconj<float>(d));
-      }
+      for (int s2 = tid; s2 < w; s2 += 256) rinv[s2] = crecip<float>(D[s2 * 64 + s2]);
     __syncthreads();
-    const int cc = tid & 31, rg = tid >> 5;
-    // column cc of the block; each step's pivot value xs is read by every
-    // thread before the barrier and written back (scaled) after it
-    if (mode == 0 || mode == 2) {
-      for (int s2 = 0; s2 < w; ++s2) {
-        float2 xs = tile[cc][s2];
-        if (mode == 2) xs = cmul<float>(xs, rinv[s2]);
-        for (int r = s2 + 1 + rg; r < w; r += 8) {
-          const float2 l = mode == 0 ? D[r * 64 + s2] : cconj<float>(D[s2 * 64 + r]);
-          tile[cc][r] = csub<float>(tile[cc][r], cmul<float>(l, xs));
+    const int lane = tid & 31, warp = tid >> 5;
+    float2 x[4][2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j][0] = tile[4 * warp + j][lane];
+      x[j][1] = tile[4 * warp + j][lane + 32];
+    }
+    const bool fwd = mode == 0 || mode == 2, divide = mode == 1 || mode == 2;
+    for (int it = 0; it < w; ++it) {
+      const int s2 = fwd ? it : w - 1 - it;
+      const int owner = s2 & 31, hs = s2 >> 5;
+      const float2 d0 = D[s2 * 64 + lane], d1 = D[s2 * 64 + lane + 32];
+      const float2 ri = divide ? rinv[s2] : make_float2(1.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 v = hs ? x[j][1] : x[j][0];
+        float2 xs = make_float2(__shfl_sync(0xffffffffu, v.x, owner), __shfl_sync(0xffffffffu, v.y, owner));
+        if (divide) xs = cmul<float>(xs, ri);
+        if (lane == owner) {
+          if (hs) x[j][1] = xs; else x[j][0] = xs;
         }
-        __syncthreads();
-        if (mode == 2 && rg == 0) tile[cc][s2] = xs;
+        const bool a0 = fwd ? lane > s2 : lane < s2;
+        const bool a1 = fwd ? lane + 32 > s2 : lane + 32 < s2;
+        if (a0 && lane < w) x[j][0] = csub<float>(x[j][0], cmul<float>(d0, xs));
+        if (a1 && lane + 32 < w) x[j][1] = csub<float>(x[j][1], cmul<float>(d1, xs));
       }
-    } else {
-      for (int s2 = w - 1; s2 >= 0; --s2) {
-        float2 xs = tile[cc][s2];
-        if (mode == 1) xs = cmul<float>(xs, rinv[s2]);
-        for (int r = rg; r < s2; r += 8) {
-          const float2 u = mode == 1 ? D[r * 64 + s2] : cconj<float>(D[s2 * 64 + r]);
-          tile[cc][r] = csub<float>(tile[cc][r], cmul<float>(u, xs));
-        }
-        __syncthreads();
-        if (mode == 1 && rg == 0) tile[cc][s2] = xs;
-      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      tile[4 * warp + j][lane] = x[j][0];
+      tile[4 * warp + j][lane + 32] = x[j][1];
     }
     __syncthreads();
     // the solved rows back to X
