@@ -49,9 +49,23 @@ __device__ void panel_ll(float2* A, long long ld, int N, int r0, int w, int* piv
   __syncthreads();
   for (int g0 = 0; g0 < w; g0 += GW) {
     const int gw = min(GW, w - g0);
-    for (int idx = tid; idx < R * gw; idx += NT) {
-      const int c = idx / R, r = idx - c * R;
-      G[idx] = __ldcg(A + (size_t)(r0 + pl[r]) + (size_t)(r0 + g0 + c) * ld);
+    // the group's columns, several loads per thread in flight
+    constexpr int GB = NT < 512 ? 4 : 8;
+    for (int base = 0; base < R * gw; base += GB * NT) {
+      float2 v[GB];
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int idx = base + u * NT + tid;
+        if (idx < R * gw) {
+          const int c = idx / R, r = idx - c * R;
+          v[u] = __ldcg(A + (size_t)(r0 + pl[r]) + (size_t)(r0 + g0 + c) * ld);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int idx = base + u * NT + tid;
+        if (idx < R * gw) G[idx] = v[u];
+      }
     }
     const int lrows = min(64, R);
     for (int idx = tid; idx < 64 * g0; idx += NT) {
@@ -76,50 +90,51 @@ __device__ void panel_ll(float2* A, long long ld, int N, int r0, int w, int* piv
       }
       __syncthreads();
       // the remaining rows: G[r, c] -= sum_{t < g0} L[r, t] U[t, c].  The L
-      // entries come from L2; each thread takes two rows and loads PF entries
-      // of each before using them, so that 2 PF loads per thread are in flight.
-      constexpr int PF = GW >= 2 ? 8 : 16;
-      for (int r = g0 + tid; r < R; r += 2 * NT) {
-        const int r2 = r + NT;
-        const bool two = r2 < R;
-        float2 acc0[GW], acc1[GW];
+      // entries come from L2 and the loop is bound by their latency: each
+      // thread takes RR rows and loads PF entries of each before using them,
+      // so that RR * PF loads per thread are in flight.
+      constexpr int PF = 8;
+      // (the 256-thread persistent batch kernel keeps one row per thread: its
+      // register budget is shared with its other task types)
+      constexpr int RR = NT < 512 ? 1 : (GW >= 8 ? 2 : 4);
+      for (int r = g0 + tid; r < R; r += RR * NT) {
+        float2 acc[RR][GW];
 #pragma unroll
-        for (int c = 0; c < GW; ++c) {
-          acc0[c] = make_float2(0.f, 0.f);
-          acc1[c] = make_float2(0.f, 0.f);
+        for (int q = 0; q < RR; ++q)
+#pragma unroll
+          for (int c = 0; c < GW; ++c) acc[q][c] = make_float2(0.f, 0.f);
+        const float2* Lp[RR];
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+          const int rq = r + q * NT;
+          Lp[q] = A + (size_t)(r0 + pl[rq < R ? rq : r]) + (size_t)r0 * ld;
         }
-        const float2* L0 = A + (size_t)(r0 + pl[r]) + (size_t)r0 * ld;
-        const float2* L1 = two ? A + (size_t)(r0 + pl[r2]) + (size_t)r0 * ld : L0;
         for (int t0 = 0; t0 < g0; t0 += PF) {
-          float2 la[PF], lb[PF];
+          float2 lv[RR][PF];
 #pragma unroll
-          for (int u = 0; u < PF; ++u) {
-            const int t = t0 + u;
-            if (t < g0) {
-              la[u] = __ldcg(L0 + (size_t)t * ld);
-              lb[u] = __ldcg(L1 + (size_t)t * ld);
-            }
-          }
+          for (int u = 0; u < PF; ++u)
 #pragma unroll
-          for (int u = 0; u < PF; ++u) {
-            const int t = t0 + u;
-            if (t < g0) {
+            for (int q = 0; q < RR; ++q)
+              if (t0 + u < g0) lv[q][u] = __ldcg(Lp[q] + (size_t)(t0 + u) * ld);
+#pragma unroll
+          for (int u = 0; u < PF; ++u)
+            if (t0 + u < g0)
 #pragma unroll
               for (int c = 0; c < GW; ++c)
                 if (c < gw) {
-                  const float2 gv = G[c * R + t];
-                  cfma<float>(acc0[c], la[u], gv);
-                  cfma<float>(acc1[c], lb[u], gv);
+                  const float2 gv = G[c * R + t0 + u];
+#pragma unroll
+                  for (int q = 0; q < RR; ++q) cfma<float>(acc[q][c], lv[q][u], gv);
                 }
-            }
-          }
         }
 #pragma unroll
-        for (int c = 0; c < GW; ++c)
-          if (c < gw) {
-            G[c * R + r] = csub<float>(G[c * R + r], acc0[c]);
-            if (two) G[c * R + r2] = csub<float>(G[c * R + r2], acc1[c]);
-          }
+        for (int q = 0; q < RR; ++q) {
+          const int rq = r + q * NT;
+          if (rq < R)
+#pragma unroll
+            for (int c = 0; c < GW; ++c)
+              if (c < gw) G[c * R + rq] = csub<float>(G[c * R + rq], acc[q][c]);
+        }
       }
       __syncthreads();
     }
