@@ -241,6 +241,7 @@ LuBatch<T> lu_view(feast_handle* h) {
   lu.info = h->info;
   lu.flags = h->flags;
   lu.mv = h->mv;
+  lu.mv_panels = (int)((h->n + 63) / 64);
   if (std::is_same<T, float>::value && h->staging.Ast) lu.tc = &h->staging;
   return lu;
 }
@@ -735,7 +736,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->piv, (size_t)h->q * n * sizeof(int32_t));
   AL(h->perm, (size_t)h->q * n * sizeof(int32_t));
   AL(h->pinv, (size_t)h->q * n * sizeof(int32_t));
-  AL(h->mv, (size_t)h->q * LU_MV_STRIDE * sizeof(int32_t));
+  AL(h->mv, (size_t)((n + 63) / 64) * h->q * LU_MV_STRIDE * sizeof(int32_t));
   AL(h->info, h->q * sizeof(int));
   AL(h->flags, 64);
   AL(h->Xs, nm * std::max(h->q, 2) * esz);

@@ -156,9 +156,10 @@ k_laswp_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, c
 }
 
 // The same from the panel's moved-row list (mv: count, dst[128], src[128], rows
-// relative to k0): every moved element of a column is read first, then written
-// to its new row, so the loads of a column are all in flight at once instead of
-// one interchange after another.  Then U12 = L11^{-1} A12 on the right columns.
+// relative to k0) on the columns right of the panel only (the columns left of
+// it go to k_laswp_mv_left): every moved element of a column is read first,
+// then written to its new row, so the loads of a column are all in flight at
+// once instead of one interchange after another.  Then U12 = L11^{-1} A12.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, const int32_t* mv) {
@@ -177,28 +178,19 @@ k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w
   }
   __syncthreads();
   const int cnt = s_cnt;
-  const int nother = n - w;
+  const int nright = n - k0 - w;
   for (int idx = tid; idx < cnt * 32; idx += 256) {
     const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
-    if (o < nother) {
-      const int c = o < k0 ? o : o + w;
-      vals[idx] = A[(size_t)(k0 + s_s[e]) + (size_t)c * ld];
-    }
+    if (o < nright) vals[idx] = A[(size_t)(k0 + s_s[e]) + (size_t)(k0 + w + o) * ld];
   }
   __syncthreads();
   for (int idx = tid; idx < cnt * 32; idx += 256) {
     const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
-    if (o < nother) {
-      const int c = o < k0 ? o : o + w;
-      A[(size_t)(k0 + s_d[e]) + (size_t)c * ld] = vals[idx];
-    }
+    if (o < nright) A[(size_t)(k0 + s_d[e]) + (size_t)(k0 + w + o) * ld] = vals[idx];
   }
   const int o = blockIdx.x * 32 + (tid & 31);
-  const bool valid = o < nother;
-  const int c = valid ? (o < k0 ? o : o + w) : 0;
-  const bool right = valid && c >= k0 + w;
-  const int o_last = min(blockIdx.x * 32 + 31, nother - 1);
-  if (o_last < k0) return;  // no column of this CTA lies right of the panel
+  const bool right = o < nright;
+  const int c = k0 + w + (right ? o : 0);
   __syncthreads();
   for (int idx = tid; idx < w * w; idx += 256) {
     const int r = idx % w, s2 = idx / w;
@@ -215,6 +207,34 @@ k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w
   }
   if (right)
     for (int r = tid >> 5; r < w; r += 8) A[(size_t)(k0 + r) + (size_t)c * ld] = X[r * 32 + cc];
+}
+
+// The moved rows of one panel (mv as above) on the columns left of it
+// (0 .. k0-1, the finished L part): off the factorisation's critical path.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_laswp_mv_left(cplx<T>* S, long long ld, long long stride, int k0, const int32_t* mv) {
+  __shared__ cplx<T> vals[128 * 32];
+  __shared__ int s_d[128], s_s[128], s_cnt;
+  const int b = blockIdx.y, tid = threadIdx.x;
+  cplx<T>* A = S + (size_t)b * stride;
+  const int32_t* m = mv + (size_t)b * LU_MV_STRIDE;
+  if (tid == 0) s_cnt = min(max(m[0], 0), 128);
+  for (int e = tid; e < 128; e += 256) {
+    s_d[e] = m[1 + e];
+    s_s[e] = m[129 + e];
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  for (int idx = tid; idx < cnt * 32; idx += 256) {
+    const int e = idx >> 5, c = blockIdx.x * 32 + (idx & 31);
+    if (c < k0) vals[idx] = A[(size_t)(k0 + s_s[e]) + (size_t)c * ld];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < cnt * 32; idx += 256) {
+    const int e = idx >> 5, c = blockIdx.x * 32 + (idx & 31);
+    if (c < k0) A[(size_t)(k0 + s_d[e]) + (size_t)c * ld] = vals[idx];
+  }
 }
 
 // Row permutation vector from the interchange sequence: perm = P applied to 0..n-1.
@@ -379,7 +399,8 @@ cudaError_t launch_panel_ll(const LuBatch<float>& lu, int k0, int w, int gcap, c
   if (e != cudaSuccess) return e;
   feast_count_launch();
   k_panel_ll<GW><<<lu.q, PLL_THREADS, smem, s>>>(reinterpret_cast<float2*>(lu.S), lu.ld, lu.stride, lu.n, k0, w,
-                                                 lu.piv, lu.info, lu.flags, gcap, lu.mv);
+                                                 lu.piv, lu.info, lu.flags, gcap,
+                                                 lu.mv ? lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE : nullptr);
   return cudaGetLastError();
 }
 
@@ -416,19 +437,24 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
   // soon as SMs free up) and the two events of each step
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
+  cudaStream_t side = nullptr, lstream = nullptr;  // panels; interchanges on the finished L columns
+  cudaEvent_t ev_next = nullptr, ev_panel = nullptr, ev_left = nullptr;
   if ((e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
   auto cleanup = [&](cudaError_t r) {
     if (ev_next) cudaEventDestroy(ev_next);
     if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_left) cudaEventDestroy(ev_left);
+    if (lstream) cudaStreamDestroy(lstream);
     cudaStreamDestroy(side);
     return r;
   };
   if ((e = cudaEventCreateWithFlags(&ev_next, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
   if ((e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaEventCreateWithFlags(&ev_left, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaStreamCreateWithPriority(&lstream, cudaStreamNonBlocking, lo)) != cudaSuccess) return cleanup(e);
   // the complex64 group panel leaves its moved-row list for the interchanges
-  const bool use_mv = std::is_same<T, float>::value && lu.mv && nb <= 64 && lu.n <= PLL_GCAP;
+  const bool use_mv = std::is_same<T, float>::value && lu.mv && nb == 64 && lu.n <= PLL_GCAP &&
+                      lu.mv_panels >= (lu.n + 63) / 64;
   if constexpr (std::is_same<T, float>::value) {
     if (use_mv && (e = cudaFuncSetAttribute(k_laswp_mv_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)diag_smem<float>(nb))) != cudaSuccess)
@@ -441,8 +467,25 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
     feast_count_launch();
     if constexpr (std::is_same<T, float>::value) {
       if (use_mv) {
-        k_laswp_mv_trsm<float><<<grid, 256, diag_smem<float>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.mv);
-        return cudaGetLastError();
+        // right columns here; the left ones on their own stream after this panel
+        const int32_t* mvk = lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE;
+        const int nright = lu.n - k0 - w;
+        if (nright > 0) {
+          k_laswp_mv_trsm<float><<<dim3(ceil_div(nright, 32), lu.q), 256, diag_smem<float>(w), s>>>(
+              lu.S, lu.ld, lu.stride, lu.n, k0, w, mvk);
+          cudaError_t r = cudaGetLastError();
+          if (r != cudaSuccess) return r;
+        }
+        if (k0 > 0) {
+          // s has waited for this panel: the left stream starts from here
+          cudaError_t r = cudaEventRecord(ev_left, s);
+          if (r == cudaSuccess) r = cudaStreamWaitEvent(lstream, ev_left, 0);
+          if (r != cudaSuccess) return r;
+          feast_count_launch();
+          k_laswp_mv_left<float><<<dim3(ceil_div(k0, 32), lu.q), 256, 0, lstream>>>(lu.S, lu.ld, lu.stride, k0, mvk);
+          return cudaGetLastError();
+        }
+        return cudaSuccess;
       }
     }
     k_laswp_trsm<T><<<grid, 256, diag_smem<T>(w), s>>>(lu.S, lu.ld, lu.stride, lu.n, k0, w, lu.piv);
@@ -465,6 +508,9 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
     if ((e = cudaStreamWaitEvent(s, ev_panel, 0)) != cudaSuccess) return cleanup(e);
     if ((e = laswp(k1, w1)) != cudaSuccess) return cleanup(e);
   }
+  // the left interchanges are done before anything reads L
+  if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
   feast_count_launch();
   k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
   return cleanup(cudaGetLastError());

@@ -16,9 +16,11 @@ struct LuBatch {
   int* info = nullptr;      // q ints: 0 or 1 + first column with an exact zero pivot
   unsigned* flags = nullptr;
   void* tc = nullptr;       // tensor-core staging (complex64 path), or nullptr
-  // q x LU_MV_STRIDE ints, or nullptr: the last panel's moved rows {count, dst[128], src[128]}
-  // (relative to the panel's first row), written by the complex64 panel for the interchanges
+  // mv_panels x q x LU_MV_STRIDE ints, or nullptr: each panel's moved rows
+  // {count, dst[128], src[128]} (relative to the panel's first row), written by
+  // the complex64 panel for the interchanges on the other columns
   int32_t* mv = nullptr;
+  int mv_panels = 0;
 };
 constexpr int LU_MV_STRIDE = 257;
 
