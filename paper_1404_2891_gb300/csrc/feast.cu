@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <mutex>
 #include <vector>
 
 #include "../../include/feast_gb300.h"
@@ -153,6 +154,12 @@ struct feast_handle {
   double R = 1.0, aspect = 1.0;
   std::vector<zc> z, w;
   double normA = 0.0;
+  double2* At = nullptr;
+  // ||A||_2 is estimated on its own stream at creation, beside the first
+  // factorisation; norm_ev marks its end and the value is read on first use
+  cudaStream_t norm_st = nullptr;
+  cudaEvent_t norm_ev = nullptr;
+  bool norm_ready = false;
   bool factored = false;
   feast_status factor_status = FEAST_OK;
   int nb = 64, nbs = 64;
@@ -215,10 +222,37 @@ feast_status cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
+// Device memory of the handles comes from one stream-ordered pool per device
+// that keeps the blocks it gets back (release threshold: unlimited), so a
+// handle created after another was destroyed reuses that memory instead of
+// paying for cudaMalloc and cudaFree again.  The pool holds the largest set of
+// handles alive at once until the process exits.
+cudaMemPool_t handle_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pl = nullptr;
+    if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pl;
+  }
+  return pools[dev];
+}
+
 template <typename P>
 cudaError_t dalloc(feast_handle* h, P** p, size_t bytes) {
   void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+  cudaMemPool_t pool = handle_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&v, bytes ? bytes : 16, pool, h->st) : cudaErrorMemoryAllocation;
   if (e != cudaSuccess) return e;
   h->allocs.push_back(v);
   *p = reinterpret_cast<P*>(v);
@@ -633,13 +667,27 @@ feast_status copy_out(feast_handle* h, feast_z* dst, const double2* src, size_t 
   return FEAST_OK;
 }
 
+// Start the ||A||_2 estimate on the handle's norm stream (after the upload of A
+// on the main stream); norm_of() waits for it where the value is first needed.
 feast_status estimate_norm2(feast_handle* h) {
-  CK(norm2_power(h->A, h->n, (int)h->n, 50, h->pw_scratch, h->scal, h->flags, h->st));
-  double s = 0.0;
-  CK(cudaMemcpyAsync(&s, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  h->normA = s;
-  return read_flags(h);
+  CK(cudaEventRecord(h->norm_ev, h->st));
+  CK(cudaStreamWaitEvent(h->norm_st, h->norm_ev, 0));
+  CK(norm2_power(h->A, h->n, (int)h->n, 50, h->pw_scratch, h->scal, h->flags + 8, h->norm_st, h->At));  // own flag word
+  CK(cudaEventRecord(h->norm_ev, h->norm_st));
+  return FEAST_OK;
+}
+
+double norm_of(feast_handle* h) {
+  if (!h->norm_ready) {
+    double s = 0.0;
+    unsigned f = 0;
+    if (cudaEventSynchronize(h->norm_ev) == cudaSuccess &&
+        cudaMemcpy(&s, h->scal, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemcpy(&f, h->flags + 8, sizeof(unsigned), cudaMemcpyDeviceToHost) == cudaSuccess)
+      h->normA = (f & DEVFLAG_TIMEOUT) ? NAN : s;  // a timed-out estimate poisons the residuals
+    h->norm_ready = true;
+  }
+  return h->normA;
 }
 
 }  // namespace
@@ -681,17 +729,19 @@ const char* feast_status_str(feast_status s) {
 
 void feast_destroy(feast_handle* h) {
   if (!h) return;
-  if (h->st) cudaStreamSynchronize(h->st);
-  for (void* p : h->allocs) cudaFree(p);
+  if (h->side) cudaStreamSynchronize(h->side);
+  if (h->norm_st) cudaStreamSynchronize(h->norm_st);
+  cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->st);  // back to the pool
+  cudaStreamSynchronize(h->st);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->upd_ev) cudaEventDestroy(e);
-  if (h->side) {
-    cudaStreamSynchronize(h->side);
-    cudaStreamDestroy(h->side);
-  }
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
+  if (h->norm_st) cudaStreamDestroy(h->norm_st);
+  if (h->norm_ev) cudaEventDestroy(h->norm_ev);
   delete h;
 }
 
@@ -728,6 +778,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   cudaError_t e;
 #define AL(p, bytes) if ((e = dalloc(h, &(p), (bytes))) != cudaSuccess) return fail(e)
   AL(h->A, nn * sizeof(double2));
+  AL(h->At, nn * sizeof(double2));  // A^T for the norm estimate
   if (h->hasB) AL(h->B, nn * sizeof(double2));
   AL(h->dz, h->q * sizeof(double2));
   AL(h->dw, h->q * sizeof(double2));
@@ -796,6 +847,8 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     if ((e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   }
 #undef AL
+  if ((e = cudaStreamCreateWithFlags(&h->norm_st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreateWithFlags(&h->norm_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   if (h->opt.timing)
     for (auto& ev : h->ev) cudaEventCreate(&ev);
   std::vector<double2> zd(h->q);
@@ -805,10 +858,15 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   for (int k = 0; k < h->q; ++k) wd[k] = d2(h->w[k]);
   if ((e = cudaMemcpyAsync(h->dw, wd.data(), h->q * sizeof(double2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemsetAsync(h->flags, 0, 64, h->st)) != cudaSuccess) return fail(e);
-  if ((e = cudaMemcpy2DAsync(h->A, n * sizeof(double2), A, lda * sizeof(double2), n * sizeof(double2), n,
-                             cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
-  if (h->hasB && (e = cudaMemcpy2DAsync(h->B, n * sizeof(double2), B, ldb * sizeof(double2), n * sizeof(double2), n,
-                                       cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
+  // contiguous operands go as one linear copy (the faster path for large
+  // host-to-device transfers), strided ones column by column
+  auto upload = [&](double2* dst, const feast_z* src, int64_t ld) -> cudaError_t {
+    if (ld == n) return cudaMemcpyAsync(dst, src, nn * sizeof(double2), cudaMemcpyDefault, h->st);
+    return cudaMemcpy2DAsync(dst, n * sizeof(double2), src, ld * sizeof(double2), n * sizeof(double2), n,
+                             cudaMemcpyDefault, h->st);
+  };
+  if ((e = upload(h->A, A, lda)) != cudaSuccess) return fail(e);
+  if (h->hasB && (e = upload(h->B, B, ldb)) != cudaSuccess) return fail(e);
   if ((e = check_finite(h->A, nn, h->flags, h->st)) != cudaSuccess) return fail(e);
   if (h->hasB && (e = check_finite(h->B, nn, h->flags, h->st)) != cudaSuccess) return fail(e);
   feast_status s = read_flags(h);
@@ -832,7 +890,7 @@ feast_status feast_get_quadrature(const feast_handle* h, int* q, feast_z* nodes,
 feast_status feast_get_stats(const feast_handle* h, feast_stats* st) {
   if (!h || !st) return FEAST_ERR_ARG;
   std::memset(st, 0, sizeof(*st));
-  st->normA = h->normA;
+  st->normA = norm_of(const_cast<feast_handle*>(h));
   st->t_factor_ms = h->t_factor;
   st->t_update_ms = h->t_update;
   st->update_launches = h->n_update;
@@ -1019,7 +1077,8 @@ feast_status feast_rayleigh_ritz(feast_handle* h, const feast_z* Q, const feast_
   if ((s = copy_out(h, X, h->X, cnt)) != FEAST_OK) return s;
   if (Qhat && (s = copy_out(h, Xl, h->Xl, cnt)) != FEAST_OK) return s;
   std::vector<double> r(m);
-  for (int i = 0; i < m; ++i) r[i] = h->h_res[i] / h->normA;
+  const double nA = norm_of(h);
+  for (int i = 0; i < m; ++i) r[i] = h->h_res[i] / nA;
   if (res) CK(cudaMemcpyAsync(res, r.data(), m * sizeof(double), cudaMemcpyDefault, h->st));
   CK(cudaStreamSynchronize(h->st));
   if (m_inside) *m_inside = (int)candidates(h).size();
@@ -1101,7 +1160,7 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
     cand = candidates(h);
     const int count = (int)cand.size();
     max_res = count ? 0.0 : INFINITY;
-    for (int i : cand) max_res = std::max(max_res, h->h_res[i] / h->normA);
+    for (int i : cand) max_res = std::max(max_res, h->h_res[i] / norm_of(h));
     if (it - 1 < 64) {
       st.res_hist[it - 1] = max_res;
       st.count_hist[it - 1] = count;
@@ -1120,7 +1179,7 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
   std::vector<double> r(m, 0.0);
   for (int j = 0; j < k; ++j) {
     lam[j] = d2(h->h_lam[cand[j]]);
-    r[j] = h->h_res[cand[j]] / h->normA;
+    r[j] = h->h_res[cand[j]] / norm_of(h);
   }
   CK(cudaMemcpyAsync(lambda, lam.data(), m * sizeof(double2), cudaMemcpyDefault, h->st));
   if (res) CK(cudaMemcpyAsync(res, r.data(), m * sizeof(double), cudaMemcpyDefault, h->st));
@@ -1140,7 +1199,7 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
   st.iters = it;
   st.m_found = k;
   st.max_res = max_res;
-  st.normA = h->normA;
+  st.normA = norm_of(h);
   st.t_filter_ms = h->t_filter;
   st.t_rr_ms = h->t_rr;
   if (h->opt.timing) {

@@ -15,6 +15,7 @@ constexpr int PW_ROWS = 16;
 
 struct PowArgs {
   const double2* A;
+  const double2* At;  // A^T (ld n) or nullptr
   long long lda;
   int n, iters;
   double2* x;
@@ -71,7 +72,26 @@ __global__ void __launch_bounds__(PW_THREADS) k_norm2_power(PowArgs a) {
   if (!pw_barrier(a.bar, G, a.flags, &s_ok)) return;
   double s = 0.0;
   for (int it = 0; it < a.iters; ++it) {
-    // y = xs A x
+    // y = xs A x: with A^T at hand one warp per row, lanes down the contiguous
+    // column of A^T; else 16-row blocks of A
+    if (a.At) {
+      for (int blk = g; blk < nblk; blk += G) {
+        for (int rr = warp; rr < PW_ROWS; rr += PW_THREADS / 32) {
+          const int r = blk * PW_ROWS + rr;
+          if (r >= n) continue;
+          const double2* row = a.At + (size_t)r * n;
+          double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 8
+          for (int c = lane; c < n; c += 32) cfma<double>(acc, row[c], a.x[c]);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+          }
+          if (lane == 0) a.y[r] = cscale<double>(acc, xs);
+        }
+      }
+    } else
     for (int blk = g; blk < nblk; blk += G) {
       const int r = blk * PW_ROWS + (lane & 15);
       const int stream = 2 * warp + (lane >> 4);
@@ -119,8 +139,17 @@ __global__ void __launch_bounds__(PW_THREADS) k_norm2_power(PowArgs a) {
       a.part[g] = t;
     }
     if (!pw_barrier(a.bar, G, a.flags, &s_ok)) return;
+    // every block sums the G partials in the same order (one per thread, then a
+    // fixed shuffle tree), so all blocks hold the same total
     double tot = 0.0;
-    for (int k = 0; k < G; ++k) tot += a.part[k];
+    for (int k = tid; k < G; k += PW_THREADS) tot += __ldcg(&a.part[k]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = tot;
+    __syncthreads();
+    tot = 0.0;
+    for (int w = 0; w < PW_THREADS / 32; ++w) tot += red[w];
     const double nz = sqrt(tot);  // ||A^H A u|| for the unit vector u of this step
     s = sqrt(nz);
     xs = nz > 0.0 ? 1.0 / nz : 0.0;
@@ -145,11 +174,31 @@ size_t norm2_scratch_bytes(int n) {
   return 256 + (size_t)2 * n * sizeof(double2) + 1024 * sizeof(double);
 }
 
+// A^T (n x n, ld n) from A (ld lda): 32 x 32 tiles through shared memory.
+__global__ void k_transpose_c128(const double2* A, long long lda, int n, double2* At) {
+  __shared__ double2 tile[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = i0 + threadIdx.x, j = j0 + k;
+    if (i < n && j < n) tile[k][threadIdx.x] = A[(size_t)i + (size_t)j * lda];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int j = j0 + threadIdx.x, i = i0 + k;
+    if (i < n && j < n) At[(size_t)j + (size_t)i * n] = tile[threadIdx.x][k];
+  }
+}
+
 cudaError_t norm2_power(const double2* A, long long lda, int n, int iters, void* scratch, double* out_dev,
-                        unsigned* flags, cudaStream_t s) {
+                        unsigned* flags, cudaStream_t s, double2* At) {
   if (n < 1 || iters < 1 || !A || !scratch || !out_dev) return cudaErrorInvalidValue;
   char* base = reinterpret_cast<char*>(scratch);
+  if (At) {
+    feast_count_launch();
+    k_transpose_c128<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(A, lda, n, At);
+  }
   PowArgs a;
+  a.At = At;
   a.A = A;
   a.lda = lda;
   a.n = n;
