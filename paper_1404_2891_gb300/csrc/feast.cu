@@ -363,6 +363,9 @@ feast_status factor_impl(feast_handle* h) {
   void* ctx = nullptr;
   select_trailing_update<T>(&upd, &ctx, &h->staging);
   if (!upd) upd = default_trailing_update<T>;
+  // complex64 with staging: the tensor-core update (its operands always fit the
+  // staging sized for n and q) solves U12 while staging it
+  lu.u12_in_stage = std::is_same<T, float>::value && h->staging.Ast != nullptr;
   UpdateTimer<T> timer{upd, ctx, h, 0, 0.0};
   if (h->opt.timing) {
     const int panels = (int)((h->n + h->nb - 1) / h->nb);

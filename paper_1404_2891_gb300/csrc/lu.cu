@@ -162,7 +162,7 @@ k_laswp_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, c
 // once instead of one interchange after another.  Then U12 = L11^{-1} A12.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, const int32_t* mv) {
+k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w, const int32_t* mv, int do_trsm) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* L = reinterpret_cast<cplx<T>*>(smem_raw);  // w x w, [r * w + s]
   cplx<T>* X = L + w * w;                              // w x 32, [r * 32 + cc]
@@ -188,6 +188,7 @@ k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w
     const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
     if (o < nright) A[(size_t)(k0 + s_d[e]) + (size_t)(k0 + w + o) * ld] = vals[idx];
   }
+  if (!do_trsm) return;  // U12 is solved where it is staged
   const int o = blockIdx.x * 32 + (tid & 31);
   const bool right = o < nright;
   const int c = k0 + w + (right ? o : 0);
@@ -472,7 +473,7 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
         const int nright = lu.n - k0 - w;
         if (nright > 0) {
           k_laswp_mv_trsm<float><<<dim3(ceil_div(nright, 32), lu.q), 256, diag_smem<float>(w), s>>>(
-              lu.S, lu.ld, lu.stride, lu.n, k0, w, mvk);
+              lu.S, lu.ld, lu.stride, lu.n, k0, w, mvk, lu.u12_in_stage ? 0 : 1);
           cudaError_t r = cudaGetLastError();
           if (r != cudaSuccess) return r;
         }

@@ -21,6 +21,9 @@ struct LuBatch {
   // the complex64 panel for the interchanges on the other columns
   int32_t* mv = nullptr;
   int mv_panels = 0;
+  // the trailing update's staging kernel solves U12 = L11^{-1} A12 (in place)
+  // when it stages U12, so the interchange kernel leaves that solve out
+  bool u12_in_stage = false;
 };
 constexpr int LU_MV_STRIDE = 257;
 

@@ -695,6 +695,23 @@ cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cuda
   return tc_run(g, 0, g.N, ctx, flags, s);
 }
 
+// Stage g's operands with the B block first solved by its diagonal block (k_stage_solve).
+cudaError_t launch_stage_solve(const TcGemm& g, const TcStaging* ctx, int mode, cudaStream_t s) {
+  constexpr int smem = (64 * 64 + 64) * (int)sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int blocks = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), ST_ROWS);
+  feast_count_launch();
+  k_stage_solve<<<dim3(blocks, g.q, 2), 256, smem, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
+                                                        reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max,
+                                                        ctx->cols_max, mode);
+  return cudaGetLastError();
+}
+
 // LU trailing update of step (k0, w): C = S[k0+w:, k0+w:], A = L21 = S[k0+w:, k0:k0+w],
 // B = U12 = S[k0:k0+w, k0+w:]; this call updates the columns c0 .. c0+nc-1 of S
 // (staging the whole step's operands when `stage`).
@@ -709,9 +726,20 @@ cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, int c0, 
   g.SB = S; g.ldb = lu.ld; g.sb = lu.stride; g.br0 = k0; g.bc0 = k0 + w;
   g.SC = reinterpret_cast<float2*>(lu.S); g.ldc = lu.ld; g.sc = lu.stride; g.cr0 = k0 + w; g.cc0 = k0 + w;
   g.M = rest; g.N = rest; g.K = w; g.q = lu.q;
-  if (!tc_gemm_fits(g, ctx)) return default_trailing_update<float>(lu, k0, w, c0, nc, stage, nullptr, s);
+  if (!tc_gemm_fits(g, ctx)) {
+    // the plain update needs U12 solved already, which this path leaves to the staging
+    if (lu.u12_in_stage) return cudaErrorInvalidValue;
+    return default_trailing_update<float>(lu, k0, w, c0, nc, stage, nullptr, s);
+  }
   if (stage) {
-    cudaError_t e = tc_stage(g, ctx, s);
+    cudaError_t e;
+    if (lu.u12_in_stage) {
+      // U12 = L11^{-1} A12 (unit lower L11 of this panel) solved in the staging
+      // kernel's B part, written back to the factor, then staged
+      e = launch_stage_solve(g, ctx, 0, s);
+    } else {
+      e = tc_stage(g, ctx, s);
+    }
     if (e != cudaSuccess) return e;
   }
   return tc_run(g, c0 - (k0 + w), nc, ctx, lu.flags, s);
@@ -750,22 +778,7 @@ bool tc_solve_update(const LuBatch<float>& lu, float2* X, int m, int M, int K, i
     return true;
   }
   if (M <= 0 || m <= 0) return false;
-  constexpr int smem = (64 * 64 + 64) * (int)sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) {
-      *err = e;
-      return true;
-    }
-    attr = true;
-  }
-  const int blocks = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), ST_ROWS);
-  feast_count_launch();
-  k_stage_solve<<<dim3(blocks, g.q, 2), 256, smem, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
-                                                        reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max,
-                                                        ctx->cols_max, diag_mode);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_stage_solve(g, ctx, diag_mode, s);
   *err = e != cudaSuccess ? e : tc_run(g, 0, g.N, ctx, lu.flags, s);
   return true;
 }
