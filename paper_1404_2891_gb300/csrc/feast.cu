@@ -1026,7 +1026,6 @@ feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat
   if (s != FEAST_OK) return s;
   const int n = (int)h->n, m = h->m0;
   const size_t cnt = (size_t)n * m;
-  const zc one(1.0), zero(0.0);
   if ((s = copy_in(h, h->Y, Y, cnt)) != FEAST_OK) return s;
   if (Yhat && (s = copy_in(h, h->Yh, Yhat, cnt)) != FEAST_OK) return s;
   std::vector<zc> th;

@@ -9,7 +9,6 @@
 
 namespace {
 
-constexpr double ULP = 2.220446049250313e-16;
 constexpr double SAFE_MIN = 2.2250738585072014e-308;
 
 // ---------------------------------------------------------------- grid barrier
