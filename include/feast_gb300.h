@@ -20,9 +20,12 @@
  *   copies every input into its own device buffers and every output back with
  *   cudaMemcpyDefault).  Caller memory is never retained after a call returns.
  * - All GPU work is enqueued on the stream given to feast_create (NULL = the
- *   legacy default stream).  A call returns after its work is complete
- *   (results in host buffers are valid; device outputs are complete on that
- *   stream).
+ *   legacy default stream) and on the handle's own streams, which are joined
+ *   to it before anything reads their results.  A call returns after its work
+ *   is complete (results in host buffers are valid; device outputs are
+ *   complete on that stream); the ||A||_2 estimate started by feast_create
+ *   may still run until the first call that needs it (feast_rayleigh_ritz,
+ *   feast_solve, feast_get_stats) waits for it.
  * - Errors are returned as feast_status; nothing aborts or traps.  After a
  *   FEAST_ERR_CUDA status the handle should be destroyed.
  * - Not thread-safe per handle; distinct handles are independent.
@@ -136,8 +139,11 @@ void feast_default_options(feast_options* o);
  *   m0   : subspace dimension p of Sec. 4, 1 <= m0 <= n and m0 <= 160.
  *   stream : a cudaStream_t, or NULL.
  * The handle owns the device copies of A and B, the q factorisations and all
- * workspace until feast_destroy.  Returns FEAST_ERR_ARG for n < 1, m0 > n,
- * N_e < 1 or a NULL A; FEAST_ERR_ALLOC if device memory runs out. */
+ * workspace until feast_destroy.  Its device memory comes from a stream-ordered
+ * pool of the library that keeps blocks returned by feast_destroy for later
+ * handles (it holds the largest set of handles alive at once until the process
+ * exits).  Returns FEAST_ERR_ARG for n < 1, m0 > n, N_e < 1 or a NULL A;
+ * FEAST_ERR_ALLOC if device memory runs out. */
 feast_status feast_create(feast_handle** h, int64_t n, const feast_z* A, int64_t lda,
                           const feast_z* B, int64_t ldb, const feast_contour* c, int m0,
                           const feast_options* o, void* stream);
