@@ -127,14 +127,6 @@ __global__ void __launch_bounds__(256) k_col_dots(const double2* X, const double
   if (threadIdx.x == 0) d[blockIdx.x] = s;
 }
 
-__global__ void k_conj_transpose(const double2* src, int n, int m, double2* dst) {
-  const size_t total = (size_t)n * m;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = idx % n, c = idx / n;
-    dst[c + r * m] = cconj<double>(src[idx]);
-  }
-}
 
 __global__ void k_conj_copy(const double2* src, double2* dst, size_t count) {
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
@@ -261,11 +253,6 @@ cudaError_t column_dots(const double2* X, const double2* Y, int n, int m, double
   return cudaGetLastError();
 }
 
-cudaError_t conj_transpose(const double2* src, int n, int m, double2* dst, cudaStream_t s) {
-  feast_count_launch();
-  k_conj_transpose<<<grid_for((size_t)n * m), 256, 0, s>>>(src, n, m, dst);
-  return cudaGetLastError();
-}
 
 cudaError_t conj_copy(const double2* src, double2* dst, size_t count, cudaStream_t s) {
   feast_count_launch();

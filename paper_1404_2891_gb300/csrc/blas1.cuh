@@ -32,8 +32,6 @@ cudaError_t residual_columns(const double2* AX, const double2* BX, const double2
 // d[i] = X[:, i]^H Y[:, i]
 cudaError_t column_dots(const double2* X, const double2* Y, int n, int m, double2* d, cudaStream_t s);
 
-// dst (m x n, ld m) = src^H (src n x m, ld n)
-cudaError_t conj_transpose(const double2* src, int n, int m, double2* dst, cudaStream_t s);
 
 // dst = conj(src) (count complex values)
 cudaError_t conj_copy(const double2* src, double2* dst, size_t count, cudaStream_t s);
