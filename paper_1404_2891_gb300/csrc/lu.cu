@@ -426,8 +426,9 @@ cudaError_t launch_panel(const LuBatch<T>& lu, int k0, int w, cudaStream_t s) {
 }  // namespace
 
 template <typename T>
-cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> upd, void* ctx,
+cudaError_t lu_factor_batched(const LuBatch<T>& lu_in, int nb, TrailingUpdateFn<T> upd, void* ctx,
                               cudaStream_t s) {
+  LuBatch<T> lu = lu_in;
   if (nb < 1 || nb > MAX_NB || diag_smem<T>(nb) > 227 * 1024) return cudaErrorInvalidValue;
   if (!upd) upd = default_trailing_update<T>;
   cudaError_t e = cudaFuncSetAttribute(k_laswp_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -456,6 +457,9 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
   // the complex64 group panel leaves its moved-row list for the interchanges
   const bool use_mv = std::is_same<T, float>::value && lu.mv && nb == 64 && lu.n <= PLL_GCAP &&
                       lu.mv_panels >= (lu.n + 63) / 64;
+  // the staging kernel takes over the interchanges on the right columns and
+  // U12 = L11^{-1} A12 only together with the moved-row lists
+  lu.u12_in_stage = lu.u12_in_stage && use_mv;
   if constexpr (std::is_same<T, float>::value) {
     if (use_mv && (e = cudaFuncSetAttribute(k_laswp_mv_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)diag_smem<float>(nb))) != cudaSuccess)
@@ -471,7 +475,7 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
         // right columns here; the left ones on their own stream after this panel
         const int32_t* mvk = lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE;
         const int nright = lu.n - k0 - w;
-        if (nright > 0) {
+        if (nright > 0 && !lu.u12_in_stage) {
           k_laswp_mv_trsm<float><<<dim3(ceil_div(nright, 32), lu.q), 256, diag_smem<float>(w), s>>>(
               lu.S, lu.ld, lu.stride, lu.n, k0, w, mvk, lu.u12_in_stage ? 0 : 1);
           cudaError_t r = cudaGetLastError();

@@ -175,8 +175,10 @@ k_stage_operands(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long row
 // shared memory with the entries a step reads (one column of the triangle)
 // contiguous: as stored for modes 0 and 1, transposed for 2 and 3.
 __global__ void __launch_bounds__(256)
-k_stage_solve(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max, int mode) {
+k_stage_solve(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_max, long long cols_max, int mode,
+              const int32_t* mv) {
   __shared__ StageTile tile[ST_ROWS];
+  __shared__ int s_d[128], s_s[128], s_cnt;
   extern __shared__ __align__(16) unsigned char stage_smem[];
   float2* D = reinterpret_cast<float2*>(stage_smem);  // [s * 64 + r]: the entry that step s applies to row r
   float2* rinv = D + 64 * 64;
@@ -184,6 +186,30 @@ k_stage_solve(TcGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst, long long rows_m
   const int base = blockIdx.x * ST_ROWS;
   const bool isA = blockIdx.z == 0;
   if (!isA && base >= g.N) return;  // no columns of X here (uniform per block)
+  if (!isA && mv) {
+    // the panel's interchanges on this block's 32 columns of the trailing
+    // matrix: moved rows {dst, src} relative to br0, all read (through D's
+    // space) before any is written
+    const int32_t* m = mv + (size_t)b * LU_MV_STRIDE;
+    if (tid == 0) s_cnt = min(max(m[0], 0), 128);
+    for (int e = tid; e < 128; e += 256) {
+      s_d[e] = m[1 + e];
+      s_s[e] = m[129 + e];
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    float2* Xb = const_cast<float2*>(g.SB) + (size_t)b * g.sb;
+    for (int idx = tid; idx < cnt * ST_ROWS; idx += 256) {
+      const int e = idx >> 5, j = base + (idx & 31);
+      if (j < g.N) D[idx] = Xb[(size_t)(g.br0 + s_s[e]) + (size_t)(g.bc0 + j) * g.ldb];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < cnt * ST_ROWS; idx += 256) {
+      const int e = idx >> 5, j = base + (idx & 31);
+      if (j < g.N) Xb[(size_t)(g.br0 + s_d[e]) + (size_t)(g.bc0 + j) * g.ldb] = D[idx];
+    }
+    __syncthreads();
+  }
   stage_load(g, tile, isA, b, base);
   if (!isA) {
     const int w = g.K, k0 = g.br0;
@@ -696,7 +722,8 @@ cudaError_t tc_gemm(const TcGemm& g, const TcStaging* ctx, unsigned* flags, cuda
 }
 
 // Stage g's operands with the B block first solved by its diagonal block (k_stage_solve).
-cudaError_t launch_stage_solve(const TcGemm& g, const TcStaging* ctx, int mode, cudaStream_t s) {
+cudaError_t launch_stage_solve(const TcGemm& g, const TcStaging* ctx, int mode, cudaStream_t s,
+                               const int32_t* mv = nullptr) {
   constexpr int smem = (64 * 64 + 64) * (int)sizeof(float2);
   static bool attr = false;
   if (!attr) {
@@ -708,7 +735,7 @@ cudaError_t launch_stage_solve(const TcGemm& g, const TcStaging* ctx, int mode, 
   feast_count_launch();
   k_stage_solve<<<dim3(blocks, g.q, 2), 256, smem, s>>>(g, reinterpret_cast<__nv_bfloat16*>(ctx->Ast),
                                                         reinterpret_cast<__nv_bfloat16*>(ctx->Bst), ctx->rows_max,
-                                                        ctx->cols_max, mode);
+                                                        ctx->cols_max, mode, mv);
   return cudaGetLastError();
 }
 
@@ -734,9 +761,10 @@ cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, int c0, 
   if (stage) {
     cudaError_t e;
     if (lu.u12_in_stage) {
-      // U12 = L11^{-1} A12 (unit lower L11 of this panel) solved in the staging
-      // kernel's B part, written back to the factor, then staged
-      e = launch_stage_solve(g, ctx, 0, s);
+      // the panel's interchanges on the trailing columns and U12 = L11^{-1} A12
+      // (unit lower L11 of this panel), both in the staging kernel's B part,
+      // written back to the factor, then staged
+      e = launch_stage_solve(g, ctx, 0, s, lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE);
     } else {
       e = tc_stage(g, ctx, s);
     }
