@@ -7,6 +7,13 @@
 // largest |Re|+|Im| with the lowest row on ties; (2) the panel's interchanges
 // applied to the other columns and U12 = L11^{-1} A12; (3) the trailing update
 // A22 -= L21 U12 as one batched contraction over all shifts.
+//
+// Schedule (complex64 with the tensor-core update): the next block column is
+// updated first and its panel factored on a high-priority side stream beside
+// the rest of the update (look-ahead); the panel leaves a list of its moved
+// rows, from which the interchanges on the finished L columns run on a third,
+// low-priority stream, while those on the trailing columns and the U12 solve
+// are done by the update's staging kernel before it stages U12.
 #include "lu.cuh"
 
 #include <type_traits>

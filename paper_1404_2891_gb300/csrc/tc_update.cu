@@ -13,14 +13,21 @@
 // hi*hi + hi*lo + lo*hi with FP32 accumulation, about 16 significant bits.
 //
 // Kernel.  One CTA owns a 128-row stripe of C~ (64 complex rows) of one
-// shift and loops over the column tiles (BN = 128):
+// shift and loops over the column tiles (BN = 128; 64 in k_tc_update_c):
 //   warp 0   TMA producer: the stripe's A' once, then U~ tiles, two stages
+//            (k_tc_update_c: also the C~ tiles, into their own two-stage ring)
 //   warp 1   TMEM allocation and the MMA issuer (one thread)
-//   warps 2-5 epilogue: TMEM -> registers, C~ -= D with coalesced 128-byte
-//            accesses (adjacent lanes hold the Re/Im rows of one complex row)
-// Two TMEM accumulator buffers (2 x 128 columns) let the MMAs of tile t+1 run
-// while the epilogue drains tile t.  Every mbarrier wait is bounded; on
-// timeout the CTA raises DEVFLAG_TIMEOUT, drains, frees its TMEM and returns.
+//   warps 2-9 epilogue, two per TMEM lane quarter: TMEM -> registers,
+//            C~ -= D with coalesced 128-byte accesses (adjacent lanes hold
+//            the Re/Im rows of one complex row)
+// Two TMEM accumulator buffers let the MMAs of tile t+1 run while the
+// epilogue drains tile t.  Every mbarrier wait is bounded; on timeout the CTA
+// raises DEVFLAG_TIMEOUT, drains, frees its TMEM and returns.
+//
+// Staging kernels: k_stage_operands writes A' and U~ as split BF16;
+// k_stage_solve first solves the B block with its diagonal block (and, for
+// the LU, applies the panel's interchanges to its columns), writes it back to
+// the matrix, then stages it.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
