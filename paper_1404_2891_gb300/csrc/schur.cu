@@ -4,11 +4,12 @@
 // Scalar FP64 issues at about 1/64 of the FP32 rate on GB300, and the
 // Hessenberg QR iteration is a long chain of dependent scalar work (one Givens
 // rotation after another).  So the Schur form is computed in FP32 (one block,
-// the matrix packed in shared memory, the sweep run by one warp, the rotations
+// the whole matrix in shared memory, the sweeps run by one warp, the rotations
 // logged and applied to Z by a second kernel), and FP64 accuracy is recovered
 // afterwards by refinement sweeps built from FP64 tensor-core products
-// (eig_refine_step; see feast.cu).  The same kernels instantiated for double
-// give a plain FP64 Schur form.
+// (eig_refine_step; see feast.cu).  Instantiated for double (the matrix then
+// packed, column j holding rows 0 .. j+2) the kernels give a plain FP64 Schur
+// form.
 #include <float.h>
 
 #include <type_traits>

@@ -1,10 +1,12 @@
 // FP64 kernels of the Rayleigh-Ritz step (Algorithm R-FEAST steps 4-5,
-// Algorithm Bi-FEAST steps 6-7): orthonormal bases of the filtered blocks and
-// the dense m0 x m0 eigenproblem.
+// Algorithm Bi-FEAST steps 6-7): orthonormal bases of the filtered blocks
+// (CGS2, with every CTA's rows of Q in shared memory where they fit), the
+// small dense LU and its solves, the FP32 Gauss-Jordan start of the
+// Newton-Schulz inverses and the device-side checks that guard them, and the
+// grouped forms of these for the batched path.
 //
-// GB300 executes FP64 at about 1/900 of its BF16 rate, so the m0 x m0 work is
-// kept small and on chip where possible: the Hessenberg QR iteration keeps
-// the matrix (with room for the bulge) packed in shared memory.
+// GB300 executes FP64 at about 1/900 of its BF16 rate, so this work is kept
+// small and on chip where possible.
 #include "small.cuh"
 
 namespace {
