@@ -1,11 +1,13 @@
 // Power iteration for ||A||_2 as one persistent cooperative kernel.
 //
-// Phase 1, y = c A x (c = 1 / ||x|| from the previous step): a block owns 16
-// rows; lane l of a warp reads row l % 16 of column 2w + l / 16, 16 columns
-// per sweep over the 8 warps (256-byte segments).  Phase 2, x <- A^H y: one warp
-// per column, lanes down the contiguous column; one partial sum of |x|^2 per
-// block.  Two bounded grid barriers per iteration; A streams from HBM twice per
-// iteration, eight loads in flight per thread.
+// Phase 1, y = c A x (c = 1 / ||x|| from the previous step): with A^T at hand
+// (k_transpose_c128) one warp per row of A, lanes down the contiguous column
+// of A^T; else a block owns 16 rows and lane l of a warp reads row l % 16 of
+// column 2w + l / 16 (256-byte segments).  Phase 2, x <- A^H y: one warp per
+// column, lanes down the contiguous column; one partial sum of |x|^2 per block,
+// reduced by every block in the same order.  Two bounded grid barriers per
+// iteration.  Each step does 8 n^2 FP64 FMA on 2 n^2 16-byte reads, so on
+// GB300 (FP64 at about 1/64 of FP32) the FP64 pipes bound it, not HBM.
 #include "norm2.cuh"
 
 namespace {
