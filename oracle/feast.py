@@ -3,8 +3,8 @@ iterations of Sec. 4, with the monitoring of Sec. 5.
 
 Notation follows the paper: the shifted systems are (phi_k B - A) with nodes
 phi_k and weights sigma_k from ``oracle.contour.quadrature``; U, V are the right
-and left subspaces (BASELINE's Y, Yhat); U^, V^ their filtered images (Q, Qhat);
-p is the subspace dimension (m0).
+and left subspaces (the blocks Y, Yhat of the filter); U^, V^ their filtered
+images (Q, Qhat); p is the subspace dimension (m0).
 """
 import numpy as np
 import scipy.linalg

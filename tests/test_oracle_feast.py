@@ -208,3 +208,110 @@ def test_planted_mistakes_are_caught(monkeypatch):
         orig_lu = dense.lu_factor
         mp.setattr(dense, "lu_factor", lambda S: (lambda r: (r[0].T.copy(), r[1], r[2]))(orig_lu(S)))
         assert fails(check_filter_equals_spectral_form, cfg)
+
+
+# ---------------------------------------------------------------- residual denominators
+def svd_prescribed(n, s, seed):
+    """A = U diag(s) W^H with Haar U, W: ||A||_2 = s[0] exactly."""
+    rng = np.random.default_rng(seed)
+    return workloads.haar_unitary(rng, n) @ np.diag(np.asarray(s, dtype=complex)) @ workloads.haar_unitary(rng, n)
+
+
+def check_norm2(est):
+    """The Sec. 5 gate divides by ||A||_2.  Power iteration on A^H A converges
+    like (s2/s1)^(2k); with s1/s2 = 2 the 50 steps are far past FP64 rounding,
+    so the estimate must equal the largest singular value to rounding.  On a
+    pencil with a close second value it stays a lower bound."""
+    for seed in (1, 2):
+        s = np.concatenate([[2.0], np.linspace(1.0, 0.1, 47)])
+        A = svd_prescribed(48, s, seed)
+        v = est(A, np.ones(48, dtype=complex))
+        assert abs(v - 2.0) <= 1e-12 * 2.0, v
+        assert abs(v - np.linalg.norm(A, 2)) <= 1e-12 * 2.0
+    s = np.concatenate([[1.0, 0.99], np.linspace(0.5, 0.1, 30)])
+    A = svd_prescribed(32, s, 3)
+    v = est(A, np.ones(32, dtype=complex))
+    assert 0.99 <= v <= 1.0 * (1 + 1e-14), v
+
+
+def test_norm2_estimate_equals_largest_singular_value():
+    check_norm2(feast.norm2_estimate)
+
+
+def test_norm2_estimate_planted_mistakes():
+    """A missing square root, a doubled value, or a single step must fail the pin."""
+    def fails(est):
+        try:
+            check_norm2(est)
+        except AssertionError:
+            return True
+        return False
+
+    assert fails(lambda A, x0: feast.norm2_estimate(A, x0) ** 2)
+    assert fails(lambda A, x0: 2.0 * feast.norm2_estimate(A, x0))
+    assert fails(lambda A, x0: feast.norm2_estimate(A, x0, iters=1))
+    assert not fails(feast.norm2_estimate)
+
+
+def normal_pair(seed=5, n=12):
+    """A normal matrix Q diag(lam) Q^H: its left and right eigenvectors are the
+    columns of Q, so for y = q_1 + d q_2 both residuals have the closed form
+    d |lam_2 - lam_1| / sqrt(1 + d^2) (spectral theorem)."""
+    rng = np.random.default_rng(seed)
+    Q = workloads.haar_unitary(rng, n)
+    lam = workloads.cgauss(rng, n, 1)[:, 0] + 0.5j
+    return Q @ np.diag(lam) @ Q.conj().T, Q, lam
+
+
+def check_residual_fn(fn):
+    A, Q, lam = normal_pair()
+    for d in (0.0, 1e-3, 0.3):
+        y = (Q[:, 0] + d * Q[:, 1])[:, None]
+        expect = d * abs(lam[1] - lam[0]) / np.sqrt(1 + d * d)
+        got = fn(A, None, lam[:1], y)[0]
+        assert abs(got - expect) <= 1e-13 * max(1.0, np.abs(lam).max()), (d, got, expect)
+
+
+def test_right_residuals_closed_form():
+    check_residual_fn(feast.right_residuals)
+
+
+def test_left_residuals_closed_form():
+    check_residual_fn(feast.left_residuals)
+
+
+def test_left_residuals_vanish_only_on_left_eigenvectors():
+    """Generalized pencil: brute-force (QZ) left eigenvectors give residuals at
+    rounding level; the right eigenvectors of the same non-normal pencil do not."""
+    A, B = small_generalized(n=30, seed=11)
+    lam, X, Yl = brute.eigenpairs(A, B)
+    lr = feast.left_residuals(A, B, lam, Yl)
+    scale = np.linalg.norm(A, 2) + np.abs(lam).max() * np.linalg.norm(B, 2)
+    assert lr.max() <= 1e-13 * scale
+    assert feast.left_residuals(A, B, lam, X).min() >= 1e-6 * scale
+    rr = feast.right_residuals(A, B, lam, X)
+    assert rr.max() <= 1e-13 * scale
+    assert feast.right_residuals(A, B, lam, Yl).min() >= 1e-6 * scale
+
+
+def test_residual_planted_mistakes(monkeypatch):
+    """lam instead of conj(lam) on the left, or a plus sign in A^H y - conj(lam) y,
+    must fail the closed-form pin."""
+    def fails(fn):
+        try:
+            check_residual_fn(fn)
+        except AssertionError:
+            return True
+        return False
+
+    def no_conj(A, B, lam, Y):
+        R = A.conj().T @ Y - Y * lam[None, :]
+        return np.linalg.norm(R, axis=0) / np.linalg.norm(Y, axis=0)
+
+    def plus_sign(A, B, lam, Y):
+        R = A.conj().T @ Y + Y * np.conj(lam)[None, :]
+        return np.linalg.norm(R, axis=0) / np.linalg.norm(Y, axis=0)
+
+    assert fails(no_conj)
+    assert fails(plus_sign)
+    assert not fails(feast.left_residuals)
