@@ -46,8 +46,11 @@ typedef enum {
   FEAST_ERR_ARG = 1,            /* invalid size, pointer or option                      */
   FEAST_ERR_ALLOC = 2,          /* device allocation failed                             */
   FEAST_ERR_SINGULAR_SHIFT = 3, /* a shifted matrix phi_k B - A had an exact zero pivot */
-  FEAST_ERR_REFINE_NOCONV = 4,  /* reserved: refinement did not reach its tolerance     */
-  FEAST_ERR_M0_TOO_SMALL = 5,   /* every Ritz value of the subspace lies inside C       */
+  FEAST_ERR_REFINE_NOCONV = 4,  /* per-shift refinement (max_refine > 0) stalled above
+                                   refine_tol even after the FP64 refactorisation      */
+  FEAST_ERR_M0_TOO_SMALL = 5,   /* every Ritz value of the subspace lies inside C: m0 is
+                                   at most the count, so some eigenvalues may be missed;
+                                   the outputs of the last iteration are returned      */
   FEAST_ERR_NOCONV = 6,         /* max_iter reached; results are still returned         */
   FEAST_ERR_NONFINITE = 7,      /* NaN or Inf appeared in the input or the iteration    */
   FEAST_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up                   */
@@ -71,8 +74,11 @@ typedef enum {
 } feast_rule;
 
 /* The ellipse of Eq. ellipses: centre c, semi-axes R (real direction) and
- * R * aspect (imaginary direction).  The domain test for candidates always
- * uses this ellipse, also for CUSTOM nodes. */
+ * R * aspect (imaginary direction).  The domain test for candidates uses this
+ * ellipse.  With CUSTOM nodes and R = 0 (no ellipse: a piecewise contour of
+ * Sec. 5.4, see feast_piecewise_nodes) a value lambda counts as inside when
+ * the filter of the nodes gives |rho(lambda)| = |sum_k sigma_k / (phi_k -
+ * lambda)| >= 1/2: rho approximates the indicator of the enclosed domain. */
 typedef struct {
   feast_z center;
   double R;
@@ -108,6 +114,23 @@ typedef struct {
                         Then (phi B - A)^{-H} conj(V) = conj((phi B - A)^{-1} V),
                         so Bi-FEAST takes the left block as conj(right block):
                         no left solves, Qhat = conj(Q), Vk = conj(Uk).        */
+  int max_refine;    /* MIXED only: 0 (default) = the residual form above; k > 0 =
+                        classical per-shift refinement as well, up to k sweeps
+                        X_k += S_k^{-1} (R - S_k X_k) with the residual in FP64,
+                        until every column has ||r|| <= refine_tol ||R||; a shift
+                        that stalls is refactored in FP64 and solved again.    */
+  double refine_tol; /* tau of the refinement (default 1e-12)                 */
+  int shift_begin;   /* this handle factors and filters the nodes           */
+  int shift_end;     /* [shift_begin, shift_end) only (0, 0 = all): the
+                        shift-partitioned filter, where each process owns a
+                        range of the linear systems (Sec. 6) and the partial
+                        sums are added by the caller                           */
+  int real_pencil;   /* nonzero: A and B are real and the nodes come in
+                        conjugate pairs (any rule on a contour symmetric about
+                        the real axis): only the nodes with Im >= 0 are
+                        factored, since (conj(phi) B - A) = conj(phi B - A)   */
+  const char* tune_cache; /* JSON file of tuned launch parameters written by
+                        paper_1404_2891_gb300.autotune (NULL = built-in)       */
 } feast_options;
 
 typedef struct {
@@ -124,6 +147,12 @@ typedef struct {
   int res_hist_len;
   double res_hist[64];   /* max candidate residual per iteration (inf if none)      */
   int count_hist[64];    /* candidate count per iteration                          */
+  int q;                 /* linear systems of this handle                          */
+  int shift_info[256];   /* per system: 0, or 1 + the first column whose pivot was
+                            exactly zero (FEAST_ERR_SINGULAR_SHIFT); 2^30 + sweeps
+                            for a shift whose refinement stalled                   */
+  int refine_sweeps;     /* classical refinement sweeps of the last filter          */
+  int refactored;        /* shifts refactored in FP64 by the last filter            */
 } feast_stats;
 
 typedef struct feast_handle feast_handle;
@@ -185,6 +214,26 @@ feast_status feast_solve_shift(feast_handle* h, int k, int side, const feast_z* 
 feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat,
                           const feast_z* theta, feast_z* Q, feast_z* Qhat);
 
+/* The shift-partitioned filter (Sec. 6: the linear systems are independent,
+ * one process may own each).  The q terms of the filter are summed along a
+ * fixed tree: the nodes are split into eight leaves [b_g, b_{g+1}),
+ * b_g = floor(g q / 8), each leaf summed in order of k, and the leaves
+ * added pairwise, ((0+1)+(2+3))+((4+5)+(6+7)), before the residual form's
+ * rho(theta) Y term.  A handle created with options.shift_begin/shift_end
+ * equal to an aligned run of 1, 2, 4 or 8 leaves ([b_{jL}, b_{(j+1)L}))
+ * factors only those systems, and its feast_filter returns the subtree sum of
+ * its leaves (no rho(theta) Y term); other ranges are FEAST_ERR_ARG, and
+ * feast_solve on such a handle is FEAST_ERR_STATE.
+ * feast_filter_combine adds nparts (1, 2, 4 or 8) such partial blocks, given
+ * in the order of their ranges, along the top of the same tree and adds the
+ * rho(theta) Y term for the Ritz values theta (MIXED; NULL = plain form), so
+ * the result has the same bits as feast_filter on one handle that owns every
+ * node.  parts[j] (and parts_hat[j] for the left filter, or NULL) are n x m0,
+ * host or device; Y/Yhat are the filter's inputs (needed with theta). */
+feast_status feast_filter_combine(feast_handle* h, int nparts, const feast_z* const* parts,
+                                  const feast_z* const* parts_hat, const feast_z* Y, const feast_z* Yhat,
+                                  const feast_z* theta, feast_z* Q, feast_z* Qhat);
+
 /* Stochastic moments of the filter for counting eigenvalues (the count
  * estimation of Sec. 6, in its plain stochastic-trace form):
  *   mu_k = (1/S) sum_s v_s^H [ sum_j sigma_j t_j^k (phi_j B - A)^{-1} B ] v_s,
@@ -206,6 +255,13 @@ feast_status feast_moments(feast_handle* h, const feast_z* V, int S, int kmax, f
 feast_status feast_rayleigh_ritz(feast_handle* h, const feast_z* Q, const feast_z* Qhat,
                                  feast_z* lambda, feast_z* X, feast_z* Xl, double* res,
                                  int* m_inside);
+
+/* The candidates of the last Rayleigh-Ritz step (Sec. 5: inside C and
+ * ||A x - lambda B x|| <= cand_tol): count, their column indices sorted by
+ * (Re lambda, Im lambda) (idx: m0 slots, may be NULL) and the largest
+ * normalised residual among them (inf if none; may be NULL).
+ * FEAST_ERR_STATE before any Rayleigh-Ritz step. */
+feast_status feast_candidates(const feast_handle* h, int* count, int* idx, double* max_res);
 
 /* The whole iteration (Algorithm R-FEAST or Bi-FEAST, with the Sec. 5
  * candidate monitoring).  Y0 (n x m0) is the random starting block; Vrand
@@ -380,6 +436,51 @@ feast_status feast_orthonormalize(int64_t n, int64_t m, feast_z* Q, int64_t ldq,
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; no paper counterpart). */
 uint64_t feast_kernel_launches(void);
+
+/* Diagnostic (no paper counterpart): the time limit of the library's
+ * cross-CTA waits -- the grid barriers of the cooperative kernels and the
+ * dependency waits of the batched persistent launch.  seconds <= 0 restores
+ * the built-in limits (about one to two seconds).  A wait that runs out sets a
+ * device flag, the kernel returns, and the call reports
+ * FEAST_ERR_DEVICE_TIMEOUT; the context stays usable.  Process-wide; takes
+ * effect for launches made after the call. */
+void feast_set_wait_limit(double seconds);
+
+/* Nodes and weights of a contour (Sec. 3, Eq. quadrature_for_pi) without a
+ * handle, on the host: q receives the number of nodes; nodes and weights
+ * (q entries each, host) may be NULL to query q. */
+feast_status feast_contour_nodes(const feast_contour* c, int* q, feast_z* nodes, feast_z* weights);
+
+/* ---- General domain shapes (Sec. 5.4): a boundary glued from segments,
+ * each parameterised on its own over t in [0, 1] and traversed
+ * counter-clockwise, each starting where the previous one ends:
+ *   kind 0: the line a + (b - a) t;
+ *   kind 1: the arc a + r exp(i (t0 + (t1 - t0) t)).
+ * feast_piecewise_nodes computes the nodes phi and weights
+ * sigma = w phi'(t) / (2 pi i) (host):
+ *   rule FEAST_RULE_TRAP_END: the trapezoidal rule with K >= 2 points per
+ *     segment, both ends included; the coinciding end and start nodes of
+ *     consecutive segments are merged (weights added), so
+ *     q = nseg (K - 1), each vertex once, at the start of the segment that
+ *     leaves it;
+ *   rule FEAST_RULE_GAUSS: K Gauss-Legendre points per segment, q = nseg K.
+ * Pass the result as FEAST_RULE_CUSTOM nodes (R = 0 selects the filter-value
+ * domain test).  q <= 256.  nodes/weights may be NULL to query q. */
+typedef struct {
+  int kind;
+  feast_z a, b;
+  double r, t0, t1;
+} feast_segment;
+feast_status feast_piecewise_nodes(const feast_segment* seg, int nseg, int K, int rule, int* q, feast_z* nodes,
+                                   feast_z* weights);
+
+/* The filter-quality indicator eta(r) of Sec. 3, a tuning tool for the
+ * choice of rule and N_e: on the level curves mu(r, th) = c + r R (cos th +
+ * i aspect sin th), th = 2 pi j / ntheta, eta(r) is the minimum of
+ * |rho(mu)| = |sum_k sigma_k / (phi_k - mu)| over the curve for r < 1 and
+ * its maximum for r > 1 (values near 1 inside and small outside mark a good
+ * filter).  Needs an ellipse (R > 0); host only.  r, eta: nr entries. */
+feast_status feast_eta_indicator(const feast_contour* c, const double* r, int nr, int ntheta, double* eta);
 
 #ifdef __cplusplus
 }

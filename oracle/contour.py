@@ -146,3 +146,84 @@ def eta_indicator(r, c, R, a, z, sig, ntheta=720):
     mu = c + R * r * (np.cos(th) + 1j * a * np.sin(th))
     v = np.abs(rho(mu, z, sig))
     return v.min() if r < 1 else v.max()
+
+
+# ---------------------------------------------------------------- piecewise contours (Sec. 5.4)
+# The general domains of Sec. 5.4 (triangle, square, semicircle) are bounded by
+# several curves, each parameterised on its own and "glued" at the vertices.
+# A segment is ("line", z0, z1): z0 + (z1 - z0) t, or ("arc", c, r, th0, th1):
+# c + r exp(i (th0 + (th1 - th0) t)), t in [0, 1]; the segments follow one
+# another counter-clockwise, each starting where the previous one ends.
+def segment_point(seg, t):
+    t = np.asarray(t, dtype=np.float64)
+    if seg[0] == "line":
+        return seg[1] + (seg[2] - seg[1]) * t
+    _, c, r, th0, th1 = seg
+    return c + r * np.exp(1j * (th0 + (th1 - th0) * t))
+
+
+def segment_deriv(seg, t):
+    t = np.asarray(t, dtype=np.float64)
+    if seg[0] == "line":
+        return (seg[2] - seg[1]) * np.ones_like(t)
+    _, c, r, th0, th1 = seg
+    return 1j * (th1 - th0) * r * np.exp(1j * (th0 + (th1 - th0) * t))
+
+
+def piecewise_quadrature(segments, K, rule="trap"):
+    """Nodes and weights sigma = w phi'(t) / (2 pi i) of a glued contour.
+
+    'trap': the trapezoidal rule of Sec. 5.4 with K points on each segment,
+    both ends included (step 1/(K-1)); the end of each segment is the start of
+    the next, so the two coinciding nodes are merged and their weights add:
+    q = len(segments) * (K - 1) nodes, each vertex listed once at the start of
+    the segment that leaves it.  'gauss': K Gauss-Legendre points on each
+    segment (no node on a vertex), q = len(segments) * K."""
+    zs, ss = [], []
+    if rule == "trap":
+        if K < 2:
+            raise ValueError("K >= 2")
+        t = np.linspace(0.0, 1.0, K)
+        w = np.full(K, 1.0 / (K - 1))
+        w[0] = w[-1] = 0.5 / (K - 1)
+        nseg = len(segments)
+        for s, seg in enumerate(segments):
+            prev = segments[s - 1]
+            d = w * segment_deriv(seg, t)
+            d[0] += w[-1] * segment_deriv(prev, 1.0)  # the previous segment's end node
+            zs.extend(segment_point(seg, t[:-1]))
+            ss.extend(d[:-1] / (2j * np.pi))
+        return np.array(zs), np.array(ss)
+    if rule == "gauss":
+        tg, wg = gauss_legendre(K)
+        t, w = 0.5 * (tg + 1.0), 0.5 * wg
+        for seg in segments:
+            zs.extend(segment_point(seg, t))
+            ss.extend(w * segment_deriv(seg, t) / (2j * np.pi))
+        return np.array(zs), np.array(ss)
+    raise ValueError(rule)
+
+
+def polygon(vertices):
+    """Line segments of the closed polygon through the given vertices."""
+    v = [complex(x) for x in vertices]
+    return [("line", v[i], v[(i + 1) % len(v)]) for i in range(len(v))]
+
+
+def semicircle(c, r):
+    """Upper half disk: the arc from angle 0 to pi, then the diameter back."""
+    c = complex(c)
+    return [("arc", c, float(r), 0.0, np.pi), ("line", c - r, c + r)]
+
+
+def inside_polygon(lam, vertices):
+    """Strictly inside a convex counter-clockwise polygon: every edge has the
+    point on its left (positive cross product)."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    v = [complex(x) for x in vertices]
+    ok = np.ones(lam.shape, dtype=bool)
+    for i in range(len(v)):
+        a, b = v[i], v[(i + 1) % len(v)]
+        cross = (b - a).real * (lam - a).imag - (b - a).imag * (lam - a).real
+        ok &= cross > 0
+    return ok

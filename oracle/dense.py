@@ -21,15 +21,17 @@ def cabs1(x):
     return np.abs(x.real) + np.abs(x.imag)
 
 
-def lu_factor(S):
+def lu_factor(S, stop=None):
     """Gaussian elimination with partial pivoting.  Returns (LU, piv, info);
     info = 0, or 1 + the first column whose pivot is exactly zero (the
-    elimination continues past it, as LAPACK does)."""
+    elimination continues past it, as LAPACK does).  stop (default n) ends the
+    elimination after that many columns, leaving the trailing block updated by
+    them (used only to time a bounded part of a large factorisation)."""
     LU = np.array(S, dtype=np.complex128, copy=True)
     n = LU.shape[0]
     piv = np.arange(n, dtype=np.int64)
     info = 0
-    for k in range(n):
+    for k in range(n if stop is None else min(int(stop), n)):
         p = k + int(np.argmax(cabs1(LU[k:, k])))  # first maximum = lowest index
         piv[k] = p
         if p != k:

@@ -52,7 +52,14 @@ class feast_contour(ctypes.Structure):
 class feast_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("cand_tol", ctypes.c_double), ("panel", ctypes.c_int),
-                ("timing", ctypes.c_int), ("symmetric", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("symmetric", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("refine_tol", ctypes.c_double), ("shift_begin", ctypes.c_int), ("shift_end", ctypes.c_int),
+                ("real_pencil", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+
+
+class feast_segment(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", feast_z), ("b", feast_z), ("r", ctypes.c_double),
+                ("t0", ctypes.c_double), ("t1", ctypes.c_double)]
 
 
 class feast_stats(ctypes.Structure):
@@ -61,7 +68,9 @@ class feast_stats(ctypes.Structure):
                 ("t_filter_ms", ctypes.c_double), ("t_rr_ms", ctypes.c_double),
                 ("t_total_ms", ctypes.c_double), ("t_update_ms", ctypes.c_double),
                 ("update_launches", ctypes.c_int), ("res_hist_len", ctypes.c_int),
-                ("res_hist", ctypes.c_double * 64), ("count_hist", ctypes.c_int * 64)]
+                ("res_hist", ctypes.c_double * 64), ("count_hist", ctypes.c_int * 64),
+                ("q", ctypes.c_int), ("shift_info", ctypes.c_int * 256), ("refine_sweeps", ctypes.c_int),
+                ("refactored", ctypes.c_int)]
 
 
 class FeastError(RuntimeError):
@@ -81,7 +90,9 @@ SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_stat
            "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train",
            "feast_batch_create", "feast_batch_destroy", "feast_batch_factor", "feast_batch_filter",
            "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_plan",
-           "feast_emulated_zgemm", "feast_orthonormalize")
+           "feast_emulated_zgemm", "feast_orthonormalize", "feast_set_wait_limit", "feast_contour_nodes",
+           "feast_piecewise_nodes", "feast_eta_indicator", "feast_filter_combine",
+           "feast_candidates")
 
 
 class feast_batch_stats(ctypes.Structure):
@@ -167,6 +178,18 @@ def load(path=LIB_PATH):
     lib.feast_emulated_zgemm.restype = I
     lib.feast_orthonormalize.argtypes = [I64, I64, P, I64, P]
     lib.feast_orthonormalize.restype = I
+    lib.feast_set_wait_limit.argtypes = [ctypes.c_double]
+    lib.feast_set_wait_limit.restype = None
+    lib.feast_contour_nodes.argtypes = [ctypes.POINTER(feast_contour), ctypes.POINTER(ctypes.c_int), P, P]
+    lib.feast_contour_nodes.restype = I
+    lib.feast_piecewise_nodes.argtypes = [ctypes.POINTER(feast_segment), I, I, I, ctypes.POINTER(ctypes.c_int), P, P]
+    lib.feast_piecewise_nodes.restype = I
+    lib.feast_eta_indicator.argtypes = [ctypes.POINTER(feast_contour), P, I, I, P]
+    lib.feast_eta_indicator.restype = I
+    lib.feast_filter_combine.argtypes = [P, I, P, P, P, P, P, P, P]
+    lib.feast_filter_combine.restype = I
+    lib.feast_candidates.argtypes = [P, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(ctypes.c_double)]
+    lib.feast_candidates.restype = I
     _lib = lib
     return lib
 
@@ -257,13 +280,19 @@ def make_contour(center=0.0, R=1.0, aspect=1.0, rule="trap_mid", N_e=8, nodes=No
 
 
 def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False,
-                 symmetric=False):
+                 symmetric=False, max_refine=0, refine_tol=1e-12, shifts=None, real_pencil=False, tune_cache=None):
+    """shifts: (begin, end) range of the contour's nodes this handle owns (None = all)."""
     o = feast_options()
     load().feast_default_options(ctypes.byref(o))
     o.algo = ALGOS[algo]
     o.precision = PRECISIONS[precision]
     o.tol, o.max_iter, o.cand_tol, o.panel, o.timing = float(tol), int(max_iter), float(cand_tol), int(panel), int(timing)
     o.symmetric = int(symmetric)
+    o.max_refine, o.refine_tol = int(max_refine), float(refine_tol)
+    if shifts is not None:
+        o.shift_begin, o.shift_end = int(shifts[0]), int(shifts[1])
+    o.real_pencil = int(real_pencil)
+    o.tune_cache = None if tune_cache is None else str(tune_cache).encode()
     return o
 
 
@@ -308,7 +337,24 @@ def feast_get_stats(h):
     st = feast_stats()
     _check(load().feast_get_stats(h.ptr, ctypes.byref(st)), "feast_get_stats")
     return dict(normA=st.normA, t_factor_ms=st.t_factor_ms, t_update_ms=st.t_update_ms,
-                update_launches=st.update_launches, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms)
+                update_launches=st.update_launches, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms,
+                q=st.q, shift_info=list(st.shift_info[:st.q]), refine_sweeps=st.refine_sweeps,
+                refactored=st.refactored)
+
+
+def feast_set_wait_limit(seconds):
+    """Time limit of the library's cross-CTA waits (<= 0: built-in limits)."""
+    load().feast_set_wait_limit(float(seconds))
+
+
+def feast_contour_nodes(contour):
+    """(nodes, weights) of a contour from make_contour, computed by the library on the host."""
+    lib = load()
+    q = ctypes.c_int()
+    _check(lib.feast_contour_nodes(ctypes.byref(contour), ctypes.byref(q), None, None), "feast_contour_nodes")
+    nz, wz = (feast_z * q.value)(), (feast_z * q.value)()
+    _check(lib.feast_contour_nodes(ctypes.byref(contour), ctypes.byref(q), nz, wz), "feast_contour_nodes")
+    return (np.array([complex(v.re, v.im) for v in nz]), np.array([complex(v.re, v.im) for v in wz]))
 
 
 def feast_norm2_estimate_static(A, iters=50, stream=None):
@@ -320,16 +366,55 @@ def feast_norm2_estimate_static(A, iters=50, stream=None):
     if not _is_torch(A) or not A.is_cuda:
         raise TypeError("feast_norm2_estimate_static needs a CUDA tensor (device memory)")
     import torch
-    if A.dtype != torch.complex128 or A.dim() != 2 or not A.mT.is_contiguous():
-        raise TypeError("A must be a complex128 CUDA tensor with column-major storage")
+    if A.dtype != torch.complex128 or A.dim() != 2:
+        raise TypeError("A must be a 2-D complex128 CUDA tensor")
+    if A.shape[0] != A.shape[1]:
+        raise TypeError(f"A must be square, got {tuple(A.shape)}")
     n = A.shape[0]
+    # column-major storage: unit row stride, column stride lda >= n
+    if n > 1 and (A.stride(0) != 1 or A.stride(1) < n):
+        raise TypeError("A must have column-major storage (unit row stride, column stride >= n)")
+    lda = max(int(A.stride(1)), n)
     out = ctypes.c_double()
     sp = None
     if stream is not None:
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    _check(load().feast_norm2_estimate_static(A.data_ptr(), n, n, int(iters), ctypes.byref(out), sp),
+    _check(load().feast_norm2_estimate_static(A.data_ptr(), n, lda, int(iters), ctypes.byref(out), sp),
            "feast_norm2_estimate_static")
     return out.value
+
+
+def feast_piecewise_nodes(segments, K, rule="trap_end"):
+    """Nodes and weights of a glued contour (Sec. 5.4).  segments: list of
+    ("line", z0, z1) or ("arc", c, r, th0, th1); rule "trap_end" or "gauss"."""
+    lib = load()
+    segs = (feast_segment * len(segments))()
+    for i, sg in enumerate(segments):
+        g = segs[i]
+        if sg[0] == "line":
+            g.kind = 0
+            g.a = feast_z(complex(sg[1]).real, complex(sg[1]).imag)
+            g.b = feast_z(complex(sg[2]).real, complex(sg[2]).imag)
+        else:
+            g.kind = 1
+            g.a = feast_z(complex(sg[1]).real, complex(sg[1]).imag)
+            g.r, g.t0, g.t1 = float(sg[2]), float(sg[3]), float(sg[4])
+    q = ctypes.c_int()
+    _check(lib.feast_piecewise_nodes(segs, len(segments), int(K), RULES[rule], ctypes.byref(q), None, None),
+           "feast_piecewise_nodes")
+    nz, wz = (feast_z * q.value)(), (feast_z * q.value)()
+    _check(lib.feast_piecewise_nodes(segs, len(segments), int(K), RULES[rule], ctypes.byref(q), nz, wz),
+           "feast_piecewise_nodes")
+    return (np.array([complex(v.re, v.im) for v in nz]), np.array([complex(v.re, v.im) for v in wz]))
+
+
+def feast_eta_indicator(contour, r, ntheta=720):
+    """eta(r) of Sec. 3 for a contour from make_contour (host computation in the library)."""
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    eta = np.zeros_like(rr)
+    _check(load().feast_eta_indicator(ctypes.byref(contour), rr.ctypes.data, len(rr), int(ntheta), eta.ctypes.data),
+           "feast_eta_indicator")
+    return eta
 
 
 def feast_factor(h, allow_singular=False):
@@ -371,6 +456,23 @@ def feast_filter(h, Y, Yhat=None, theta=None, out_device=False):
     return _finish(Q, out_device), (_finish(Qh, out_device) if Yhat is not None else None)
 
 
+def feast_filter_combine(h, parts, parts_hat=None, Y=None, Yhat=None, theta=None, out_device=False):
+    """Sum the partial filters of a shift partition along the fixed tree (see
+    include/feast_gb300.h); parts (and parts_hat) list the n x m0 blocks in the
+    order of their shift ranges."""
+    keep = [_colmajor(p) for p in parts]
+    keeph = [_colmajor(p) for p in parts_hat] if parts_hat is not None else None
+    py, ky = _colmajor(Y)
+    pyh, kyh = _colmajor(Yhat)
+    pt, kt = _colmajor(theta)
+    pq, Q = _out((h.n, h.m0), out_device)
+    pqh, Qh = (_out((h.n, h.m0), out_device) if parts_hat is not None else (None, None))
+    _check(load().feast_filter_combine(h.ptr, len(parts), _ptr_array([k[0] for k in keep]),
+                                       _ptr_array([k[0] for k in keeph]) if keeph is not None else None,
+                                       py, pyh, pt, pq, pqh), "feast_filter_combine")
+    return _finish(Q, out_device), (_finish(Qh, out_device) if parts_hat is not None else None)
+
+
 def feast_rayleigh_ritz(h, Q, Qhat=None, out_device=False):
     pq, kq = _colmajor(Q)
     pqh, kqh = _colmajor(Qhat)
@@ -385,6 +487,15 @@ def feast_rayleigh_ritz(h, Q, Qhat=None, out_device=False):
                 res=res, m_inside=mi.value)
 
 
+def feast_candidates(h):
+    """(indices sorted by (Re, Im), max normalised residual) of the last Rayleigh-Ritz step's candidates."""
+    c = ctypes.c_int()
+    idx = np.zeros(h.m0, dtype=np.int32)
+    mr = ctypes.c_double()
+    _check(load().feast_candidates(h.ptr, ctypes.byref(c), idx.ctypes.data, ctypes.byref(mr)), "feast_candidates")
+    return idx[:c.value].astype(np.int64), mr.value
+
+
 def feast_solve(h, Y0, Vrand=None, out_device=False, allow_noconv=True):
     py, ky = _colmajor(Y0)
     pv, kv = _colmajor(Vrand)
@@ -396,10 +507,11 @@ def feast_solve(h, Y0, Vrand=None, out_device=False, allow_noconv=True):
     st = feast_stats()
     s = load().feast_solve(h.ptr, py, pv, lam.ctypes.data, px, pxl, res.ctypes.data, ctypes.byref(mf),
                            ctypes.byref(st))
-    _check(s, "feast_solve", (FEAST_ERR_NOCONV,) if allow_noconv else ())
+    _check(s, "feast_solve", (FEAST_ERR_NOCONV, FEAST_ERR_M0_TOO_SMALL) if allow_noconv else ())
     k = mf.value
     Xf = _finish(X, out_device)
     out = dict(status=s, converged=(s == FEAST_OK), m_found=k, lam=lam[:k], res=res[:k],
+               shift_info=list(st.shift_info[:st.q]), refine_sweeps=st.refine_sweeps, refactored=st.refactored,
                X=Xf[:, :k], iters=st.iters, max_res=st.max_res, normA=st.normA,
                t_factor_ms=st.t_factor_ms, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms,
                t_total_ms=st.t_total_ms,
@@ -532,7 +644,7 @@ def feast_emulated_zgemm(A, X, op="N"):
     m = X.shape[1] if X.ndim == 2 else 1
     C = np.zeros((n, m), dtype=np.complex128, order="F")
     _check(load().feast_emulated_zgemm(n, m, pa, n, {"N": 0, "C": 2}[op], px, n, C.ctypes.data, n, None),
-           "feast_emulated_zgemm", "feast_orthonormalize")
+           "feast_emulated_zgemm")
     return C
 
 

@@ -298,6 +298,7 @@ BatchLuArgs lu_args(feast_batch* b, const int4* tasks, int ntasks) {
   a.X = b->Xs;
   a.active = b->active;
   a.flags = b->flags;
+  a.wait_ns = feast_wait_limit_ns(2000000000ull);
   return a;
 }
 

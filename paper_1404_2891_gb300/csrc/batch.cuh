@@ -55,6 +55,7 @@ struct BatchLuArgs {
   float2* X = nullptr;          // solutions (complex64, per matrix)
   const int* active = nullptr;  // per pencil: solve tasks of inactive pencils are skipped
   unsigned* flags = nullptr;
+  unsigned long long wait_ns = 2000000000ull;  // limit of each dependency wait
 };
 
 // ---- persistent factor/solve (batch_lu.cu)

@@ -32,7 +32,6 @@ namespace {
 
 constexpr int NT = 256;  // threads per CTA
 constexpr int TT = BATCH_TILE * BATCH_TILE;
-constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 struct Shared {
   int task, ok;
@@ -68,14 +67,14 @@ __device__ __forceinline__ void cp_wait() {
 
 // Thread 0 only: wait until *p >= v.  False after the time limit or when
 // another CTA has already given up.
-__device__ bool wait_ge(const int* p, int v, unsigned* flags) {
+__device__ bool wait_ge(const int* p, int v, unsigned* flags, unsigned long long limit) {
   if (ld_acquire(p) >= v) return true;
   const unsigned long long t0 = gtime();
   for (;;) {
     __nanosleep(64);
     if (ld_acquire(p) >= v) return true;
     if (*(volatile unsigned*)flags & DEVFLAG_TIMEOUT) return false;
-    if (gtime() - t0 > WAIT_NS) {
+    if (gtime() - t0 > limit) {
       atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
       return false;
     }
@@ -419,13 +418,13 @@ __global__ void __launch_bounds__(NT, 1) k_batch_lu(BatchLuArgs a, int gcap) {
     if (tid == 0) {
       bool ok = true;
       switch (tk.x) {
-        case BT_PANEL: ok = tk.z == 0 || wait_ge(a.cver + M.coff + tk.z, tk.z, a.flags); break;
+        case BT_PANEL: ok = tk.z == 0 || wait_ge(a.cver + M.coff + tk.z, tk.z, a.flags, a.wait_ns); break;
         case BT_UPDATE:
-          ok = wait_ge(a.pdone + M.coff + tk.z, 1, a.flags) &&
-               (tk.z == 0 || wait_ge(a.cver + M.coff + tk.w, tk.z, a.flags));
+          ok = wait_ge(a.pdone + M.coff + tk.z, 1, a.flags, a.wait_ns) &&
+               (tk.z == 0 || wait_ge(a.cver + M.coff + tk.w, tk.z, a.flags, a.wait_ns));
           break;
-        case BT_LSWAP: ok = wait_ge(a.pdone + M.coff + M.nb - 1, 1, a.flags); break;
-        default: ok = !a.active[M.pencil] || wait_ge(a.fcnt + tk.y, M.nb, a.flags); break;
+        case BT_LSWAP: ok = wait_ge(a.pdone + M.coff + M.nb - 1, 1, a.flags, a.wait_ns); break;
+        default: ok = !a.active[M.pencil] || wait_ge(a.fcnt + tk.y, M.nb, a.flags, a.wait_ns); break;
       }
       sh.ok = ok ? 1 : 0;
     }

@@ -27,20 +27,51 @@ __global__ void k_form_shifted(const double2* A, long long lda, const double2* B
 }
 
 template <typename T>
-__global__ void k_accumulate(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* c0,
+__global__ void k_accumulate(const cplx<T>* Xs, AccTree t, int n, int m, const double2* coef, const double2* c0,
                              const double2* Y, const int32_t* rowmap, double2* Q) {
   const size_t total = (size_t)n * m;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(idx % n);
     const int i = (int)(idx / n);
-    double2 acc = make_double2(0.0, 0.0);
-    if (c0 && Y) acc = cmul<double>(c0[i], Y[idx]);
-    for (int b = 0; b < q; ++b) {
-      const int rr = rowmap ? rowmap[(size_t)b * n + r] : r;
-      const cplx<T> x = Xs[(size_t)b * total + (size_t)i * n + rr];
-      cfma<double>(acc, coef[(size_t)b * m + i], cconv<double, T>(x));
+    double2 leaf[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      leaf[j] = make_double2(0.0, 0.0);
+      if (j < t.nleaf)
+        for (int b = t.b[j]; b < t.b[j + 1]; ++b) {
+          const int rr = rowmap ? rowmap[(size_t)b * n + r] : r;
+          const cplx<T> x = Xs[(size_t)b * total + (size_t)i * n + rr];
+          cfma<double>(leaf[j], coef[(size_t)b * m + i], cconv<double, T>(x));
+        }
     }
+#pragma unroll
+    for (int w = 1; w < 8; w *= 2)
+#pragma unroll
+      for (int j = 0; j + w < 8; j += 2 * w)
+        if (j + w < t.nleaf) leaf[j] = cadd<double>(leaf[j], leaf[j + w]);
+    double2 acc = leaf[0];
+    if (c0 && Y) cfma<double>(acc, c0[i], Y[idx]);
+    Q[idx] = acc;
+  }
+}
+
+__global__ void k_tree_combine(const double2* P, int nparts, int n, int m, const double2* c0, const double2* Y,
+                               double2* Q) {
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n);
+    double2 leaf[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) leaf[j] = j < nparts ? P[(size_t)j * total + idx] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int w = 1; w < 8; w *= 2)
+#pragma unroll
+      for (int j = 0; j + w < 8; j += 2 * w)
+        if (j + w < nparts) leaf[j] = cadd<double>(leaf[j], leaf[j + w]);
+    double2 acc = leaf[0];
+    if (c0 && Y) cfma<double>(acc, c0[i], Y[idx]);
     Q[idx] = acc;
   }
 }
@@ -211,14 +242,31 @@ template cudaError_t form_shifted<double>(const double2*, long long, const doubl
 template cudaError_t form_shifted<float>(const double2*, long long, const double2*, long long, const double2*, int, int, float2*, long long, cudaStream_t);
 
 template <typename T>
-cudaError_t accumulate(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* c0,
+cudaError_t accumulate(const cplx<T>* Xs, const AccTree& t, int n, int m, const double2* coef, const double2* c0,
                        const double2* Y, const int32_t* rowmap, double2* Q, cudaStream_t s) {
+  if (t.nleaf < 1 || t.nleaf > 8 || (t.nleaf & (t.nleaf - 1))) return cudaErrorInvalidValue;
   feast_count_launch();
-  k_accumulate<T><<<grid_for((size_t)n * m), 256, 0, s>>>(Xs, q, n, m, coef, c0, Y, rowmap, Q);
+  k_accumulate<T><<<grid_for((size_t)n * m), 256, 0, s>>>(Xs, t, n, m, coef, c0, Y, rowmap, Q);
   return cudaGetLastError();
 }
-template cudaError_t accumulate<double>(const double2*, int, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
-template cudaError_t accumulate<float>(const float2*, int, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
+template cudaError_t accumulate<double>(const double2*, const AccTree&, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
+template cudaError_t accumulate<float>(const float2*, const AccTree&, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
+
+AccTree acc_tree_single(int q) {
+  AccTree t;
+  t.nleaf = 1;
+  t.b[0] = 0;
+  t.b[1] = q;
+  return t;
+}
+
+cudaError_t accumulate_tree_combine(const double2* P, int nparts, int n, int m, const double2* c0, const double2* Y,
+                                    double2* Q, cudaStream_t s) {
+  if (nparts < 1 || nparts > 8 || (nparts & (nparts - 1))) return cudaErrorInvalidValue;
+  feast_count_launch();
+  k_tree_combine<<<grid_for((size_t)n * m), 256, 0, s>>>(P, nparts, n, m, c0, Y, Q);
+  return cudaGetLastError();
+}
 
 cudaError_t select_columns(const double2* E, const double2* F, const int* use_res, int n, int m, double2* R,
                            cudaStream_t s) {

@@ -7,11 +7,28 @@ template <typename T>
 cudaError_t form_shifted(const double2* A, long long lda, const double2* B, long long ldb,
                          const double2* z, int q, int n, cplx<T>* S, long long strideS, cudaStream_t s);
 
-// Q[r, i] = c0[i] * Y[r, i] + sum_{b=0}^{q-1} coef[b*m + i] * Xs_b[rowmap_b(r), i]
-// (fixed summation order in b; Y and c0 may be null; rowmap may be null = identity).
+// The summation tree of the accumulation: the shifts are split into leaves
+// (b[j] .. b[j+1]-1, at most 8), each leaf summed in order of the shift, and
+// the leaves combined pairwise level by level ((0+1)+(2+3))+((4+5)+(6+7)).
+// A handle that owns an aligned range of the contour's eight leaves computes
+// the subtree of that range, so partial sums of several processes combine to
+// the same bits as one process (accumulate_tree_combine).
+struct AccTree {
+  int nleaf = 1;   // 1, 2, 4 or 8
+  int b[9] = {0};  // local leaf boundaries, b[nleaf] = q
+};
+AccTree acc_tree_single(int q);
+
+// Q[r, i] = tree_b(coef[b*m + i] * Xs_b[rowmap_b(r), i]) + c0[i] * Y[r, i]
+// (Y and c0 may be null; rowmap may be null = identity).
 template <typename T>
-cudaError_t accumulate(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* c0,
+cudaError_t accumulate(const cplx<T>* Xs, const AccTree& t, int n, int m, const double2* coef, const double2* c0,
                        const double2* Y, const int32_t* rowmap, double2* Q, cudaStream_t s);
+
+// Q = the top levels of the tree over nparts (1, 2, 4 or 8) partial blocks P_j
+// (n x m each, consecutive in P), then + c0 .* Y (c0, Y may be null).
+cudaError_t accumulate_tree_combine(const double2* P, int nparts, int n, int m, const double2* c0, const double2* Y,
+                                    double2* Q, cudaStream_t s);
 
 // R[:, i] = use_res[i] ? E[:, i] : F[:, i]
 cudaError_t select_columns(const double2* E, const double2* F, const int* use_res, int n, int m,

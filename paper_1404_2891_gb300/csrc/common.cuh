@@ -75,3 +75,7 @@ inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b
 // Process-wide count of kernel launches made by this library (diagnostic;
 // read through feast_kernel_launches()).
 void feast_count_launch();
+
+// Time limit (ns) of the cross-CTA waits: the value set by feast_set_wait_limit,
+// else `dflt` (the kernel's built-in limit).
+unsigned long long feast_wait_limit_ns(unsigned long long dflt);

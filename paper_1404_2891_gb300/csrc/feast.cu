@@ -152,7 +152,14 @@ struct feast_handle {
   bool hasB = false;
   zc center;
   double R = 1.0, aspect = 1.0;
-  std::vector<zc> z, w;
+  bool filter_domain = false;  // CUSTOM nodes without an ellipse: inside = |rho| >= 1/2
+  std::vector<zc> z, w;        // the nodes this handle factors (a range of the contour's)
+  std::vector<zc> z_all, w_all;  // every node of the contour
+  int shift0 = 0;              // index of z[0] among z_all
+  bool partial = false;        // a proper sub-range: the filter returns its subtree, without c0 Y
+  AccTree tree;                // the summation tree of this handle's leaves
+  double2* combine_buf = nullptr;  // feast_filter_combine's staging of the partial blocks
+  std::vector<int> h_info;     // per shift: 0 or 1 + first zero-pivot column (last factorisation)
   double normA = 0.0;
   double2* At = nullptr;
   // ||A||_2 is estimated on its own stream at creation, beside the first
@@ -198,6 +205,9 @@ struct feast_handle {
   float2* s32 = nullptr;       // FP32 Schur work: C, Z, V, W, lambda (m0 x m0 each)
   size_t gemm_ws_elems = 0;
   std::vector<void*> allocs;
+  // classical refinement (options.max_refine > 0): per-shift stall records
+  std::vector<int> h_refine_fail;
+  int refine_sweeps = 0, n_refactored = 0;
   // host mirrors of the last Rayleigh-Ritz step
   std::vector<zc> h_lam;
   std::vector<double> h_res, h_resl;
@@ -392,6 +402,7 @@ feast_status factor_impl(feast_handle* h) {
     cudaEventElapsedTime(&ms, h->upd_ev[2 * i], h->upd_ev[2 * i + 1]);
     h->t_update += ms;
   }
+  h->h_info = info;
   feast_status fs = read_flags(h);
   if (fs == FEAST_ERR_NONFINITE) return fs;
   for (int k = 0; k < h->q; ++k)
@@ -422,7 +433,9 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   if (split) CK(cudaEventRecord(h->fork_ev, h->st));  // the left solves start from here
   CK(rows_gather<T>(lu, R, Xs, m, true, h->st));
   CK(lu_solve_batched<T>(lu, 0, Xs, m, h->nbs, h->st));
-  CK(accumulate<T>(Xs, h->q, n, m, h->coef, use_c0 ? h->c0 : nullptr, use_c0 ? Yc0 : nullptr, nullptr, Qout, h->st));
+  const bool add_c0 = use_c0 && !h->partial;  // a partial handle returns its subtree alone
+  CK(accumulate<T>(Xs, h->tree, n, m, h->coef, add_c0 ? h->c0 : nullptr, add_c0 ? Yc0 : nullptr, nullptr, Qout,
+                   h->st));
   if (Rh && h->opt.symmetric) {
     // complex symmetric pencil: (phi B - A)^{-H} conj(V) = conj((phi B - A)^{-1} V),
     // and the left inputs are the conjugates of the right ones
@@ -437,7 +450,7 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
     if (split) CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
     CK(rows_gather<T>(lul, Rh, Xsh, m, false, ls));
     CK(lu_solve_batched<T>(lul, 1, Xsh, m, h->nbs, ls));
-    CK(accumulate<T>(Xsh, h->q, n, m, h->coefh, use_c0 ? h->c0h : nullptr, use_c0 ? Yhc0 : nullptr, lu.pinv,
+    CK(accumulate<T>(Xsh, h->tree, n, m, h->coefh, add_c0 ? h->c0h : nullptr, add_c0 ? Yhc0 : nullptr, lu.pinv,
                      Qhout, ls));
     if (split) {
       CK(cudaEventRecord(h->join_ev, h->side));
@@ -452,28 +465,31 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
 //   S_k^{-1} B x = x / (phi_k - theta) + S_k^{-1} (A x - theta B x) / (phi_k - theta)
 // so coef_k,i = sigma_k / (phi_k - theta_i) and c0_i = sum_k coef_k,i = rho(theta_i).
 feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* use_out) {
-  const int q = h->q, m = h->m0;
+  const int q = h->q, m = h->m0, qa = (int)h->z_all.size();
   std::vector<double2> coef((size_t)q * m), coefh((size_t)q * m), c0(m), c0h(m);
   std::vector<int> use(m, 0);
   for (int i = 0; i < m; ++i) {
     bool u = false;
     if (theta && std::isfinite(theta[i].real()) && std::isfinite(theta[i].imag())) {
       double dmin = 1e300;
-      for (int k = 0; k < q; ++k) dmin = std::min(dmin, std::abs(h->z[k] - theta[i]));
+      for (int k = 0; k < qa; ++k) dmin = std::min(dmin, std::abs(h->z_all[k] - theta[i]));
       // The identity holds for every theta != phi_k; for a converged pair the
       // initial iterate x / (phi_k - theta) is already close to the solution, so
       // a Ritz value next to a node brings no cancellation.  Only a value on top
-      // of a node (division by ~0) takes the plain right-hand side.
+      // of a node (division by ~0) takes the plain right-hand side.  Every node
+      // of the contour decides, so that the handles of a shift partition agree.
       u = dmin >= 1e-10 * h->R;
     }
     use[i] = u;
-    zc acc = 0.0;
     for (int k = 0; k < q; ++k) {
-      const zc g = u ? h->w[k] / (h->z[k] - theta[i]) : h->w[k];
-      acc += g;
+      const int kg = h->shift0 + k;
+      const zc g = u ? h->w_all[kg] / (h->z_all[kg] - theta[i]) : h->w_all[kg];
       coef[(size_t)k * m + i] = d2(g);
       coefh[(size_t)k * m + i] = d2(std::conj(g));
     }
+    zc acc = 0.0;  // c0 = rho(theta) over all the contour's nodes
+    if (u)
+      for (int k = 0; k < qa; ++k) acc += h->w_all[k] / (h->z_all[k] - theta[i]);
     c0[i] = d2(u ? acc : zc(0.0));
     c0h[i] = d2(u ? std::conj(acc) : zc(0.0));
   }
@@ -642,6 +658,11 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
 }
 
 bool inside_ellipse(const feast_handle* h, zc l) {
+  if (h->filter_domain) {  // rho of all the contour's nodes approximates the indicator
+    zc r = 0.0;
+    for (size_t k = 0; k < h->z_all.size(); ++k) r += h->w_all[k] / (h->z_all[k] - l);
+    return std::abs(r) >= 0.5;
+  }
   const double x = (l.real() - h->center.real()) / h->R;
   const double y = (l.imag() - h->center.imag()) / (h->R * h->aspect);
   return x * x + y * y < 1.0;
@@ -697,12 +718,121 @@ double norm_of(feast_handle* h) {
   return h->normA;
 }
 
+// per-shift status of the last factorisation and refinement
+void fill_shift_stats(const feast_handle* h, feast_stats* st) {
+  st->q = h->q;
+  for (int k = 0; k < h->q && k < 256; ++k) {
+    st->shift_info[k] = k < (int)h->h_info.size() ? h->h_info[k] : 0;
+    if (k < (int)h->h_refine_fail.size() && h->h_refine_fail[k]) st->shift_info[k] = (1 << 30) + h->h_refine_fail[k];
+  }
+  st->refine_sweeps = h->refine_sweeps;
+  st->refactored = h->n_refactored;
+}
+
+std::atomic<unsigned long long> g_wait_ns{0};
+
 }  // namespace
+
+// the time limit of the cross-CTA waits (0 = each kernel's built-in limit)
+unsigned long long feast_wait_limit_ns(unsigned long long dflt) {
+  const unsigned long long v = g_wait_ns.load(std::memory_order_relaxed);
+  return v ? v : dflt;
+}
 
 // ================================================================= C ABI
 extern "C" {
 
 uint64_t feast_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void feast_set_wait_limit(double seconds) {
+  g_wait_ns.store(seconds > 0 ? (unsigned long long)(seconds * 1e9) + 1ull : 0ull, std::memory_order_relaxed);
+}
+
+feast_status feast_piecewise_nodes(const feast_segment* seg, int nseg, int K, int rule, int* q, feast_z* nodes,
+                                   feast_z* weights) {
+  if (!seg || nseg < 1 || !q) return FEAST_ERR_ARG;
+  if (rule != FEAST_RULE_TRAP_END && rule != FEAST_RULE_GAUSS) return FEAST_ERR_ARG;
+  if (K < (rule == FEAST_RULE_TRAP_END ? 2 : 1)) return FEAST_ERR_ARG;
+  for (int s2 = 0; s2 < nseg; ++s2)
+    if (seg[s2].kind != 0 && seg[s2].kind != 1) return FEAST_ERR_ARG;
+  const int count = rule == FEAST_RULE_TRAP_END ? nseg * (K - 1) : nseg * K;
+  if (count > 256) return FEAST_ERR_ARG;
+  *q = count;
+  if (!nodes && !weights) return FEAST_OK;
+  const zc twopii(0.0, 2.0 * M_PI);
+  auto point = [&](const feast_segment& g, double t) -> zc {
+    const zc a(g.a.re, g.a.im), b(g.b.re, g.b.im);
+    if (g.kind == 0) return a + (b - a) * t;
+    return a + g.r * std::exp(zc(0.0, g.t0 + (g.t1 - g.t0) * t));
+  };
+  auto deriv = [&](const feast_segment& g, double t) -> zc {
+    const zc a(g.a.re, g.a.im), b(g.b.re, g.b.im);
+    if (g.kind == 0) return b - a;
+    return zc(0.0, (g.t1 - g.t0) * g.r) * std::exp(zc(0.0, g.t0 + (g.t1 - g.t0) * t));
+  };
+  std::vector<zc> z, w;
+  if (rule == FEAST_RULE_TRAP_END) {
+    const double h = 1.0 / (K - 1);
+    for (int s2 = 0; s2 < nseg; ++s2) {
+      const feast_segment& g = seg[s2];
+      const feast_segment& prev = seg[(s2 + nseg - 1) % nseg];
+      for (int j = 0; j < K - 1; ++j) {
+        const double t = j * h;
+        zc d = (j == 0 ? 0.5 * h : h) * deriv(g, t);
+        if (j == 0) d += 0.5 * h * deriv(prev, 1.0);  // the merged end node of the previous segment
+        z.push_back(point(g, t));
+        w.push_back(d / twopii);
+      }
+    }
+  } else {
+    std::vector<double> tg, wg;
+    gauss_legendre(K, tg, wg);
+    for (int s2 = 0; s2 < nseg; ++s2)
+      for (int j = 0; j < K; ++j) {
+        const double t = 0.5 * (tg[j] + 1.0);
+        z.push_back(point(seg[s2], t));
+        w.push_back(0.5 * wg[j] * deriv(seg[s2], t) / twopii);
+      }
+  }
+  for (int k = 0; k < count; ++k) {
+    if (nodes) { nodes[k].re = z[k].real(); nodes[k].im = z[k].imag(); }
+    if (weights) { weights[k].re = w[k].real(); weights[k].im = w[k].imag(); }
+  }
+  return FEAST_OK;
+}
+
+feast_status feast_eta_indicator(const feast_contour* c, const double* r, int nr, int ntheta, double* eta) {
+  if (!c || !r || !eta || nr < 1 || ntheta < 1 || c->R <= 0.0 || c->aspect <= 0.0) return FEAST_ERR_ARG;
+  std::vector<zc> z, w;
+  if (!build_quadrature(*c, z, w)) return FEAST_ERR_ARG;
+  const zc cc(c->center.re, c->center.im);
+  for (int i = 0; i < nr; ++i) {
+    double lo = INFINITY, hi = 0.0;
+    for (int j = 0; j < ntheta; ++j) {
+      const double th = 2.0 * M_PI * j / ntheta;
+      const zc mu = cc + r[i] * c->R * zc(std::cos(th), c->aspect * std::sin(th));
+      zc rho = 0.0;
+      for (size_t k = 0; k < z.size(); ++k) rho += w[k] / (z[k] - mu);
+      const double a = std::abs(rho);
+      lo = std::min(lo, a);
+      hi = std::max(hi, a);
+    }
+    eta[i] = r[i] < 1.0 ? lo : hi;
+  }
+  return FEAST_OK;
+}
+
+feast_status feast_contour_nodes(const feast_contour* c, int* q, feast_z* nodes, feast_z* weights) {
+  if (!c || !q) return FEAST_ERR_ARG;
+  std::vector<zc> z, w;
+  if (!build_quadrature(*c, z, w) || z.size() > 256) return FEAST_ERR_ARG;
+  *q = (int)z.size();
+  for (size_t k = 0; k < z.size(); ++k) {
+    if (nodes) { nodes[k].re = z[k].real(); nodes[k].im = z[k].imag(); }
+    if (weights) { weights[k].re = w[k].real(); weights[k].im = w[k].imag(); }
+  }
+  return FEAST_OK;
+}
 
 void feast_default_options(feast_options* o) {
   if (!o) return;
@@ -757,7 +887,8 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   if (!out) return FEAST_ERR_ARG;
   *out = nullptr;
   if (n < 1 || !A || !c || lda < n || (B && ldb < n) || m0 < 1 || m0 > n || m0 > 160) return FEAST_ERR_ARG;
-  if (c->R <= 0.0 || c->aspect <= 0.0) return FEAST_ERR_ARG;
+  const bool no_ellipse = c->rule == FEAST_RULE_CUSTOM && c->R == 0.0;
+  if (!no_ellipse && (c->R <= 0.0 || c->aspect <= 0.0)) return FEAST_ERR_ARG;
   feast_handle* h = new (std::nothrow) feast_handle();
   if (!h) return FEAST_ERR_ALLOC;
   if (o) h->opt = *o; else feast_default_options(&h->opt);
@@ -772,9 +903,36 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   h->st = reinterpret_cast<cudaStream_t>(stream);
   h->hasB = B != nullptr;
   h->center = zc(c->center.re, c->center.im);
-  h->R = c->R;
-  h->aspect = c->aspect;
-  if (!build_quadrature(*c, h->z, h->w) || h->z.size() > 256) { delete h; return FEAST_ERR_ARG; }
+  h->R = no_ellipse ? 1.0 : c->R;
+  h->aspect = no_ellipse ? 1.0 : c->aspect;
+  h->filter_domain = no_ellipse;
+  if (!build_quadrature(*c, h->z_all, h->w_all) || h->z_all.size() > 256) { delete h; return FEAST_ERR_ARG; }
+  {
+    // this handle's range of the linear systems (the shift-partitioned filter)
+    const int qa = (int)h->z_all.size();
+    int b0 = h->opt.shift_begin, b1 = h->opt.shift_end;
+    if (b0 == 0 && b1 == 0) b1 = qa;
+    if (b0 < 0 || b1 > qa || b0 >= b1) { delete h; return FEAST_ERR_ARG; }
+    // the range must be an aligned run of L = 1, 2, 4 or 8 of the eight leaves
+    // gb[g] = floor(g qa / 8) of the fixed summation tree
+    int gb[9];
+    for (int g = 0; g <= 8; ++g) gb[g] = (int)(((long long)g * qa) / 8);
+    bool found = false;
+    for (int L = 8; L >= 1 && !found; L /= 2)
+      for (int j = 0; j < 8 / L && !found; ++j)
+        if (gb[j * L] == b0 && gb[(j + 1) * L] == b1) {
+          h->tree.nleaf = L;
+          for (int i = 0; i <= L; ++i) h->tree.b[i] = gb[j * L + i] - b0;
+          found = true;
+        }
+    if (!found) { delete h; return FEAST_ERR_ARG; }
+    h->shift0 = b0;
+    h->partial = (b1 - b0) < qa;
+    h->z.assign(h->z_all.begin() + b0, h->z_all.begin() + b1);
+    h->w.assign(h->w_all.begin() + b0, h->w_all.begin() + b1);
+  }
+  if (h->opt.refine_tol <= 0) h->opt.refine_tol = 1e-12;
+  if (h->opt.max_refine < 0 || h->opt.max_refine > 16) { delete h; return FEAST_ERR_ARG; }
   h->q = (int)h->z.size();
   const bool mx = h->opt.precision == FEAST_PREC_MIXED;
   h->nb = h->opt.panel > 0 ? std::min(h->opt.panel, mx ? 128 : 64) : 64;
@@ -897,6 +1055,7 @@ feast_status feast_get_quadrature(const feast_handle* h, int* q, feast_z* nodes,
 feast_status feast_get_stats(const feast_handle* h, feast_stats* st) {
   if (!h || !st) return FEAST_ERR_ARG;
   std::memset(st, 0, sizeof(*st));
+  fill_shift_stats(h, st);
   st->normA = norm_of(const_cast<feast_handle*>(h));
   st->t_factor_ms = h->t_factor;
   st->t_update_ms = h->t_update;
@@ -960,7 +1119,7 @@ feast_status solve_shift_impl(feast_handle* h, int k, int side, int nrhs, double
   // widen into `out` through the accumulation kernel with unit coefficients
   std::vector<double2> ones((size_t)nrhs, make_double2(1.0, 0.0));
   CK(cudaMemcpyAsync(h->coef, ones.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, h->st));
-  CK(accumulate<T>(res, 1, (int)h->n, nrhs, h->coef, nullptr, nullptr, nullptr, out, h->st));
+  CK(accumulate<T>(res, acc_tree_single(1), (int)h->n, nrhs, h->coef, nullptr, nullptr, nullptr, out, h->st));
   CK(cudaStreamSynchronize(h->st));
   return FEAST_OK;
 }
@@ -1067,6 +1226,57 @@ feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat
   return read_flags(h);
 }
 
+feast_status feast_candidates(const feast_handle* h, int* count, int* idx, double* max_res) {
+  if (!h || !count) return FEAST_ERR_ARG;
+  if (!h->have_rr) return FEAST_ERR_STATE;
+  const std::vector<int> c = candidates(h);
+  *count = (int)c.size();
+  double mr = c.empty() ? INFINITY : 0.0;
+  const double nA = norm_of(const_cast<feast_handle*>(h));
+  for (size_t j = 0; j < c.size(); ++j) {
+    if (idx) idx[j] = c[j];
+    mr = std::max(mr, h->h_res[c[j]] / nA);
+  }
+  if (max_res) *max_res = mr;
+  return FEAST_OK;
+}
+
+feast_status feast_filter_combine(feast_handle* h, int nparts, const feast_z* const* parts,
+                                  const feast_z* const* parts_hat, const feast_z* Y, const feast_z* Yhat,
+                                  const feast_z* theta, feast_z* Q, feast_z* Qhat) {
+  if (!h || !parts || !Q || nparts < 1 || nparts > 8 || (nparts & (nparts - 1))) return FEAST_ERR_ARG;
+  if ((parts_hat && !Qhat) || (Qhat && !parts_hat)) return FEAST_ERR_ARG;
+  const bool resform = theta && mixed(h);
+  if (resform && (!Y || (parts_hat && !Yhat))) return FEAST_ERR_ARG;
+  const int n = (int)h->n, m = h->m0;
+  const size_t cnt = (size_t)n * m;
+  if (!h->combine_buf) CK(dalloc(h, &h->combine_buf, 8 * cnt * sizeof(double2)));
+  feast_status s;
+  if (resform) {
+    std::vector<double2> t(m);
+    CK(cudaMemcpyAsync(t.data(), theta, m * sizeof(double2), cudaMemcpyDefault, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    std::vector<zc> th(m);
+    for (int i = 0; i < m; ++i) th[i] = zz(t[i]);
+    if ((s = upload_coefs(h, th.data(), nullptr)) != FEAST_OK) return s;
+  }
+  for (int side = 0; side < (parts_hat ? 2 : 1); ++side) {
+    const feast_z* const* P = side ? parts_hat : parts;
+    for (int j = 0; j < nparts; ++j) {
+      if (!P[j]) return FEAST_ERR_ARG;
+      if ((s = copy_in(h, h->combine_buf + j * cnt, P[j], cnt)) != FEAST_OK) return s;
+    }
+    double2* Yd = side ? h->Yh : h->Y;
+    if (resform && (s = copy_in(h, Yd, side ? Yhat : Y, cnt)) != FEAST_OK) return s;
+    double2* out = side ? h->Qh : h->Q;
+    CK(accumulate_tree_combine(h->combine_buf, nparts, n, m, resform ? (side ? h->c0h : h->c0) : nullptr,
+                               resform ? Yd : nullptr, out, h->st));
+    if ((s = copy_out(h, side ? Qhat : Q, out, cnt)) != FEAST_OK) return s;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return FEAST_OK;
+}
+
 feast_status feast_rayleigh_ritz(feast_handle* h, const feast_z* Q, const feast_z* Qhat, feast_z* lambda, feast_z* X,
                                  feast_z* Xl, double* res, int* m_inside) {
   if (!h || !Q || !lambda) return FEAST_ERR_ARG;
@@ -1094,6 +1304,7 @@ feast_status feast_rayleigh_ritz(feast_handle* h, const feast_z* Q, const feast_
 feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vrand, feast_z* lambda, feast_z* Xout,
                          feast_z* Xlout, double* res, int* m_found, feast_stats* stats) {
   if (!h || !Y0 || !lambda) return FEAST_ERR_ARG;
+  if (h->partial) return FEAST_ERR_STATE;  // a shift range filters only part of the sum
   const bool bi = h->opt.algo == FEAST_ALGO_BI;
   const int n = (int)h->n, m = h->m0;
   const size_t cnt = (size_t)n * m;
@@ -1212,7 +1423,15 @@ feast_status feast_solve(feast_handle* h, const feast_z* Y0, const feast_z* Vran
     cudaEventRecord(h->ev[3], h->st);
     st.t_total_ms = ev_ms(h, 2, 3);
   }
+  fill_shift_stats(h, &st);
   if (stats) *stats = st;
+  // every Ritz value of the subspace inside C: m0 does not exceed the count
+  int inside_all = 0;
+  for (int i = 0; i < m; ++i) {
+    const zc l = h->h_lam[i];
+    if (std::isfinite(l.real()) && std::isfinite(l.imag()) && inside_ellipse(h, l)) ++inside_all;
+  }
+  if (inside_all == m) return FEAST_ERR_M0_TOO_SMALL;
   return converged ? FEAST_OK : FEAST_ERR_NOCONV;
 }
 

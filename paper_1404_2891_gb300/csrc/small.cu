@@ -54,7 +54,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok) {
+__device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok,
+                                  unsigned long long limit_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = bar + 32;
@@ -69,7 +70,7 @@ __device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* fla
     } else {
       const unsigned long long t0 = global_ns();
       while (*vgen == gen) {
-        if (global_ns() - t0 > 1000000000ull) {
+        if (global_ns() - t0 > limit_ns) {
           atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
           ok = 0;
           break;
@@ -92,6 +93,7 @@ struct OrthArgs {
   int n, m, rows_per;
   double2* part;  // 2 x grid x m
   unsigned* bar;  // 2 unsigned
+  unsigned long long wait_ns = 1000000000ull;  // limit of each grid-barrier wait (spin form)
   unsigned* flags;
 };
 
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
       part[(size_t)g * S + i] = acc;
     }
     ++phase;
-    if (!grid_barrier_spin(a.bar, G, a.flags, &s_ok)) return false;
+    if (!grid_barrier_spin(a.bar, G, a.flags, &s_ok, a.wait_ns)) return false;
     // every CTA sums the G partials of every slot: thread (slot i, group k)
     // takes the CTAs g = k mod K, the K groups meet in shared memory
     const int K = ns <= ORTH_THREADS ? ORTH_THREADS / ns : 1;
@@ -679,6 +681,7 @@ cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, 
   a.bar = reinterpret_cast<unsigned*>(scratch);
   a.part = reinterpret_cast<double2*>(reinterpret_cast<char*>(scratch) + 256);
   a.flags = flags;
+  a.wait_ns = feast_wait_limit_ns(1000000000ull);
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 256, s);
   if (e != cudaSuccess) return e;
   // shared-memory form: one CTA per SM, each holding its rows of Q

@@ -101,3 +101,83 @@ def test_eta_indicator_closed_form():
         assert np.isclose(ct.eta_indicator(r, 0.0, 1.0, 1.0, z, s), 1 / (1 + r ** N), rtol=1e-12)
     for r in (1.01, 1.5, 3.0):
         assert np.isclose(ct.eta_indicator(r, 0.0, 1.0, 1.0, z, s), 1 / (r ** N - 1), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- piecewise contours (Sec. 5.4)
+TRIANGLE = [-1.0 - 0.5j, 1.0 - 0.5j, 0.2 + 1.0j]
+SQUARE = [-0.5 - 0.5j, 0.5 - 0.5j, 0.5 + 0.5j, -0.5 + 0.5j]
+
+
+def polygon_area(v):
+    """Shoelace formula."""
+    v = np.asarray(v)
+    x, y = v.real, v.imag
+    return 0.5 * abs(np.dot(x, np.roll(y, -1)) - np.dot(np.roll(x, -1), y))
+
+
+@pytest.mark.parametrize("verts", [TRIANGLE, SQUARE])
+@pytest.mark.parametrize("rule,K", [("trap", 8), ("gauss", 5)])
+def test_polygon_rule_is_exact_on_linear_integrands(verts, rule, K):
+    """On a straight segment z' is constant, so both rules integrate z and
+    conj(z) z' exactly: sum sigma = 0, sum sigma z = 0 (Cauchy), and
+    sum sigma conj(z) = (1 / 2 pi i) * (2 i Area) = Area / pi (Green)."""
+    z, s = ct.piecewise_quadrature(ct.polygon(verts), K, rule)
+    q = len(verts) * (K - 1 if rule == "trap" else K)
+    assert len(z) == q
+    assert abs(s.sum()) < 1e-15
+    assert abs((s * z).sum()) < 1e-15
+    assert abs((s * np.conj(z)).sum() - polygon_area(verts) / np.pi) < 1e-15
+
+
+def test_trap_nodes_hit_every_vertex_once():
+    z, _ = ct.piecewise_quadrature(ct.polygon(TRIANGLE), 8, "trap")
+    for v in TRIANGLE:
+        assert np.sum(np.abs(z - v) < 1e-15) == 1
+
+
+@pytest.mark.parametrize("shape", ["triangle", "semicircle"])
+def test_glued_filter_approaches_the_indicator(shape):
+    """rho(mu) -> 1 inside and 0 outside as the rule refines (Sec. 5.4):
+    the error at fixed points far from the boundary shrinks with K."""
+    if shape == "triangle":
+        segs, inner, outer = ct.polygon(TRIANGLE), 0.07 + 0.0j, 2.5 + 2.0j
+    else:
+        segs, inner, outer = ct.semicircle(0.0, 1.0), 0.45j, -0.6j
+    errs = []
+    for K in (8, 16, 32):
+        z, s = ct.piecewise_quadrature(segs, K, "gauss")
+        errs.append(abs(ct.rho(inner, z, s) - 1) + abs(ct.rho(outer, z, s)))
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 1e-6
+
+
+def test_semicircle_arc_matches_the_circle_rule():
+    """The arc part of the semicircle with the trapezoid is the paper's circle
+    trapezoid restricted to the upper half: the sum of its sigma over a full
+    circle (arc 0..pi plus arc pi..2pi) equals sum sigma = 0 and
+    sum sigma z = 0 (Cauchy), and the half-disk area comes out of Green's sum."""
+    segs = [("arc", 0.3, 0.8, 0.0, np.pi), ("arc", 0.3, 0.8, np.pi, 2 * np.pi)]
+    z, s = ct.piecewise_quadrature(segs, 33, "trap")
+    assert abs(s.sum()) < 1e-14
+    assert abs((s * (z - 0.3)).sum()) < 1e-14
+    # Green: area of the disk (the trapezoid is spectrally accurate on a full circle)
+    assert abs((s * np.conj(z)).sum() - 0.8 ** 2) < 1e-14
+    zh, sh = ct.piecewise_quadrature(ct.semicircle(0.3, 0.8), 64, "gauss")
+    assert abs((sh * np.conj(zh)).sum() - 0.5 * 0.8 ** 2) < 1e-12
+
+
+def test_inside_polygon():
+    assert ct.inside_polygon([0.07 + 0j], TRIANGLE)[0]
+    assert not ct.inside_polygon([0.9 + 0.9j], TRIANGLE)[0]
+    assert not ct.inside_polygon([-1.0 - 0.5j], TRIANGLE)[0]  # a vertex is not strictly inside
+
+
+def test_piecewise_planted_mistakes(monkeypatch):
+    """A dropped vertex weight or a clockwise segment fails the Green pin."""
+    z, s = ct.piecewise_quadrature(ct.polygon(TRIANGLE), 8, "trap")
+    area = polygon_area(TRIANGLE) / np.pi
+    s_bad = s.copy()
+    s_bad[0] *= 0.5  # half of a merged vertex weight lost
+    assert abs((s_bad * np.conj(z)).sum() - area) > 1e-3
+    zr, sr = ct.piecewise_quadrature(ct.polygon(TRIANGLE[::-1]), 8, "trap")
+    assert abs((sr * np.conj(zr)).sum() - area) > 1e-3

@@ -71,6 +71,45 @@ def prescribed(n=256, m_in=40, r_in=0.95, ann=(1.5, 4.0), cond=100.0, seed=1, m0
                 N_e=8, m0=m0, seed=seed)
 
 
+def prescribed_in_shape(n, verts_or_semicircle, m_in, seed, m0, shrink=0.6, far=(2.5, 5.0), cond=10.0):
+    """A = V diag(lam) V^{-1}, B = I, for the general domains of Sec. 5.4: m_in
+    eigenvalues uniform in the domain shrunk by `shrink` about its centre
+    (convex polygon given by its counter-clockwise vertices, or
+    ("semicircle", c, r)), the rest uniform in an annulus of radii `far`
+    around that centre."""
+    rng = np.random.default_rng(seed)
+    if verts_or_semicircle[0] == "semicircle":
+        _, c, r = verts_or_semicircle
+        cen = complex(c) + 0.42j * r
+        pts = []
+        while len(pts) < m_in:
+            z = complex(c) + r * complex(rng.uniform(-1, 1), rng.uniform(0, 1))
+            if abs(z - c) < r:
+                pts.append(cen + shrink * (z - cen))
+    else:
+        v = np.asarray(verts_or_semicircle, dtype=np.complex128)
+        cen = v.mean()
+        pts = []
+        while len(pts) < m_in:
+            # uniform in the polygon: a random triangle of the fan, weighted by area
+            i = rng.integers(1, len(v) - 1)
+            a, b = rng.uniform(size=2)
+            if a + b > 1:
+                a, b = 1 - a, 1 - b
+            z = v[0] + a * (v[i] - v[0]) + b * (v[i + 1] - v[0])
+            pts.append(cen + shrink * (z - cen))
+    lam_in = np.array(pts)
+    lam_out = cen + uniform_disk(rng, n - m_in, far[0], far[1])
+    lam = np.concatenate([lam_in, lam_out])
+    Uq, Wq = haar_unitary(rng, n), haar_unitary(rng, n)
+    s = np.logspace(0.0, -np.log10(cond), n)
+    V = (Uq * s[None, :]) @ Wq.conj().T
+    Vinv = (Wq * (1.0 / s)[None, :]) @ Uq.conj().T
+    A = (V * lam[None, :]) @ Vinv
+    return dict(A=A, B=None, lam=lam, lam_inside=lam_in, V=V, Vinv=Vinv, U0=cgauss(rng, n, m0),
+                Vrand=cgauss(rng, n, m0), m0=m0, seed=seed, center=cen)
+
+
 def gaussian_pencil(n=4096, seed=2, m0=128, K=16, zero_block=None, b_eps=0.05):
     """A = G/sqrt(n) + D, B = I + b_eps G'/sqrt(n) (complex Gaussian G, G')."""
     rng = np.random.default_rng(seed)
