@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-pencil workload")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--batch-only", action="store_true", help="run only the batched workload (prints its object)")
+    p.add_argument("--lu-outer", type=int, default=0,
+                   help="outer block of the two-level LU (0 = library default, -1 = one-level)")
     return p.parse_args()
 
 
@@ -455,7 +457,8 @@ def run_ours(args):
         return e0.elapsed_time(e1) / count
 
     # ---- mixed path (headline)
-    opts = fg.make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True)
+    opts = fg.make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True,
+                           lu_outer=args.lu_outer)
     h = fg.feast_create(A_d, B_d, contour, m0, opts, stream=stream)
     # the residual gate: a full solve from the same start block
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -483,7 +486,7 @@ def run_ours(args):
                                    if len(lam) == len(ref) else None)}
     for _ in range(args.warmup):
         step(h)
-    upd_ms, upd_launches, lu_ms = [], [], []
+    stats = []
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = fg.feast_kernel_launches()
@@ -491,21 +494,16 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(args.steps):
         step(h)
-        st = fg.feast_get_stats(h)
-        upd_ms.append(st["t_update_ms"])
-        upd_launches.append(st["update_launches"])
-        lu_ms.append(st["t_factor_ms"])
+        stats.append(fg.feast_get_stats(h))
     e1.record(stream)
     barrier()
     launches = fg.feast_kernel_launches() - launches0
     clk = clocks.stop()
     iter_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     steady_ms = timed(steady, h, max(1, args.steps))
-    lu_mean = float(np.mean(lu_ms))
-    nb = 64
-    upd_flops = trailing_update_flops(n, q, nb)
-    upd_time = float(np.mean(upd_ms))
-    upd_n = int(np.mean(upd_launches))
+    mean = lambda key: float(np.mean([st[key] for st in stats]))
+    lu_mean = mean("t_factor_ms")
+    lu_outer = stats[-1]["lu_outer"]
     fg.feast_destroy(h)
 
     # ---- plain FP64 path
@@ -571,32 +569,51 @@ def run_ours(args):
     peak_note = "MEASURED_PEAKS.json hbm_gbs (of measured)"
     if hbm is None:
         hbm, peak_note = 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
-    # dominant kernel: the tcgen05 trailing update, HBM-bound (C streamed once per launch)
-    upd_n = max(upd_n, 1)
-    avg_launch_s = upd_time * 1e-3 / upd_n
-    bytes_per_launch = trailing_update_bytes(n, q, nb) / upd_n
-    achieved = bytes_per_launch / avg_launch_s / 1e9 if upd_time > 0 else 0.0
+    # The LU's updates, each kernel on both frames.  Algorithmic flops are 8 per
+    # complex MAC; the interleaved real form does 4 real products per complex
+    # one (no expansion) and the split-BF16 product takes 3 MMA terms, so the
+    # tensor pipe issues 3 BF16 flops per algorithmic flop and the algorithmic
+    # peak of these kernels is 1/3 of the measured BF16 peak.
+    bf16 = peaks.get("bf16_tflops")
+    bf16_note = "MEASURED_PEAKS.json bf16_tflops (of measured)"
+    if bf16 is None:
+        bf16, bf16_note = 1900.0, "profiling recipe fallback 1.9 PFLOP/s (of fallback)"
     ratio = profiled_traffic_ratio()
-    roofline = {"kernel": "k_tc_update_c: LU trailing update A22 -= L21 U12 (complex64 C streamed by TMA, "
-                          "split-BF16 tcgen05)",
-                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": (ratio * bytes_per_launch) if ratio else None,
-                "algorithmic_bytes_per_launch": bytes_per_launch, "launches": upd_n,
-                "avg_launch_ms": avg_launch_s * 1e3, "peak_note": peak_note}
-    # the same kernel and the whole LU on the tensor-pipe frame: algorithmic
-    # flops (8 per complex MAC) and the issued BF16 flops (the interleaved real
-    # form does 4 real products per complex one, 8 flops: no expansion; the
-    # split-BF16 product takes 3 MMA terms: x3)
-    bf16 = peaks.get("bf16_tflops") or 1900.0
-    upd_tf = upd_flops / (upd_time * 1e-3) / 1e12 if upd_time > 0 else 0.0
+
+    def frame(t_ms, launches, flops, nbytes):
+        if t_ms <= 0 or launches <= 0:
+            return None
+        tf = flops / (t_ms * 1e-3) / 1e12
+        return {"launches": launches, "avg_launch_ms": t_ms / launches, "algorithmic_tflops": tf,
+                "issued_tflops": 3.0 * tf, "frac_of_tensor_peak": 3.0 * tf / bf16,
+                "achieved_gbs": nbytes / (t_ms * 1e-3) / 1e9, "frac_of_hbm": nbytes / (t_ms * 1e-3) / 1e9 / hbm,
+                "flops_per_launch": flops / launches, "bytes_per_launch": nbytes / launches}
+
+    deep = frame(mean("t_deep_ms"), int(mean("deep_launches")), mean("deep_flops"), mean("deep_bytes"))
+    k64 = frame(mean("t_update_ms"), int(mean("update_launches")), mean("update_flops"), mean("update_bytes"))
     lu_tf = lu_flops(n, q) / (lu_mean * 1e-3) / 1e12
-    roofline["tensor"] = {"peak_tflops": bf16, "peak_note": "MEASURED_PEAKS.json bf16_tflops (of measured)"
-                          if peaks.get("bf16_tflops") else "profiling recipe fallback (of fallback)",
-                          "issued_per_algorithmic": 3.0,
-                          "update_kernel": {"algorithmic_tflops": upd_tf, "issued_tflops": 3.0 * upd_tf,
-                                            "frac_algorithmic": upd_tf / bf16, "frac_issued": 3.0 * upd_tf / bf16},
-                          "lu": {"algorithmic_tflops": lu_tf, "frac_algorithmic": lu_tf / bf16,
-                                 "frac_issued": 3.0 * lu_tf / bf16}}
+    if deep is not None:
+        # two-level LU: the deep update carries almost all of the flops and is tensor-bound
+        roofline = {"kernel": f"k_tc_deep: two-level LU update C -= L U with K = {lu_outer} (split-BF16 tcgen05, "
+                              "K streamed by TMA, persistent)",
+                    "bound": "tensor", "achieved": deep["algorithmic_tflops"], "peak": bf16 / 3.0,
+                    "unit": "TFLOP/s", "frac": deep["algorithmic_tflops"] / (bf16 / 3.0),
+                    "traffic": None, "launches": deep["launches"], "avg_launch_ms": deep["avg_launch_ms"],
+                    "algorithmic_flops_per_launch": deep["flops_per_launch"],
+                    "peak_note": f"{bf16_note} / 3: the split-BF16 product issues 3 BF16 MMA flops per algorithmic "
+                                 "flop", "hbm_frame": {"achieved": deep["achieved_gbs"], "peak": hbm,
+                                                       "frac": deep["frac_of_hbm"], "peak_note": peak_note}}
+    else:
+        roofline = {"kernel": "k_tc_update_c: LU trailing update A22 -= L21 U12 with K = 64 (complex64 C streamed "
+                              "by TMA, split-BF16 tcgen05)",
+                    "bound": "hbm", "achieved": k64["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": k64["frac_of_hbm"],
+                    "traffic": (ratio * k64["bytes_per_launch"]) if ratio else None,
+                    "algorithmic_bytes_per_launch": k64["bytes_per_launch"], "launches": k64["launches"],
+                    "avg_launch_ms": k64["avg_launch_ms"], "peak_note": peak_note}
+    roofline["lu"] = {"form": f"two-level, outer blocks of {lu_outer}" if lu_outer else "one-level, panels of 64",
+                      "algorithmic_tflops": lu_tf, "frac_of_tensor_peak_issued": 3.0 * lu_tf / bf16,
+                      "deep_update": deep, "k64_update": k64, "tensor_peak_tflops": bf16, "tensor_peak_note": bf16_note}
     if rank == 0:
         line = {
             "metric": METRIC, "value": iter_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,

@@ -131,6 +131,10 @@ typedef struct {
                         factored, since (conj(phi) B - A) = conj(phi B - A)   */
   const char* tune_cache; /* JSON file of tuned launch parameters written by
                         paper_1404_2891_gb300.autotune (NULL = built-in)       */
+  int lu_outer;      /* MIXED: outer block of the two-level LU in columns (a
+                        multiple of 64, at most 256); 0 = library default (256
+                        for n >= 1024), -1 = one-level LU (every trailing
+                        update with K = 64)                                    */
 } feast_options;
 
 typedef struct {
@@ -142,7 +146,8 @@ typedef struct {
   double t_filter_ms;
   double t_rr_ms;
   double t_total_ms;
-  double t_update_ms;    /* summed duration of the LU trailing-update launches     */
+  double t_update_ms;    /* summed duration of the LU trailing-update launches
+                            with K = 64 (panel width)                             */
   int update_launches;   /* number of those launches in the last factorisation     */
   int res_hist_len;
   double res_hist[64];   /* max candidate residual per iteration (inf if none)      */
@@ -153,6 +158,13 @@ typedef struct {
                             for a shift whose refinement stalled                   */
   int refine_sweeps;     /* classical refinement sweeps of the last filter          */
   int refactored;        /* shifts refactored in FP64 by the last filter            */
+  int lu_outer;          /* outer block of the last factorisation (0 = one-level)   */
+  double t_deep_ms;      /* summed duration of its deep (K = lu_outer) updates      */
+  int deep_launches;     /* number of those launches                              */
+  double deep_flops;     /* their algorithmic flops (8 per complex MAC), all shifts */
+  double deep_bytes;     /* their algorithmic HBM bytes (C read + written, L, U)    */
+  double update_flops;   /* algorithmic flops of the K = 64 update launches         */
+  double update_bytes;   /* and their algorithmic HBM bytes                         */
 } feast_stats;
 
 typedef struct feast_handle feast_handle;

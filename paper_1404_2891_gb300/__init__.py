@@ -54,7 +54,7 @@ class feast_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("cand_tol", ctypes.c_double), ("panel", ctypes.c_int),
                 ("timing", ctypes.c_int), ("symmetric", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("shift_begin", ctypes.c_int), ("shift_end", ctypes.c_int),
-                ("real_pencil", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("real_pencil", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("lu_outer", ctypes.c_int)]
 
 
 class feast_segment(ctypes.Structure):
@@ -70,7 +70,9 @@ class feast_stats(ctypes.Structure):
                 ("update_launches", ctypes.c_int), ("res_hist_len", ctypes.c_int),
                 ("res_hist", ctypes.c_double * 64), ("count_hist", ctypes.c_int * 64),
                 ("q", ctypes.c_int), ("shift_info", ctypes.c_int * 256), ("refine_sweeps", ctypes.c_int),
-                ("refactored", ctypes.c_int)]
+                ("refactored", ctypes.c_int), ("lu_outer", ctypes.c_int), ("t_deep_ms", ctypes.c_double),
+                ("deep_launches", ctypes.c_int), ("deep_flops", ctypes.c_double), ("deep_bytes", ctypes.c_double),
+                ("update_flops", ctypes.c_double), ("update_bytes", ctypes.c_double)]
 
 
 class FeastError(RuntimeError):
@@ -280,7 +282,8 @@ def make_contour(center=0.0, R=1.0, aspect=1.0, rule="trap_mid", N_e=8, nodes=No
 
 
 def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False,
-                 symmetric=False, max_refine=0, refine_tol=1e-12, shifts=None, real_pencil=False, tune_cache=None):
+                 symmetric=False, max_refine=0, refine_tol=1e-12, shifts=None, real_pencil=False, tune_cache=None,
+                 lu_outer=0):
     """shifts: (begin, end) range of the contour's nodes this handle owns (None = all)."""
     o = feast_options()
     load().feast_default_options(ctypes.byref(o))
@@ -293,6 +296,7 @@ def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=
         o.shift_begin, o.shift_end = int(shifts[0]), int(shifts[1])
     o.real_pencil = int(real_pencil)
     o.tune_cache = None if tune_cache is None else str(tune_cache).encode()
+    o.lu_outer = int(lu_outer)
     return o
 
 
@@ -339,7 +343,9 @@ def feast_get_stats(h):
     return dict(normA=st.normA, t_factor_ms=st.t_factor_ms, t_update_ms=st.t_update_ms,
                 update_launches=st.update_launches, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms,
                 q=st.q, shift_info=list(st.shift_info[:st.q]), refine_sweeps=st.refine_sweeps,
-                refactored=st.refactored)
+                refactored=st.refactored, lu_outer=st.lu_outer, t_deep_ms=st.t_deep_ms,
+                deep_launches=st.deep_launches, deep_flops=st.deep_flops, deep_bytes=st.deep_bytes,
+                update_flops=st.update_flops, update_bytes=st.update_bytes)
 
 
 def feast_set_wait_limit(seconds):

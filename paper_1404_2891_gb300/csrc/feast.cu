@@ -21,6 +21,7 @@
 #include "norm2.cuh"
 #include "small.cuh"
 #include "ozaki.cuh"
+#include "tc_deep.cuh"
 #include "tc_update.cuh"
 
 using zc = std::complex<double>;
@@ -191,6 +192,12 @@ struct feast_handle {
   void* orth_scratch2 = nullptr;       // the left block's orthonormalisation (side stream)
   void* pw_scratch = nullptr;
   TcStaging staging;
+  DeepStaging deep;                    // the two-level LU's deep-update operands
+  int lu_outer = 0;                    // its outer block (0: one-level LU)
+  std::vector<cudaEvent_t> deep_ev;
+  int n_deep = 0;
+  double t_deep = 0, deep_flops = 0, deep_bytes = 0;
+  double upd_flops = 0, upd_bytes = 0;
   TcStaging staging_left;              // the left solves' own staging (they run beside the right ones)
   cudaStream_t side = nullptr;         // stream of the left solves
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -352,6 +359,7 @@ struct UpdateTimer {
   feast_handle* h;
   int used;
   double ms;
+  double flops = 0.0, bytes = 0.0;  // algorithmic work of the timed launches
 };
 
 template <typename T>
@@ -362,10 +370,31 @@ cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bo
     cudaError_t e = t->inner(lu, k0, w, c0, 0, true, t->ctx, s);
     if (e != cudaSuccess) return e;
   }
+  if (2 * t->used + 1 >= (int)t->h->upd_ev.size()) return t->inner(lu, k0, w, c0, nc, false, t->ctx, s);
   cudaEventRecord(t->h->upd_ev[2 * t->used], s);
   cudaError_t e = t->inner(lu, k0, w, c0, nc, false, t->ctx, s);
   cudaEventRecord(t->h->upd_ev[2 * t->used + 1], s);
   ++t->used;
+  const double M = (double)(lu.n - k0 - w);
+  t->flops += 8.0 * lu.q * M * nc * w;
+  t->bytes += 8.0 * lu.q * (2.0 * M * nc + M * w + (double)w * nc);
+  return e;
+}
+
+// The deep update of the two-level LU: operands staged, then the timed kernel.
+cudaError_t deep_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStream_t s) {
+  feast_handle* h = reinterpret_cast<feast_handle*>(c);
+  cudaError_t e = tc_deep_stage(lu, K0, KB, h->deep, s);
+  if (e != cudaSuccess) return e;
+  const bool timing = h->opt.timing && 2 * h->n_deep + 1 < (int)h->deep_ev.size();
+  if (timing) cudaEventRecord(h->deep_ev[2 * h->n_deep], s);
+  e = tc_deep_run(lu, K0, KB, h->deep, s);
+  if (timing) {
+    cudaEventRecord(h->deep_ev[2 * h->n_deep + 1], s);
+    ++h->n_deep;
+  }
+  h->deep_flops += tc_deep_flops(lu.n, lu.q, K0, KB);
+  h->deep_bytes += tc_deep_bytes(lu.n, lu.q, K0, KB);
   return e;
 }
 
@@ -380,7 +409,7 @@ feast_status factor_impl(feast_handle* h) {
   // complex64 with staging: the tensor-core update (its operands always fit the
   // staging sized for n and q) solves U12 while staging it
   lu.u12_in_stage = std::is_same<T, float>::value && h->staging.Ast != nullptr;
-  UpdateTimer<T> timer{upd, ctx, h, 0, 0.0};
+  UpdateTimer<T> timer{upd, ctx, h, 0, 0.0, 0.0, 0.0};
   if (h->opt.timing) {
     const int panels = (int)((h->n + h->nb - 1) / h->nb);
     while ((int)h->upd_ev.size() < 4 * panels) {  // two update launches per step
@@ -388,15 +417,40 @@ feast_status factor_impl(feast_handle* h) {
       CK(cudaEventCreate(&e));
       h->upd_ev.push_back(e);
     }
-    CK(lu_factor_batched<T>(lu, h->nb, timed_update<T>, &timer, h->st));
+  }
+  h->n_deep = 0;
+  h->t_deep = h->deep_flops = h->deep_bytes = 0.0;
+  TrailingUpdateFn<T> use_upd = h->opt.timing ? timed_update<T> : upd;
+  void* use_ctx = h->opt.timing ? (void*)&timer : ctx;
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->lu_outer > 0) {
+      if (h->opt.timing) {
+        const int blocks = (int)((h->n + h->lu_outer - 1) / h->lu_outer);
+        while ((int)h->deep_ev.size() < 2 * blocks + 2) {
+          cudaEvent_t e;
+          CK(cudaEventCreate(&e));
+          h->deep_ev.push_back(e);
+        }
+      }
+      CK(lu_factor_two_level(lu, 64, h->lu_outer, use_upd, use_ctx, tc_far_fn(), deep_hook, h, h->st));
+    } else {
+      CK(lu_factor_batched<T>(lu, h->nb, use_upd, use_ctx, h->st));
+    }
   } else {
-    CK(lu_factor_batched<T>(lu, h->nb, upd, ctx, h->st));
+    CK(lu_factor_batched<T>(lu, h->nb, use_upd, use_ctx, h->st));
   }
   std::vector<int> info(h->q);
   CK(cudaMemcpyAsync(info.data(), h->info, sizeof(int) * h->q, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   h->t_update = 0.0;
   h->n_update = timer.used;
+  h->upd_flops = timer.flops;
+  h->upd_bytes = timer.bytes;
+  for (int i = 0; i < h->n_deep; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->deep_ev[2 * i], h->deep_ev[2 * i + 1]);
+    h->t_deep += ms;
+  }
   for (int i = 0; i < timer.used; ++i) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->upd_ev[2 * i], h->upd_ev[2 * i + 1]);
@@ -874,6 +928,7 @@ void feast_destroy(feast_handle* h) {
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->upd_ev) cudaEventDestroy(e);
+  for (auto& e : h->deep_ev) cudaEventDestroy(e);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
@@ -997,6 +1052,18 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     h->staging.rows_max = 2 * n;
     h->staging.cols_max = n;
     h->staging.q = h->q;
+    // two-level LU: outer blocks of lu_outer columns with deep (K = lu_outer) updates
+    int outer = h->opt.lu_outer;
+    if (outer == 0) outer = n >= 1024 ? 256 : -1;
+    if (outer > 0 && (outer % 64 || outer > 256 || n <= outer || n > 16384)) { feast_destroy(h); return FEAST_ERR_ARG; }
+    if (outer > 0 && h->nb == 64) {
+      AL(h->deep.Ast, deep_staging_bytes_A(n, h->q));
+      AL(h->deep.Bst, deep_staging_bytes_B(n, h->q));
+      h->deep.rows_max = 2 * n;
+      h->deep.cols_max = n;
+      h->deep.q = h->q;
+      h->lu_outer = outer;
+    }
     if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
       AL(h->staging_left.Ast, tc_staging_bytes_A(n, h->q));
       AL(h->staging_left.Bst, tc_staging_bytes_B(n, h->q));
@@ -1060,6 +1127,13 @@ feast_status feast_get_stats(const feast_handle* h, feast_stats* st) {
   st->t_factor_ms = h->t_factor;
   st->t_update_ms = h->t_update;
   st->update_launches = h->n_update;
+  st->lu_outer = h->lu_outer;
+  st->t_deep_ms = h->t_deep;
+  st->deep_launches = h->n_deep;
+  st->deep_flops = h->deep_flops;
+  st->deep_bytes = h->deep_bytes;
+  st->update_flops = h->upd_flops;
+  st->update_bytes = h->upd_bytes;
   st->t_filter_ms = h->t_filter;
   st->t_rr_ms = h->t_rr;
   return FEAST_OK;

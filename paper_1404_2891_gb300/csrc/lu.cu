@@ -245,6 +245,35 @@ k_laswp_mv_left(cplx<T>* S, long long ld, long long stride, int k0, const int32_
   }
 }
 
+// The moved rows of the panel at k0 (mv relative to k0) on the columns
+// col0 .. col0+ncols-1: each block gathers its 32 columns' moved entries, then
+// writes them to their new rows.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, int ncols, const int32_t* mv) {
+  __shared__ cplx<T> vals[128 * 32];
+  __shared__ int s_d[128], s_s[128], s_cnt;
+  const int b = blockIdx.y, tid = threadIdx.x;
+  cplx<T>* A = S + (size_t)b * stride;
+  const int32_t* m = mv + (size_t)b * LU_MV_STRIDE;
+  if (tid == 0) s_cnt = min(max(m[0], 0), 128);
+  for (int e = tid; e < 128; e += 256) {
+    s_d[e] = m[1 + e];
+    s_s[e] = m[129 + e];
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  for (int idx = tid; idx < cnt * 32; idx += 256) {
+    const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
+    if (o < ncols) vals[idx] = A[(size_t)(k0 + s_s[e]) + (size_t)(col0 + o) * ld];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < cnt * 32; idx += 256) {
+    const int e = idx >> 5, o = blockIdx.x * 32 + (idx & 31);
+    if (o < ncols) A[(size_t)(k0 + s_d[e]) + (size_t)(col0 + o) * ld] = vals[idx];
+  }
+}
+
 // Row permutation vector from the interchange sequence: perm = P applied to 0..n-1.
 __global__ void k_piv_to_perm(const int32_t* piv, int32_t* perm, int32_t* pinv, int n) {
   const int b = blockIdx.x;
@@ -622,3 +651,95 @@ template cudaError_t rows_gather<double>(const LuBatch<double>&, const double2*,
 template cudaError_t rows_gather<float>(const LuBatch<float>&, const double2*, float2*, int, bool, cudaStream_t);
 template cudaError_t rows_scatter<double>(const LuBatch<double>&, const double2*, double2*, int, cudaStream_t);
 template cudaError_t rows_scatter<float>(const LuBatch<float>&, const float2*, float2*, int, cudaStream_t);
+
+cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int ncols, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  if (!lu.mv || k0 % 64) return cudaErrorInvalidValue;
+  feast_count_launch();
+  k_laswp_mv_cols<float><<<dim3(ceil_div(ncols, 32), lu.q), 256, 0, s>>>(
+      lu.S, lu.ld, lu.stride, k0, col0, ncols, lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE);
+  return cudaGetLastError();
+}
+
+// Two-level blocked LU (complex64, tensor-core updates).  Inside each outer
+// block of KB columns the panels of nb = 64 columns run as in the one-level
+// schedule (the next block column updated first, the next panel on the
+// high-priority side stream beside the rest of the update), except that every
+// step touches only the block's own columns (lu.col_end).  At the end of the
+// block `far` applies its panels to the block's rows of the columns beyond it,
+// and `deep` subtracts the K = KB product from the rest of the matrix: that
+// update carries almost all of the factorisation's flops at four times the
+// arithmetic intensity of a K = 64 update.  The interchanges on the finished
+// L columns run on a low-priority stream and are joined before `deep` stages L.
+cudaError_t lu_factor_two_level(const LuBatch<float>& lu_in, int nb, int KB, TrailingUpdateFn<float> upd, void* ctx,
+                                FarFn far, DeepFn deep, void* dctx, cudaStream_t s) {
+  LuBatch<float> lu = lu_in;
+  if (nb != 64 || KB < nb || KB % nb || !upd || !far || !deep || !lu.mv || lu.n > PLL_GCAP ||
+      lu.mv_panels < (lu.n + 63) / 64)
+    return cudaErrorInvalidValue;
+  lu.u12_in_stage = true;
+  cudaMemsetAsync(lu.info, 0, sizeof(int) * lu.q, s);
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t side = nullptr, lstream = nullptr;
+  cudaEvent_t ev_next = nullptr, ev_panel = nullptr, ev_left = nullptr;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
+  auto cleanup = [&](cudaError_t r) {
+    if (ev_next) cudaEventDestroy(ev_next);
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_left) cudaEventDestroy(ev_left);
+    if (lstream) cudaStreamDestroy(lstream);
+    cudaStreamDestroy(side);
+    return r;
+  };
+  if ((e = cudaEventCreateWithFlags(&ev_next, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaEventCreateWithFlags(&ev_left, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaStreamCreateWithPriority(&lstream, cudaStreamNonBlocking, lo)) != cudaSuccess) return cleanup(e);
+  // the panel's moved rows on the finished L columns (0 .. k0-1), off the critical path
+  auto left = [&](int k0) -> cudaError_t {
+    if (k0 <= 0) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(ev_left, s);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(lstream, ev_left, 0);
+    if (r != cudaSuccess) return r;
+    feast_count_launch();
+    k_laswp_mv_left<float><<<dim3(ceil_div(k0, 32), lu.q), 256, 0, lstream>>>(
+        lu.S, lu.ld, lu.stride, k0, lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE);
+    return cudaGetLastError();
+  };
+  if ((e = launch_panel<float>(lu, 0, min(nb, lu.n), s)) != cudaSuccess) return cleanup(e);
+  for (int K0 = 0; K0 < lu.n; K0 += KB) {
+    const int cend = min(K0 + KB, lu.n);
+    lu.col_end = cend;
+    for (int k0 = K0; k0 < cend; k0 += nb) {
+      const int w = min(nb, lu.n - k0);
+      const int k1 = k0 + w;
+      if (k1 >= cend) break;  // the block's last panel: no columns of the block right of it
+      const int w1 = min(nb, cend - k1);
+      if ((e = upd(lu, k0, w, k1, w1, true, ctx, s)) != cudaSuccess) return cleanup(e);
+      if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) return cleanup(e);
+      if ((e = cudaStreamWaitEvent(side, ev_next, 0)) != cudaSuccess) return cleanup(e);
+      if ((e = launch_panel<float>(lu, k1, w1, side)) != cudaSuccess) return cleanup(e);
+      if ((e = cudaEventRecord(ev_panel, side)) != cudaSuccess) return cleanup(e);
+      if (cend > k1 + w1 && (e = upd(lu, k0, w, k1 + w1, cend - k1 - w1, false, ctx, s)) != cudaSuccess)
+        return cleanup(e);
+      if ((e = cudaStreamWaitEvent(s, ev_panel, 0)) != cudaSuccess) return cleanup(e);
+      if ((e = left(k1)) != cudaSuccess) return cleanup(e);
+    }
+    if (cend >= lu.n) break;
+    lu.col_end = 0;
+    if ((e = far(lu, K0, cend - K0, s)) != cudaSuccess) return cleanup(e);
+    // the L block is final once the interchanges of its later panels are on it
+    if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+    if ((e = deep(lu, K0, cend - K0, dctx, s)) != cudaSuccess) return cleanup(e);
+    if ((e = launch_panel<float>(lu, cend, min(nb, lu.n - cend), s)) != cudaSuccess) return cleanup(e);
+    if ((e = left(cend)) != cudaSuccess) return cleanup(e);
+  }
+  if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
+  if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+  feast_count_launch();
+  k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
+  return cleanup(cudaGetLastError());
+}

@@ -24,6 +24,9 @@ struct LuBatch {
   // the trailing update's staging kernel solves U12 = L11^{-1} A12 (in place)
   // when it stages U12, so the interchange kernel leaves that solve out
   bool u12_in_stage = false;
+  // two-level LU: the inner steps see only the columns before col_end (the
+  // current outer block); 0 = all n columns
+  int col_end = 0;
 };
 constexpr int LU_MV_STRIDE = 257;
 
@@ -47,6 +50,21 @@ cudaError_t default_trailing_update(const LuBatch<T>& lu, int k0, int w, int c0,
 template <typename T>
 cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> upd, void* ctx,
                               cudaStream_t s);
+
+// Two-level form (complex64 with the tensor-core updates): outer blocks of KB
+// columns (a multiple of nb).  Inside an outer block the panels and their
+// trailing updates touch only the block's own columns (lu.col_end); at the end
+// of the block, far(lu, K0, KB) applies the block's panels to the rows K0 ..
+// K0+KB of the columns beyond it (interchanges, U12 solve, updates inside the
+// block's rows), and deep(lu, K0, KB) subtracts the K = KB product of the
+// block's L and U from everything below and to the right of it.
+using FarFn = cudaError_t (*)(const LuBatch<float>& lu, int K0, int KB, cudaStream_t s);
+// The moved rows of the panel at k0 (its list in lu.mv) applied to the columns
+// col0 .. col0+ncols-1 of every shifted matrix.
+cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int ncols, cudaStream_t s);
+using DeepFn = cudaError_t (*)(const LuBatch<float>& lu, int K0, int KB, void* ctx, cudaStream_t s);
+cudaError_t lu_factor_two_level(const LuBatch<float>& lu, int nb, int KB, TrailingUpdateFn<float> upd, void* ctx,
+                                FarFn far, DeepFn deep, void* dctx, cudaStream_t s);
 
 // X (q x n x m, leading dimension n, batch stride n*m) overwritten with
 //   side 0:  S_b^{-1} X_b          side 1:  S_b^{-H} X_b
