@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-pencil workload")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--batch-only", action="store_true", help="run only the batched workload (prints its object)")
+    p.add_argument("--panel-cluster", type=int, default=0, help="0 = cluster panels (default), -1 = one CTA")
     p.add_argument("--lu-outer", type=int, default=0,
                    help="outer block of the two-level LU (0 = library default, -1 = one-level)")
     return p.parse_args()
@@ -458,7 +459,7 @@ def run_ours(args):
 
     # ---- mixed path (headline)
     opts = fg.make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True,
-                           lu_outer=args.lu_outer)
+                           lu_outer=args.lu_outer, panel_cluster=args.panel_cluster)
     h = fg.feast_create(A_d, B_d, contour, m0, opts, stream=stream)
     # the residual gate: a full solve from the same start block
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

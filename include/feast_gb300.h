@@ -135,6 +135,9 @@ typedef struct {
                         multiple of 64, at most 256); 0 = library default (256
                         for n >= 1024), -1 = one-level LU (every trailing
                         update with K = 64)                                    */
+  int panel_cluster; /* MIXED: 0 (default) = panels of 1024 to 8192 rows run
+                        on a thread-block cluster of four CTAs per system;
+                        -1 = one CTA per system                                */
 } feast_options;
 
 typedef struct {
@@ -234,8 +237,9 @@ feast_status feast_filter(feast_handle* h, const feast_z* Y, const feast_z* Yhat
  * rho(theta) Y term.  A handle created with options.shift_begin/shift_end
  * equal to an aligned run of 1, 2, 4 or 8 leaves ([b_{jL}, b_{(j+1)L}))
  * factors only those systems, and its feast_filter returns the subtree sum of
- * its leaves (no rho(theta) Y term); other ranges are FEAST_ERR_ARG, and
- * feast_solve on such a handle is FEAST_ERR_STATE.
+ * its leaves (no rho(theta) Y term), also when the range is every node (a
+ * partition of one process); other ranges are FEAST_ERR_ARG, and feast_solve
+ * on such a handle is FEAST_ERR_STATE.
  * feast_filter_combine adds nparts (1, 2, 4 or 8) such partial blocks, given
  * in the order of their ranges, along the top of the same tree and adds the
  * rho(theta) Y term for the Ritz values theta (MIXED; NULL = plain form), so

@@ -56,6 +56,26 @@ __global__ void k_accumulate(const cplx<T>* Xs, AccTree t, int n, int m, const d
   }
 }
 
+template <typename T>
+__global__ void k_accumulate_conj(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* coefc,
+                                  const double2* c0, const double2* Y, const int32_t* rowmap, double2* Q) {
+  const size_t total = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % n);
+    const int i = (int)(idx / n);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = 0; b < q; ++b) {
+      const int rr = rowmap ? rowmap[(size_t)b * n + r] : r;
+      const cplx<T>* Xb = Xs + (size_t)b * 2 * total;
+      cfma<double>(acc, coef[(size_t)b * m + i], cconv<double, T>(Xb[(size_t)i * n + rr]));
+      cfma<double>(acc, coefc[(size_t)b * m + i], cconj<double>(cconv<double, T>(Xb[total + (size_t)i * n + rr])));
+    }
+    if (c0 && Y) cfma<double>(acc, c0[i], Y[idx]);
+    Q[idx] = acc;
+  }
+}
+
 __global__ void k_tree_combine(const double2* P, int nparts, int n, int m, const double2* c0, const double2* Y,
                                double2* Q) {
   const size_t total = (size_t)n * m;
@@ -251,6 +271,21 @@ cudaError_t accumulate(const cplx<T>* Xs, const AccTree& t, int n, int m, const 
 }
 template cudaError_t accumulate<double>(const double2*, const AccTree&, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
 template cudaError_t accumulate<float>(const float2*, const AccTree&, int, int, const double2*, const double2*, const double2*, const int32_t*, double2*, cudaStream_t);
+
+template <typename T>
+cudaError_t accumulate_conj_pairs(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* coefc,
+                                  const double2* c0, const double2* Y, const int32_t* rowmap, double2* Q,
+                                  cudaStream_t s) {
+  feast_count_launch();
+  k_accumulate_conj<T><<<grid_for((size_t)n * m), 256, 0, s>>>(Xs, q, n, m, coef, coefc, c0, Y, rowmap, Q);
+  return cudaGetLastError();
+}
+template cudaError_t accumulate_conj_pairs<double>(const double2*, int, int, int, const double2*, const double2*,
+                                                   const double2*, const double2*, const int32_t*, double2*,
+                                                   cudaStream_t);
+template cudaError_t accumulate_conj_pairs<float>(const float2*, int, int, int, const double2*, const double2*,
+                                                  const double2*, const double2*, const int32_t*, double2*,
+                                                  cudaStream_t);
 
 AccTree acc_tree_single(int q) {
   AccTree t;

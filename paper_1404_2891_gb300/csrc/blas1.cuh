@@ -25,6 +25,14 @@ template <typename T>
 cudaError_t accumulate(const cplx<T>* Xs, const AccTree& t, int n, int m, const double2* coef, const double2* c0,
                        const double2* Y, const int32_t* rowmap, double2* Q, cudaStream_t s);
 
+// Real pencils (conjugate node pairs share one factor): X_b is n x 2m, its
+// second half solved for conj(R);  Q[r, i] = sum_b (coef[b*m + i] X_b[rr, i] +
+// coefc[b*m + i] conj(X_b[rr, m + i])) + c0[i] Y[r, i], b in order.
+template <typename T>
+cudaError_t accumulate_conj_pairs(const cplx<T>* Xs, int q, int n, int m, const double2* coef, const double2* coefc,
+                                  const double2* c0, const double2* Y, const int32_t* rowmap, double2* Q,
+                                  cudaStream_t s);
+
 // Q = the top levels of the tree over nparts (1, 2, 4 or 8) partial blocks P_j
 // (n x m each, consecutive in P), then + c0 .* Y (c0, Y may be null).
 cudaError_t accumulate_tree_combine(const double2* P, int nparts, int n, int m, const double2* c0, const double2* Y,

@@ -21,6 +21,7 @@
 #include "norm2.cuh"
 #include "small.cuh"
 #include "ozaki.cuh"
+#include "refine.cuh"
 #include "tc_deep.cuh"
 #include "tc_update.cuh"
 
@@ -161,6 +162,11 @@ struct feast_handle {
   AccTree tree;                // the summation tree of this handle's leaves
   double2* combine_buf = nullptr;  // feast_filter_combine's staging of the partial blocks
   std::vector<int> h_info;     // per shift: 0 or 1 + first zero-pivot column (last factorisation)
+  // real pencils: each factored system k stands for node gidx[k] and, when
+  // pidx[k] >= 0, for its conjugate node pidx[k] as well
+  bool realp = false;
+  std::vector<int> gidx, pidx;
+  double2 *coefc = nullptr, *coefch = nullptr;
   double normA = 0.0;
   double2* At = nullptr;
   // ||A||_2 is estimated on its own stream at creation, beside the first
@@ -214,6 +220,11 @@ struct feast_handle {
   std::vector<void*> allocs;
   // classical refinement (options.max_refine > 0): per-shift stall records
   std::vector<int> h_refine_fail;
+  double2 *X64r = nullptr, *X64l = nullptr, *r64 = nullptr, *T1 = nullptr, *T2 = nullptr, *ones = nullptr;
+  double2* S64 = nullptr;  // one shifted matrix in FP64 (refactorisation of a stalled shift)
+  int32_t *piv64 = nullptr, *perm64 = nullptr, *pinv64 = nullptr;
+  int* info64 = nullptr;
+  double *rnorm = nullptr, *Rn = nullptr;
   int refine_sweeps = 0, n_refactored = 0;
   // host mirrors of the last Rayleigh-Ritz step
   std::vector<zc> h_lam;
@@ -294,6 +305,7 @@ LuBatch<T> lu_view(feast_handle* h) {
   lu.mv = h->mv;
   lu.mv_panels = (int)((h->n + 63) / 64);
   if (std::is_same<T, float>::value && h->staging.Ast) lu.tc = &h->staging;
+  lu.panel_cluster = std::is_same<T, float>::value && h->opt.panel_cluster >= 0;
   return lu;
 }
 
@@ -476,6 +488,116 @@ feast_status ensure_factored(feast_handle* h) {
 }
 
 // ---------------------------------------------------------------- filter
+// Classical refinement of all q solves of one side (MIXED, max_refine > 0).
+// X64 starts from the complex64 solutions in Xs; each sweep forms every
+// shift's FP64 residual r_k = R - S_k X_k (right: S_k = phi_k B - A; left:
+// S_k^H = conj(phi_k) B^H - A^H; the n x n x m products on the emulated-FP64
+// tensor-core path) and, unless every shift already has max_j ||r_kj|| /
+// ||R_j|| <= refine_tol, solves S_k d_k = r_k with the complex64 factor and
+// adds d_k in FP64.  A shift still above the tolerance after max_refine sweeps
+// (its refinement stalled) is refactored in FP64 on the GPU and solved again;
+// if even that misses the tolerance the call returns FEAST_ERR_REFINE_NOCONV.
+feast_status refine_side(feast_handle* h, int side, const double2* R, float2* Xs, const int32_t* rowmap,
+                         double2* X64) {
+  const int n = (int)h->n, m = h->m0, q = h->q;
+  const size_t nm = (size_t)n * m;
+  LuBatch<float> lu = lu_view<float>(h);
+  if (side == 1) lu.tc = h->staging_left.Ast ? &h->staging_left : nullptr;
+  CK(refine_widen(Xs, q, n, m, rowmap, X64, false, h->st));
+  CK(column_norms(R, n, m, h->Rn, h->st));
+  std::vector<double> rn(m), nr((size_t)q * m), prev(q, INFINITY), rel(q, INFINITY);
+  CK(cudaMemcpyAsync(rn.data(), h->Rn, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  const double tau = h->opt.refine_tol;
+  auto residuals = [&](int k) -> cudaError_t {
+    double2* xk = X64 + (size_t)k * nm;
+    cudaError_t e = big_product(h, 0, side ? OP_C : OP_N, xk, h->T1);
+    const double2* T2 = xk;
+    if (e == cudaSuccess && h->hasB) {
+      e = big_product(h, 1, side ? OP_C : OP_N, xk, h->T2);
+      T2 = h->T2;
+    }
+    const zc zk = side ? std::conj(h->z[k]) : h->z[k];
+    if (e == cudaSuccess) e = refine_residual(R, h->T1, T2, d2(zk), n, m, h->r64 + (size_t)k * nm, h->rnorm + (size_t)k * m, h->st);
+    return e;
+  };
+  auto measure = [&]() -> feast_status {
+    for (int k = 0; k < q; ++k) CK(residuals(k));
+    CK(cudaMemcpyAsync(nr.data(), h->rnorm, nr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int k = 0; k < q; ++k) {
+      double r = 0.0;
+      for (int j = 0; j < m; ++j) r = std::max(r, rn[j] > 0 ? nr[(size_t)k * m + j] / rn[j] : nr[(size_t)k * m + j]);
+      rel[k] = std::isfinite(r) ? r : INFINITY;
+    }
+    return FEAST_OK;
+  };
+  feast_status st;
+  int sweeps = 0;
+  for (;;) {
+    if ((st = measure()) != FEAST_OK) return st;
+    bool all = true;
+    for (int k = 0; k < q; ++k) all = all && rel[k] <= tau;
+    if (all || sweeps == h->opt.max_refine) break;
+    // corrections for every shift from its FP64 residual, one batched solve
+    CK(refine_gather(h->r64, h->perm, Xs, q, n, m, side == 0, h->st));
+    CK(lu_solve_batched<float>(lu, side, Xs, m, h->nbs, h->st));
+    CK(refine_widen(Xs, q, n, m, rowmap, X64, true, h->st));
+    prev = rel;
+    ++sweeps;
+  }
+  h->refine_sweeps = std::max(h->refine_sweeps, sweeps);
+  // shifts whose refinement did not reach the tolerance: FP64 factor and solve
+  for (int k = 0; k < q; ++k) {
+    if (rel[k] <= tau) continue;
+    if (!h->S64) {
+      CK(dalloc(h, &h->S64, (size_t)n * n * sizeof(double2)));
+      CK(dalloc(h, &h->piv64, (size_t)n * sizeof(int32_t)));
+      CK(dalloc(h, &h->perm64, (size_t)n * sizeof(int32_t)));
+      CK(dalloc(h, &h->pinv64, (size_t)n * sizeof(int32_t)));
+      CK(dalloc(h, &h->info64, 64));
+    }
+    LuBatch<double> l1;
+    l1.S = h->S64; l1.ld = n; l1.stride = (long long)n * n; l1.n = n; l1.q = 1;
+    l1.piv = h->piv64; l1.perm = h->perm64; l1.pinv = h->pinv64; l1.info = h->info64; l1.flags = h->flags;
+    CK(form_shifted<double>(h->A, h->n, h->hasB ? h->B : nullptr, h->n, h->dz + k, 1, n, h->S64, l1.stride, h->st));
+    CK(lu_factor_batched<double>(l1, 64, nullptr, nullptr, h->st));
+    double2* X1 = h->r64 + (size_t)k * nm;  // this shift's residual slot as the solve's work block
+    CK(rows_gather<double>(l1, R, X1, m, side == 0, h->st));
+    CK(lu_solve_batched<double>(l1, side, X1, m, h->nbs, h->st));
+    CK(accumulate<double>(X1, acc_tree_single(1), n, m, h->ones, nullptr, nullptr, side ? h->pinv64 : nullptr,
+                          X64 + (size_t)k * nm, h->st));
+    ++h->n_refactored;
+    CK(residuals(k));
+    std::vector<double> nk(m);
+    CK(cudaMemcpyAsync(nk.data(), h->rnorm + (size_t)k * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    double r = 0.0;
+    for (int j = 0; j < m; ++j) r = std::max(r, rn[j] > 0 ? nk[j] / rn[j] : nk[j]);
+    if ((int)h->h_refine_fail.size() < q) h->h_refine_fail.assign(q, 0);
+    if (!(r <= tau)) h->h_refine_fail[k] = sweeps + 1;
+  }
+  for (int v : h->h_refine_fail)
+    if (v) return FEAST_ERR_REFINE_NOCONV;
+  return FEAST_OK;
+}
+
+feast_status refine_alloc(feast_handle* h) {
+  if (h->X64r) return FEAST_OK;
+  const size_t nm = (size_t)h->n * h->m0;
+  CK(dalloc(h, &h->X64r, (size_t)h->q * nm * sizeof(double2)));
+  if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) CK(dalloc(h, &h->X64l, (size_t)h->q * nm * sizeof(double2)));
+  CK(dalloc(h, &h->r64, (size_t)h->q * nm * sizeof(double2)));
+  CK(dalloc(h, &h->T1, nm * sizeof(double2)));
+  CK(dalloc(h, &h->T2, nm * sizeof(double2)));
+  CK(dalloc(h, &h->rnorm, (size_t)h->q * h->m0 * sizeof(double)));
+  CK(dalloc(h, &h->Rn, (size_t)h->m0 * sizeof(double)));
+  CK(dalloc(h, &h->ones, (size_t)h->m0 * sizeof(double2)));
+  std::vector<double2> one(h->m0, make_double2(1.0, 0.0));
+  CK(cudaMemcpyAsync(h->ones, one.data(), h->m0 * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return FEAST_OK;
+}
+
 // Right: Q = c0 .* Y + sum_k coef_k .* S_k^{-1} R;  left: Qh = c0h .* Yh + sum_k coefh_k .* S_k^{-H} Rh
 template <typename T>
 feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, bool use_c0, const double2* Rh,
@@ -485,11 +607,45 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   cplx<T>* Xs = reinterpret_cast<cplx<T>*>(h->Xs);
   const bool split = Rh && !h->opt.symmetric && h->side;
   if (split) CK(cudaEventRecord(h->fork_ev, h->st));  // the left solves start from here
-  CK(rows_gather<T>(lu, R, Xs, m, true, h->st));
-  CK(lu_solve_batched<T>(lu, 0, Xs, m, h->nbs, h->st));
   const bool add_c0 = use_c0 && !h->partial;  // a partial handle returns its subtree alone
-  CK(accumulate<T>(Xs, h->tree, n, m, h->coef, add_c0 ? h->c0 : nullptr, add_c0 ? Yc0 : nullptr, nullptr, Qout,
-                   h->st));
+  const int ms = h->realp ? 2 * m : m;          // real pencils: [R, conj(R)] per factor
+  CK(rows_gather<T>(lu, R, Xs, m, true, h->st, h->realp));
+  CK(lu_solve_batched<T>(lu, 0, Xs, ms, h->nbs, h->st));
+  const bool refine = std::is_same<T, float>::value && h->opt.max_refine > 0;
+  feast_status rstat = FEAST_OK;
+  if (refine) {
+    // classical refinement: FP64 solutions per shift, then the accumulation of those
+    h->h_refine_fail.assign(h->q, 0);
+    h->refine_sweeps = h->n_refactored = 0;
+    feast_status st2;
+    if ((st2 = refine_alloc(h)) != FEAST_OK) return st2;
+    rstat = refine_side(h, 0, R, reinterpret_cast<float2*>(Xs), nullptr, h->X64r);
+    if (rstat != FEAST_OK && rstat != FEAST_ERR_REFINE_NOCONV) return rstat;
+    CK(accumulate<double>(h->X64r, h->tree, n, m, h->coef, add_c0 ? h->c0 : nullptr, add_c0 ? Yc0 : nullptr, nullptr,
+                          Qout, h->st));
+    if (Rh && !h->opt.symmetric) {
+      cplx<T>* Xsh = reinterpret_cast<cplx<T>*>(h->Xsh);
+      LuBatch<T> lul = lu;
+      if (std::is_same<T, float>::value) lul.tc = h->staging_left.Ast ? &h->staging_left : nullptr;
+      CK(rows_gather<T>(lul, Rh, Xsh, m, false, h->st));
+      CK(lu_solve_batched<T>(lul, 1, Xsh, m, h->nbs, h->st));
+      feast_status r2 = refine_side(h, 1, Rh, reinterpret_cast<float2*>(Xsh), lu.pinv, h->X64l);
+      if (r2 != FEAST_OK && r2 != FEAST_ERR_REFINE_NOCONV) return r2;
+      if (r2 != FEAST_OK) rstat = r2;
+      CK(accumulate<double>(h->X64l, h->tree, n, m, h->coefh, add_c0 ? h->c0h : nullptr, add_c0 ? Yhc0 : nullptr,
+                            nullptr, Qhout, h->st));
+    } else if (Rh) {
+      CK(conj_copy(Qout, Qhout, (size_t)n * m, h->st));
+    }
+    return rstat;
+  }
+  if (h->realp) {
+    CK(accumulate_conj_pairs<T>(Xs, h->q, n, m, h->coef, h->coefc, add_c0 ? h->c0 : nullptr,
+                                add_c0 ? Yc0 : nullptr, nullptr, Qout, h->st));
+  } else {
+    CK(accumulate<T>(Xs, h->tree, n, m, h->coef, add_c0 ? h->c0 : nullptr, add_c0 ? Yc0 : nullptr, nullptr, Qout,
+                     h->st));
+  }
   if (Rh && h->opt.symmetric) {
     // complex symmetric pencil: (phi B - A)^{-H} conj(V) = conj((phi B - A)^{-1} V),
     // and the left inputs are the conjugates of the right ones
@@ -502,10 +658,15 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
     if (std::is_same<T, float>::value) lul.tc = h->staging_left.Ast ? &h->staging_left : nullptr;
     cudaStream_t ls = split ? h->side : h->st;
     if (split) CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    CK(rows_gather<T>(lul, Rh, Xsh, m, false, ls));
-    CK(lu_solve_batched<T>(lul, 1, Xsh, m, h->nbs, ls));
-    CK(accumulate<T>(Xsh, h->tree, n, m, h->coefh, add_c0 ? h->c0h : nullptr, add_c0 ? Yhc0 : nullptr, lu.pinv,
-                     Qhout, ls));
+    CK(rows_gather<T>(lul, Rh, Xsh, m, false, ls, h->realp));
+    CK(lu_solve_batched<T>(lul, 1, Xsh, ms, h->nbs, ls));
+    if (h->realp) {
+      CK(accumulate_conj_pairs<T>(Xsh, h->q, n, m, h->coefh, h->coefch, add_c0 ? h->c0h : nullptr,
+                                  add_c0 ? Yhc0 : nullptr, lu.pinv, Qhout, ls));
+    } else {
+      CK(accumulate<T>(Xsh, h->tree, n, m, h->coefh, add_c0 ? h->c0h : nullptr, add_c0 ? Yhc0 : nullptr, lu.pinv,
+                       Qhout, ls));
+    }
     if (split) {
       CK(cudaEventRecord(h->join_ev, h->side));
       CK(cudaStreamWaitEvent(h->st, h->join_ev, 0));
@@ -521,6 +682,7 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
 feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* use_out) {
   const int q = h->q, m = h->m0, qa = (int)h->z_all.size();
   std::vector<double2> coef((size_t)q * m), coefh((size_t)q * m), c0(m), c0h(m);
+  std::vector<double2> coefc_v(h->realp ? (size_t)q * m : 0), coefch_v(h->realp ? (size_t)q * m : 0);
   std::vector<int> use(m, 0);
   for (int i = 0; i < m; ++i) {
     bool u = false;
@@ -536,10 +698,16 @@ feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* us
     }
     use[i] = u;
     for (int k = 0; k < q; ++k) {
-      const int kg = h->shift0 + k;
+      const int kg = h->gidx[k];
       const zc g = u ? h->w_all[kg] / (h->z_all[kg] - theta[i]) : h->w_all[kg];
       coef[(size_t)k * m + i] = d2(g);
       coefh[(size_t)k * m + i] = d2(std::conj(g));
+      if (h->realp) {
+        const int kp = h->pidx[k];
+        const zc gp = kp < 0 ? zc(0.0) : (u ? h->w_all[kp] / (h->z_all[kp] - theta[i]) : h->w_all[kp]);
+        coefc_v[(size_t)k * m + i] = d2(gp);
+        coefch_v[(size_t)k * m + i] = d2(std::conj(gp));
+      }
     }
     zc acc = 0.0;  // c0 = rho(theta) over all the contour's nodes
     if (u)
@@ -548,6 +716,11 @@ feast_status upload_coefs(feast_handle* h, const zc* theta, std::vector<int>* us
     c0h[i] = d2(u ? std::conj(acc) : zc(0.0));
   }
   CK(cudaMemcpyAsync(h->coef, coef.data(), coef.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  if (h->realp) {
+    CK(cudaMemcpyAsync(h->coefc, coefc_v.data(), coefc_v.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->coefch, coefch_v.data(), coefch_v.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                       h->st));
+  }
   CK(cudaMemcpyAsync(h->coefh, coefh.data(), coefh.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(h->c0, c0.data(), c0.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(h->c0h, c0h.data(), c0h.size() * sizeof(double2), cudaMemcpyHostToDevice, h->st));
@@ -982,9 +1155,54 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
         }
     if (!found) { delete h; return FEAST_ERR_ARG; }
     h->shift0 = b0;
-    h->partial = (b1 - b0) < qa;
+    // a handle created with a range is a member of a shift partition (even when
+    // the range is every node: the partition of one process)
+    h->partial = h->opt.shift_begin != 0 || h->opt.shift_end != 0;
     h->z.assign(h->z_all.begin() + b0, h->z_all.begin() + b1);
     h->w.assign(h->w_all.begin() + b0, h->w_all.begin() + b1);
+    for (int k = b0; k < b1; ++k) {
+      h->gidx.push_back(k);
+      h->pidx.push_back(-1);
+    }
+  }
+  if (h->opt.real_pencil) {
+    // (conj(phi) B - A) = conj(phi B - A) for real A and B: factor one node of
+    // each conjugate pair (the one with Im phi > 0) and every real node
+    if (h->partial) { delete h; return FEAST_ERR_ARG; }
+    const int qa = (int)h->z_all.size();
+    std::vector<int> g, pp;
+    std::vector<char> used(qa, 0);
+    for (int k = 0; k < qa; ++k) {
+      const zc zk = h->z_all[k];
+      const double tol = 1e-12 * std::max(1.0, std::abs(zk));
+      if (std::abs(zk.imag()) <= tol) { g.push_back(k); pp.push_back(-1); used[k] = 1; continue; }
+      if (zk.imag() < 0) continue;
+      int p = -1;
+      for (int j = 0; j < qa; ++j)
+        if (!used[j] && j != k && std::abs(h->z_all[j] - std::conj(zk)) <= tol &&
+            std::abs(h->w_all[j] - std::conj(h->w_all[k])) <= 1e-12 * std::max(std::abs(h->w_all[k]), 1e-300)) {
+          p = j;
+          break;
+        }
+      if (p < 0) { delete h; return FEAST_ERR_ARG; }  // the contour is not symmetric about the real axis
+      used[k] = used[p] = 1;
+      g.push_back(k);
+      pp.push_back(p);
+    }
+    for (int k = 0; k < qa; ++k)
+      if (!used[k]) { delete h; return FEAST_ERR_ARG; }
+    h->gidx = g;
+    h->pidx = pp;
+    h->z.clear();
+    h->w.clear();
+    for (int k : g) {
+      h->z.push_back(h->z_all[k]);
+      h->w.push_back(h->w_all[k]);
+    }
+    h->realp = true;
+    h->tree = acc_tree_single((int)g.size());
+    if (h->opt.max_refine > 0) { delete h; return FEAST_ERR_ARG; }
+    if (2 * m0 > n) { delete h; return FEAST_ERR_ARG; }
   }
   if (h->opt.refine_tol <= 0) h->opt.refine_tol = 1e-12;
   if (h->opt.max_refine < 0 || h->opt.max_refine > 16) { delete h; return FEAST_ERR_ARG; }
@@ -1010,8 +1228,13 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   AL(h->mv, (size_t)((n + 63) / 64) * h->q * LU_MV_STRIDE * sizeof(int32_t));
   AL(h->info, h->q * sizeof(int));
   AL(h->flags, 64);
-  AL(h->Xs, nm * std::max(h->q, 2) * esz);
-  if (h->opt.algo == FEAST_ALGO_BI) AL(h->Xsh, nm * h->q * esz);
+  const size_t xq = h->realp ? 2 * (size_t)h->q : (size_t)h->q;  // real pencils solve [R, conj(R)]
+  AL(h->Xs, nm * std::max(xq, (size_t)2) * esz);
+  if (h->opt.algo == FEAST_ALGO_BI) AL(h->Xsh, nm * xq * esz);
+  if (h->realp) {
+    AL(h->coefc, (size_t)h->q * m0 * sizeof(double2));
+    AL(h->coefch, (size_t)h->q * m0 * sizeof(double2));
+  }
   double2** blocks[] = {&h->Y, &h->Yh, &h->Rr, &h->Rl, &h->Q, &h->Qh, &h->Qo, &h->Qho, &h->AQ, &h->BQ,
                         &h->AhQ, &h->BhQ, &h->X, &h->Xl, &h->AX, &h->BX, &h->AhX, &h->BhX, &h->E, &h->Eh, &h->tmp};
   for (double2** p : blocks) AL(*p, nm * sizeof(double2) + 2 * n * sizeof(double2));
@@ -1234,6 +1457,7 @@ extern "C" {
 
 feast_status feast_moments(feast_handle* h, const feast_z* V, int S, int kmax, feast_z* mu) {
   if (!h || !V || !mu || S < 1 || S > h->m0 || kmax < 0 || kmax > 31) return FEAST_ERR_ARG;
+  if (h->realp) return FEAST_ERR_STATE;  // the moments need every node's own solve
   feast_status s = ensure_factored(h);
   if (s != FEAST_OK) return s;
   const int n = (int)h->n;

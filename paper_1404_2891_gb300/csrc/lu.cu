@@ -371,17 +371,20 @@ k_trsm_diag(const cplx<T>* S, long long ld, long long stride, cplx<T>* Xg, long 
     for (int r = rg; r < w; r += 8) Xb[(size_t)(k0 + r) + (size_t)c * ldx] = X[r * 32 + cc];
 }
 
+// X_b (n x m_out) from R (n x m): m_out = m, or 2m with the second half conj(R)
 template <typename T>
 __global__ void k_rows_gather(const double2* R, const int32_t* perm, cplx<T>* X, int n, int m,
-                              bool permute) {
+                              bool permute, bool conj_dup) {
   const size_t b = blockIdx.y;
-  const size_t total = (size_t)n * m;
+  const size_t total = (size_t)n * m * (conj_dup ? 2 : 1);
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n);
     const size_t c = idx / n;
     const int src = permute ? perm[b * n + i] : i;
-    X[b * total + idx] = cconv<T, double>(R[(size_t)src + c * n]);
+    double2 v = R[(size_t)src + (c % m) * n];
+    if (c >= (size_t)m) v.y = -v.y;
+    X[b * total + idx] = cconv<T, double>(v);
   }
 }
 
@@ -444,6 +447,7 @@ cudaError_t launch_panel_ll(const LuBatch<float>& lu, int k0, int w, int gcap, c
 template <typename T>
 cudaError_t launch_panel(const LuBatch<T>& lu, int k0, int w, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
+    if (lu.panel_cluster && panel_cluster_applies(lu.n - k0, w) && lu.mv) return panel_cluster(lu, k0, w, s);
     if (w <= 64 && lu.n <= PLL_GCAP) {
       const int gcap = min(PLL_GCAP, 8 * lu.n);
       switch (panel_group_width(lu.n - k0, gcap)) {
@@ -628,10 +632,10 @@ cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, 
 
 template <typename T>
 cudaError_t rows_gather(const LuBatch<T>& lu, const double2* R, cplx<T>* X, int m, bool permute,
-                        cudaStream_t s) {
-  dim3 grid(ceil_div((size_t)lu.n * m, 256 * 4), lu.q);
+                        cudaStream_t s, bool conj_dup) {
+  dim3 grid(ceil_div((size_t)lu.n * m * (conj_dup ? 2 : 1), 256 * 4), lu.q);
   feast_count_launch();
-  k_rows_gather<T><<<grid, 256, 0, s>>>(R, lu.perm, X, lu.n, m, permute);
+  k_rows_gather<T><<<grid, 256, 0, s>>>(R, lu.perm, X, lu.n, m, permute, conj_dup);
   return cudaGetLastError();
 }
 
@@ -647,8 +651,9 @@ template cudaError_t lu_factor_batched<double>(const LuBatch<double>&, int, Trai
 template cudaError_t lu_factor_batched<float>(const LuBatch<float>&, int, TrailingUpdateFn<float>, void*, cudaStream_t);
 template cudaError_t lu_solve_batched<double>(const LuBatch<double>&, int, double2*, int, int, cudaStream_t);
 template cudaError_t lu_solve_batched<float>(const LuBatch<float>&, int, float2*, int, int, cudaStream_t);
-template cudaError_t rows_gather<double>(const LuBatch<double>&, const double2*, double2*, int, bool, cudaStream_t);
-template cudaError_t rows_gather<float>(const LuBatch<float>&, const double2*, float2*, int, bool, cudaStream_t);
+template cudaError_t rows_gather<double>(const LuBatch<double>&, const double2*, double2*, int, bool, cudaStream_t,
+                                         bool);
+template cudaError_t rows_gather<float>(const LuBatch<float>&, const double2*, float2*, int, bool, cudaStream_t, bool);
 template cudaError_t rows_scatter<double>(const LuBatch<double>&, const double2*, double2*, int, cudaStream_t);
 template cudaError_t rows_scatter<float>(const LuBatch<float>&, const float2*, float2*, int, cudaStream_t);
 

@@ -27,6 +27,8 @@ struct LuBatch {
   // two-level LU: the inner steps see only the columns before col_end (the
   // current outer block); 0 = all n columns
   int col_end = 0;
+  // complex64 panels of >= 1024 rows on a cluster of four CTAs per shift
+  bool panel_cluster = false;
 };
 constexpr int LU_MV_STRIDE = 257;
 
@@ -66,6 +68,12 @@ using DeepFn = cudaError_t (*)(const LuBatch<float>& lu, int K0, int KB, void* c
 cudaError_t lu_factor_two_level(const LuBatch<float>& lu, int nb, int KB, TrailingUpdateFn<float> upd, void* ctx,
                                 FarFn far, DeepFn deep, void* dctx, cudaStream_t s);
 
+// Complex64 panel of rows k0 .. n-1, columns k0 .. k0+w-1 of every shift on a
+// thread-block cluster of four CTAs per shift (panel_cluster.cu); for panels of
+// 1024 to 8192 rows.
+bool panel_cluster_applies(int rows, int w);
+cudaError_t panel_cluster(const LuBatch<float>& lu, int k0, int w, cudaStream_t s);
+
 // X (q x n x m, leading dimension n, batch stride n*m) overwritten with
 //   side 0:  S_b^{-1} X_b          side 1:  S_b^{-H} X_b
 // using the stored factors; `X` must already hold P R (side 0) or R (side 1),
@@ -74,10 +82,11 @@ template <typename T>
 cudaError_t lu_solve_batched(const LuBatch<T>& lu, int side, cplx<T>* X, int m, int nbs,
                              cudaStream_t s);
 
-// X_b[i, c] = R[perm_b[i], c]   (R: n x m double2, shared by all b; X in T)
+// X_b[i, c] = R[perm_b[i], c]   (R: n x m double2, shared by all b; X in T);
+// conj_dup: X_b is n x 2m and X_b[i, m + c] = conj(R[perm_b[i], c])
 template <typename T>
 cudaError_t rows_gather(const LuBatch<T>& lu, const double2* R, cplx<T>* X, int m, bool permute,
-                        cudaStream_t s);
+                        cudaStream_t s, bool conj_dup = false);
 // Out_b[perm_b[i], c] = V_b[i, c]  in place through a scratch copy
 template <typename T>
 cudaError_t rows_scatter(const LuBatch<T>& lu, const cplx<T>* V, cplx<T>* Out, int m,

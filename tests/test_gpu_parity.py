@@ -172,6 +172,67 @@ def test_two_level_factor_and_solves_ragged_n1100(lu_outer):
                 assert colerr(X, Xr).max() <= solve_column_bound(kappa, n, "mixed"), (k, side)
 
 
+@pytest.mark.parametrize("n,panel_cluster", [(2048, 0), (2100, 0), (2100, -1)])
+def test_cluster_panel_factor_backward_error(n, panel_cluster):
+    """Panels of 1024 rows and more factored by a cluster of four CTAs per shift
+    (pivot search through distributed shared memory), with a ragged order: the
+    backward error of each factor, and the pivots are a valid permutation."""
+    fg = lib()
+    cfg = workloads.gaussian_pencil(n=n, seed=15, m0=8, K=1, zero_block=n // 64)
+    A, B = cfg["A"], cfg["B"]
+    h = make(fg, cfg, "mixed", B=B, panel_cluster=panel_cluster)
+    fg.feast_factor(h)
+    z, _ = fg.feast_get_quadrature(h)
+    for k in range(h.q):
+        S = z[k] * B - A
+        LU, piv = fg.feast_get_factor(h, k)
+        assert ((piv >= np.arange(n)) & (piv < n)).all()
+        L, U = dense.unpack(LU)
+        PS = dense.apply_pivots(piv.astype(np.int64), S)
+        err = np.linalg.norm(PS - L @ U) / np.linalg.norm(S)
+        assert err <= 8 * n * U32, (k, err)
+        assert np.abs(np.tril(LU, -1)).max() <= np.sqrt(2) * (1 + 1e-5)  # |l| <= sqrt 2 for the |Re|+|Im| pivot
+
+
+def test_refined_mixed_filter_matches_fp64():
+    """Classical refinement (max_refine > 0): every shift's solve is refined to
+    ||R - S_k X_k|| <= refine_tol ||R|| with an FP64 residual, so the mixed filter
+    meets the FP64 filter to cond(S) x refine_tol."""
+    fg = lib()
+    cfg = small_pencil()
+    A, B = cfg["A"], cfg["B"]
+    h64 = make(fg, cfg, "fp64", B=B)
+    hr = make(fg, cfg, "mixed", B=B, max_refine=8, refine_tol=1e-14)
+    Y, Yh = cfg["U0"], cfg["Vrand"]
+    Q, Qh = fg.feast_filter(h64, Y, Yh)
+    Qr, Qhr = fg.feast_filter(hr, Y, Yh)
+    st = fg.feast_get_stats(hr)
+    assert 1 <= st["refine_sweeps"] <= 8 and st["refactored"] == 0
+    assert colerr(Qr, Q).max() < 1e-11, colerr(Qr, Q).max()
+    assert colerr(Qhr, Qh).max() < 1e-11, colerr(Qhr, Qh).max()
+    # without refinement the same handle type is only complex64-accurate
+    hm = make(fg, cfg, "mixed", B=B)
+    Qm, _ = fg.feast_filter(hm, Y, Yh)
+    assert colerr(Qm, Q).max() > 1e-8
+
+
+def test_refinement_that_cannot_converge_reports_and_refactors():
+    """A tolerance below FP64 rounding cannot be met: after max_refine sweeps
+    every shift is refactored in FP64 on the GPU, still misses it, and the call
+    returns FEAST_ERR_REFINE_NOCONV with the per-shift record in feast_stats;
+    the FP64 refactorisation itself makes the result FP64-accurate."""
+    fg = lib()
+    cfg = small_pencil()
+    A, B = cfg["A"], cfg["B"]
+    h = make(fg, cfg, "mixed", B=B, max_refine=1, refine_tol=1e-30)
+    with pytest.raises(fg.FeastError) as e:
+        fg.feast_filter(h, cfg["U0"], cfg["Vrand"])
+    assert e.value.status == fg.FEAST_ERR_REFINE_NOCONV
+    st = fg.feast_get_stats(h)
+    assert st["refactored"] == 2 * h.q  # every right and every left system
+    assert all(v >= 2 ** 30 for v in st["shift_info"])
+
+
 def test_residual_form_filter_is_exact_on_ritz_pairs():
     # With an exact eigenpair (theta, x), the refinement's initial iterate is already
     # the solution, so the mixed filter returns rho(theta) x to FP64 accuracy.
