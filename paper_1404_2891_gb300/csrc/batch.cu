@@ -225,6 +225,7 @@ struct feast_batch {
   std::vector<std::vector<zc>> z, w;
   std::vector<zc> center;
   std::vector<double> R, aspect, normA;
+  std::vector<int> fdom;  // per pencil: CUSTOM nodes without an ellipse (domain test by the filter value)
   size_t snn = 0, snm = 0, smm = 0, sm = 0, sqm = 0, slog = 0, sS = 0, sX = 0, sN = 0, snb = 0;
   // device
   GrpDesc* d_pd = nullptr;
@@ -491,6 +492,11 @@ void host_coefs(feast_batch* b, int p, const double2* theta) {
 }
 
 bool inside(const feast_batch* b, int p, zc l) {
+  if (b->fdom[p]) {
+    zc r = 0.0;
+    for (size_t k = 0; k < b->z[p].size(); ++k) r += b->w[p][k] / (b->z[p][k] - l);
+    return std::abs(r) >= 0.5;
+  }
   const double x = (l.real() - b->center[p].real()) / b->R[p];
   const double y = (l.imag() - b->center[p].imag()) / (b->R[p] * b->aspect[p]);
   return x * x + y * y < 1.0;
@@ -605,11 +611,14 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
     if (np_ < 1 || np_ > BATCH_MAX_N || m0[p] < 1 || m0[p] > np_ || m0[p] > 160 || !A[p] || ld < np_)
       return bad(FEAST_ERR_ARG);
     const feast_contour& c = contours[p];
-    if (c.R <= 0.0 || c.aspect <= 0.0) return bad(FEAST_ERR_ARG);
+    // CUSTOM nodes with R = 0: no ellipse, the domain test is |rho(lambda)| >= 1/2
+    const bool fdom = c.rule == FEAST_RULE_CUSTOM && c.R == 0.0;
+    if (!fdom && (c.R <= 0.0 || c.aspect <= 0.0)) return bad(FEAST_ERR_ARG);
     if (!feast_quadrature_host(c, b->z[p], b->w[p]) || b->z[p].size() > 256) return bad(FEAST_ERR_ARG);
     b->center.push_back(zc(c.center.re, c.center.im));
-    b->R.push_back(c.R);
-    b->aspect.push_back(c.aspect);
+    b->R.push_back(fdom ? 1.0 : c.R);
+    b->aspect.push_back(fdom ? 1.0 : c.aspect);
+    b->fdom.push_back(fdom ? 1 : 0);
     GrpDesc& d = b->pd[p];
     d.n = (int)np_;
     d.m = m0[p];

@@ -1,0 +1,32 @@
+"""Several target domains of one pencil (Sec. 6: multiple target domains, and
+the partition of a region into subregions of about equal eigenvalue counts):
+the library's count estimates place the cuts, and all strips are solved in one
+batched launch per iteration.  The union of the strips' eigenvalues must be the
+prescribed spectrum inside the region (the plain definition), each strip must
+hold exactly the eigenvalues inside it, and the partition must be balanced."""
+import numpy as np
+import pytest
+
+import workloads
+from helpers import lib
+from oracle import feast
+
+pytestmark = pytest.mark.gpu
+
+
+def test_region_split_into_balanced_strips_and_solved_in_one_batch():
+    lib()
+    from paper_1404_2891_gb300 import multi
+    cfg = workloads.clustered_strip(n=400, clusters=8, per_cluster=6, seed=3)
+    out = multi.solve_region(cfg["A"], cfg["region"], parts=4, K=8, seed=1)
+    assert out["stats"]["converged"] == 4, out["stats"]
+    lam_all = np.concatenate([s["lam"] for s in out["strips"]])
+    ref = cfg["lam_inside"]
+    assert len(lam_all) == len(ref) == 48
+    assert feast.match_eigenvalues(lam_all, ref, 1.0).max() < 1e-10
+    edges = out["edges"]
+    for s, a, b in zip(out["strips"], edges, edges[1:]):
+        inside = ref[(ref.real > a) & (ref.real < b)]
+        assert s["m_found"] == len(inside) == 12  # two clusters per strip: the cuts fall in the gaps
+        assert s["res"].max() <= 1e-10
+    assert all(abs(c - 12) < 1.5 for c in out["est_counts"])  # stochastic counts near the true shares

@@ -236,3 +236,21 @@ def batch_schedule(n_rows, batch, steps, seed):
             if len(out) == steps:
                 break
     return np.array(out, dtype=np.int32)
+
+
+def clustered_strip(n=400, clusters=8, per_cluster=6, seed=3, cond=10.0):
+    """Several target domains on one pencil (multi-contour workload): A =
+    V diag(lam) V^{-1}, B = I, with `clusters` tight groups of `per_cluster`
+    eigenvalues (radius 0.06) at Re = -1.75, -1.25, ... spaced 0.5 apart
+    inside the rectangle [-2, 2] x [-0.5, 0.5], and the other eigenvalues in
+    the annulus 4 <= |lambda| < 6."""
+    rng = np.random.default_rng(seed)
+    xs = -0.25 * (clusters - 1) + 0.5 * np.arange(clusters)
+    cl = np.concatenate([x + 0.06 * uniform_disk(rng, per_cluster, 0.0, 1.0) for x in xs])
+    lam = np.concatenate([cl, uniform_disk(rng, n - len(cl), 4.0, 6.0)])
+    U, W = haar_unitary(rng, n), haar_unitary(rng, n)
+    s = np.logspace(0.0, -np.log10(cond), n)
+    V = (U * s[None, :]) @ W.conj().T
+    Vinv = (W * (1.0 / s)[None, :]) @ U.conj().T
+    A = (V * lam[None, :]) @ Vinv
+    return dict(A=A, B=None, lam=lam, lam_inside=cl, region=(-0.25 * clusters, 0.25 * clusters, -0.5, 0.5), seed=seed)
