@@ -168,6 +168,7 @@ typedef struct {
   double deep_bytes;     /* their algorithmic HBM bytes (C read + written, L, U)    */
   double update_flops;   /* algorithmic flops of the K = 64 update launches         */
   double update_bytes;   /* and their algorithmic HBM bytes                         */
+  int tuned;             /* 1 if lu_outer / panel_cluster came from options.tune_cache */
 } feast_stats;
 
 typedef struct feast_handle feast_handle;
@@ -383,6 +384,8 @@ typedef struct {
   double plan_makespan_us;  /* makespan of the host schedule's cost model           */
   double t_factor_ms;       /* first launch (factorisations + first solves), timing */
   double t_iter_ms[64];     /* wall time of each iteration, timing option           */
+  int tuned;                /* 1 if the persistent grid and the scheduler's cost
+                               model were read from options.tune_cache             */
 } feast_batch_stats;
 
 feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, const feast_z* const* A,

@@ -73,7 +73,7 @@ class feast_stats(ctypes.Structure):
                 ("q", ctypes.c_int), ("shift_info", ctypes.c_int * 256), ("refine_sweeps", ctypes.c_int),
                 ("refactored", ctypes.c_int), ("lu_outer", ctypes.c_int), ("t_deep_ms", ctypes.c_double),
                 ("deep_launches", ctypes.c_int), ("deep_flops", ctypes.c_double), ("deep_bytes", ctypes.c_double),
-                ("update_flops", ctypes.c_double), ("update_bytes", ctypes.c_double)]
+                ("update_flops", ctypes.c_double), ("update_bytes", ctypes.c_double), ("tuned", ctypes.c_int)]
 
 
 class FeastError(RuntimeError):
@@ -101,7 +101,7 @@ SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_stat
 class feast_batch_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("tasks_factor", ctypes.c_int),
                 ("grid", ctypes.c_int), ("graph", ctypes.c_int), ("plan_makespan_us", ctypes.c_double),
-                ("t_factor_ms", ctypes.c_double), ("t_iter_ms", ctypes.c_double * 64)]
+                ("t_factor_ms", ctypes.c_double), ("t_iter_ms", ctypes.c_double * 64), ("tuned", ctypes.c_int)]
 
 
 def load(path=LIB_PATH):
@@ -347,7 +347,7 @@ def feast_get_stats(h):
                 q=st.q, shift_info=list(st.shift_info[:st.q]), refine_sweeps=st.refine_sweeps,
                 refactored=st.refactored, lu_outer=st.lu_outer, t_deep_ms=st.t_deep_ms,
                 deep_launches=st.deep_launches, deep_flops=st.deep_flops, deep_bytes=st.deep_bytes,
-                update_flops=st.update_flops, update_bytes=st.update_bytes)
+                update_flops=st.update_flops, update_bytes=st.update_bytes, tuned=st.tuned)
 
 
 def feast_set_wait_limit(seconds):
@@ -606,7 +606,7 @@ def feast_batch_solve(b, Y0s, allow_noconv=True):
         out.append(dict(m_found=k, lam=lams[p][:k], res=ress[p][:k], X=Xs[p][:, :k]))
     stats = dict(status=s, converged=st.converged, iters=st.iters, tasks_factor=st.tasks_factor, grid=st.grid,
                  graph=st.graph, plan_makespan_us=st.plan_makespan_us, t_factor_ms=st.t_factor_ms,
-                 t_iter_ms=list(st.t_iter_ms[:st.iters]))
+                 t_iter_ms=list(st.t_iter_ms[:st.iters]), tuned=st.tuned)
     return out, stats
 
 

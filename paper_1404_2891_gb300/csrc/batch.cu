@@ -27,6 +27,7 @@
 #include <functional>
 #include <new>
 #include <queue>
+#include <cstdio>
 #include <vector>
 
 #include "../../include/feast_gb300.h"
@@ -36,6 +37,7 @@
 #include "norm2.cuh"
 #include "ozaki.cuh"
 #include "small.cuh"
+#include "tune.cuh"
 
 using zc = std::complex<double>;
 
@@ -47,9 +49,14 @@ inline double2 d2(zc v) { return make_double2(v.real(), v.imag()); }
 inline zc zz(double2 v) { return zc(v.x, v.y); }
 
 // ---------------------------------------------------------------- scheduling
-// Model costs in microseconds of one SM (only their ratios matter).
-double cost_panel(int rows) { return 8.0 + 0.06 * rows; }
-double cost_update(int tiles) { return 3.0 + 4.5 * tiles; }
+// Model costs in microseconds of one SM (only their ratios matter).  The
+// per-row panel and per-tile update rates are the autotuner's parameters
+// (defaults below; tuned values come from options.tune_cache).
+struct CostModel {
+  double panel_row = 0.06, update_tile = 4.5;
+};
+double cost_panel(const CostModel& c, int rows) { return 8.0 + c.panel_row * rows; }
+double cost_update(const CostModel& c, int tiles) { return 3.0 + c.update_tile * tiles; }
 double cost_lswap(int panels) { return 1.0 + 1.0 * panels; }
 double cost_solve(int nb, int w) { return 6.0 * nb + 2.2 * nb * (nb - 1) * (w / 32.0); }
 
@@ -79,7 +86,7 @@ struct Plan {
 
 // Topological task order by list scheduling on `workers` identical workers.
 std::vector<int4> plan_order(const std::vector<int>& nbv, const std::vector<int>& mv, bool lu, bool solve,
-                             int workers, double* makespan) {
+                             int workers, double* makespan, const CostModel& cm = CostModel()) {
   Plan pl;
   pl.nb = nbv;
   pl.m = mv;
@@ -97,11 +104,11 @@ std::vector<int4> plan_order(const std::vector<int>& nbv, const std::vector<int>
     if (lu) {
       for (int k = 0; k < nb; ++k) {
         task[pl.P(i, k)] = make_int4(BT_PANEL, i, k, k);
-        cost[pl.P(i, k)] = cost_panel(BATCH_TILE * (nb - k));
+        cost[pl.P(i, k)] = cost_panel(cm, BATCH_TILE * (nb - k));
         pend[pl.P(i, k)] = k > 0 ? 1 : 0;
         for (int j = k + 1; j < nb; ++j) {
           task[pl.U(i, k, j)] = make_int4(BT_UPDATE, i, k, j);
-          cost[pl.U(i, k, j)] = cost_update(nb - k - 1);
+          cost[pl.U(i, k, j)] = cost_update(cm, nb - k - 1);
           pend[pl.U(i, k, j)] = 1 + (k > 0 ? 1 : 0);
         }
       }
@@ -226,6 +233,7 @@ struct feast_batch {
   std::vector<zc> center;
   std::vector<double> R, aspect, normA;
   std::vector<int> fdom;  // per pencil: CUSTOM nodes without an ellipse (domain test by the filter value)
+  int tuned = 0;          // launch parameters read from options.tune_cache
   size_t snn = 0, snm = 0, smm = 0, sm = 0, sqm = 0, slog = 0, sS = 0, sX = 0, sN = 0, snb = 0;
   // device
   GrpDesc* d_pd = nullptr;
@@ -758,6 +766,20 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
   // persistent launch: resident CTAs and the three task lists
   b->grid = batch_lu_grid(b->Nmax);
   if (b->grid < 1) return bad(FEAST_ERR_CUDA);
+  CostModel cm;
+  if (b->opt.tune_cache) {
+    // the autotuner's choice for this GPU, batch size and largest order
+    char key[256];
+    std::snprintf(key, sizeof(key), "%s|batch|count%d|nmax%lld|mixed", tune_gpu_name().c_str(), b->np,
+                  tune_bucket(b->Nmax));
+    std::map<std::string, double> t;
+    if (tune_lookup(b->opt.tune_cache, key, t)) {
+      if (t.count("grid")) b->grid = std::max(1, std::min(b->grid, (int)t["grid"]));
+      if (t.count("cost_panel_row") && t["cost_panel_row"] > 0) cm.panel_row = t["cost_panel_row"];
+      if (t.count("cost_update_tile") && t["cost_update_tile"] > 0) cm.update_tile = t["cost_update_tile"];
+      b->tuned = 1;
+    }
+  }
   {
     std::vector<int> nbv, mv;
     for (const BMat& M : b->mats) {
@@ -765,7 +787,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
       mv.push_back(M.m);
     }
     auto upload = [&](bool lu, bool solve, int4** dst, int* cnt, double* mk) -> cudaError_t {
-      const std::vector<int4> ord = plan_order(nbv, mv, lu, solve, b->grid, mk);
+      const std::vector<int4> ord = plan_order(nbv, mv, lu, solve, b->grid, mk, cm);
       *cnt = (int)ord.size();
       cudaError_t ee = dalloc(b, dst, ord.size() * sizeof(int4));
       if (ee != cudaSuccess) return ee;
@@ -899,6 +921,7 @@ feast_status feast_batch_solve(feast_batch* b, const feast_z* const* Y0, feast_z
   feast_batch_stats st;
   std::memset(&st, 0, sizeof(st));
   st.grid = b->grid;
+  st.tuned = b->tuned;
   st.tasks_factor = b->n_factor;
   st.plan_makespan_us = b->makespan;
   const bool was_factored = b->factored;

@@ -8,7 +8,10 @@
 #include <atomic>
 #include <cmath>
 #include <complex>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <string>
 #include <new>
 #include <type_traits>
 #include <mutex>
@@ -23,6 +26,7 @@
 #include "ozaki.cuh"
 #include "refine.cuh"
 #include "tc_deep.cuh"
+#include "tune.cuh"
 #include "tc_update.cuh"
 
 using zc = std::complex<double>;
@@ -199,7 +203,9 @@ struct feast_handle {
   void* pw_scratch = nullptr;
   TcStaging staging;
   DeepStaging deep;                    // the two-level LU's deep-update operands
+  float2* Tinv = nullptr;              // its I - L11^{-1} blocks, q x lu_outer x lu_outer
   int lu_outer = 0;                    // its outer block (0: one-level LU)
+  bool tuned = false;                  // launch parameters read from the tune cache
   std::vector<cudaEvent_t> deep_ev;
   int n_deep = 0;
   double t_deep = 0, deep_flops = 0, deep_bytes = 0;
@@ -393,6 +399,31 @@ cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bo
   return e;
 }
 
+// The far step of the two-level LU: every panel's interchanges on the columns
+// beyond the block, then U12 = L11^{-1} A12 as one deep product with
+// T = I - L11^{-1} (timed with the deep updates).
+cudaError_t far_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStream_t s) {
+  feast_handle* h = reinterpret_cast<feast_handle*>(c);
+  const int far0 = K0 + KB, nfar = lu.n - far0;
+  if (nfar <= 0) return cudaSuccess;
+  for (int k0 = K0; k0 < far0; k0 += 64) {
+    cudaError_t e = laswp_moved_rows(lu, k0, far0, nfar, s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = unit_lower_inverse_complement(lu, K0, KB, h->Tinv, s);
+  if (e != cudaSuccess) return e;
+  const bool timing = h->opt.timing && 2 * h->n_deep + 1 < (int)h->deep_ev.size();
+  if (timing) cudaEventRecord(h->deep_ev[2 * h->n_deep], s);
+  e = tc_far_gemm(lu, K0, KB, h->Tinv, h->deep, s);
+  if (timing) {
+    cudaEventRecord(h->deep_ev[2 * h->n_deep + 1], s);
+    ++h->n_deep;
+  }
+  h->deep_flops += 8.0 * lu.q * (double)KB * KB * nfar;
+  h->deep_bytes += 8.0 * lu.q * (2.0 * KB * nfar + (double)KB * KB + (double)KB * nfar);
+  return e;
+}
+
 // The deep update of the two-level LU: operands staged, then the timed kernel.
 cudaError_t deep_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStream_t s) {
   feast_handle* h = reinterpret_cast<feast_handle*>(c);
@@ -438,13 +469,13 @@ feast_status factor_impl(feast_handle* h) {
     if (h->lu_outer > 0) {
       if (h->opt.timing) {
         const int blocks = (int)((h->n + h->lu_outer - 1) / h->lu_outer);
-        while ((int)h->deep_ev.size() < 2 * blocks + 2) {
+        while ((int)h->deep_ev.size() < 4 * blocks + 2) {  // far and deep products per block
           cudaEvent_t e;
           CK(cudaEventCreate(&e));
           h->deep_ev.push_back(e);
         }
       }
-      CK(lu_factor_two_level(lu, 64, h->lu_outer, use_upd, use_ctx, tc_far_fn(), deep_hook, h, h->st));
+      CK(lu_factor_two_level(lu, 64, h->lu_outer, use_upd, use_ctx, far_hook, deep_hook, h, h->st));
     } else {
       CK(lu_factor_batched<T>(lu, h->nb, use_upd, use_ctx, h->st));
     }
@@ -1275,6 +1306,21 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     h->staging.rows_max = 2 * n;
     h->staging.cols_max = n;
     h->staging.q = h->q;
+    // the autotuner's choice for this GPU, order bucket, m0, shift count and precision
+    if (h->opt.tune_cache) {
+      char key[256];
+      std::snprintf(key, sizeof(key), "%s|single|n%lld|m0%d|q%d|mixed", tune_gpu_name().c_str(),
+                    tune_bucket(n), m0, (int)h->z_all.size());
+      std::map<std::string, double> t;
+      if (tune_lookup(h->opt.tune_cache, key, t)) {
+        if (h->opt.lu_outer == 0 && t.count("lu_outer")) {
+          const int v = (int)t["lu_outer"];
+          if (v < 0 || (v % 64 == 0 && v <= 256 && n > v)) h->opt.lu_outer = v;
+        }
+        if (h->opt.panel_cluster == 0 && t.count("panel_cluster")) h->opt.panel_cluster = (int)t["panel_cluster"];
+        h->tuned = true;
+      }
+    }
     // two-level LU: outer blocks of lu_outer columns with deep (K = lu_outer) updates
     int outer = h->opt.lu_outer;
     if (outer == 0) outer = n >= 1024 ? 256 : -1;
@@ -1285,6 +1331,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
       h->deep.rows_max = 2 * n;
       h->deep.cols_max = n;
       h->deep.q = h->q;
+      AL(h->Tinv, (size_t)h->q * outer * outer * sizeof(float2));
       h->lu_outer = outer;
     }
     if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
@@ -1357,6 +1404,7 @@ feast_status feast_get_stats(const feast_handle* h, feast_stats* st) {
   st->deep_bytes = h->deep_bytes;
   st->update_flops = h->upd_flops;
   st->update_bytes = h->upd_bytes;
+  st->tuned = h->tuned ? 1 : 0;
   st->t_filter_ms = h->t_filter;
   st->t_rr_ms = h->t_rr;
   return FEAST_OK;

@@ -274,6 +274,65 @@ k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, in
   }
 }
 
+// T = I - L11^{-1} for the unit lower KB x KB block L11 = S[K0:K0+KB, K0:K0+KB]
+// (strictly lower part stored) of every shift.  One CTA per (64-column block
+// j of the inverse, shift): X = L11^{-1} E_j by block forward substitution --
+// for each block row I >= j, the products with the earlier block rows of X
+// (L from global memory through shared memory, X in shared memory), then the
+// 64 x 64 unit lower solve, one thread per column with no barrier inside it.
+__global__ void __launch_bounds__(256)
+k_unit_lower_inv(const float2* S, long long ld, long long stride, int K0, int KB, float2* T) {
+  extern __shared__ __align__(16) unsigned char ti_smem[];
+  float2* X = reinterpret_cast<float2*>(ti_smem);  // [KB][64]
+  float2* Lb = X + (size_t)KB * 64;                // [64][65]
+  const int j = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, c = tid & 63, rq = tid >> 6;
+  const float2* A = S + (size_t)b * stride + (size_t)K0 + (size_t)K0 * ld;
+  const int nbk = KB / 64;
+  for (int I = j; I < nbk; ++I) {
+    float2 acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = rq + 4 * k;
+      acc[k] = make_float2(64 * I + r == 64 * j + c ? 1.f : 0.f, 0.f);
+    }
+    for (int J = j; J < I; ++J) {
+      __syncthreads();
+      for (int e = tid; e < 64 * 64; e += 256) {
+        const int r = e & 63, t = e >> 6;
+        Lb[r * 65 + t] = A[(size_t)(64 * I + r) + (size_t)(64 * J + t) * ld];
+      }
+      __syncthreads();
+      for (int t = 0; t < 64; ++t) {
+        const float2 xv = X[(size_t)(64 * J + t) * 64 + c];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] = csub<float>(acc[k], cmul<float>(Lb[(rq + 4 * k) * 65 + t], xv));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) X[(size_t)(64 * I + rq + 4 * k) * 64 + c] = acc[k];
+    __syncthreads();
+    for (int e = tid; e < 64 * 64; e += 256) {
+      const int r = e & 63, t = e >> 6;
+      Lb[r * 65 + t] = A[(size_t)(64 * I + r) + (size_t)(64 * I + t) * ld];
+    }
+    __syncthreads();
+    if (tid < 64) {  // unit lower 64 x 64 solve of column c, in place
+      float2* Xc = X + (size_t)(64 * I) * 64 + c;
+      for (int t = 0; t < 63; ++t) {
+        const float2 xt = Xc[(size_t)t * 64];
+        for (int r = t + 1; r < 64; ++r) Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Lb[r * 65 + t], xt));
+      }
+    }
+    __syncthreads();
+  }
+  float2* Tb = T + (size_t)b * KB * KB;
+  for (int e = tid; e < KB * 64; e += 256) {
+    const int r = e % KB, cc = e / KB, col = 64 * j + cc;
+    const float2 x = r >= 64 * j ? X[(size_t)r * 64 + cc] : make_float2(0.f, 0.f);
+    Tb[(size_t)r + (size_t)col * KB] = make_float2((r == col ? 1.f : 0.f) - x.x, -x.y);
+  }
+}
+
 // Row permutation vector from the interchange sequence: perm = P applied to 0..n-1.
 __global__ void k_piv_to_perm(const int32_t* piv, int32_t* perm, int32_t* pinv, int n) {
   const int b = blockIdx.x;
@@ -666,6 +725,17 @@ cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int nco
   return cudaGetLastError();
 }
 
+cudaError_t unit_lower_inverse_complement(const LuBatch<float>& lu, int K0, int KB, float2* T, cudaStream_t s) {
+  if (KB % 64 || KB > 256 || K0 + KB > lu.n) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)KB * 64 * sizeof(float2) + 64 * 65 * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_unit_lower_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  feast_count_launch();
+  k_unit_lower_inv<<<dim3(KB / 64, lu.q), 256, smem, s>>>(reinterpret_cast<const float2*>(lu.S), lu.ld, lu.stride, K0,
+                                                         KB, T);
+  return cudaGetLastError();
+}
+
 // Two-level blocked LU (complex64, tensor-core updates).  Inside each outer
 // block of KB columns the panels of nb = 64 columns run as in the one-level
 // schedule (the next block column updated first, the next panel on the
@@ -734,10 +804,10 @@ cudaError_t lu_factor_two_level(const LuBatch<float>& lu_in, int nb, int KB, Tra
     }
     if (cend >= lu.n) break;
     lu.col_end = 0;
-    if ((e = far(lu, K0, cend - K0, s)) != cudaSuccess) return cleanup(e);
-    // the L block is final once the interchanges of its later panels are on it
+    // the block's L is final once the interchanges of its later panels are on it
     if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
     if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+    if ((e = far(lu, K0, cend - K0, dctx, s)) != cudaSuccess) return cleanup(e);
     if ((e = deep(lu, K0, cend - K0, dctx, s)) != cudaSuccess) return cleanup(e);
     if ((e = launch_panel<float>(lu, cend, min(nb, lu.n - cend), s)) != cudaSuccess) return cleanup(e);
     if ((e = left(cend)) != cudaSuccess) return cleanup(e);

@@ -11,11 +11,14 @@
 //   * every CTA brings its rows of the group's columns up to date with the
 //     panel's earlier columns (L from global memory, U of the top rows from
 //     CTA 0's shared memory);
-//   * per column, each CTA finds the largest entry among its rows, and after a
-//     cluster barrier every CTA reads the CTAs' candidates from distributed
-//     shared memory and takes the same decision; the pivot row's group entries
-//     (and the row it replaces) are read the same way, a second cluster barrier
-//     separates those reads from the writes of the interchange, and each CTA
+//   * per column, each CTA finds the largest entry among its rows and posts it
+//     with the row's group entries (CTA 0 also posts the entries at the pivot
+//     position); after one cluster barrier every CTA reads the posted
+//     candidates from distributed shared memory, takes the same decision, and
+//     copies the pivot row (and, in the two CTAs involved, the row it
+//     replaces) before writing the interchange locally.  The posts are
+//     double-buffered by the parity of the column, so a CTA that runs ahead
+//     never overwrites what another CTA may still be reading.  Each CTA then
 //     applies the rank-1 update to its own rows with its copy of the pivot row.
 // CTA 0 owns logical rows 0 .. 63 (every pivot position), so each interchange
 // involves CTA 0 and the owner of the pivot row.  Every CTA runs the same
@@ -37,9 +40,16 @@ constexpr int PC_MAXW = 64;      // panel width
 struct PcShared {
   float best[PC_NT / 32];
   int bidx[PC_NT / 32];
-  float cand_v;                  // this CTA's pivot candidate (read by the others)
-  int cand_i;
-  int piv;
+  // posted for the other CTAs, double-buffered by the parity of the column:
+  // this CTA's pivot candidate with its group entries and physical row, and
+  // (CTA 0) the entries and physical row of the pivot position itself
+  float cand_v[2];
+  int cand_i[2];
+  float2 cand_row[2][16];
+  int cand_pl[2];
+  float2 col_row[2][16];
+  int col_pl[2];
+  int piv, owner;
   int cnt;                       // moved rows of this CTA
   int mvd[128], mvs[128];
   float2 u[16];                  // the pivot row's group entries (local copy)
@@ -178,45 +188,57 @@ k_panel_cluster(float2* S, long long ld, long long stride, int n, int r0, int w,
       }
       if (lane == 0) { sh.best[warp] = best; sh.bidx[warp] = bi; }
       __syncthreads();
+      const int slot = col & 1;
       if (tid == 0) {
         float v = sh.best[0];
         int ii = sh.bidx[0];
         for (int k = 1; k < PC_NT / 32; ++k)
           if (better(sh.best[k], sh.bidx[k], v, ii)) { v = sh.best[k]; ii = sh.bidx[k]; }
-        sh.cand_v = v;
-        sh.cand_i = ii;
+        sh.cand_v[slot] = v;
+        sh.cand_i[slot] = ii;
+        sh.cand_pl[slot] = ii < R ? pl[ii - lo] : 0;
+        if (rank == 0) sh.col_pl[slot] = pl[col];
       }
-      cluster.sync();  // [P1] candidates of every CTA are ready
+      __syncthreads();
+      if (tid < gw) {
+        const int ii = sh.cand_i[slot];
+        sh.cand_row[slot][tid] = ii < R ? G[tid * chunk + (ii - lo)] : make_float2(0.f, 0.f);
+        if (rank == 0) sh.col_row[slot][tid] = G[tid * chunk + col];
+      }
+      cluster.sync();  // [P1] every CTA's candidate (and CTA 0's pivot position) is posted
       if (tid == 0) {
         float v = -1.f;
-        int ii = R;
+        int ii = R, ow = 0;
         for (int k = 0; k < PC_C; ++k) {
           const PcShared* o = cluster.map_shared_rank(&sh, k);
-          if (better(o->cand_v, o->cand_i, v, ii)) { v = o->cand_v; ii = o->cand_i; }
+          if (better(o->cand_v[slot], o->cand_i[slot], v, ii)) { v = o->cand_v[slot]; ii = o->cand_i[slot]; ow = k; }
         }
         if (ii >= R) {  // the column held only NaN: keep the diagonal, flag it
           ii = col;
+          ow = 0;
           if (rank == 0) atomicOr(flags, (unsigned)DEVFLAG_NONFINITE);
         }
         sh.piv = ii;
+        sh.owner = ow;
       }
       __syncthreads();
       const int p = sh.piv;
-      const int owner = p / chunk;
-      // the pivot row's entries (every CTA) and, for the owner of the pivot
-      // row, the entries and map value of the row it replaces
+      const int owner = sh.owner;
       {
-        const float2* Gp = cluster.map_shared_rank(G, owner);
-        const int pr = p - owner * chunk;
-        if (tid < gw) sh.u[tid] = Gp[tid * chunk + pr];
-        if (rank == owner && p != col) {
-          const float2* G0 = cluster.map_shared_rank(G, 0);
-          if (tid < gw) sh.oldrow[tid] = G0[tid * chunk + col];
-          if (tid == 0) sh.pl_col = *cluster.map_shared_rank(pl + col, 0);
+        const PcShared* po = cluster.map_shared_rank(&sh, owner);
+        const PcShared* p0 = cluster.map_shared_rank(&sh, 0);
+        if (p == col) {
+          if (tid < gw) sh.u[tid] = p0->col_row[slot][tid];
+        } else {
+          if (tid < gw) sh.u[tid] = po->cand_row[slot][tid];
+          if (tid == 0) sh.pl_p = po->cand_pl[slot];
+          if (rank == owner) {
+            if (tid < gw) sh.oldrow[tid] = p0->col_row[slot][tid];
+            if (tid == 0) sh.pl_col = p0->col_pl[slot];
+          }
         }
-        if (rank == 0 && p != col && tid == 0) sh.pl_p = *cluster.map_shared_rank(pl + pr, owner);
       }
-      cluster.sync();  // [P2] every read of the interchange is done before its writes
+      __syncthreads();  // the posted values of this column are read (the slot is reused two columns later)
       if (p != col) {
         if (rank == 0) {
           if (tid < gw) G[tid * chunk + col] = sh.u[tid];

@@ -242,7 +242,11 @@ __global__ void __launch_bounds__(256) k_deep_stage(DeepGemm g, __nv_bfloat16* A
     for (int e = tid; e < 32 * 32; e += 256) {
       const int i = e & 31, k = e >> 5;
       const int gi = i0 + i, gk = kg * 32 + k;
-      tile[k][i] = (gi < g.M && gk < g.K) ? Sb[(size_t)(g.lr0 + gi) + (size_t)(g.kc0 + gk) * g.ld] : make_float2(0.f, 0.f);
+      float2 v = make_float2(0.f, 0.f);
+      if (gi < g.M && gk < g.K)
+        v = g.L ? g.L[(size_t)shift * g.strl + (size_t)gi + (size_t)gk * g.ldl]
+                : Sb[(size_t)(g.lr0 + gi) + (size_t)(g.kc0 + gk) * g.ld];
+      tile[k][i] = v;
     }
     __syncthreads();
     // per complex row i: A' rows 2i ([Re, -Im] pairs) and 2i+1 ([Im, Re]), hi and lo
@@ -401,6 +405,28 @@ cudaError_t tc_deep_stage(const LuBatch<float>& lu, int K0, int KB, const DeepSt
 cudaError_t tc_deep_run(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s) {
   const DeepGemm g = deep_of(lu, K0, KB);
   if (g.M <= 0) return cudaSuccess;
+  return deep_run(g, 0, g.N, st, lu.flags, s);
+}
+
+cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* T, const DeepStaging& st,
+                        cudaStream_t s) {
+  DeepGemm g;
+  g.S = reinterpret_cast<float2*>(lu.S);
+  g.ld = lu.ld;
+  g.stride = lu.stride;
+  g.lr0 = K0;        // C: the block's rows
+  g.kc0 = K0;        // U: the same rows (staged before the product overwrites them)
+  g.uc0 = K0 + KB;   // of the columns beyond the block
+  g.M = KB;
+  g.N = lu.n - K0 - KB;
+  g.K = KB;
+  g.q = lu.q;
+  g.L = T;
+  g.ldl = KB;
+  g.strl = (long long)KB * KB;
+  if (g.N <= 0) return cudaSuccess;
+  cudaError_t e = deep_stage(g, st, s);
+  if (e != cudaSuccess) return e;
   return deep_run(g, 0, g.N, st, lu.flags, s);
 }
 

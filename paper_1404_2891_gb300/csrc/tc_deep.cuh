@@ -21,11 +21,14 @@ size_t deep_staging_bytes_B(long long n, int q);
 // One batched product C_b -= L_b U_b (complex64, column-major, same ld and
 // batch stride for all three):  L = S[lr0 : lr0+M, kc0 : kc0+K],
 // U = S[kc0 : kc0+K, uc0 : uc0+N],  C = S[lr0 : lr0+M, uc0 : uc0+N].
+// With L set, the L operand is L_b[i + k ldl] (matrix b at L + b strl) instead.
 struct DeepGemm {
   float2* S = nullptr;
   long long ld = 0, stride = 0;
   int lr0 = 0, kc0 = 0, uc0 = 0;
   int M = 0, N = 0, K = 0, q = 0;
+  const float2* L = nullptr;
+  long long ldl = 0, strl = 0;
 };
 
 // Stage L (rows 0..M) and U (columns 0..N) as split BF16 (one launch).
@@ -40,6 +43,14 @@ bool deep_fits(const DeepGemm& g, const DeepStaging& st);
 // shifted matrix's S[K0+KB:, K0+KB:] -= S[K0+KB:, K0:K0+KB] S[K0:K0+KB, K0+KB:].
 cudaError_t tc_deep_stage(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s);
 cudaError_t tc_deep_run(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s);
+// The far step of outer block [K0, K0+KB) in one product: with
+// T = I - L11^{-1} (L11 the block's unit lower KB x KB diagonal block, T made
+// by unit_lower_inverse_complement), the block's rows of the columns beyond it
+// become S[K0:K0+KB, K0+KB:] -= T S[K0:K0+KB, K0+KB:] = L11^{-1} S[K0:K0+KB, K0+KB:]
+// (the operands are staged before the product, so it may run in place).
+// The caller has applied every panel's interchanges to those columns.
+cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* T, const DeepStaging& st,
+                        cudaStream_t s);
 // Algorithmic flops and HBM bytes of one such update (8 flops per complex MAC;
 // C read and written once, L and U read once, 8 bytes per complex64 entry).
 double tc_deep_flops(long long n, int q, int K0, int KB);

@@ -785,41 +785,7 @@ cudaError_t tc_trailing_update(const LuBatch<float>& lu, int k0, int w, int c0, 
   return tc_run(g, c0 - (k0 + w), nc, ctx, lu.flags, s);
 }
 
-// Two-level LU: the panels of the outer block [K0, K0+KB) applied to the
-// columns beyond the block.  First every panel's interchanges, in order, on
-// whole columns (those columns have seen none of the block's updates yet, so
-// rows inside and below the block are in the same state); then panel by panel
-// U_j = L_jj^{-1} A_j (rows k0 .. k0+64) in the staging kernel and the rows
-// below it inside the block's rows, k0+64 .. K0+KB, minus L U_j on the tensor
-// cores.  Afterwards rows K0 .. K0+KB of those columns hold the block's U; the
-// rows below wait for the deep update.
-cudaError_t tc_far_update(const LuBatch<float>& lu, int K0, int KB, cudaStream_t s) {
-  const int far0 = K0 + KB, nfar = lu.n - far0;
-  if (nfar <= 0) return cudaSuccess;
-  const TcStaging* ctx = reinterpret_cast<const TcStaging*>(lu.tc);
-  if (!ctx || !lu.mv) return cudaErrorInvalidValue;
-  float2* S = reinterpret_cast<float2*>(lu.S);
-  for (int k0 = K0; k0 < far0; k0 += 64) {
-    cudaError_t e = laswp_moved_rows(lu, k0, far0, nfar, s);
-    if (e != cudaSuccess) return e;
-  }
-  for (int k0 = K0; k0 < far0; k0 += 64) {
-    const int w = 64;
-    TcGemm g;
-    g.SA = S; g.lda = lu.ld; g.sa = lu.stride; g.ar0 = k0 + w; g.ac0 = k0; g.opA = OP_N;
-    g.SB = S; g.ldb = lu.ld; g.sb = lu.stride; g.br0 = k0; g.bc0 = far0;
-    g.SC = S; g.ldc = lu.ld; g.sc = lu.stride; g.cr0 = k0 + w; g.cc0 = far0;
-    g.M = far0 - (k0 + w); g.N = nfar; g.K = w; g.q = lu.q;
-    cudaError_t e = launch_stage_solve(g, ctx, 0, s, nullptr);
-    if (e != cudaSuccess) return e;
-    if (g.M > 0 && (e = tc_run(g, 0, nfar, ctx, lu.flags, s)) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
 }  // namespace
-
-FarFn tc_far_fn() { return tc_far_update; }
 
 size_t tc_staging_bytes_A(long long n, int q) { return (size_t)q * 2 * (2 * (size_t)n) * TC_KP * sizeof(__nv_bfloat16); }
 size_t tc_staging_bytes_B(long long n, int q) { return (size_t)q * 2 * (size_t)n * TC_KP * sizeof(__nv_bfloat16); }

@@ -15,9 +15,6 @@ struct TcStaging {
 size_t tc_staging_bytes_A(long long n, int q);
 size_t tc_staging_bytes_B(long long n, int q);
 
-// The far-column step of the two-level LU on the tensor cores (see lu.cuh).
-FarFn tc_far_fn();
-
 // complex128: the DMMA batched GEMM (fn = nullptr); complex64: the tcgen05
 // kernel, with ctx pointing at the handle's TcStaging.
 template <typename T>
