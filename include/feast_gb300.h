@@ -137,7 +137,8 @@ typedef struct {
                         update with K = 64)                                    */
   int panel_cluster; /* MIXED: 0 (default) = panels of 1024 to 8192 rows run
                         on a thread-block cluster of four CTAs per system;
-                        -1 = one CTA per system                                */
+                        k > 0 = from k rows on (k >= 256); -1 = one CTA per
+                        system                                                 */
 } feast_options;
 
 typedef struct {

@@ -5,7 +5,8 @@ Single pencil (key "<gpu>|single|n<bucket>|m0<m0>|q<q>|mixed"):
   lu_outer       outer block of the two-level LU: -1 (one-level, every
                  trailing update with K = 64), 128, 192 or 256 (deep updates
                  with K = lu_outer)
-  panel_cluster  0: panels of 1024 to 8192 rows on a cluster of four CTAs per
+  panel_cluster  panels from this many rows on (256, 512, 1024 or 2048; 0 =
+                 the library's 1024) run on a cluster of four CTAs per
                  system; -1: one CTA per system
 Batched path (key "<gpu>|batch|count<pencils>|nmax<bucket>|mixed"):
   grid            CTAs of the persistent factor/solve launch
@@ -93,7 +94,7 @@ def tune_single(n, m0, K=16, cache="tune.json", candidates=None, reps=2, seed=0,
     con = make_contour(center=0.2 + 0.1j, R=0.6, aspect=0.5, rule="gauss", N_e=K)
     if candidates is None:
         outers = [-1] + [v for v in (128, 192, 256) if n > v]
-        candidates = [(o, pc) for o in outers for pc in (0, -1)]
+        candidates = [(o, pc) for o in outers for pc in (256, 512, 1024, -1)]
     times = {}
     q = None
     for outer, pc in candidates:

@@ -312,6 +312,7 @@ LuBatch<T> lu_view(feast_handle* h) {
   lu.mv_panels = (int)((h->n + 63) / 64);
   if (std::is_same<T, float>::value && h->staging.Ast) lu.tc = &h->staging;
   lu.panel_cluster = std::is_same<T, float>::value && h->opt.panel_cluster >= 0;
+  lu.cluster_min_rows = h->opt.panel_cluster > 0 ? h->opt.panel_cluster : 0;
   return lu;
 }
 

@@ -279,7 +279,7 @@ k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, in
 // j of the inverse, shift): X = L11^{-1} E_j by block forward substitution --
 // for each block row I >= j, the products with the earlier block rows of X
 // (L from global memory through shared memory, X in shared memory), then the
-// 64 x 64 unit lower solve, one thread per column with no barrier inside it.
+// 64 x 64 unit lower solve (four threads per column, one barrier per step).
 __global__ void __launch_bounds__(256)
 k_unit_lower_inv(const float2* S, long long ld, long long stride, int K0, int KB, float2* T) {
   extern __shared__ __align__(16) unsigned char ti_smem[];
@@ -316,14 +316,15 @@ k_unit_lower_inv(const float2* S, long long ld, long long stride, int K0, int KB
       Lb[r * 65 + t] = A[(size_t)(64 * I + r) + (size_t)(64 * I + t) * ld];
     }
     __syncthreads();
-    if (tid < 64) {  // unit lower 64 x 64 solve of column c, in place
+    {  // unit lower 64 x 64 solve in place: column c, rows r = rq mod 4 per thread
       float2* Xc = X + (size_t)(64 * I) * 64 + c;
       for (int t = 0; t < 63; ++t) {
         const float2 xt = Xc[(size_t)t * 64];
-        for (int r = t + 1; r < 64; ++r) Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Lb[r * 65 + t], xt));
+        int r = t + 1 + ((rq - (t + 1)) & 3);
+        for (; r < 64; r += 4) Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Lb[r * 65 + t], xt));
+        __syncthreads();
       }
     }
-    __syncthreads();
   }
   float2* Tb = T + (size_t)b * KB * KB;
   for (int e = tid; e < KB * 64; e += 256) {
@@ -506,7 +507,8 @@ cudaError_t launch_panel_ll(const LuBatch<float>& lu, int k0, int w, int gcap, c
 template <typename T>
 cudaError_t launch_panel(const LuBatch<T>& lu, int k0, int w, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (lu.panel_cluster && panel_cluster_applies(lu.n - k0, w) && lu.mv) return panel_cluster(lu, k0, w, s);
+    if (lu.panel_cluster && panel_cluster_applies(lu.n - k0, w, lu.cluster_min_rows) && lu.mv)
+      return panel_cluster(lu, k0, w, s);
     if (w <= 64 && lu.n <= PLL_GCAP) {
       const int gcap = min(PLL_GCAP, 8 * lu.n);
       switch (panel_group_width(lu.n - k0, gcap)) {

@@ -27,8 +27,9 @@ struct LuBatch {
   // two-level LU: the inner steps see only the columns before col_end (the
   // current outer block); 0 = all n columns
   int col_end = 0;
-  // complex64 panels of >= 1024 rows on a cluster of four CTAs per shift
+  // complex64 panels of >= cluster_min_rows rows (0: 1024) on a cluster of four CTAs per shift
   bool panel_cluster = false;
+  int cluster_min_rows = 0;
 };
 constexpr int LU_MV_STRIDE = 257;
 
@@ -74,8 +75,8 @@ cudaError_t lu_factor_two_level(const LuBatch<float>& lu, int nb, int KB, Traili
 
 // Complex64 panel of rows k0 .. n-1, columns k0 .. k0+w-1 of every shift on a
 // thread-block cluster of four CTAs per shift (panel_cluster.cu); for panels of
-// 1024 to 8192 rows.
-bool panel_cluster_applies(int rows, int w);
+// min_rows (0: 1024) to 8192 rows.
+bool panel_cluster_applies(int rows, int w, int min_rows);
 cudaError_t panel_cluster(const LuBatch<float>& lu, int k0, int w, cudaStream_t s);
 
 // X (q x n x m, leading dimension n, batch stride n*m) overwritten with

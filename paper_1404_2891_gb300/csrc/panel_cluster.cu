@@ -189,69 +189,81 @@ k_panel_cluster(float2* S, long long ld, long long stride, int n, int r0, int w,
       if (lane == 0) { sh.best[warp] = best; sh.bidx[warp] = bi; }
       __syncthreads();
       const int slot = col & 1;
-      if (tid == 0) {
-        float v = sh.best[0];
-        int ii = sh.bidx[0];
-        for (int k = 1; k < PC_NT / 32; ++k)
-          if (better(sh.best[k], sh.bidx[k], v, ii)) { v = sh.best[k]; ii = sh.bidx[k]; }
-        sh.cand_v[slot] = v;
-        sh.cand_i[slot] = ii;
-        sh.cand_pl[slot] = ii < R ? pl[ii - lo] : 0;
-        if (rank == 0) sh.col_pl[slot] = pl[col];
-      }
-      __syncthreads();
-      if (tid < gw) {
-        const int ii = sh.cand_i[slot];
-        sh.cand_row[slot][tid] = ii < R ? G[tid * chunk + (ii - lo)] : make_float2(0.f, 0.f);
-        if (rank == 0) sh.col_row[slot][tid] = G[tid * chunk + col];
+      if (warp == 0) {
+        // this CTA's candidate (a shuffle over the warps' results), posted with
+        // its group entries; CTA 0 also posts the entries at the pivot position
+        float v = lane < PC_NT / 32 ? sh.best[lane] : -1.f;
+        int ii = lane < PC_NT / 32 ? sh.bidx[lane] : R;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float v2 = __shfl_down_sync(0xffffffffu, v, off);
+          const int i2 = __shfl_down_sync(0xffffffffu, ii, off);
+          if (better(v2, i2, v, ii)) { v = v2; ii = i2; }
+        }
+        ii = __shfl_sync(0xffffffffu, ii, 0);
+        if (lane == 0) {
+          sh.cand_v[slot] = v;
+          sh.cand_i[slot] = ii;
+          sh.cand_pl[slot] = ii < R ? pl[ii - lo] : 0;
+          if (rank == 0) sh.col_pl[slot] = pl[col];
+        }
+        if (lane < gw) {
+          sh.cand_row[slot][lane] = ii < R ? G[lane * chunk + (ii - lo)] : make_float2(0.f, 0.f);
+          if (rank == 0) sh.col_row[slot][lane] = G[lane * chunk + col];
+        }
       }
       cluster.sync();  // [P1] every CTA's candidate (and CTA 0's pivot position) is posted
-      if (tid == 0) {
+      if (warp == 0) {
+        // the same decision in every CTA: lane k reads CTA k's candidate
         float v = -1.f;
         int ii = R, ow = 0;
-        for (int k = 0; k < PC_C; ++k) {
-          const PcShared* o = cluster.map_shared_rank(&sh, k);
-          if (better(o->cand_v[slot], o->cand_i[slot], v, ii)) { v = o->cand_v[slot]; ii = o->cand_i[slot]; ow = k; }
+        if (lane < PC_C) {
+          const PcShared* o = cluster.map_shared_rank(&sh, lane);
+          v = o->cand_v[slot];
+          ii = o->cand_i[slot];
+          ow = lane;
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float v2 = __shfl_down_sync(0xffffffffu, v, off);
+          const int i2 = __shfl_down_sync(0xffffffffu, ii, off);
+          const int o2 = __shfl_down_sync(0xffffffffu, ow, off);
+          if (better(v2, i2, v, ii)) { v = v2; ii = i2; ow = o2; }
+        }
+        ii = __shfl_sync(0xffffffffu, ii, 0);
+        ow = __shfl_sync(0xffffffffu, ow, 0);
         if (ii >= R) {  // the column held only NaN: keep the diagonal, flag it
           ii = col;
           ow = 0;
-          if (rank == 0) atomicOr(flags, (unsigned)DEVFLAG_NONFINITE);
+          if (rank == 0 && lane == 0) atomicOr(flags, (unsigned)DEVFLAG_NONFINITE);
         }
-        sh.piv = ii;
-        sh.owner = ow;
-      }
-      __syncthreads();
-      const int p = sh.piv;
-      const int owner = sh.owner;
-      {
-        const PcShared* po = cluster.map_shared_rank(&sh, owner);
+        const PcShared* po = cluster.map_shared_rank(&sh, ow);
         const PcShared* p0 = cluster.map_shared_rank(&sh, 0);
-        if (p == col) {
-          if (tid < gw) sh.u[tid] = p0->col_row[slot][tid];
+        if (ii == col) {
+          if (lane < gw) sh.u[lane] = p0->col_row[slot][lane];
         } else {
-          if (tid < gw) sh.u[tid] = po->cand_row[slot][tid];
-          if (tid == 0) sh.pl_p = po->cand_pl[slot];
-          if (rank == owner) {
-            if (tid < gw) sh.oldrow[tid] = p0->col_row[slot][tid];
-            if (tid == 0) sh.pl_col = p0->col_pl[slot];
+          float2 u = make_float2(0.f, 0.f), old = make_float2(0.f, 0.f);
+          if (lane < gw) {
+            u = po->cand_row[slot][lane];
+            if (rank == ow) old = p0->col_row[slot][lane];
+          }
+          const int plp = lane == 0 ? po->cand_pl[slot] : 0;
+          const int plc = (lane == 0 && rank == ow) ? p0->col_pl[slot] : 0;
+          if (lane < gw) {
+            sh.u[lane] = u;
+            if (rank == 0) G[lane * chunk + col] = u;
+            if (rank == ow) G[lane * chunk + (ii - ow * chunk)] = old;
+          }
+          if (lane == 0) {
+            if (rank == 0) pl[col] = plp;
+            if (rank == ow) pl[ii - ow * chunk] = plc;
           }
         }
+        if (lane == 0) sh.piv = ii;
       }
-      __syncthreads();  // the posted values of this column are read (the slot is reused two columns later)
-      if (p != col) {
-        if (rank == 0) {
-          if (tid < gw) G[tid * chunk + col] = sh.u[tid];
-          if (tid == 0) pl[col] = sh.pl_p;
-        }
-        if (rank == owner) {
-          const int pr = p - owner * chunk;
-          if (tid < gw) G[tid * chunk + pr] = sh.oldrow[tid];
-          if (tid == 0) pl[pr] = sh.pl_col;
-        }
-      }
+      __syncthreads();  // the interchange and the pivot row are in place
+      const int p = sh.piv;
       if (rank == 0 && tid == 0) pv[col] = r0 + p;
-      __syncthreads();
       const float2 d = sh.u[c];
       if (d.x == 0.f && d.y == 0.f) {
         if (rank == 0 && tid == 0) {
@@ -269,8 +281,10 @@ k_panel_cluster(float2* S, long long ld, long long stride, int n, int r0, int w,
             if (c + c2 < gw) G[(c + c2) * chunk + r] = csub<float>(G[(c + c2) * chunk + r], cmul<float>(l, sh.u[c + c2]));
         }
       }
-      __syncthreads();
+      // each thread's next pivot search reads only the rows it has just
+      // updated; the next barrier (after the search) orders the rest
     }
+    __syncthreads();
     // 4. the group's columns back to their physical rows
     for (int idx = tid; idx < rows * gw; idx += PC_NT) {
       const int c = idx / rows, r = idx - c * rows;
@@ -360,14 +374,17 @@ cudaError_t launch_pc(const LuBatch<float>& lu, int k0, int w, int chunk, int32_
 
 }  // namespace
 
-// The cluster panel applies to panels of 1024 to 8192 rows: below that the
-// per-column cluster barriers cost more than the split saves, above it a
-// CTA's rows of an eight-column group no longer fit in shared memory.
-bool panel_cluster_applies(int rows, int w) { return rows >= 1024 && rows <= 8192 && w <= PC_MAXW; }
+// The cluster panel applies to panels of min_rows (default 1024, at least 256)
+// to 8192 rows: below that the per-column cluster barrier costs more than the
+// split saves, above it a CTA's rows of an eight-column group no longer fit in
+// shared memory.
+bool panel_cluster_applies(int rows, int w, int min_rows) {
+  return rows >= (min_rows > 0 ? min_rows : 1024) && rows >= 256 && rows <= 8192 && w <= PC_MAXW;
+}
 
 cudaError_t panel_cluster(const LuBatch<float>& lu, int k0, int w, cudaStream_t s) {
   const int R = lu.n - k0;
-  if (!panel_cluster_applies(R, w)) return cudaErrorInvalidValue;
+  if (!panel_cluster_applies(R, w, lu.cluster_min_rows)) return cudaErrorInvalidValue;
   const int chunk = ((R + PC_C - 1) / PC_C + 1) & ~1;
   int32_t* mvk = lu.mv ? lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE : nullptr;
   if (chunk * 16 <= 16384) return launch_pc<16>(lu, k0, w, chunk, mvk, s);
