@@ -49,7 +49,9 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-pencil workload")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--batch-only", action="store_true", help="run only the batched workload (prints its object)")
-    p.add_argument("--panel-cluster", type=int, default=0, help="0 = cluster panels (default), -1 = one CTA")
+    p.add_argument("--panel-cluster", type=int, default=0,
+                   help="0 = library default or tuned, k > 0 = cluster panels from k rows, -1 = one CTA")
+    p.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     p.add_argument("--lu-outer", type=int, default=0,
                    help="outer block of the two-level LU (0 = library default, -1 = one-level)")
     return p.parse_args()
@@ -458,8 +460,22 @@ def run_ours(args):
         return e0.elapsed_time(e1) / count
 
     # ---- mixed path (headline)
+    # the autotuner picks the LU's outer block and panel form for this shape
+    # (a synthetic pencil of the same order; a few factorisations per candidate)
+    tune = None
+    tune_cache = None
+    if not args.no_tune and args.lu_outer == 0 and args.panel_cluster == 0:
+        import tempfile
+        from paper_1404_2891_gb300 import autotune
+        tune_cache = os.path.join(tempfile.mkdtemp(), "tune.json")
+        outers = [v for v in (192, 256) if n > v] or [-1]
+        t0 = time.perf_counter()
+        key, entry, times = autotune.tune_single(n, m0, K, tune_cache,
+                                                 candidates=[(o, pc) for o in outers for pc in (256, 512, 1024)])
+        tune = {"key": key, "choice": {"lu_outer": entry["lu_outer"], "panel_cluster": entry["panel_cluster"]},
+                "factor_ms_by_candidate": times, "tuning_s": time.perf_counter() - t0}
     opts = fg.make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True,
-                           lu_outer=args.lu_outer, panel_cluster=args.panel_cluster)
+                           lu_outer=args.lu_outer, panel_cluster=args.panel_cluster, tune_cache=tune_cache)
     h = fg.feast_create(A_d, B_d, contour, m0, opts, stream=stream)
     # the residual gate: a full solve from the same start block
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -633,7 +649,7 @@ def run_ours(args):
                       "res_hist": sol["res_hist"], "t_factor_ms": sol["t_factor_ms"],
                       "t_filter_ms": sol["t_filter_ms"], "t_rr_ms": sol["t_rr_ms"], "eig_err": eig_err},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": int(launches), "batched": batched,
+            "gpu_launches": int(launches), "batched": batched, "autotune": tune,
         }
         print(json.dumps(line))
     if world > 1:

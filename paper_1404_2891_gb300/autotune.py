@@ -5,7 +5,7 @@ Single pencil (key "<gpu>|single|n<bucket>|m0<m0>|q<q>|mixed"):
   lu_outer       outer block of the two-level LU: -1 (one-level, every
                  trailing update with K = 64), 128, 192 or 256 (deep updates
                  with K = lu_outer)
-  panel_cluster  panels from this many rows on (256, 512, 1024 or 2048; 0 =
+  panel_cluster  panels from this many rows on (256, 512 or 1024; 0 =
                  the library's 1024) run on a cluster of four CTAs per
                  system; -1: one CTA per system
 Batched path (key "<gpu>|batch|count<pencils>|nmax<bucket>|mixed"):
