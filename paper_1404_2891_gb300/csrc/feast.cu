@@ -202,8 +202,12 @@ struct feast_handle {
   void* orth_scratch2 = nullptr;       // the left block's orthonormalisation (side stream)
   void* pw_scratch = nullptr;
   TcStaging staging;
-  DeepStaging deep;                    // the two-level LU's deep-update operands
-  float2* Tinv = nullptr;              // its I - L11^{-1} blocks, q x lu_outer x lu_outer
+  DeepStaging deep;                    // the two-level LU's deep-update operands (and the right solves')
+  DeepStaging deep_left;               // the left solves' own (they run beside the right ones)
+  // I - D^{-1} of every diagonal block (lu_outer columns) of the unit lower L and
+  // of the upper U, for the far steps of the LU and the blocked solves
+  float2 *TL = nullptr, *TU = nullptr;
+  int nblk = 0;
   int lu_outer = 0;                    // its outer block (0: one-level LU)
   bool tuned = false;                  // launch parameters read from the tune cache
   std::vector<cudaEvent_t> deep_ev;
@@ -411,11 +415,13 @@ cudaError_t far_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStre
     cudaError_t e = laswp_moved_rows(lu, k0, far0, nfar, s);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = unit_lower_inverse_complement(lu, K0, KB, h->Tinv, s);
+  // T = I - L11^{-1} of this block, kept for the solves (block-major, all blocks)
+  float2* T = h->TL + (size_t)(K0 / KB) * lu.q * KB * KB;
+  cudaError_t e = block_inverse_complement(lu, false, KB, K0 / KB, 1, T, s);
   if (e != cudaSuccess) return e;
   const bool timing = h->opt.timing && 2 * h->n_deep + 1 < (int)h->deep_ev.size();
   if (timing) cudaEventRecord(h->deep_ev[2 * h->n_deep], s);
-  e = tc_far_gemm(lu, K0, KB, h->Tinv, h->deep, s);
+  e = tc_far_gemm(lu, K0, KB, T, h->deep, s);
   if (timing) {
     cudaEventRecord(h->deep_ev[2 * h->n_deep + 1], s);
     ++h->n_deep;
@@ -477,6 +483,12 @@ feast_status factor_impl(feast_handle* h) {
         }
       }
       CK(lu_factor_two_level(lu, 64, h->lu_outer, use_upd, use_ctx, far_hook, deep_hook, h, h->st));
+      // I - D^{-1} of the last L block (the far steps made the others) and of every
+      // U block, for the blocked solves
+      const int KB = h->lu_outer;
+      CK(block_inverse_complement(lu, false, KB, h->nblk - 1, 1, h->TL + (size_t)(h->nblk - 1) * h->q * KB * KB,
+                                  h->st));
+      CK(block_inverse_complement(lu, true, KB, 0, h->nblk, h->TU, h->st));
     } else {
       CK(lu_factor_batched<T>(lu, h->nb, use_upd, use_ctx, h->st));
     }
@@ -631,6 +643,19 @@ feast_status refine_alloc(feast_handle* h) {
 }
 
 // Right: Q = c0 .* Y + sum_k coef_k .* S_k^{-1} R;  left: Qh = c0h .* Yh + sum_k coefh_k .* S_k^{-H} Rh
+// The filter's triangular solves of all shifts: with the two-level factors the
+// blocked deep-K form (diagonal blocks through I - D^{-1}, K = lu_outer
+// updates), else the 64-row block form.
+template <typename T>
+cudaError_t solve_all(feast_handle* h, const LuBatch<T>& lu, int side, cplx<T>* X, int m, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    const DeepStaging& st = side == 0 ? h->deep : h->deep_left;
+    if (h->lu_outer > 0 && h->TU && st.Ast && m <= st.cols_max && h->n > 2 * h->lu_outer)
+      return tc_solve_deep(lu, side, X, m, h->lu_outer, h->TL, h->TU, st, s);
+  }
+  return lu_solve_batched<T>(lu, side, X, m, h->nbs, s);
+}
+
 template <typename T>
 feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, bool use_c0, const double2* Rh,
                          const double2* Yhc0, double2* Qout, double2* Qhout) {
@@ -642,7 +667,7 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   const bool add_c0 = use_c0 && !h->partial;  // a partial handle returns its subtree alone
   const int ms = h->realp ? 2 * m : m;          // real pencils: [R, conj(R)] per factor
   CK(rows_gather<T>(lu, R, Xs, m, true, h->st, h->realp));
-  CK(lu_solve_batched<T>(lu, 0, Xs, ms, h->nbs, h->st));
+  CK(solve_all<T>(h, lu, 0, Xs, ms, h->st));
   const bool refine = std::is_same<T, float>::value && h->opt.max_refine > 0;
   feast_status rstat = FEAST_OK;
   if (refine) {
@@ -691,7 +716,7 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
     cudaStream_t ls = split ? h->side : h->st;
     if (split) CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
     CK(rows_gather<T>(lul, Rh, Xsh, m, false, ls, h->realp));
-    CK(lu_solve_batched<T>(lul, 1, Xsh, ms, h->nbs, ls));
+    CK(solve_all<T>(h, lul, 1, Xsh, ms, ls));
     if (h->realp) {
       CK(accumulate_conj_pairs<T>(Xsh, h->q, n, m, h->coefh, h->coefch, add_c0 ? h->c0h : nullptr,
                                   add_c0 ? Yhc0 : nullptr, lu.pinv, Qhout, ls));
@@ -1332,7 +1357,16 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
       h->deep.rows_max = 2 * n;
       h->deep.cols_max = n;
       h->deep.q = h->q;
-      AL(h->Tinv, (size_t)h->q * outer * outer * sizeof(float2));
+      if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
+        AL(h->deep_left.Ast, deep_staging_bytes_A(n, h->q));
+        AL(h->deep_left.Bst, deep_staging_bytes_B(n, h->q));
+        h->deep_left.rows_max = 2 * n;
+        h->deep_left.cols_max = n;
+        h->deep_left.q = h->q;
+      }
+      h->nblk = (int)((n + outer - 1) / outer);
+      AL(h->TL, (size_t)h->nblk * h->q * outer * outer * sizeof(float2));
+      AL(h->TU, (size_t)h->nblk * h->q * outer * outer * sizeof(float2));
       h->lu_outer = outer;
     }
     if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {

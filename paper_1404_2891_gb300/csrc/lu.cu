@@ -274,38 +274,55 @@ k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, in
   }
 }
 
-// T = I - L11^{-1} for the unit lower KB x KB block L11 = S[K0:K0+KB, K0:K0+KB]
-// (strictly lower part stored) of every shift.  One CTA per (64-column block
-// j of the inverse, shift): X = L11^{-1} E_j by block forward substitution --
-// for each block row I >= j, the products with the earlier block rows of X
-// (L from global memory through shared memory, X in shared memory), then the
-// 64 x 64 unit lower solve (four threads per column, one barrier per step).
+// T = I - D^{-1} for diagonal blocks D of the factor: D = the unit lower part
+// (UPPER = false) or the upper part with its diagonal (UPPER = true) of
+// S[r0:r0+KB, r0:r0+KB], r0 = KB * block; rows and columns at or beyond n act as
+// the identity (a ragged last block).  One CTA per (64-column block j of the
+// inverse, diagonal block, shift): X = D^{-1} E_j by block substitution -- for
+// each 64-row block I reached from j (downward for L, upward for U), the
+// products with the blocks of X already solved (D from global memory through
+// shared memory, X in shared memory), then the 64 x 64 triangular solve (four
+// threads per column, one barrier per step).  T goes to
+// T + ((block - block0) q + shift) KB^2, column-major with leading dimension KB.
+template <bool UPPER>
 __global__ void __launch_bounds__(256)
-k_unit_lower_inv(const float2* S, long long ld, long long stride, int K0, int KB, float2* T) {
+k_block_tri_inv(const float2* S, long long ld, long long stride, int n, int KB, int block0, float2* T) {
   extern __shared__ __align__(16) unsigned char ti_smem[];
   float2* X = reinterpret_cast<float2*>(ti_smem);  // [KB][64]
-  float2* Lb = X + (size_t)KB * 64;                // [64][65]
-  const int j = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, c = tid & 63, rq = tid >> 6;
-  const float2* A = S + (size_t)b * stride + (size_t)K0 + (size_t)K0 * ld;
+  float2* Db = X + (size_t)KB * 64;                // [64][65]
+  const int j = blockIdx.x, blk = block0 + blockIdx.y, b = blockIdx.z, q = gridDim.z;
+  const int tid = threadIdx.x, c = tid & 63, rq = tid >> 6;
+  const int r0 = KB * blk, nr = min(KB, n - r0);
+  const float2* A = S + (size_t)b * stride + (size_t)r0 + (size_t)r0 * ld;
   const int nbk = KB / 64;
-  for (int I = j; I < nbk; ++I) {
+  // D(r, t) of the block, identity outside the valid nr x nr part
+  auto dval = [&](int r, int t) -> float2 {
+    if (r == t && (!UPPER || r >= nr)) return make_float2(1.f, 0.f);
+    if (r >= nr || t >= nr) return make_float2(0.f, 0.f);
+    if (UPPER ? r > t : r < t) return make_float2(0.f, 0.f);
+    return A[(size_t)r + (size_t)t * ld];
+  };
+  for (int s2 = 0; s2 < nbk; ++s2) {
+    const int I = UPPER ? j - s2 : j + s2;
+    if (I < 0 || I >= nbk) continue;
     float2 acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int r = rq + 4 * k;
       acc[k] = make_float2(64 * I + r == 64 * j + c ? 1.f : 0.f, 0.f);
     }
-    for (int J = j; J < I; ++J) {
+    for (int s3 = 0; s3 < s2; ++s3) {
+      const int J = UPPER ? j - s3 : j + s3;  // blocks of X solved before I
       __syncthreads();
       for (int e = tid; e < 64 * 64; e += 256) {
         const int r = e & 63, t = e >> 6;
-        Lb[r * 65 + t] = A[(size_t)(64 * I + r) + (size_t)(64 * J + t) * ld];
+        Db[r * 65 + t] = dval(64 * I + r, 64 * J + t);
       }
       __syncthreads();
       for (int t = 0; t < 64; ++t) {
         const float2 xv = X[(size_t)(64 * J + t) * 64 + c];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] = csub<float>(acc[k], cmul<float>(Lb[(rq + 4 * k) * 65 + t], xv));
+        for (int k = 0; k < 16; ++k) acc[k] = csub<float>(acc[k], cmul<float>(Db[(rq + 4 * k) * 65 + t], xv));
       }
     }
 #pragma unroll
@@ -313,23 +330,33 @@ k_unit_lower_inv(const float2* S, long long ld, long long stride, int K0, int KB
     __syncthreads();
     for (int e = tid; e < 64 * 64; e += 256) {
       const int r = e & 63, t = e >> 6;
-      Lb[r * 65 + t] = A[(size_t)(64 * I + r) + (size_t)(64 * I + t) * ld];
+      Db[r * 65 + t] = dval(64 * I + r, 64 * I + t);
     }
     __syncthreads();
-    {  // unit lower 64 x 64 solve in place: column c, rows r = rq mod 4 per thread
-      float2* Xc = X + (size_t)(64 * I) * 64 + c;
+    float2* Xc = X + (size_t)(64 * I) * 64 + c;
+    if (!UPPER) {  // unit lower: forward
       for (int t = 0; t < 63; ++t) {
         const float2 xt = Xc[(size_t)t * 64];
-        int r = t + 1 + ((rq - (t + 1)) & 3);
-        for (; r < 64; r += 4) Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Lb[r * 65 + t], xt));
+        for (int r = t + 1 + ((rq - (t + 1)) & 3); r < 64; r += 4)
+          Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Db[r * 65 + t], xt));
         __syncthreads();
       }
+    } else {  // upper with its diagonal: backward, the owner of row t divides first
+      for (int t = 63; t >= 0; --t) {
+        if ((t & 3) == rq) Xc[(size_t)t * 64] = cdiv<float>(Xc[(size_t)t * 64], Db[t * 65 + t]);
+        __syncthreads();
+        const float2 xt = Xc[(size_t)t * 64];
+        for (int r = rq; r < t; r += 4)
+          Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Db[r * 65 + t], xt));
+      }
+      __syncthreads();
     }
   }
-  float2* Tb = T + (size_t)b * KB * KB;
+  float2* Tb = T + ((size_t)(blk - block0) * q + b) * KB * KB;
   for (int e = tid; e < KB * 64; e += 256) {
     const int r = e % KB, cc = e / KB, col = 64 * j + cc;
-    const float2 x = r >= 64 * j ? X[(size_t)r * 64 + cc] : make_float2(0.f, 0.f);
+    const bool solved = UPPER ? r < 64 * (j + 1) : r >= 64 * j;
+    const float2 x = solved ? X[(size_t)r * 64 + cc] : make_float2(0.f, 0.f);
     Tb[(size_t)r + (size_t)col * KB] = make_float2((r == col ? 1.f : 0.f) - x.x, -x.y);
   }
 }
@@ -727,14 +754,21 @@ cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int nco
   return cudaGetLastError();
 }
 
-cudaError_t unit_lower_inverse_complement(const LuBatch<float>& lu, int K0, int KB, float2* T, cudaStream_t s) {
-  if (KB % 64 || KB > 256 || K0 + KB > lu.n) return cudaErrorInvalidValue;
+cudaError_t block_inverse_complement(const LuBatch<float>& lu, bool upper, int KB, int block0, int nblocks, float2* T,
+                                     cudaStream_t s) {
+  if (KB % 64 || KB > 256 || KB < 64 || nblocks < 1 || block0 < 0 || (long long)KB * (block0 + nblocks - 1) >= lu.n)
+    return cudaErrorInvalidValue;
   const size_t smem = (size_t)KB * 64 * sizeof(float2) + 64 * 65 * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_unit_lower_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = upper ? cudaFuncSetAttribute(k_block_tri_inv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(k_block_tri_inv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   feast_count_launch();
-  k_unit_lower_inv<<<dim3(KB / 64, lu.q), 256, smem, s>>>(reinterpret_cast<const float2*>(lu.S), lu.ld, lu.stride, K0,
-                                                         KB, T);
+  const dim3 grid(KB / 64, nblocks, lu.q);
+  const float2* S = reinterpret_cast<const float2*>(lu.S);
+  if (upper)
+    k_block_tri_inv<true><<<grid, 256, smem, s>>>(S, lu.ld, lu.stride, lu.n, KB, block0, T);
+  else
+    k_block_tri_inv<false><<<grid, 256, smem, s>>>(S, lu.ld, lu.stride, lu.n, KB, block0, T);
   return cudaGetLastError();
 }
 

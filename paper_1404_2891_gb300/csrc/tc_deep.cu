@@ -34,6 +34,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "tc_deep.cuh"
@@ -234,7 +235,8 @@ __global__ void __launch_bounds__(256) k_deep_stage(DeepGemm g, __nv_bfloat16* A
   const int tid = threadIdx.x;
   const int shift = blockIdx.y / ((g.K + 31) / 32);
   const int kg = blockIdx.y % ((g.K + 31) / 32);
-  const float2* Sb = g.S + (size_t)shift * g.stride;
+  const float2* Lb = g.L + (size_t)shift * g.strl;
+  const float2* Ub = g.U + (size_t)shift * g.stru;
   if (blockIdx.z == 0) {
     __shared__ float2 tile[32][33];
     const int i0 = blockIdx.x * 32;
@@ -244,8 +246,8 @@ __global__ void __launch_bounds__(256) k_deep_stage(DeepGemm g, __nv_bfloat16* A
       const int gi = i0 + i, gk = kg * 32 + k;
       float2 v = make_float2(0.f, 0.f);
       if (gi < g.M && gk < g.K)
-        v = g.L ? g.L[(size_t)shift * g.strl + (size_t)gi + (size_t)gk * g.ldl]
-                : Sb[(size_t)(g.lr0 + gi) + (size_t)(g.kc0 + gk) * g.ld];
+        v = g.opL == OP_C ? cconj<float>(Lb[(size_t)(g.lc + gk) + (size_t)(g.lr + gi) * g.ldl])
+                          : Lb[(size_t)(g.lr + gi) + (size_t)(g.lc + gk) * g.ldl];
       tile[k][i] = v;
     }
     __syncthreads();
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(256) k_deep_stage(DeepGemm g, __nv_bfloat16* A
       const int k = e & 31, j = e >> 5;
       const int gj = j0 + j, gk = kg * 32 + k;
       if (gj >= g.N) continue;
-      const float2 u = gk < g.K ? Sb[(size_t)(g.kc0 + gk) + (size_t)(g.uc0 + gj) * g.ld] : make_float2(0.f, 0.f);
+      const float2 u = gk < g.K ? Ub[(size_t)(g.ur + gk) + (size_t)(g.uc + gj) * g.ldu] : make_float2(0.f, 0.f);
       __nv_bfloat16 hr, lr, him, lim;
       split2(u.x, hr, lr);
       split2(u.y, him, lim);
@@ -354,10 +356,10 @@ cudaError_t deep_run(const DeepGemm& g, int c0, int nc, const DeepStaging& st, u
   if (!encode_deep_map(&mA, st.Ast, 2LL * g.M, st.rows_max, 2 * g.q, DK_BM)) return cudaErrorInvalidValue;
   if (!encode_deep_map(&mB, st.Bst, g.N, st.cols_max, 2 * g.q, DK_BN)) return cudaErrorInvalidValue;
   DeepArgs a;
-  a.S = reinterpret_cast<float*>(g.S);
-  a.ld2 = 2 * g.ld;
-  a.stride2 = 2 * g.stride;
-  a.c_off = 2LL * g.lr0 + (long long)(g.uc0 + c0) * a.ld2;
+  a.S = reinterpret_cast<float*>(g.C);
+  a.ld2 = 2 * g.ldc;
+  a.stride2 = 2 * g.strc;
+  a.c_off = 2LL * g.cr + (long long)(g.cc + c0) * a.ld2;
   a.M2 = 2 * g.M;
   a.N = nc;
   a.b_col0 = c0;
@@ -382,12 +384,10 @@ cudaError_t deep_run(const DeepGemm& g, int c0, int nc, const DeepStaging& st, u
 namespace {
 DeepGemm deep_of(const LuBatch<float>& lu, int K0, int KB) {
   DeepGemm g;
-  g.S = reinterpret_cast<float2*>(lu.S);
-  g.ld = lu.ld;
-  g.stride = lu.stride;
-  g.lr0 = K0 + KB;
-  g.kc0 = K0;
-  g.uc0 = K0 + KB;
+  float2* S = reinterpret_cast<float2*>(lu.S);
+  g.C = S; g.ldc = lu.ld; g.strc = lu.stride; g.cr = K0 + KB; g.cc = K0 + KB;
+  g.L = S; g.ldl = lu.ld; g.strl = lu.stride; g.lr = K0 + KB; g.lc = K0; g.opL = OP_N;
+  g.U = S; g.ldu = lu.ld; g.stru = lu.stride; g.ur = K0; g.uc = K0 + KB;
   g.M = lu.n - K0 - KB;
   g.N = g.M;
   g.K = KB;
@@ -411,23 +411,57 @@ cudaError_t tc_deep_run(const LuBatch<float>& lu, int K0, int KB, const DeepStag
 cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* T, const DeepStaging& st,
                         cudaStream_t s) {
   DeepGemm g;
-  g.S = reinterpret_cast<float2*>(lu.S);
-  g.ld = lu.ld;
-  g.stride = lu.stride;
-  g.lr0 = K0;        // C: the block's rows
-  g.kc0 = K0;        // U: the same rows (staged before the product overwrites them)
-  g.uc0 = K0 + KB;   // of the columns beyond the block
+  float2* S = reinterpret_cast<float2*>(lu.S);
+  // C and U: the block's rows of the columns beyond it (U staged before the product)
+  g.C = S; g.ldc = lu.ld; g.strc = lu.stride; g.cr = K0; g.cc = K0 + KB;
+  g.U = S; g.ldu = lu.ld; g.stru = lu.stride; g.ur = K0; g.uc = K0 + KB;
+  g.L = T; g.ldl = KB; g.strl = (long long)KB * KB; g.lr = 0; g.lc = 0; g.opL = OP_N;
   g.M = KB;
   g.N = lu.n - K0 - KB;
   g.K = KB;
   g.q = lu.q;
-  g.L = T;
-  g.ldl = KB;
-  g.strl = (long long)KB * KB;
   if (g.N <= 0) return cudaSuccess;
   cudaError_t e = deep_stage(g, st, s);
   if (e != cudaSuccess) return e;
   return deep_run(g, 0, g.N, st, lu.flags, s);
+}
+
+cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, int KB, const float2* TL,
+                          const float2* TU, const DeepStaging& st, cudaStream_t s) {
+  const int n = lu.n, q = lu.q, nB = (n + KB - 1) / KB;
+  if (m < 1 || m > st.cols_max || KB % 64 || KB > 256) return cudaErrorInvalidValue;
+  float2* S = reinterpret_cast<float2*>(lu.S);
+  const long long tstr = (long long)KB * KB, xs = (long long)n * m;
+  auto gemm = [&](const float2* L, long long ldl, long long strl, int lr, int lc, int opL, int M, int K, int rowC,
+                  int rowU) -> cudaError_t {
+    if (M <= 0 || K <= 0) return cudaSuccess;
+    DeepGemm g;
+    g.C = X; g.ldc = n; g.strc = xs; g.cr = rowC; g.cc = 0;
+    g.L = L; g.ldl = ldl; g.strl = strl; g.lr = lr; g.lc = lc; g.opL = opL;
+    g.U = X; g.ldu = n; g.stru = xs; g.ur = rowU; g.uc = 0;
+    g.M = M; g.N = m; g.K = K; g.q = q;
+    cudaError_t e = deep_stage(g, st, s);
+    if (e != cudaSuccess) return e;
+    return deep_run(g, 0, m, st, lu.flags, s);
+  };
+  auto Tof = [&](const float2* T, int I) { return T + (size_t)I * q * KB * KB; };
+  const int op = side == 0 ? OP_N : OP_C;
+  const float2* Tfwd = side == 0 ? TL : TU;  // forward sweep: L (right) or U^H (left)
+  const float2* Tbwd = side == 0 ? TU : TL;  // backward sweep: U (right) or L^H (left)
+  cudaError_t e;
+  for (int I = 0; I < nB; ++I) {
+    const int r0 = KB * I, nr = std::min(KB, n - r0);
+    if ((e = gemm(Tof(Tfwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0)) != cudaSuccess) return e;
+    // rows below: right L[r0+nr:, r0:r0+nr]; left (U[r0:r0+nr, r0+nr:])^H
+    if ((e = gemm(S, lu.ld, lu.stride, r0 + nr, r0, op, n - r0 - nr, nr, r0 + nr, r0)) != cudaSuccess) return e;
+  }
+  for (int I = nB - 1; I >= 0; --I) {
+    const int r0 = KB * I, nr = std::min(KB, n - r0);
+    if ((e = gemm(Tof(Tbwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0)) != cudaSuccess) return e;
+    // rows above: right U[0:r0, r0:r0+nr]; left (L[r0:r0+nr, 0:r0])^H
+    if ((e = gemm(S, lu.ld, lu.stride, 0, r0, op, r0, nr, 0, r0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 double tc_deep_flops(long long n, int q, int K0, int KB) {

@@ -18,17 +18,24 @@ struct DeepStaging {
 size_t deep_staging_bytes_A(long long n, int q);
 size_t deep_staging_bytes_B(long long n, int q);
 
-// One batched product C_b -= L_b U_b (complex64, column-major, same ld and
-// batch stride for all three):  L = S[lr0 : lr0+M, kc0 : kc0+K],
-// U = S[kc0 : kc0+K, uc0 : uc0+N],  C = S[lr0 : lr0+M, uc0 : uc0+N].
-// With L set, the L operand is L_b[i + k ldl] (matrix b at L + b strl) instead.
+// One batched product C_b -= op(L)_b U_b (complex64, column-major, matrix b
+// of each operand at its base + b x its batch stride):
+//   C (M x N): C_b[(cr + i) + (cc + j) ldc]
+//   L (M x K): opL = OP_N: L_b[(lr + i) + (lc + k) ldl];
+//              opL = OP_C: conj(L_b[(lc + k) + (lr + i) ldl])  (a block of L^H)
+//   U (K x N): U_b[(ur + k) + (uc + j) ldu]
+// Both operands are staged before the product runs, so C may overlap U.
 struct DeepGemm {
-  float2* S = nullptr;
-  long long ld = 0, stride = 0;
-  int lr0 = 0, kc0 = 0, uc0 = 0;
-  int M = 0, N = 0, K = 0, q = 0;
+  float2* C = nullptr;
+  long long ldc = 0, strc = 0;
+  int cr = 0, cc = 0;
   const float2* L = nullptr;
   long long ldl = 0, strl = 0;
+  int lr = 0, lc = 0, opL = 0;
+  const float2* U = nullptr;
+  long long ldu = 0, stru = 0;
+  int ur = 0, uc = 0;
+  int M = 0, N = 0, K = 0, q = 0;
 };
 
 // Stage L (rows 0..M) and U (columns 0..N) as split BF16 (one launch).
@@ -45,12 +52,23 @@ cudaError_t tc_deep_stage(const LuBatch<float>& lu, int K0, int KB, const DeepSt
 cudaError_t tc_deep_run(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s);
 // The far step of outer block [K0, K0+KB) in one product: with
 // T = I - L11^{-1} (L11 the block's unit lower KB x KB diagonal block, T made
-// by unit_lower_inverse_complement), the block's rows of the columns beyond it
+// by block_inverse_complement), the block's rows of the columns beyond it
 // become S[K0:K0+KB, K0+KB:] -= T S[K0:K0+KB, K0+KB:] = L11^{-1} S[K0:K0+KB, K0+KB:]
 // (the operands are staged before the product, so it may run in place).
 // The caller has applied every panel's interchanges to those columns.
 cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* T, const DeepStaging& st,
                         cudaStream_t s);
+// Blocked triangular solves with the stored factors of all q shifts, in
+// diagonal blocks of KB rows: side 0 overwrites X (q x n x m, ld n, holding
+// P R) with S^{-1} R (forward with L, backward with U); side 1 overwrites X
+// (holding R) with the solution of S^H X = R before its final P^T (forward
+// with U^H, backward with L^H).  Each block step is two deep products: the
+// diagonal block by X_I -= T_I X_I with T_I = I - D_I^{-1} (TL for the unit
+// lower blocks, TU for the upper ones, conjugate-transposed on side 1; made by
+// block_inverse_complement), then the rest of the sweep's rows by
+// X_rest -= op(S_block) X_I with K = KB.
+cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, int KB, const float2* TL,
+                          const float2* TU, const DeepStaging& st, cudaStream_t s);
 // Algorithmic flops and HBM bytes of one such update (8 flops per complex MAC;
 // C read and written once, L and U read once, 8 bytes per complex64 entry).
 double tc_deep_flops(long long n, int q, int K0, int KB);

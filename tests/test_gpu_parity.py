@@ -172,6 +172,30 @@ def test_two_level_factor_and_solves_ragged_n1100(lu_outer):
                 assert colerr(X, Xr).max() <= solve_column_bound(kappa, n, "mixed"), (k, side)
 
 
+def test_blocked_deep_solves_filter_ragged_n1100():
+    """With the two-level factors the filter's solves run in diagonal blocks of
+    256 rows (X_I -= (I - D_I^{-1}) X_I, then K = 256 updates of the other rows,
+    conjugate-transposed on the left); n = 1100 leaves a ragged last block.
+    Both filters against the oracle's, column by column within the bound."""
+    fg = lib()
+    cfg = workloads.gaussian_pencil(n=1100, seed=14, m0=16, K=2, zero_block=17)
+    A, B = cfg["A"], cfg["B"]
+    n = A.shape[0]
+    h = make(fg, cfg, "mixed", B=B)
+    z, w = fg.feast_get_quadrature(h)
+    factors = feast.factor_shifts(A, B, z)
+    kappa = [np.linalg.cond(zk * B - A) for zk in z]
+    Y, Yh = cfg["U0"], cfg["Vrand"]
+    Q, Qh = fg.feast_filter(h, Y, Yh)
+    assert fg.feast_get_stats(h)["lu_outer"] == 256
+    Qr = feast.filter_right(factors, B, w, Y)
+    Qhr = feast.filter_left(factors, B, w, Yh)
+    bq = filter_column_bound(factors, w, B @ Y, kappa, n, "mixed", side=0)
+    bqh = filter_column_bound(factors, w, B.conj().T @ Yh, kappa, n, "mixed", side=1)
+    assert (np.linalg.norm(Q - Qr, axis=0) <= bq).all(), (np.linalg.norm(Q - Qr, axis=0) / bq).max()
+    assert (np.linalg.norm(Qh - Qhr, axis=0) <= bqh).all(), (np.linalg.norm(Qh - Qhr, axis=0) / bqh).max()
+
+
 @pytest.mark.parametrize("n,panel_cluster", [(2048, 0), (2100, 0), (2100, -1)])
 def test_cluster_panel_factor_backward_error(n, panel_cluster):
     """Panels of 1024 rows and more factored by a cluster of four CTAs per shift
