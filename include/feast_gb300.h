@@ -139,6 +139,10 @@ typedef struct {
                         on a thread-block cluster of four CTAs per system;
                         k > 0 = from k rows on (k >= 256); -1 = one CTA per
                         system                                                 */
+  int deep_solves;   /* MIXED, two-level LU: 0 (default) = the filter's solves
+                        in diagonal blocks of lu_outer rows (the stored D^{-1}
+                        of each block, K = lu_outer updates); -1 = 64-row
+                        blocks                                                 */
 } feast_options;
 
 typedef struct {

@@ -204,7 +204,7 @@ struct feast_handle {
   TcStaging staging;
   DeepStaging deep;                    // the two-level LU's deep-update operands (and the right solves')
   DeepStaging deep_left;               // the left solves' own (they run beside the right ones)
-  // I - D^{-1} of every diagonal block (lu_outer columns) of the unit lower L and
+  // -D^{-1} of every diagonal block (lu_outer columns) of the unit lower L and
   // of the upper U, for the far steps of the LU and the blocked solves
   float2 *TL = nullptr, *TU = nullptr;
   int nblk = 0;
@@ -406,7 +406,7 @@ cudaError_t timed_update(const LuBatch<T>& lu, int k0, int w, int c0, int nc, bo
 
 // The far step of the two-level LU: every panel's interchanges on the columns
 // beyond the block, then U12 = L11^{-1} A12 as one deep product with
-// T = I - L11^{-1} (timed with the deep updates).
+// T = -L11^{-1} that overwrites A12 (timed with the deep updates).
 cudaError_t far_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStream_t s) {
   feast_handle* h = reinterpret_cast<feast_handle*>(c);
   const int far0 = K0 + KB, nfar = lu.n - far0;
@@ -415,9 +415,9 @@ cudaError_t far_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStre
     cudaError_t e = laswp_moved_rows(lu, k0, far0, nfar, s);
     if (e != cudaSuccess) return e;
   }
-  // T = I - L11^{-1} of this block, kept for the solves (block-major, all blocks)
+  // T = -L11^{-1} of this block, kept for the solves (block-major, all blocks)
   float2* T = h->TL + (size_t)(K0 / KB) * lu.q * KB * KB;
-  cudaError_t e = block_inverse_complement(lu, false, KB, K0 / KB, 1, T, s);
+  cudaError_t e = block_inverse_negated(lu, false, KB, K0 / KB, 1, T, s);
   if (e != cudaSuccess) return e;
   const bool timing = h->opt.timing && 2 * h->n_deep + 1 < (int)h->deep_ev.size();
   if (timing) cudaEventRecord(h->deep_ev[2 * h->n_deep], s);
@@ -483,12 +483,12 @@ feast_status factor_impl(feast_handle* h) {
         }
       }
       CK(lu_factor_two_level(lu, 64, h->lu_outer, use_upd, use_ctx, far_hook, deep_hook, h, h->st));
-      // I - D^{-1} of the last L block (the far steps made the others) and of every
+      // -D^{-1} of the last L block (the far steps made the others) and of every
       // U block, for the blocked solves
       const int KB = h->lu_outer;
-      CK(block_inverse_complement(lu, false, KB, h->nblk - 1, 1, h->TL + (size_t)(h->nblk - 1) * h->q * KB * KB,
+      CK(block_inverse_negated(lu, false, KB, h->nblk - 1, 1, h->TL + (size_t)(h->nblk - 1) * h->q * KB * KB,
                                   h->st));
-      CK(block_inverse_complement(lu, true, KB, 0, h->nblk, h->TU, h->st));
+      CK(block_inverse_negated(lu, true, KB, 0, h->nblk, h->TU, h->st));
     } else {
       CK(lu_factor_batched<T>(lu, h->nb, use_upd, use_ctx, h->st));
     }
@@ -644,13 +644,13 @@ feast_status refine_alloc(feast_handle* h) {
 
 // Right: Q = c0 .* Y + sum_k coef_k .* S_k^{-1} R;  left: Qh = c0h .* Yh + sum_k coefh_k .* S_k^{-H} Rh
 // The filter's triangular solves of all shifts: with the two-level factors the
-// blocked deep-K form (diagonal blocks through I - D^{-1}, K = lu_outer
-// updates), else the 64-row block form.
+// blocked deep-K form (diagonal blocks through -D^{-1}, K = lu_outer updates),
+// else the 64-row block form.
 template <typename T>
 cudaError_t solve_all(feast_handle* h, const LuBatch<T>& lu, int side, cplx<T>* X, int m, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     const DeepStaging& st = side == 0 ? h->deep : h->deep_left;
-    if (h->lu_outer > 0 && h->TU && st.Ast && m <= st.cols_max && h->n > 2 * h->lu_outer)
+    if (h->opt.deep_solves >= 0 && h->lu_outer > 0 && h->TU && st.Ast && m <= st.cols_max)
       return tc_solve_deep(lu, side, X, m, h->lu_outer, h->TL, h->TU, st, s);
   }
   return lu_solve_batched<T>(lu, side, X, m, h->nbs, s);

@@ -274,7 +274,7 @@ k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, in
   }
 }
 
-// T = I - D^{-1} for diagonal blocks D of the factor: D = the unit lower part
+// T = -D^{-1} for diagonal blocks D of the factor: D = the unit lower part
 // (UPPER = false) or the upper part with its diagonal (UPPER = true) of
 // S[r0:r0+KB, r0:r0+KB], r0 = KB * block; rows and columns at or beyond n act as
 // the identity (a ragged last block).  One CTA per (64-column block j of the
@@ -282,7 +282,9 @@ k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, in
 // each 64-row block I reached from j (downward for L, upward for U), the
 // products with the blocks of X already solved (D from global memory through
 // shared memory, X in shared memory), then the 64 x 64 triangular solve (four
-// threads per column, one barrier per step).  T goes to
+// threads per column, one barrier per step).  With T, a product that
+// overwrites its output (C = 0 - T X) gives D^{-1} X without cancelling
+// against X.  T goes to
 // T + ((block - block0) q + shift) KB^2, column-major with leading dimension KB.
 template <bool UPPER>
 __global__ void __launch_bounds__(256)
@@ -357,7 +359,7 @@ k_block_tri_inv(const float2* S, long long ld, long long stride, int n, int KB, 
     const int r = e % KB, cc = e / KB, col = 64 * j + cc;
     const bool solved = UPPER ? r < 64 * (j + 1) : r >= 64 * j;
     const float2 x = solved ? X[(size_t)r * 64 + cc] : make_float2(0.f, 0.f);
-    Tb[(size_t)r + (size_t)col * KB] = make_float2((r == col ? 1.f : 0.f) - x.x, -x.y);
+    Tb[(size_t)r + (size_t)col * KB] = make_float2(-x.x, -x.y);
   }
 }
 
@@ -754,8 +756,8 @@ cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int nco
   return cudaGetLastError();
 }
 
-cudaError_t block_inverse_complement(const LuBatch<float>& lu, bool upper, int KB, int block0, int nblocks, float2* T,
-                                     cudaStream_t s) {
+cudaError_t block_inverse_negated(const LuBatch<float>& lu, bool upper, int KB, int block0, int nblocks, float2* T,
+                                   cudaStream_t s) {
   if (KB % 64 || KB > 256 || KB < 64 || nblocks < 1 || block0 < 0 || (long long)KB * (block0 + nblocks - 1) >= lu.n)
     return cudaErrorInvalidValue;
   const size_t smem = (size_t)KB * 64 * sizeof(float2) + 64 * 65 * sizeof(float2);

@@ -62,13 +62,13 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu, int nb, TrailingUpdateFn<T> 
 // block's rows), and deep(lu, K0, KB) subtracts the K = KB product of the
 // block's L and U from everything below and to the right of it.
 using FarFn = cudaError_t (*)(const LuBatch<float>& lu, int K0, int KB, void* ctx, cudaStream_t s);
-// T = I - D^{-1} for the diagonal blocks block0 .. block0+nblocks-1 of size KB
+// T = -D^{-1} for the diagonal blocks block0 .. block0+nblocks-1 of size KB
 // (a multiple of 64, at most 256) of every shift: D the unit lower part of the
 // factor (upper = false) or its upper part with the diagonal (upper = true);
 // rows and columns beyond n act as the identity.  T holds nblocks x q matrices
 // KB x KB, column-major with leading dimension KB, block-major.
-cudaError_t block_inverse_complement(const LuBatch<float>& lu, bool upper, int KB, int block0, int nblocks, float2* T,
-                                     cudaStream_t s);
+cudaError_t block_inverse_negated(const LuBatch<float>& lu, bool upper, int KB, int block0, int nblocks, float2* T,
+                                  cudaStream_t s);
 // The moved rows of the panel at k0 (its list in lu.mv) applied to the columns
 // col0 .. col0+ncols-1 of every shifted matrix.
 cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int ncols, cudaStream_t s);

@@ -64,6 +64,7 @@ struct DeepArgs {
   int b_col0;          // first staged U~ row (column of U) of this launch
   int nkb;             // K blocks of 64 bf16
   int row_tiles, col_tiles, q;
+  int overwrite;       // C = -D (C not read)
   unsigned* flags;
 };
 
@@ -189,7 +190,7 @@ k_tc_deep(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
           const int col = cbase + u;
-          cv[u] = (row_ok && col < a.N) ? __ldcs(Cb + R + (size_t)col * a.ld2) : 0.f;
+          cv[u] = (row_ok && col < a.N && !a.overwrite) ? __ldcs(Cb + R + (size_t)col * a.ld2) : 0.f;
         }
         const unsigned taddr = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * DK_BN + cl);
         tmem_ld16(taddr, *reinterpret_cast<float(*)[16]>(&v[0]));
@@ -367,6 +368,7 @@ cudaError_t deep_run(const DeepGemm& g, int c0, int nc, const DeepStaging& st, u
   a.row_tiles = (int)ceil_div((size_t)a.M2, DK_BM);
   a.col_tiles = (int)ceil_div((size_t)nc, DK_BN);
   a.q = g.q;
+  a.overwrite = g.overwrite ? 1 : 0;
   a.flags = flags;
   static bool attr = false;
   if (!attr) {
@@ -420,6 +422,7 @@ cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* 
   g.N = lu.n - K0 - KB;
   g.K = KB;
   g.q = lu.q;
+  g.overwrite = true;
   if (g.N <= 0) return cudaSuccess;
   cudaError_t e = deep_stage(g, st, s);
   if (e != cudaSuccess) return e;
@@ -433,13 +436,14 @@ cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, 
   float2* S = reinterpret_cast<float2*>(lu.S);
   const long long tstr = (long long)KB * KB, xs = (long long)n * m;
   auto gemm = [&](const float2* L, long long ldl, long long strl, int lr, int lc, int opL, int M, int K, int rowC,
-                  int rowU) -> cudaError_t {
+                  int rowU, bool overwrite = false) -> cudaError_t {
     if (M <= 0 || K <= 0) return cudaSuccess;
     DeepGemm g;
     g.C = X; g.ldc = n; g.strc = xs; g.cr = rowC; g.cc = 0;
     g.L = L; g.ldl = ldl; g.strl = strl; g.lr = lr; g.lc = lc; g.opL = opL;
     g.U = X; g.ldu = n; g.stru = xs; g.ur = rowU; g.uc = 0;
     g.M = M; g.N = m; g.K = K; g.q = q;
+    g.overwrite = overwrite;
     cudaError_t e = deep_stage(g, st, s);
     if (e != cudaSuccess) return e;
     return deep_run(g, 0, m, st, lu.flags, s);
@@ -451,13 +455,13 @@ cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, 
   cudaError_t e;
   for (int I = 0; I < nB; ++I) {
     const int r0 = KB * I, nr = std::min(KB, n - r0);
-    if ((e = gemm(Tof(Tfwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0)) != cudaSuccess) return e;
+    if ((e = gemm(Tof(Tfwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0, true)) != cudaSuccess) return e;
     // rows below: right L[r0+nr:, r0:r0+nr]; left (U[r0:r0+nr, r0+nr:])^H
     if ((e = gemm(S, lu.ld, lu.stride, r0 + nr, r0, op, n - r0 - nr, nr, r0 + nr, r0)) != cudaSuccess) return e;
   }
   for (int I = nB - 1; I >= 0; --I) {
     const int r0 = KB * I, nr = std::min(KB, n - r0);
-    if ((e = gemm(Tof(Tbwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0)) != cudaSuccess) return e;
+    if ((e = gemm(Tof(Tbwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0, true)) != cudaSuccess) return e;
     // rows above: right U[0:r0, r0:r0+nr]; left (L[r0:r0+nr, 0:r0])^H
     if ((e = gemm(S, lu.ld, lu.stride, 0, r0, op, r0, nr, 0, r0)) != cudaSuccess) return e;
   }

@@ -36,6 +36,7 @@ struct DeepGemm {
   long long ldu = 0, stru = 0;
   int ur = 0, uc = 0;
   int M = 0, N = 0, K = 0, q = 0;
+  bool overwrite = false;  // C = -op(L) U instead of C -= op(L) U (C is not read)
 };
 
 // Stage L (rows 0..M) and U (columns 0..N) as split BF16 (one launch).
@@ -51,9 +52,9 @@ bool deep_fits(const DeepGemm& g, const DeepStaging& st);
 cudaError_t tc_deep_stage(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s);
 cudaError_t tc_deep_run(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s);
 // The far step of outer block [K0, K0+KB) in one product: with
-// T = I - L11^{-1} (L11 the block's unit lower KB x KB diagonal block, T made
-// by block_inverse_complement), the block's rows of the columns beyond it
-// become S[K0:K0+KB, K0+KB:] -= T S[K0:K0+KB, K0+KB:] = L11^{-1} S[K0:K0+KB, K0+KB:]
+// T = -L11^{-1} (L11 the block's unit lower KB x KB diagonal block, T made by
+// block_inverse_negated), the block's rows of the columns beyond it become
+// S[K0:K0+KB, K0+KB:] = -T S[K0:K0+KB, K0+KB:] = L11^{-1} S[K0:K0+KB, K0+KB:]
 // (the operands are staged before the product, so it may run in place).
 // The caller has applied every panel's interchanges to those columns.
 cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* T, const DeepStaging& st,
@@ -63,9 +64,9 @@ cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* 
 // P R) with S^{-1} R (forward with L, backward with U); side 1 overwrites X
 // (holding R) with the solution of S^H X = R before its final P^T (forward
 // with U^H, backward with L^H).  Each block step is two deep products: the
-// diagonal block by X_I -= T_I X_I with T_I = I - D_I^{-1} (TL for the unit
-// lower blocks, TU for the upper ones, conjugate-transposed on side 1; made by
-// block_inverse_complement), then the rest of the sweep's rows by
+// diagonal block by X_I = -T_I X_I with T_I = -D_I^{-1} (TL for the unit lower
+// blocks, TU for the upper ones, conjugate-transposed on side 1; made by
+// block_inverse_negated), then the rest of the sweep's rows by
 // X_rest -= op(S_block) X_I with K = KB.
 cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, int KB, const float2* TL,
                           const float2* TU, const DeepStaging& st, cudaStream_t s);

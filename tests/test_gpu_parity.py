@@ -174,9 +174,10 @@ def test_two_level_factor_and_solves_ragged_n1100(lu_outer):
 
 def test_blocked_deep_solves_filter_ragged_n1100():
     """With the two-level factors the filter's solves run in diagonal blocks of
-    256 rows (X_I -= (I - D_I^{-1}) X_I, then K = 256 updates of the other rows,
-    conjugate-transposed on the left); n = 1100 leaves a ragged last block.
-    Both filters against the oracle's, column by column within the bound."""
+    256 rows (X_I = D_I^{-1} X_I as a product with the stored -D_I^{-1}, then
+    K = 256 updates of the other rows, conjugate-transposed on the left); n = 1100
+    leaves a ragged last block.  Both filters against the oracle's, column by
+    column within the bound, and against the 64-row block solves."""
     fg = lib()
     cfg = workloads.gaussian_pencil(n=1100, seed=14, m0=16, K=2, zero_block=17)
     A, B = cfg["A"], cfg["B"]
@@ -194,6 +195,12 @@ def test_blocked_deep_solves_filter_ragged_n1100():
     bqh = filter_column_bound(factors, w, B.conj().T @ Yh, kappa, n, "mixed", side=1)
     assert (np.linalg.norm(Q - Qr, axis=0) <= bq).all(), (np.linalg.norm(Q - Qr, axis=0) / bq).max()
     assert (np.linalg.norm(Qh - Qhr, axis=0) <= bqh).all(), (np.linalg.norm(Qh - Qhr, axis=0) / bqh).max()
+    h64 = make(fg, cfg, "mixed", B=B, deep_solves=-1)
+    Q6, Qh6 = fg.feast_filter(h64, Y, Yh)
+    e_deep = (colerr(Q, Qr).max(), colerr(Qh, Qhr).max())
+    e_64 = (colerr(Q6, Qr).max(), colerr(Qh6, Qhr).max())
+    print("deep", e_deep, "64-row", e_64)
+    assert max(e_deep) <= 10 * max(e_64)  # the blocked form keeps the accuracy of the 64-row solves
 
 
 @pytest.mark.parametrize("n,panel_cluster", [(2048, 0), (2100, 0), (2100, -1)])
