@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--panel-cluster", type=int, default=0,
                    help="0 = library default or tuned, k > 0 = cluster panels from k rows, -1 = one CTA")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    p.add_argument("--deep-solves", type=int, default=0,
+                   help="0 = the filter's solves in 256-row blocks (two-level factors), -1 = 64-row blocks")
     p.add_argument("--lu-outer", type=int, default=0,
                    help="outer block of the two-level LU (0 = library default, -1 = one-level)")
     return p.parse_args()
@@ -475,7 +477,8 @@ def run_ours(args):
         tune = {"key": key, "choice": {"lu_outer": entry["lu_outer"], "panel_cluster": entry["panel_cluster"]},
                 "factor_ms_by_candidate": times, "tuning_s": time.perf_counter() - t0}
     opts = fg.make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True,
-                           lu_outer=args.lu_outer, panel_cluster=args.panel_cluster, tune_cache=tune_cache)
+                           lu_outer=args.lu_outer, panel_cluster=args.panel_cluster, tune_cache=tune_cache,
+                           deep_solves=args.deep_solves)
     h = fg.feast_create(A_d, B_d, contour, m0, opts, stream=stream)
     # the residual gate: a full solve from the same start block
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
