@@ -337,11 +337,11 @@ def trailing_update_bytes(n, q, nb):
     return q * tot
 
 
-def profiled_traffic_ratio():
-    """DRAM bytes per algorithmic byte of the trailing-update kernel, from the
-    committed ncu summary (None when absent)."""
+def profiled_traffic_ratio(name="k_tc_update_c_bifeast_n2048_mixed.md"):
+    """DRAM bytes per algorithmic byte of a kernel, from its committed ncu
+    summary (None when absent)."""
     import re
-    path = os.path.join(ROOT, "profiles", "k_tc_update_c_bifeast_n2048_mixed.md")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         m = re.search(r"traffic_per_algorithmic_byte:\s*([0-9.]+)", open(path).read())
         return float(m.group(1)) if m else None
@@ -599,6 +599,7 @@ def run_ours(args):
     if bf16 is None:
         bf16, bf16_note = 1900.0, "profiling recipe fallback 1.9 PFLOP/s (of fallback)"
     ratio = profiled_traffic_ratio()
+    deep_ratio = profiled_traffic_ratio("k_tc_deep_bifeast_n2048_mixed.md")
 
     def frame(t_ms, launches, flops, nbytes):
         if t_ms <= 0 or launches <= 0:
@@ -618,7 +619,11 @@ def run_ours(args):
                               "K streamed by TMA, persistent)",
                     "bound": "tensor", "achieved": deep["algorithmic_tflops"], "peak": bf16 / 3.0,
                     "unit": "TFLOP/s", "frac": deep["algorithmic_tflops"] / (bf16 / 3.0),
-                    "traffic": None, "launches": deep["launches"], "avg_launch_ms": deep["avg_launch_ms"],
+                    "traffic": (deep_ratio * deep["bytes_per_launch"]) if deep_ratio else None,
+                    "traffic_note": "DRAM bytes per launch: the n = 2048 capture's DRAM / algorithmic byte ratio "
+                                    "(profiles/k_tc_deep_bifeast_n2048_mixed.md) times this launch's algorithmic "
+                                    "bytes (C streamed once, so traffic grows with the algorithmic bytes)",
+                    "launches": deep["launches"], "avg_launch_ms": deep["avg_launch_ms"],
                     "algorithmic_flops_per_launch": deep["flops_per_launch"],
                     "peak_note": f"{bf16_note} / 3: the split-BF16 product issues 3 BF16 MMA flops per algorithmic "
                                  "flop", "hbm_frame": {"achieved": deep["achieved_gbs"], "peak": hbm,
