@@ -352,8 +352,9 @@ def profiled_traffic_ratio(name="k_tc_update_c_bifeast_n2048_mixed.md"):
 def run_batch(fg, torch, args, barrier):
     """The batched workload: 64 standard pencils, n log-uniform in [256, 2048],
     20-80 eigenvalues inside each circle, 8 midpoint nodes each (512 shifted
-    matrices), R-FEAST in mixed precision, the factorisations and solves in
-    one persistent launch."""
+    matrices), R-FEAST in mixed precision.  Pencils of order >= 768 are
+    factored by the tensor-core LU in classes of equal padded order; the other
+    factorisations and all solves run in one persistent launch."""
     import workloads
     rank = dist_env()[0]
     cfgs = workloads.batch_prescribed(count=args.batch_count, seed=rank_seeds(rank)["batch"])
@@ -364,6 +365,7 @@ def run_batch(fg, torch, args, barrier):
     Y_d = [colmajor_device(torch, c["U0"]) for c in cfgs]
     b = fg.feast_batch_create(A_d, cons, [c["m0"] for c in cfgs], opts)
     info = fg.feast_batch_info(b)
+    tci = fg.feast_batch_tc_info(b)
     for _ in range(max(1, args.warmup)):
         fg.feast_batch_factor(b)
     lu = []
@@ -396,7 +398,8 @@ def run_batch(fg, torch, args, barrier):
                          "[256, 2048], 20-80 eigenvalues inside each circle, 8 midpoint nodes, m0 in 32..128, "
                          "R-FEAST mixed"),
             "pencils": info["count"], "shifted_matrices": info["nmat"], "persistent_ctas": info["grid"],
-            "factor_tasks": info["tasks_factor"], "lu_ms": lu_ms,
+            "factor_tasks": info["tasks_factor"], "tc_min": tci["tc_min"], "tc_classes": tci["classes"],
+            "tc_matrices": tci["matrices"], "lu_ms": lu_ms,
             "lu_tflops": info["lu_flops"] / (lu_ms * 1e-3) / 1e12,
             "iter1_ms": it[0] if it else None, "steady_iter_ms": float(np.median(it[1:])) if len(it) > 1 else None,
             "iters": st["iters"], "converged": st["converged"], "counts_exact": count_ok,

@@ -143,6 +143,13 @@ typedef struct {
                         in diagonal blocks of lu_outer rows (the stored D^{-1}
                         of each block, K = lu_outer updates); -1 = 64-row
                         blocks                                                 */
+  int batch_tc_min;  /* batched path: shifted matrices of pencils of order
+                        >= batch_tc_min (at least 512) are padded to a multiple
+                        of 256 and factored by the tensor-core LU in classes of
+                        equal padded order (two-level from 1024 on), the rest
+                        by the persistent launch; 0 (default) = the tuned
+                        value of options.tune_cache, else 768; -1 = every
+                        matrix in the persistent launch                        */
 } feast_options;
 
 typedef struct {
@@ -363,8 +370,12 @@ feast_status feast_norm2_estimate_static(const feast_z* A, int64_t n, int64_t ld
  * z I - A_p with partial pivoting (complex64, padded to a multiple of 64) and
  * solves them for their pencil's right-hand sides.  A device task queue in an
  * order planned on the host drives it: critical path first, largest pencils
- * first.  The Rayleigh-Ritz steps run as grouped kernels (one launch per step
- * for all pencils), and the steady iterations replay one CUDA graph.
+ * first.  Pencils of order >= opts.batch_tc_min (default 768) are instead
+ * factored by the tensor-core LU of the single-pencil path, in classes of
+ * equal padded order (a multiple of 256), each class on its own stream before
+ * the persistent launch, which then only solves them.  The Rayleigh-Ritz
+ * steps run as grouped kernels (one launch per step for all pencils), and the
+ * steady iterations replay one CUDA graph.
  *
  *   n        : count orders, 1 <= n[p] <= 4096.
  *   A        : count pointers to n[p] x n[p] column-major matrices (host or
@@ -421,6 +432,10 @@ feast_status feast_batch_get_factor(feast_batch* b, int pencil, int shift, feast
  * the algorithmic LU flops sum_i 8/3 n_i^3. Any output may be NULL. */
 feast_status feast_batch_info(const feast_batch* b, int* count, int* nmat, int* grid, int* tasks_factor,
                               double* plan_makespan_us, double* lu_flops);
+/* The tensor-core classes of the batch: the order from which pencils join
+ * them (0 = none), the number of classes (distinct padded orders) and of
+ * shifted matrices they hold. Any output may be NULL. */
+feast_status feast_batch_tc_info(const feast_batch* b, int* tc_min, int* classes, int* matrices);
 /* The host scheduler alone (no GPU): the task order of the persistent launch
  * for nmat matrices with nb[i] = ceil(n_i / 64) block columns and m[i]
  * right-hand sides on `workers` CTAs, with factorisation tasks (with_lu) and/or

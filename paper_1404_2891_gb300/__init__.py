@@ -55,7 +55,7 @@ class feast_options(ctypes.Structure):
                 ("timing", ctypes.c_int), ("symmetric", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("shift_begin", ctypes.c_int), ("shift_end", ctypes.c_int),
                 ("real_pencil", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("lu_outer", ctypes.c_int),
-                ("panel_cluster", ctypes.c_int), ("deep_solves", ctypes.c_int)]
+                ("panel_cluster", ctypes.c_int), ("deep_solves", ctypes.c_int), ("batch_tc_min", ctypes.c_int)]
 
 
 class feast_segment(ctypes.Structure):
@@ -92,7 +92,7 @@ SYMBOLS = ("feast_default_options", "feast_create", "feast_destroy", "feast_stat
            "feast_mlp_param_count", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_get_params",
            "feast_mlp_predict", "feast_mlp_grad", "feast_mlp_train",
            "feast_batch_create", "feast_batch_destroy", "feast_batch_factor", "feast_batch_filter",
-           "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_plan",
+           "feast_batch_solve", "feast_batch_get_factor", "feast_batch_info", "feast_batch_tc_info", "feast_batch_plan",
            "feast_emulated_zgemm", "feast_orthonormalize", "feast_set_wait_limit", "feast_contour_nodes",
            "feast_piecewise_nodes", "feast_eta_indicator", "feast_filter_combine",
            "feast_candidates")
@@ -174,6 +174,8 @@ def load(path=LIB_PATH):
     lib.feast_batch_get_factor.restype = I
     lib.feast_batch_info.argtypes = [P, P, P, P, P, P, P]
     lib.feast_batch_info.restype = I
+    lib.feast_batch_tc_info.argtypes = [P, P, P, P]
+    lib.feast_batch_tc_info.restype = I
     lib.feast_batch_plan.argtypes = [I, P, P, I, I, I, P, I, P, P]
     lib.feast_batch_plan.restype = I
     I64 = ctypes.c_int64
@@ -284,7 +286,7 @@ def make_contour(center=0.0, R=1.0, aspect=1.0, rule="trap_mid", N_e=8, nodes=No
 
 def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False,
                  symmetric=False, max_refine=0, refine_tol=1e-12, shifts=None, real_pencil=False, tune_cache=None,
-                 lu_outer=0, panel_cluster=0, deep_solves=0):
+                 lu_outer=0, panel_cluster=0, deep_solves=0, batch_tc_min=0):
     """shifts: (begin, end) range of the contour's nodes this handle owns (None = all)."""
     o = feast_options()
     load().feast_default_options(ctypes.byref(o))
@@ -300,6 +302,7 @@ def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=
     o.lu_outer = int(lu_outer)
     o.panel_cluster = int(panel_cluster)
     o.deep_solves = int(deep_solves)
+    o.batch_tc_min = int(batch_tc_min)
     return o
 
 
@@ -627,6 +630,14 @@ def feast_batch_info(b):
                                    ctypes.byref(mk), ctypes.byref(fl)), "feast_batch_info")
     return dict(count=c.value, nmat=nm.value, grid=g.value, tasks_factor=t.value, plan_makespan_us=mk.value,
                 lu_flops=fl.value)
+
+
+def feast_batch_tc_info(b):
+    """The batch's tensor-core classes: tc_min (0 = none), classes, matrices."""
+    t, c, m = (ctypes.c_int() for _ in range(3))
+    _check(load().feast_batch_tc_info(b.ptr, ctypes.byref(t), ctypes.byref(c), ctypes.byref(m)),
+           "feast_batch_tc_info")
+    return dict(tc_min=t.value, classes=c.value, matrices=m.value)
 
 
 def feast_batch_plan(nb, m, with_lu=True, with_solve=True, workers=152):

@@ -9,6 +9,9 @@ Single pencil (key "<gpu>|single|n<bucket>|m0<m0>|q<q>|mixed"):
                  the library's 1024) run on a cluster of four CTAs per
                  system; -1: one CTA per system
 Batched path (key "<gpu>|batch|count<pencils>|nmax<bucket>|mixed"):
+  tc_min          order from which pencils are factored by the tensor-core
+                  LU in classes of equal padded order (-1: none); timed first,
+                  with the default launch parameters
   grid            CTAs of the persistent factor/solve launch
   cost_panel_row, cost_update_tile
                   the host scheduler's cost model (per-row panel cost and
@@ -119,9 +122,10 @@ def tune_single(n, m0, K=16, cache="tune.json", candidates=None, reps=2, seed=0,
 
 
 def tune_batch(As, contours, m0, cache="tune.json", grids=None, panel_rows=(0.03, 0.06, 0.12),
-               update_tiles=(3.0, 4.5, 6.0), reps=2, verbose=False):
-    """Time the persistent factorisation launch of a batch for each grid and
-    cost-model candidate (each a fresh batch planned with it) and store the fastest."""
+               update_tiles=(3.0, 4.5, 6.0), tc_mins=None, reps=2, verbose=False):
+    """Time the batch's factorisation for each tensor-core class threshold, then
+    for each grid and cost-model candidate with the best threshold (each a
+    fresh batch planned with it), and store the fastest."""
     opts = lambda path: make_options(algo="R", precision="mixed", timing=True, tune_cache=path)
     b = feast_batch_create(As, contours, m0, opts(None))
     info = feast_batch_info(b)
@@ -131,36 +135,56 @@ def tune_batch(As, contours, m0, cache="tune.json", grids=None, panel_rows=(0.03
     key = batch_key(len(As), nmax)
     if grids is None:
         grids = sorted({resident, max(1, (resident * 7) // 8), max(1, (resident * 3) // 4)}, reverse=True)
+    if tc_mins is None:
+        tc_mins = [v for v in (768, 1024, 1536) if nmax >= v] + [-1]
     import torch
-    times = {}
+
     fd, tmp = tempfile.mkstemp(suffix=".json")
     os.close(fd)
+
+    def timed(entry):
+        with open(tmp, "w") as f:
+            json.dump({key: entry}, f)
+        b = feast_batch_create(As, contours, m0, opts(tmp))
+        feast_batch_factor(b)
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            feast_batch_factor(b)
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        feast_batch_destroy(b)
+        return float(np.median(t))
+
+    times = {}
     try:
+        tc_times = {}
+        for tc in tc_mins:
+            tc_times[tc] = timed({"tc_min": tc})
+            if verbose:
+                print(f"tc_min={tc}: {tc_times[tc]:.2f} ms")
+        tc_best = min(tc_times.items(), key=lambda kv: kv[1])[0] if tc_times else 0
         for g in grids:
             for pr in panel_rows:
                 for ut in update_tiles:
-                    with open(tmp, "w") as f:
-                        json.dump({key: {"grid": g, "cost_panel_row": pr, "cost_update_tile": ut}}, f)
-                    b = feast_batch_create(As, contours, m0, opts(tmp))
-                    feast_batch_factor(b)
-                    t = []
-                    for _ in range(reps):
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        torch.cuda.synchronize()
-                        e0.record()
-                        feast_batch_factor(b)
-                        e1.record()
-                        torch.cuda.synchronize()
-                        t.append(e0.elapsed_time(e1))
-                    feast_batch_destroy(b)
-                    times[(g, pr, ut)] = float(np.median(t))
+                    e = {"grid": g, "cost_panel_row": pr, "cost_update_tile": ut}
+                    if tc_times:
+                        e["tc_min"] = tc_best
+                    times[(g, pr, ut)] = timed(e)
                     if verbose:
                         print(f"grid={g} panel_row={pr} update_tile={ut}: {times[(g, pr, ut)]:.2f} ms")
     finally:
         os.unlink(tmp)
     (g, pr, ut), t = min(times.items(), key=lambda kv: kv[1])
-    entry = {"grid": g, "cost_panel_row": pr, "cost_update_tile": ut, "t_factor_ms": t, "candidates": len(times),
-             "note": f"median of {reps} persistent factorisation launches, {len(As)} pencils"}
+    entry = {"grid": g, "cost_panel_row": pr, "cost_update_tile": ut, "t_factor_ms": t,
+             "candidates": len(times) + len(tc_times),
+             "note": f"median of {reps} factorisations of the batch, {len(As)} pencils"}
+    if tc_times:
+        entry["tc_min"] = tc_best
+        entry["tc_min_ms"] = {str(k): v for k, v in tc_times.items()}
     store(cache, key, entry)
     return key, entry, {f"{a},{b_},{c}": v for (a, b_, c), v in times.items()}
 

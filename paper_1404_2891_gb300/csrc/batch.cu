@@ -25,6 +25,7 @@
 #include <complex>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <new>
 #include <queue>
 #include <cstdio>
@@ -34,9 +35,12 @@
 #include "batch.cuh"
 #include "blas1.cuh"
 #include "gemm.cuh"
+#include "lu.cuh"
 #include "norm2.cuh"
 #include "ozaki.cuh"
 #include "small.cuh"
+#include "tc_deep.cuh"
+#include "tc_update.cuh"
 #include "tune.cuh"
 
 using zc = std::complex<double>;
@@ -63,10 +67,12 @@ double cost_solve(int nb, int w) { return 6.0 * nb + 2.2 * nb * (nb - 1) * (w / 
 struct Plan {
   std::vector<int> nb, m;
   bool lu = true, solve = true;
+  const std::vector<char>* lu_mask = nullptr;  // per matrix: factored here (1) or elsewhere (0)
   std::vector<long long> base;
+  bool lu_of(int i) const { return lu && (!lu_mask || (*lu_mask)[i]); }
   long long count_of(int i) const {
     const long long n = nb[i];
-    return (lu ? n + n * (n - 1) / 2 + (n - 1) : 0) + (solve ? (m[i] + BATCH_SOLVE_W - 1) / BATCH_SOLVE_W : 0);
+    return (lu_of(i) ? n + n * (n - 1) / 2 + (n - 1) : 0) + (solve ? (m[i] + BATCH_SOLVE_W - 1) / BATCH_SOLVE_W : 0);
   }
   long long P(int i, int k) const { return base[i] + k; }
   long long U(int i, int k, int j) const {
@@ -79,19 +85,21 @@ struct Plan {
   }
   long long S(int i, int c) const {
     const long long n = nb[i];
-    return base[i] + (lu ? n + n * (n - 1) / 2 + (n - 1) : 0) + c;
+    return base[i] + (lu_of(i) ? n + n * (n - 1) / 2 + (n - 1) : 0) + c;
   }
   int nch(int i) const { return solve ? (m[i] + BATCH_SOLVE_W - 1) / BATCH_SOLVE_W : 0; }
 };
 
 // Topological task order by list scheduling on `workers` identical workers.
 std::vector<int4> plan_order(const std::vector<int>& nbv, const std::vector<int>& mv, bool lu, bool solve,
-                             int workers, double* makespan, const CostModel& cm = CostModel()) {
+                             int workers, double* makespan, const CostModel& cm = CostModel(),
+                             const std::vector<char>* lu_mask = nullptr) {
   Plan pl;
   pl.nb = nbv;
   pl.m = mv;
   pl.lu = lu;
   pl.solve = solve;
+  pl.lu_mask = lu_mask;
   const int nm = (int)nbv.size();
   pl.base.assign(nm + 1, 0);
   for (int i = 0; i < nm; ++i) pl.base[i + 1] = pl.base[i] + pl.count_of(i);
@@ -101,7 +109,7 @@ std::vector<int4> plan_order(const std::vector<int>& nbv, const std::vector<int>
   std::vector<int> pend(T, 0);
   for (int i = 0; i < nm; ++i) {
     const int nb = nbv[i], ch = pl.nch(i);
-    if (lu) {
+    if (pl.lu_of(i)) {
       for (int k = 0; k < nb; ++k) {
         task[pl.P(i, k)] = make_int4(BT_PANEL, i, k, k);
         cost[pl.P(i, k)] = cost_panel(cm, BATCH_TILE * (nb - k));
@@ -123,11 +131,11 @@ std::vector<int4> plan_order(const std::vector<int>& nbv, const std::vector<int>
       const int w = std::min(BATCH_SOLVE_W, mv[i] - BATCH_SOLVE_W * c);
       task[pl.S(i, c)] = make_int4(BT_SOLVE, i, 0, c);
       cost[pl.S(i, c)] = cost_solve(nb, w);
-      pend[pl.S(i, c)] = lu ? nb : 0;  // the last panel and the nb - 1 fix-ups
+      pend[pl.S(i, c)] = pl.lu_of(i) ? nb : 0;  // the last panel and the nb - 1 fix-ups
       bl[pl.S(i, c)] = cost[pl.S(i, c)];
       maxS = std::max(maxS, bl[pl.S(i, c)]);
     }
-    if (!lu) continue;
+    if (!pl.lu_of(i)) continue;
     double maxL = 0.0;
     for (int j = 0; j + 1 < nb; ++j) {
       bl[pl.L(i, j)] = cost[pl.L(i, j)] + maxS;
@@ -234,6 +242,23 @@ struct feast_batch {
   std::vector<double> R, aspect, normA;
   std::vector<int> fdom;  // per pencil: CUSTOM nodes without an ellipse (domain test by the filter value)
   int tuned = 0;          // launch parameters read from options.tune_cache
+  // tensor-core size classes: pencils of order >= tc_min are padded to a multiple
+  // of 256 and their shifted matrices of one padded order are factored together
+  // by the two-level tcgen05 LU, each class on its own stream
+  struct TcClass {
+    int N = 0, mat0 = 0, count = 0;
+    TcStaging st;
+    DeepStaging dst;
+    float2* T = nullptr;
+    int32_t *mv = nullptr, *pinv = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<TcClass> tcc;
+  int tc_min = 768;
+  std::vector<char> lu_mask;  // per matrix: 1 = factored by the persistent launch
+  int* d_fcnt0 = nullptr;     // per matrix: the completion count a class-factored matrix starts with
+  cudaEvent_t fork_ev = nullptr;
   size_t snn = 0, snm = 0, smm = 0, sm = 0, sqm = 0, slog = 0, sS = 0, sX = 0, sN = 0, snb = 0;
   // device
   GrpDesc* d_pd = nullptr;
@@ -387,14 +412,88 @@ feast_status read_flags(feast_batch* b) {
   return FEAST_OK;
 }
 
-// Persistent launch over one of the task lists.
+// The far and deep steps of a class's two-level LU (Sec. 5.5's factorisations
+// with 256-column outer blocks): every panel's interchanges on the columns
+// beyond the block, U12 = L11^{-1} A12 as one deep product with T = -L11^{-1},
+// then the K = 256 product of the block's L and U off everything below-right.
+cudaError_t class_far(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStream_t s) {
+  const feast_batch::TcClass* cls = reinterpret_cast<const feast_batch::TcClass*>(c);
+  const int far0 = K0 + KB, nfar = lu.n - far0;
+  if (nfar <= 0) return cudaSuccess;
+  cudaError_t e;
+  for (int k0 = K0; k0 < far0; k0 += 64)
+    if ((e = laswp_moved_rows(lu, k0, far0, nfar, s)) != cudaSuccess) return e;
+  if ((e = block_inverse_negated(lu, false, KB, K0 / KB, 1, cls->T, s)) != cudaSuccess) return e;
+  return tc_far_gemm(lu, K0, KB, cls->T, cls->dst, s);
+}
+
+cudaError_t class_deep(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStream_t s) {
+  const feast_batch::TcClass* cls = reinterpret_cast<const feast_batch::TcClass*>(c);
+  cudaError_t e = tc_deep_stage(lu, K0, KB, cls->dst, s);
+  if (e != cudaSuccess) return e;
+  return tc_deep_run(lu, K0, KB, cls->dst, s);
+}
+
+// Every tensor-core class factored on its own stream (forked from and joined
+// back into the batch's stream): the class's shifted matrices are consecutive
+// in every arena with stride N, so one LuBatch view of q = count matrices
+// covers them; the factor lands in the layout the persistent solve tasks read
+// (P S = L U in place, perm with (P S)[r] = S[perm[r]]).
+cudaError_t factor_classes(feast_batch* b) {
+  if (b->tcc.empty()) return cudaSuccess;
+  cudaError_t e;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(b->fork_ev, b->st)) != cudaSuccess) return e;
+  for (feast_batch::TcClass& c : b->tcc) {
+    if ((e = cudaStreamWaitEvent(c.s, b->fork_ev, 0)) != cudaSuccess) return e;
+    const BMat& M0 = b->mats[c.mat0];
+    LuBatch<float> lu;
+    lu.S = b->S + M0.soff;
+    lu.ld = c.N;
+    lu.stride = (long long)c.N * c.N;
+    lu.n = c.N;  // the padding is an identity block: it is never a pivot and stays untouched
+    lu.q = c.count;
+    lu.piv = b->piv + M0.poff;
+    lu.perm = b->perm + M0.poff;
+    lu.pinv = c.pinv;
+    lu.info = b->info + c.mat0;
+    lu.flags = b->flags;
+    lu.tc = &c.st;
+    lu.mv = c.mv;
+    lu.mv_panels = c.N / 64;
+    lu.u12_in_stage = true;
+    // the four-CTA cluster panel while the class's panels alone leave SMs idle
+    lu.panel_cluster = 4 * c.count <= nsm;
+    TrailingUpdateFn<float> upd = nullptr;
+    void* ctx = nullptr;
+    select_trailing_update<float>(&upd, &ctx, &c.st);
+    if (c.dst.Ast)
+      e = lu_factor_two_level(lu, 64, 256, upd, ctx, class_far, class_deep, &c, c.s);
+    else
+      e = lu_factor_batched<float>(lu, 64, upd, ctx, c.s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c.done, c.s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->st, c.done, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Persistent launch over one of the task lists; a factorisation launch runs
+// the tensor-core classes first (the persistent kernel then solves them).
 cudaError_t launch_lu(feast_batch* b, const int4* tasks, int n) {
   if (tasks == b->t_factor || tasks == b->t_first) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(b->cver, 0, b->snb * sizeof(int), b->st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->pdone, 0, b->snb * sizeof(int), b->st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(b->fcnt, 0, b->nmat * sizeof(int), b->st)) != cudaSuccess) return e;
+    if (b->d_fcnt0)
+      e = cudaMemcpyAsync(b->fcnt, b->d_fcnt0, b->nmat * sizeof(int), cudaMemcpyDeviceToDevice, b->st);
+    else
+      e = cudaMemsetAsync(b->fcnt, 0, b->nmat * sizeof(int), b->st);
+    if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->info, 0, b->nmat * sizeof(int), b->st)) != cudaSuccess) return e;
+    if ((e = factor_classes(b)) != cudaSuccess) return e;
   }
   return batch_lu_launch(lu_args(b, tasks, n), b->Nmax, b->grid, b->st);
 }
@@ -555,6 +654,8 @@ extern "C" {
 void feast_batch_destroy(feast_batch* b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
+  for (auto& c : b->tcc)
+    if (c.s) cudaStreamSynchronize(c.s);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (void* p : b->allocs) cudaFree(p);
   for (void* p : {(void*)b->h_coef, (void*)b->h_c0, (void*)b->h_lam, (void*)b->h_use, (void*)b->h_active,
@@ -562,6 +663,11 @@ void feast_batch_destroy(feast_batch* b) {
     if (p) cudaFreeHost(p);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& c : b->tcc) {
+    if (c.s) cudaStreamDestroy(c.s);
+    if (c.done) cudaEventDestroy(c.done);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   delete b;
 }
@@ -644,10 +750,51 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
     b->sm += (size_t)d.m;
     b->sqm += (size_t)d.q * d.m;
     b->slog += (schur_log_bytes(d.m) + 255) / 256 * 256;
-    const int N = (d.n + BATCH_TILE - 1) / BATCH_TILE * BATCH_TILE;
-    b->Nmax = std::max(b->Nmax, N);
     b->nmax = std::max(b->nmax, d.n);
     b->mmax = std::max(b->mmax, d.m);
+  }
+  // padded orders: multiples of 64, or of 256 for the tensor-core classes
+  // (orders from tc_min on; tc_min = 0: none)
+  if (b->opt.batch_tc_min < 0) {
+    b->tc_min = 0;
+  } else if (b->opt.batch_tc_min > 0) {
+    b->tc_min = std::max(512, b->opt.batch_tc_min);
+  } else if (b->opt.tune_cache) {
+    char key[256];
+    std::snprintf(key, sizeof(key), "%s|batch|count%d|nmax%lld|mixed", tune_gpu_name().c_str(), b->np,
+                  tune_bucket(((b->nmax + BATCH_TILE - 1) / BATCH_TILE) * BATCH_TILE));
+    std::map<std::string, double> t;
+    if (tune_lookup(b->opt.tune_cache, key, t) && t.count("tc_min"))
+      b->tc_min = t["tc_min"] > 0 ? std::max(512, (int)t["tc_min"]) : 0;
+  }
+  std::vector<int> Np(count), order(count);
+  for (int p = 0; p < count; ++p) {
+    const int nn = b->pd[p].n;
+    Np[p] = (b->tc_min > 0 && nn >= b->tc_min) ? (nn + 255) / 256 * 256 : (nn + BATCH_TILE - 1) / BATCH_TILE * BATCH_TILE;
+    order[p] = p;
+  }
+  // class pencils first (largest order first), then the others in the given order
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const bool tx = b->tc_min > 0 && b->pd[x].n >= b->tc_min, ty = b->tc_min > 0 && b->pd[y].n >= b->tc_min;
+    if (tx != ty) return tx;
+    if (tx) return Np[x] > Np[y];
+    return false;
+  });
+  for (int p : order) {
+    GrpDesc& d = b->pd[p];
+    const int N = Np[p];
+    const bool tc = b->tc_min > 0 && d.n >= b->tc_min;
+    b->Nmax = std::max(b->Nmax, N);
+    d.mat0 = b->nmat;
+    if (tc) {
+      if (b->tcc.empty() || b->tcc.back().N != N) {
+        feast_batch::TcClass c;
+        c.N = N;
+        c.mat0 = b->nmat;
+        b->tcc.push_back(c);
+      }
+      b->tcc.back().count += d.q;
+    }
     for (int k = 0; k < d.q; ++k) {
       BMat M;
       M.soff = (long long)b->sS;
@@ -666,6 +813,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
       b->snb += (size_t)M.nb;
       b->sN += (size_t)N;
       b->mats.push_back(M);
+      b->lu_mask.push_back(tc ? 0 : 1);
       ++b->nmat;
     }
   }
@@ -706,6 +854,40 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
   AL(b->perm, b->sN * sizeof(int));
   AL(b->piv, b->sN * sizeof(int));
   AL(b->flags, 64);
+  // tensor-core classes: the update's and the deep product's staging, the far
+  // step's -L11^{-1}, the panels' moved-row lists, inverse permutations, a stream
+  for (auto& c : b->tcc) {
+    AL(c.st.Ast, tc_staging_bytes_A(c.N, c.count));
+    AL(c.st.Bst, tc_staging_bytes_B(c.N, c.count));
+    c.st.rows_max = 2LL * c.N;
+    c.st.cols_max = c.N;
+    c.st.q = c.count;
+    if (c.N >= 1024) {  // two-level LU with 256-column outer blocks
+      AL(c.dst.Ast, deep_staging_bytes_A(c.N, c.count));
+      AL(c.dst.Bst, deep_staging_bytes_B(c.N, c.count));
+      c.dst.rows_max = 2LL * c.N;
+      c.dst.cols_max = c.N;
+      c.dst.q = c.count;
+      AL(c.T, (size_t)c.count * 256 * 256 * sizeof(float2));
+    }
+    AL(c.mv, (size_t)(c.N / 64) * c.count * LU_MV_STRIDE * sizeof(int32_t));
+    AL(c.pinv, (size_t)c.count * c.N * sizeof(int32_t));
+    if ((e = cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking)) != cudaSuccess) return bad(cuda_status(e));
+    if ((e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming)) != cudaSuccess) return bad(cuda_status(e));
+  }
+  if (!b->tcc.empty()) {
+    // a class-factored matrix enters the persistent launch as finished
+    // (completion count = its block columns), so only its solves run there
+    if ((e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return bad(cuda_status(e));
+    std::vector<int> f0(b->nmat, 0);
+    for (int i = 0; i < b->nmat; ++i)
+      if (!b->lu_mask[i]) f0[i] = b->mats[i].nb;
+    AL(b->d_fcnt0, b->nmat * sizeof(int));
+    if ((e = cudaMemcpyAsync(b->d_fcnt0, f0.data(), f0.size() * sizeof(int), cudaMemcpyHostToDevice, b->st)) !=
+        cudaSuccess)
+      return bad(cuda_status(e));
+    if ((e = cudaStreamSynchronize(b->st)) != cudaSuccess) return bad(cuda_status(e));
+  }
   for (void** hp : {(void**)&b->h_coef, (void**)&b->h_c0, (void**)&b->h_lam}) {
     if ((e = cudaMallocHost(hp, (hp == (void**)&b->h_coef ? b->sqm : b->sm) * sizeof(double2))) != cudaSuccess)
       return bad(cuda_status(e));
@@ -716,9 +898,8 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
   for (auto& ev : b->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bad(cuda_status(e));
   // tables
-  std::vector<double2> zd;
-  for (int p = 0; p < b->np; ++p)
-    for (const zc& v : b->z[p]) zd.push_back(d2(v));
+  std::vector<double2> zd;  // the node of every shifted matrix, in matrix order
+  for (const BMat& M : b->mats) zd.push_back(d2(b->z[M.pencil][M.shift]));
   if ((e = cudaMemcpyAsync(b->d_pd, b->pd.data(), b->np * sizeof(GrpDesc), cudaMemcpyHostToDevice, b->st)) != cudaSuccess)
     return bad(cuda_status(e));
   if ((e = cudaMemcpyAsync(b->d_mats, b->mats.data(), b->nmat * sizeof(BMat), cudaMemcpyHostToDevice, b->st)) !=
@@ -787,7 +968,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
       mv.push_back(M.m);
     }
     auto upload = [&](bool lu, bool solve, int4** dst, int* cnt, double* mk) -> cudaError_t {
-      const std::vector<int4> ord = plan_order(nbv, mv, lu, solve, b->grid, mk, cm);
+      const std::vector<int4> ord = plan_order(nbv, mv, lu, solve, b->grid, mk, cm, &b->lu_mask);
       *cnt = (int)ord.size();
       cudaError_t ee = dalloc(b, dst, ord.size() * sizeof(int4));
       if (ee != cudaSuccess) return ee;
@@ -1081,6 +1262,18 @@ feast_status feast_batch_get_factor(feast_batch* b, int pencil, int shift, feast
   if (perm) {
     CK(cudaMemcpyAsync(perm, b->perm + M.poff, M.n * sizeof(int32_t), cudaMemcpyDefault, b->st));
     CK(cudaStreamSynchronize(b->st));
+  }
+  return FEAST_OK;
+}
+
+feast_status feast_batch_tc_info(const feast_batch* b, int* tc_min, int* classes, int* matrices) {
+  if (!b) return FEAST_ERR_ARG;
+  if (tc_min) *tc_min = b->tc_min;
+  if (classes) *classes = (int)b->tcc.size();
+  if (matrices) {
+    int m = 0;
+    for (const auto& c : b->tcc) m += c.count;
+    *matrices = m;
   }
   return FEAST_OK;
 }

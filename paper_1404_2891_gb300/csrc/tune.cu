@@ -1,6 +1,7 @@
 // Reader of the autotuner's JSON cache (format in tune.cuh).  A small
 // hand-written scanner: the file is written by the project's own tuner, so
-// only its shape is accepted -- string keys, objects of numbers.
+// only its shape is accepted -- string keys, objects of numbers (with
+// strings and flat objects of numbers as non-tunable fields).
 #include <cuda_runtime.h>
 
 #include <cctype>
@@ -98,9 +99,8 @@ bool tune_lookup(const char* path, const std::string& key, std::map<std::string,
         if (i >= s.size() || s[i] != ':') return false;
         ++i;
         skip_ws(s, i);
-        if (i < s.size() && s[i] == '"') {  // a string field (a note): not a tunable
-          std::string t;
-          if (!read_string(s, i, t)) return false;
+        if (i < s.size() && (s[i] == '"' || s[i] == '{')) {  // a note or a record of timings: not a tunable
+          if (!skip_value(s, i)) return false;
         } else {
           if (!read_number(s, i, v)) return false;
           out[name] = v;

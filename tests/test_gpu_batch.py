@@ -136,3 +136,56 @@ def test_full_batch_64_pencils_log_uniform_orders():
     out, st = fg.feast_batch_solve(b, [c["U0"] for c in cfgs])
     assert st["converged"] == 64, st
     check_results(cfgs, out)
+
+
+# orders from 768 on join the tensor-core classes (padded to a multiple of 256):
+# 1100 and 1030 share the class of order 1280, 800 forms the class of 1024
+# (both two-level); 520 joins the one-level class of 768 when tc_min = 512
+MIXED = [(1100, 24, 40), (300, 12, 24), (800, 20, 32), (520, 14, 32), (1030, 18, 33)]
+
+
+def mixed_cfgs(seed=21):
+    return [workloads.prescribed(n=n, m_in=mi, m0=m0, seed=seed + i, center=0.5 * i - 0.2j * i, radius=1.0 + 0.2 * i)
+            for i, (n, mi, m0) in enumerate(MIXED)]
+
+
+@pytest.mark.parametrize("tc_min,classes,matrices", [(0, 2, 24), (512, 3, 32), (-1, 0, 0)])
+def test_tensor_core_classes_factor_every_shift(tc_min, classes, matrices):
+    """Class-factored matrices (two-level and one-level tcgen05 LU on their own
+    streams) are partial-pivoting LU factors of their shifted matrices, with
+    the padding left as the identity, exactly like the persistent launch's."""
+    fg = lib()
+    cfgs = mixed_cfgs()
+    b = make_batch(fg, cfgs, batch_tc_min=tc_min)
+    info = fg.feast_batch_tc_info(b)
+    assert (info["classes"], info["matrices"]) == (classes, matrices), info
+    fg.feast_batch_factor(b)
+    u = 2.0 ** -24
+    for p, c in enumerate(cfgs):
+        n = c["A"].shape[0]
+        z, _ = nodes(c)
+        for k in (0, len(z) // 2, len(z) - 1):
+            LU, perm = fg.feast_batch_get_factor(b, p, k)
+            S = z[k] * np.eye(n) - c["A"]
+            L, U = dense.unpack(LU)
+            assert sorted(perm.tolist()) == list(range(n))
+            err = np.linalg.norm(S[perm] - L @ U) / np.linalg.norm(S)
+            assert err <= 8 * n * u, (p, k, err)
+            assert np.abs(np.tril(LU, -1)).max() <= np.sqrt(2.0) + 1e-6
+
+
+def test_tensor_core_classes_solve_to_the_prescribed_spectra():
+    """The same pencils solved with and without the classes: both reach the
+    prescribed eigenvalues at 1e-10 and agree with each other."""
+    fg = lib()
+    cfgs = mixed_cfgs(seed=31)
+    outs = []
+    for tc_min in (0, -1):
+        b = make_batch(fg, cfgs, tol=1e-12, max_iter=16, batch_tc_min=tc_min)
+        out, st = fg.feast_batch_solve(b, [c["U0"] for c in cfgs])
+        assert st["converged"] == len(cfgs), (tc_min, st)
+        check_results(cfgs, out)
+        outs.append(out)
+    for o1, o2 in zip(*outs):
+        assert o1["m_found"] == o2["m_found"]
+        assert np.abs(np.sort_complex(o1["lam"]) - np.sort_complex(o2["lam"])).max() < 1e-10
