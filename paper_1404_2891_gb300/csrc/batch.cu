@@ -250,7 +250,7 @@ struct feast_batch {
     TcStaging st;
     DeepStaging dst;
     float2* T = nullptr;
-    int32_t *mv = nullptr, *pinv = nullptr;
+    int32_t *mv = nullptr, *pinv = nullptr, *rowmaps = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
   };
@@ -421,8 +421,7 @@ cudaError_t class_far(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStr
   const int far0 = K0 + KB, nfar = lu.n - far0;
   if (nfar <= 0) return cudaSuccess;
   cudaError_t e;
-  for (int k0 = K0; k0 < far0; k0 += 64)
-    if ((e = laswp_moved_rows(lu, k0, far0, nfar, s)) != cudaSuccess) return e;
+  if ((e = block_swaps_far(lu, K0, KB, s)) != cudaSuccess) return e;
   if ((e = block_inverse_negated(lu, false, KB, K0 / KB, 1, cls->T, s)) != cudaSuccess) return e;
   return tc_far_gemm(lu, K0, KB, cls->T, cls->dst, s);
 }
@@ -463,6 +462,7 @@ cudaError_t factor_classes(feast_batch* b) {
     lu.tc = &c.st;
     lu.mv = c.mv;
     lu.mv_panels = c.N / 64;
+    lu.rowmaps = c.rowmaps;
     lu.u12_in_stage = true;
     // the four-CTA cluster panel while the class's panels alone leave SMs idle
     lu.panel_cluster = 4 * c.count <= nsm;
@@ -872,6 +872,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
     }
     AL(c.mv, (size_t)(c.N / 64) * c.count * LU_MV_STRIDE * sizeof(int32_t));
     AL(c.pinv, (size_t)c.count * c.N * sizeof(int32_t));
+    AL(c.rowmaps, lu_rowmap_ints(c.N, c.count, c.N >= 1024 ? 256 : 64) * sizeof(int32_t));
     if ((e = cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking)) != cudaSuccess) return bad(cuda_status(e));
     if ((e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming)) != cudaSuccess) return bad(cuda_status(e));
   }

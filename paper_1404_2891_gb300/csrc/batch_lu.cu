@@ -456,15 +456,16 @@ __global__ void k_batch_form(const double2* A, const GrpDesc* pd, const BMat* ma
   const double2 zz = z[blockIdx.y];
   const double2* Ap = A + d.onn;
   float2* Sm = S + M.soff;
-  const size_t total = (size_t)M.N * M.N;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(idx % M.N), c = (int)(idx / M.N);
-    double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    if (r < M.n && c < M.n) {
-      const double2 av = Ap[(size_t)r + (size_t)c * M.n];
-      v = make_double2((r == c ? zz.x : 0.0) - av.x, (r == c ? zz.y : 0.0) - av.y);
+  // columns strided over the CTAs, rows over the threads (coalesced on both sides)
+  for (int c = blockIdx.x; c < M.N; c += gridDim.x) {
+    for (int r = threadIdx.x; r < M.N; r += blockDim.x) {
+      double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
+      if (r < M.n && c < M.n) {
+        const double2 av = Ap[(size_t)r + (size_t)c * M.n];
+        v = make_double2((r == c ? zz.x : 0.0) - av.x, (r == c ? zz.y : 0.0) - av.y);
+      }
+      Sm[(size_t)r + (size_t)c * M.N] = make_float2((float)v.x, (float)v.y);
     }
-    Sm[idx] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -600,7 +601,7 @@ cudaError_t batch_lu_launch(const BatchLuArgs& a, int Nmax, int grid, cudaStream
 cudaError_t batch_form_shifted(const double2* A, const GrpDesc* pd, const BMat* mats, const double2* z, int nmat,
                                int Nmax, float2* S, cudaStream_t s) {
   if (nmat < 1) return cudaSuccess;
-  dim3 grid(blocks_for((size_t)Nmax * Nmax), nmat);
+  dim3 grid(std::min(Nmax, 256), nmat);
   feast_count_launch();
   k_batch_form<<<grid, 256, 0, s>>>(A, pd, mats, z, S);
   return cudaGetLastError();

@@ -185,6 +185,7 @@ struct feast_handle {
   double2 *A = nullptr, *B = nullptr, *dz = nullptr, *dw = nullptr, *dmu = nullptr;
   void* S = nullptr;
   int32_t *piv = nullptr, *perm = nullptr, *pinv = nullptr, *mv = nullptr;
+  int32_t* rowmaps = nullptr;  // complex64 LU: row maps of the deferred interchanges (blocks x q x n)
   int* info = nullptr;
   unsigned* flags = nullptr;
   void *Xs = nullptr, *Xsh = nullptr;
@@ -314,6 +315,7 @@ LuBatch<T> lu_view(feast_handle* h) {
   lu.flags = h->flags;
   lu.mv = h->mv;
   lu.mv_panels = (int)((h->n + 63) / 64);
+  if (std::is_same<T, float>::value) lu.rowmaps = h->rowmaps;
   if (std::is_same<T, float>::value && h->staging.Ast) lu.tc = &h->staging;
   lu.panel_cluster = std::is_same<T, float>::value && h->opt.panel_cluster >= 0;
   lu.cluster_min_rows = h->opt.panel_cluster > 0 ? h->opt.panel_cluster : 0;
@@ -411,13 +413,11 @@ cudaError_t far_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStre
   feast_handle* h = reinterpret_cast<feast_handle*>(c);
   const int far0 = K0 + KB, nfar = lu.n - far0;
   if (nfar <= 0) return cudaSuccess;
-  for (int k0 = K0; k0 < far0; k0 += 64) {
-    cudaError_t e = laswp_moved_rows(lu, k0, far0, nfar, s);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = block_swaps_far(lu, K0, KB, s);
+  if (e != cudaSuccess) return e;
   // T = -L11^{-1} of this block, kept for the solves (block-major, all blocks)
   float2* T = h->TL + (size_t)(K0 / KB) * lu.q * KB * KB;
-  cudaError_t e = block_inverse_negated(lu, false, KB, K0 / KB, 1, T, s);
+  e = block_inverse_negated(lu, false, KB, K0 / KB, 1, T, s);
   if (e != cudaSuccess) return e;
   const bool timing = h->opt.timing && 2 * h->n_deep + 1 < (int)h->deep_ev.size();
   if (timing) cudaEventRecord(h->deep_ev[2 * h->n_deep], s);
@@ -1368,6 +1368,11 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
       AL(h->TL, (size_t)h->nblk * h->q * outer * outer * sizeof(float2));
       AL(h->TU, (size_t)h->nblk * h->q * outer * outer * sizeof(float2));
       h->lu_outer = outer;
+    }
+    {  // row maps of the interchanges: blocks of lu_outer columns, or of 64 for the one-level LU
+      const long long kb = h->lu_outer > 0 ? h->lu_outer : 64;
+      const size_t bytes = lu_rowmap_ints(n, h->q, (int)kb) * sizeof(int32_t);
+      if (bytes <= ((size_t)1 << 30)) AL(h->rowmaps, bytes);
     }
     if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
       AL(h->staging_left.Ast, tc_staging_bytes_A(n, h->q));

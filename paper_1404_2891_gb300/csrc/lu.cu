@@ -221,7 +221,7 @@ k_laswp_mv_trsm(cplx<T>* S, long long ld, long long stride, int n, int k0, int w
 // (0 .. k0-1, the finished L part): off the factorisation's critical path.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_laswp_mv_left(cplx<T>* S, long long ld, long long stride, int k0, const int32_t* mv) {
+k_laswp_mv_left(cplx<T>* S, long long ld, long long stride, int c_lo, int k0, const int32_t* mv) {
   __shared__ cplx<T> vals[128 * 32];
   __shared__ int s_d[128], s_s[128], s_cnt;
   const int b = blockIdx.y, tid = threadIdx.x;
@@ -235,13 +235,217 @@ k_laswp_mv_left(cplx<T>* S, long long ld, long long stride, int k0, const int32_
   __syncthreads();
   const int cnt = s_cnt;
   for (int idx = tid; idx < cnt * 32; idx += 256) {
-    const int e = idx >> 5, c = blockIdx.x * 32 + (idx & 31);
+    const int e = idx >> 5, c = c_lo + blockIdx.x * 32 + (idx & 31);
     if (c < k0) vals[idx] = A[(size_t)(k0 + s_s[e]) + (size_t)c * ld];
   }
   __syncthreads();
   for (int idx = tid; idx < cnt * 32; idx += 256) {
-    const int e = idx >> 5, c = blockIdx.x * 32 + (idx & 31);
+    const int e = idx >> 5, c = c_lo + blockIdx.x * 32 + (idx & 31);
     if (c < k0) A[(size_t)(k0 + s_d[e]) + (size_t)c * ld] = vals[idx];
+  }
+}
+
+// The interchanges of all panels of the outer block [K0, K1) on the columns
+// col0 .. col0+ncols-1: one warp per column applies the panels' moved-row
+// lists in order (lanes over the moved rows, so the panel's own top rows are
+// read and written contiguously), with no barrier beyond the warp.
+__global__ void __launch_bounds__(256)
+k_laswp_block_cols(float2* S, long long ld, long long stride, int n, int K0, int K1, int col0, int ncols,
+                   const int32_t* mv) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, b = blockIdx.y, q = gridDim.y;
+  const int o = blockIdx.x * 8 + warp;
+  if (o >= ncols) return;
+  float2* col = S + (size_t)b * stride + (size_t)(col0 + o) * ld;
+  for (int k0 = K0; k0 < K1; k0 += 64) {
+    const int32_t* m = mv + ((size_t)(k0 / 64) * q + b) * LU_MV_STRIDE;
+    const int cnt = min(max(__ldcg(m), 0), 128);
+    float2 v[4];
+    int d[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = lane + 32 * j;
+      d[j] = -1;
+      if (e < cnt) {
+        const int sr = k0 + __ldcg(m + 129 + e), dd = k0 + __ldcg(m + 1 + e);
+        if (sr >= k0 && sr < n && dd >= k0 && dd < n) {
+          v[j] = col[sr];
+          d[j] = dd;
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (d[j] >= 0) col[d[j]] = v[j];
+    __syncwarp();
+  }
+}
+
+// Row maps of deferred interchanges, kept per (slot, shift) in one int arena:
+// the map itself (row i holds, after the interchanges, the row that was at
+// map[i] before), and the compact list of the rows it moves (dst, src pairs in
+// increasing dst, and their count).
+struct RowMaps {
+  int32_t *map = nullptr, *dst = nullptr, *src = nullptr, *cnt = nullptr;
+};
+__host__ __device__ inline RowMaps rowmaps_view(int32_t* base, long long n, int q, int nblk) {
+  const size_t M = (size_t)nblk * q * n;
+  RowMaps r;
+  r.map = base;
+  r.dst = base + M;
+  r.src = base + 2 * M;
+  r.cnt = base + 3 * M;
+  return r;
+}
+
+// The rows i in [r0, n) with p[i - r0] != i, compacted in increasing i into
+// dst/src (any multiple of 32 threads up to 1024, warp ballots); returns the
+// count to every thread.
+__device__ int block_compact(const int* p, int r0, int n, int32_t* dst, int32_t* src) {
+  __shared__ int wcount[32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = r0; c0 < n; c0 += blockDim.x) {
+    const int i = c0 + threadIdx.x;
+    const int v = i < n ? p[i - r0] : i;
+    const bool moved = v != i;
+    const unsigned bal = __ballot_sync(0xffffffffu, moved);
+    if (lane == 0) wcount[w] = __popc(bal);
+    __syncthreads();
+    int off = base;
+    for (int k = 0; k < w; ++k) off += wcount[k];
+    off += __popc(bal & ((1u << lane) - 1u));
+    if (moved) {
+      dst[off] = i;
+      src[off] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int k = 0; k < nw; ++k) t += wcount[k];
+      base += t;
+    }
+    __syncthreads();
+  }
+  return base;
+}
+
+// Row maps of the interchanges of whole blocks of KB columns: for block
+// blk = block0 + blockIdx.x and shift b, the moved-row lists of the block's
+// panels (mv, LU_MV_STRIDE ints per panel and shift: count, dst[128],
+// src[128], rows relative to the panel's first row) applied in order to an
+// index array, so that after them row i (>= blk KB) holds the row that was at
+// map[i] before; the map and its own moved-row list go to slot blk.  1024
+// threads (one CTA per block and shift).
+__global__ void __launch_bounds__(1024)
+k_block_rowmaps(const int32_t* mv, int n, int KB, int block0, int32_t* base, int nblk) {
+  extern __shared__ int rm_sh[];
+  const int blk = block0 + blockIdx.x, b = blockIdx.y, q = gridDim.y;
+  const int K0 = blk * KB, K1 = min(K0 + KB, n), len = n - K0;
+  if (len <= 0) return;
+  const RowMaps rm = rowmaps_view(base, n, q, nblk);
+  int* p = rm_sh;  // len
+  __shared__ int vals[128];
+  for (int i = threadIdx.x; i < len; i += blockDim.x) p[i] = K0 + i;
+  __syncthreads();
+  for (int k0 = K0; k0 < K1; k0 += 64) {
+    const int32_t* m = mv + ((size_t)(k0 / 64) * q + b) * LU_MV_STRIDE;
+    const int cnt = min(max(__ldcg(m), 0), 128);
+    int d = -1, v = 0;
+    if (threadIdx.x < cnt) {
+      const int sr = k0 + __ldcg(m + 129 + threadIdx.x);
+      d = k0 + __ldcg(m + 1 + threadIdx.x);
+      if (sr >= K0 && sr < n && d >= K0 && d < n) v = p[sr - K0]; else d = -1;
+    }
+    if (threadIdx.x < 128) vals[threadIdx.x] = v;
+    __syncthreads();
+    if (d >= 0) p[d - K0] = vals[threadIdx.x];
+    __syncthreads();
+  }
+  const size_t li = (size_t)blk * q + b;
+  int32_t* mo = rm.map + li * n;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) mo[K0 + i] = p[i];
+  const int cnt = block_compact(p, K0, n, rm.dst + li * n, rm.src + li * n);
+  if (threadIdx.x == 0) rm.cnt[li] = cnt;
+}
+
+// The deferred interchanges of the finished L columns: the columns of block
+// B - 1 need the interchanges of blocks B .. nblk-1 in order, whose row map is
+// t_{B-1}[i] = s_B[t_B[i]] (s_B block B's own map, t_{nblk-1} the identity,
+// rows i >= B KB).  One CTA per shift, backward over the blocks; t_{B-1} and
+// its moved-row list overwrite slot B.
+__global__ void __launch_bounds__(1024) k_compose_tail_maps(int32_t* base, int n, int KB, int nblk) {
+  extern __shared__ int cm_sh[];
+  int* cur = cm_sh;
+  int* nxt = cm_sh + n;
+  const int b = blockIdx.x, q = gridDim.x, tid = threadIdx.x;
+  const RowMaps rm = rowmaps_view(base, n, q, nblk);
+  for (int i = tid; i < n; i += blockDim.x) cur[i] = i;
+  __syncthreads();
+  for (int B = nblk - 1; B >= 1; --B) {
+    const size_t li = (size_t)B * q + b;
+    int32_t* sB = rm.map + li * n;
+    const int K0 = B * KB;
+    for (int i = K0 + tid; i < n; i += blockDim.x) nxt[i] = __ldcg(sB + cur[i]);
+    __syncthreads();
+    for (int i = K0 + tid; i < n; i += blockDim.x) {
+      cur[i] = nxt[i];
+      sB[i] = nxt[i];
+    }
+    const int cnt = block_compact(nxt + K0, K0, n, rm.dst + li * n, rm.src + li * n);
+    if (tid == 0) rm.cnt[li] = cnt;
+    __syncthreads();
+  }
+}
+
+// Row permutation of whole columns by a moved-row list: column c
+// (col0 <= c < col0 + ncols) of every shift gets new row dst_e = old row src_e.
+// When most of the column's rows r0 .. n-1 move, the segment is read once,
+// coalesced, into shared memory; otherwise only the moved rows are read.
+// tail = false: r0 = R0 and slot `slot` for all columns (the far step);
+// tail = true: column c of block B = c / KB takes r0 = (B + 1) KB and slot
+// B + 1 (the deferred pass).
+template <bool TAIL>
+__global__ void __launch_bounds__(256)
+k_permute_rows(float2* S, long long ld, long long stride, int n, int col0, int ncols, int32_t* base, int nblk,
+               int KB, int R0, int slot) {
+  extern __shared__ float2 pr_seg[];
+  constexpr int CPB = 16;  // columns per CTA (a divisor of 64: no CTA straddles a block)
+  const int b = blockIdx.y, q = gridDim.y;
+  const RowMaps rm = rowmaps_view(base, n, q, nblk);
+  float2* A = S + (size_t)b * stride;
+  for (int j = 0; j < CPB; ++j) {
+    const int c = col0 + blockIdx.x * CPB + j;
+    if (c >= col0 + ncols) break;
+    const int r0 = TAIL ? (c / KB + 1) * KB : R0;
+    if (r0 >= n) continue;
+    const size_t li = (size_t)(TAIL ? c / KB + 1 : slot) * q + b;
+    const int cnt = min(__ldcg(rm.cnt + li), n - r0);
+    if (cnt <= 0) continue;
+    const int32_t* dl = rm.dst + li * n;
+    const int32_t* sl = rm.src + li * n;
+    float2* col = A + (size_t)c * ld;
+    __syncthreads();  // the previous column's reads of pr_seg are done
+    if (4 * cnt >= n - r0) {
+      for (int i = r0 + threadIdx.x; i < n; i += blockDim.x) pr_seg[i - r0] = __ldcg(col + i);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int d = __ldcg(dl + e), sr = __ldcg(sl + e);
+        if (d >= r0 && d < n && sr >= r0 && sr < n) col[d] = pr_seg[sr - r0];
+      }
+    } else {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int sr = __ldcg(sl + e);
+        pr_seg[e] = (sr >= r0 && sr < n) ? __ldcg(col + sr) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int d = __ldcg(dl + e), sr = __ldcg(sl + e);
+        if (d >= r0 && d < n && sr >= r0 && sr < n) col[d] = pr_seg[e];
+      }
+    }
   }
 }
 
@@ -555,6 +759,59 @@ cudaError_t launch_panel(const LuBatch<T>& lu, int k0, int w, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+cudaError_t smem_attr(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Row maps of the blocks block_from .. nblk-1 (blocks of KB columns), their
+// composition from the back, and the one deferred permutation of the finished
+// L columns of blocks 0 .. nblk-2 (lu.rowmaps holds nblk x q x n ints).
+cudaError_t deferred_left_swaps(const LuBatch<float>& lu, int KB, int block_from, cudaStream_t s) {
+  const int n = lu.n, nblk = (n + KB - 1) / KB;
+  if (nblk < 2) return cudaSuccess;
+  cudaError_t e;
+  if (block_from < nblk) {
+    const size_t sm = (size_t)n * sizeof(int);
+    if ((e = smem_attr((const void*)k_block_rowmaps, sm)) != cudaSuccess) return e;
+    feast_count_launch();
+    k_block_rowmaps<<<dim3(nblk - block_from, lu.q), 1024, sm, s>>>(lu.mv, n, KB, block_from, lu.rowmaps, nblk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const size_t smc = 2 * (size_t)n * sizeof(int);
+  if ((e = smem_attr((const void*)k_compose_tail_maps, smc)) != cudaSuccess) return e;
+  feast_count_launch();
+  k_compose_tail_maps<<<lu.q, 1024, smc, s>>>(lu.rowmaps, n, KB, nblk);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int ncols = (nblk - 1) * KB;
+  const size_t smp = (size_t)n * sizeof(float2);
+  if ((e = smem_attr((const void*)k_permute_rows<true>, smp)) != cudaSuccess) return e;
+  feast_count_launch();
+  k_permute_rows<true><<<dim3(ceil_div(ncols, 16), lu.q), 256, smp, s>>>(reinterpret_cast<float2*>(lu.S), lu.ld,
+                                                                         lu.stride, n, 0, ncols, lu.rowmaps, nblk, KB,
+                                                                         0, 0);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t lu_rowmap_ints(long long n, int q, int KB) {
+  const size_t nblk = (size_t)((n + KB - 1) / KB);
+  return 3 * nblk * q * (size_t)n + nblk * q;
+}
+
+cudaError_t block_swaps_far(const LuBatch<float>& lu, int K0, int KB, cudaStream_t s) {
+  const int far0 = K0 + KB, nfar = lu.n - far0;
+  if (nfar <= 0) return cudaSuccess;
+  if (!lu.mv || K0 % 64 || KB % 64) return cudaErrorInvalidValue;
+  feast_count_launch();
+  k_laswp_block_cols<<<dim3(ceil_div(nfar, 8), lu.q), 256, 0, s>>>(reinterpret_cast<float2*>(lu.S), lu.ld,
+                                                                  lu.stride, lu.n, K0, far0, far0, nfar, lu.mv);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t lu_factor_batched(const LuBatch<T>& lu_in, int nb, TrailingUpdateFn<T> upd, void* ctx,
                               cudaStream_t s) {
@@ -611,13 +868,14 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu_in, int nb, TrailingUpdateFn<
           cudaError_t r = cudaGetLastError();
           if (r != cudaSuccess) return r;
         }
-        if (k0 > 0) {
+        if (k0 > 0 && !lu.rowmaps) {  // (with row maps: one deferred pass at the end)
           // s has waited for this panel: the left stream starts from here
           cudaError_t r = cudaEventRecord(ev_left, s);
           if (r == cudaSuccess) r = cudaStreamWaitEvent(lstream, ev_left, 0);
           if (r != cudaSuccess) return r;
           feast_count_launch();
-          k_laswp_mv_left<float><<<dim3(ceil_div(k0, 32), lu.q), 256, 0, lstream>>>(lu.S, lu.ld, lu.stride, k0, mvk);
+          k_laswp_mv_left<float><<<dim3(ceil_div(k0, 32), lu.q), 256, 0, lstream>>>(lu.S, lu.ld, lu.stride, 0, k0,
+                                                                                     mvk);
           return cudaGetLastError();
         }
         return cudaSuccess;
@@ -646,6 +904,9 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu_in, int nb, TrailingUpdateFn<
   // the left interchanges are done before anything reads L
   if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
   if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_mv && lu.rowmaps && (e = deferred_left_swaps(lu, 64, 0, s)) != cudaSuccess) return cleanup(e);
+  }
   feast_count_launch();
   k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
   return cleanup(cudaGetLastError());
@@ -810,15 +1071,18 @@ cudaError_t lu_factor_two_level(const LuBatch<float>& lu_in, int nb, int KB, Tra
   if ((e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
   if ((e = cudaEventCreateWithFlags(&ev_left, cudaEventDisableTiming)) != cudaSuccess) return cleanup(e);
   if ((e = cudaStreamCreateWithPriority(&lstream, cudaStreamNonBlocking, lo)) != cudaSuccess) return cleanup(e);
-  // the panel's moved rows on the finished L columns (0 .. k0-1), off the critical path
+  // the panel's moved rows on the finished L columns (0 .. k0-1), off the
+  // critical path; with row maps only on the current outer block's columns
+  // (the deep update reads them), the earlier blocks' in the deferred pass
   auto left = [&](int k0) -> cudaError_t {
-    if (k0 <= 0) return cudaSuccess;
+    const int c_lo = lu.rowmaps ? (k0 / KB) * KB : 0;
+    if (k0 <= c_lo) return cudaSuccess;
     cudaError_t r = cudaEventRecord(ev_left, s);
     if (r == cudaSuccess) r = cudaStreamWaitEvent(lstream, ev_left, 0);
     if (r != cudaSuccess) return r;
     feast_count_launch();
-    k_laswp_mv_left<float><<<dim3(ceil_div(k0, 32), lu.q), 256, 0, lstream>>>(
-        lu.S, lu.ld, lu.stride, k0, lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE);
+    k_laswp_mv_left<float><<<dim3(ceil_div(k0 - c_lo, 32), lu.q), 256, 0, lstream>>>(
+        lu.S, lu.ld, lu.stride, c_lo, k0, lu.mv + (size_t)(k0 / 64) * lu.q * LU_MV_STRIDE);
     return cudaGetLastError();
   };
   if ((e = launch_panel<float>(lu, 0, min(nb, lu.n), s)) != cudaSuccess) return cleanup(e);
@@ -852,6 +1116,7 @@ cudaError_t lu_factor_two_level(const LuBatch<float>& lu_in, int nb, int KB, Tra
   }
   if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
   if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+  if (lu.rowmaps && (e = deferred_left_swaps(lu, KB, 0, s)) != cudaSuccess) return cleanup(e);
   feast_count_launch();
   k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
   return cleanup(cudaGetLastError());

@@ -30,6 +30,12 @@ struct LuBatch {
   // complex64 panels of >= cluster_min_rows rows (0: 1024) on a cluster of four CTAs per shift
   bool panel_cluster = false;
   int cluster_min_rows = 0;
+  // complex64 with moved-row lists: lu_rowmap_ints(n, q, KB) ints of row maps
+  // and moved-row lists (KB the outer block, or 64 for the one-level LU), or
+  // nullptr.  With them the interchanges of the later outer blocks reach the
+  // finished L columns in one deferred pass at the end (each column's moved
+  // rows read and written once) instead of one pass per panel
+  int32_t* rowmaps = nullptr;
 };
 constexpr int LU_MV_STRIDE = 257;
 
@@ -72,6 +78,12 @@ cudaError_t block_inverse_negated(const LuBatch<float>& lu, bool upper, int KB, 
 // The moved rows of the panel at k0 (its list in lu.mv) applied to the columns
 // col0 .. col0+ncols-1 of every shifted matrix.
 cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int ncols, cudaStream_t s);
+// The interchanges of all panels of the outer block [K0, K0+KB) applied to the
+// columns beyond it (K0+KB .. n-1) in one launch: the panels' moved-row lists
+// in order, one warp per column.
+cudaError_t block_swaps_far(const LuBatch<float>& lu, int K0, int KB, cudaStream_t s);
+// Size of LuBatch::rowmaps for blocks of KB columns.
+size_t lu_rowmap_ints(long long n, int q, int KB);
 using DeepFn = cudaError_t (*)(const LuBatch<float>& lu, int K0, int KB, void* ctx, cudaStream_t s);
 cudaError_t lu_factor_two_level(const LuBatch<float>& lu, int nb, int KB, TrailingUpdateFn<float> upd, void* ctx,
                                 FarFn far, DeepFn deep, void* dctx, cudaStream_t s);
