@@ -45,14 +45,19 @@ namespace {
 using namespace tcx;
 
 constexpr int DK_BM = 128;
-constexpr int DK_BN = 256;
 constexpr int DK_BK = 64;                     // bf16 elements per K block (one 128-byte row)
 constexpr int DK_A_HALF = DK_BM * 128;        // one of hi / lo: 16 KB
-constexpr int DK_B_HALF = DK_BN * 128;        // 32 KB
-constexpr int DK_STAGE = 2 * DK_A_HALF + 2 * DK_B_HALF;  // 96 KB
 constexpr int DK_THREADS = 320;
-constexpr int DK_SMEM = 1024 + 2 * DK_STAGE + 256;       // 197,888 bytes
-constexpr unsigned DK_IDESC = bf16_idesc(DK_BM, DK_BN);
+// Tile width BN: 256 columns, or 128 for products with at most 128 columns
+// (the blocked solves' right-hand sides), which would leave half of a 256-wide
+// tile's MMAs and operand loads on padding.
+template <int BN>
+struct DeepTile {
+  static constexpr int B_HALF = BN * 128;                      // 32 KB (BN = 256) / 16 KB
+  static constexpr int STAGE = 2 * DK_A_HALF + 2 * B_HALF;     // 96 KB / 64 KB
+  static constexpr int SMEM = 1024 + 2 * STAGE + 256;          // 197,888 / 132,352 bytes
+  static constexpr unsigned IDESC = bf16_idesc(DK_BM, BN);
+};
 
 struct DeepArgs {
   float* S;            // complex64 matrices as floats
@@ -68,8 +73,13 @@ struct DeepArgs {
   unsigned* flags;
 };
 
+template <int BN>
 __global__ void __launch_bounds__(DK_THREADS, 1)
 k_tc_deep(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, DeepArgs a) {
+  constexpr int DK_BN = BN;
+  constexpr int DK_B_HALF = DeepTile<BN>::B_HALF;
+  constexpr int DK_STAGE = DeepTile<BN>::STAGE;
+  constexpr unsigned DK_IDESC = DeepTile<BN>::IDESC;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * DK_STAGE);
@@ -183,8 +193,8 @@ k_tc_deep(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         break;
       }
       fence_after();
-      for (int c = 0; c < 4; ++c) {
-        const int cl = half * 128 + c * 32;            // column within the tile
+      for (int c = 0; c < DK_BN / 64; ++c) {
+        const int cl = half * (DK_BN / 2) + c * 32;    // column within the tile
         const int cbase = ct * DK_BN + cl;             // column within this launch
         float cv[32], v[32];
 #pragma unroll
@@ -353,9 +363,10 @@ cudaError_t deep_stage(const DeepGemm& g, const DeepStaging& st, cudaStream_t s)
 cudaError_t deep_run(const DeepGemm& g, int c0, int nc, const DeepStaging& st, unsigned* flags, cudaStream_t s) {
   if (g.M <= 0 || nc <= 0) return cudaSuccess;
   if (!deep_fits(g, st) || c0 < 0 || c0 + nc > g.N) return cudaErrorInvalidValue;
+  const int BN = nc <= 128 ? 128 : 256;
   CUtensorMap mA, mB;
   if (!encode_deep_map(&mA, st.Ast, 2LL * g.M, st.rows_max, 2 * g.q, DK_BM)) return cudaErrorInvalidValue;
-  if (!encode_deep_map(&mB, st.Bst, g.N, st.cols_max, 2 * g.q, DK_BN)) return cudaErrorInvalidValue;
+  if (!encode_deep_map(&mB, st.Bst, g.N, st.cols_max, 2 * g.q, BN)) return cudaErrorInvalidValue;
   DeepArgs a;
   a.S = reinterpret_cast<float*>(g.C);
   a.ld2 = 2 * g.ldc;
@@ -366,20 +377,26 @@ cudaError_t deep_run(const DeepGemm& g, int c0, int nc, const DeepStaging& st, u
   a.b_col0 = c0;
   a.nkb = (2 * g.K + DK_BK - 1) / DK_BK;
   a.row_tiles = (int)ceil_div((size_t)a.M2, DK_BM);
-  a.col_tiles = (int)ceil_div((size_t)nc, DK_BN);
+  a.col_tiles = (int)ceil_div((size_t)nc, BN);
   a.q = g.q;
   a.overwrite = g.overwrite ? 1 : 0;
   a.flags = flags;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_deep, cudaFuncAttributeMaxDynamicSharedMemorySize, DK_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_deep<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         DeepTile<256>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_deep<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, DeepTile<128>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const long long tiles = (long long)a.q * a.row_tiles * a.col_tiles;
   const int grid = (int)(tiles < sm_count() ? tiles : sm_count());
   feast_count_launch();
-  k_tc_deep<<<grid, DK_THREADS, DK_SMEM, s>>>(mA, mB, a);
+  if (BN == 128)
+    k_tc_deep<128><<<grid, DK_THREADS, DeepTile<128>::SMEM, s>>>(mA, mB, a);
+  else
+    k_tc_deep<256><<<grid, DK_THREADS, DeepTile<256>::SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
 }
 
