@@ -209,6 +209,9 @@ struct feast_handle {
   // of the upper U, for the far steps of the LU and the blocked solves
   float2 *TL = nullptr, *TU = nullptr;
   int nblk = 0;
+  // the blocked solves' factor operands, staged once per factorisation (per side)
+  void* pre[2] = {nullptr, nullptr};
+  bool pre_valid[2] = {false, false};
   int lu_outer = 0;                    // its outer block (0: one-level LU)
   bool tuned = false;                  // launch parameters read from the tune cache
   std::vector<cudaEvent_t> deep_ev;
@@ -451,6 +454,7 @@ cudaError_t deep_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStr
 template <typename T>
 feast_status factor_impl(feast_handle* h) {
   LuBatch<T> lu = lu_view<T>(h);
+  h->pre_valid[0] = h->pre_valid[1] = false;  // the solves' staged operands belong to the old factors
   CK(form_shifted<T>(h->A, h->n, h->hasB ? h->B : nullptr, h->n, h->dz, h->q, (int)h->n, lu.S, lu.stride, h->st));
   TrailingUpdateFn<T> upd = nullptr;
   void* ctx = nullptr;
@@ -651,7 +655,7 @@ cudaError_t solve_all(feast_handle* h, const LuBatch<T>& lu, int side, cplx<T>* 
   if constexpr (std::is_same<T, float>::value) {
     const DeepStaging& st = side == 0 ? h->deep : h->deep_left;
     if (h->opt.deep_solves >= 0 && h->lu_outer > 0 && h->TU && st.Ast && m <= st.cols_max)
-      return tc_solve_deep(lu, side, X, m, h->lu_outer, h->TL, h->TU, st, s);
+      return tc_solve_deep(lu, side, X, m, h->lu_outer, h->TL, h->TU, st, s, h->pre_valid[side] ? h->pre[side] : nullptr);
   }
   return lu_solve_batched<T>(lu, side, X, m, h->nbs, s);
 }
@@ -663,7 +667,25 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   const int n = (int)h->n, m = h->m0;
   cplx<T>* Xs = reinterpret_cast<cplx<T>*>(h->Xs);
   const bool split = Rh && !h->opt.symmetric && h->side;
+  // the first filter after a factorisation stages the solves' factor operands
+  // (the left side's first, so that the left solves can start while the right
+  // side's are staged)
+  bool stage_right = false;
+  if constexpr (std::is_same<T, float>::value) {
+    const bool deep = h->opt.deep_solves >= 0 && h->lu_outer > 0 && h->TU;
+    if (deep && Rh && !h->opt.symmetric && h->pre[1] && !h->pre_valid[1]) {
+      CK(tc_solve_prestage(lu, 1, h->lu_outer, h->TL, h->TU, h->pre[1], h->st));
+      h->pre_valid[1] = true;
+    }
+    stage_right = deep && h->pre[0] && !h->pre_valid[0];
+  }
   if (split) CK(cudaEventRecord(h->fork_ev, h->st));  // the left solves start from here
+  if constexpr (std::is_same<T, float>::value) {
+    if (stage_right) {
+      CK(tc_solve_prestage(lu, 0, h->lu_outer, h->TL, h->TU, h->pre[0], h->st));
+      h->pre_valid[0] = true;
+    }
+  }
   const bool add_c0 = use_c0 && !h->partial;  // a partial handle returns its subtree alone
   const int ms = h->realp ? 2 * m : m;          // real pencils: [R, conj(R)] per factor
   CK(rows_gather<T>(lu, R, Xs, m, true, h->st, h->realp));
@@ -1368,6 +1390,15 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
       AL(h->TL, (size_t)h->nblk * h->q * outer * outer * sizeof(float2));
       AL(h->TU, (size_t)h->nblk * h->q * outer * outer * sizeof(float2));
       h->lu_outer = outer;
+      if (h->opt.deep_solves >= 0) {
+        // the blocked solves' factor operands, staged once per factorisation, when
+        // they fit in half of the free memory (otherwise each solve stages its own)
+        const int sides = (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) ? 2 : 1;
+        const size_t bytes = tc_solve_prestage_bytes(n, h->q, outer);
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)bytes * sides < 0.5 * (double)fr)
+          for (int sd = 0; sd < sides; ++sd) AL(h->pre[sd], bytes);
+      }
     }
     {  // row maps of the interchanges: blocks of lu_outer columns, or of 64 for the one-level LU
       const long long kb = h->lu_outer > 0 ? h->lu_outer : 64;

@@ -242,23 +242,26 @@ __device__ __forceinline__ __nv_bfloat162 bpair(__nv_bfloat16 a, __nv_bfloat16 b
 // pair per complex K).  blockIdx.z = 1: U, one column per warp-row of the block,
 // read and written along K (both coalesced, no transpose).
 __global__ void __launch_bounds__(256) k_deep_stage(DeepGemm g, __nv_bfloat16* Ast, __nv_bfloat16* Bst,
-                                                     long long rows_max, long long cols_max) {
+                                                     long long rows_max, long long cols_max, int part0) {
   const int tid = threadIdx.x;
   const int shift = blockIdx.y / ((g.K + 31) / 32);
   const int kg = blockIdx.y % ((g.K + 31) / 32);
   const float2* Lb = g.L + (size_t)shift * g.strl;
   const float2* Ub = g.U + (size_t)shift * g.stru;
-  if (blockIdx.z == 0) {
+  if (part0 + (int)blockIdx.z == 0) {
     __shared__ float2 tile[32][33];
     const int i0 = blockIdx.x * 32;
     if (i0 >= g.M) return;
     for (int e = tid; e < 32 * 32; e += 256) {
-      const int i = e & 31, k = e >> 5;
+      // the index that runs along the stored columns varies fastest (coalesced):
+      // i for L itself, k for a block of L^H
+      const bool ct = g.opL == OP_C;
+      const int i = ct ? (e >> 5) : (e & 31), k = ct ? (e & 31) : (e >> 5);
       const int gi = i0 + i, gk = kg * 32 + k;
       float2 v = make_float2(0.f, 0.f);
       if (gi < g.M && gk < g.K)
-        v = g.opL == OP_C ? cconj<float>(Lb[(size_t)(g.lc + gk) + (size_t)(g.lr + gi) * g.ldl])
-                          : Lb[(size_t)(g.lr + gi) + (size_t)(g.lc + gk) * g.ldl];
+        v = ct ? cconj<float>(Lb[(size_t)(g.lc + gk) + (size_t)(g.lr + gi) * g.ldl])
+               : Lb[(size_t)(g.lr + gi) + (size_t)(g.lc + gk) * g.ldl];
       tile[k][i] = v;
     }
     __syncthreads();
@@ -349,14 +352,16 @@ bool deep_fits(const DeepGemm& g, const DeepStaging& st) {
          g.q <= st.q;
 }
 
-cudaError_t deep_stage(const DeepGemm& g, const DeepStaging& st, cudaStream_t s) {
+cudaError_t deep_stage(const DeepGemm& g, const DeepStaging& st, cudaStream_t s, int parts) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  if (!deep_fits(g, st)) return cudaErrorInvalidValue;
-  const int groups = (int)ceil_div((size_t)(g.M > g.N ? g.M : g.N), 32);
-  dim3 grid(groups, g.q * ((g.K + 31) / 32), 2);
+  if (!deep_fits(g, st) || parts < 1 || parts > 3) return cudaErrorInvalidValue;
+  const int part0 = parts == 2 ? 1 : 0, nparts = parts == 3 ? 2 : 1;
+  const long long span = parts == 1 ? g.M : parts == 2 ? g.N : (g.M > g.N ? g.M : g.N);
+  const int groups = (int)ceil_div((size_t)span, 32);
+  dim3 grid(groups, g.q * ((g.K + 31) / 32), nparts);
   feast_count_launch();
   k_deep_stage<<<grid, 256, 0, s>>>(g, reinterpret_cast<__nv_bfloat16*>(st.Ast), reinterpret_cast<__nv_bfloat16*>(st.Bst),
-                                   st.rows_max, st.cols_max);
+                                   st.rows_max, st.cols_max, part0);
   return cudaGetLastError();
 }
 
@@ -418,7 +423,7 @@ DeepGemm deep_of(const LuBatch<float>& lu, int K0, int KB) {
 cudaError_t tc_deep_stage(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s) {
   const DeepGemm g = deep_of(lu, K0, KB);
   if (g.M <= 0) return cudaSuccess;
-  return deep_stage(g, st, s);
+  return deep_stage(g, st, s, 3);
 }
 
 cudaError_t tc_deep_run(const LuBatch<float>& lu, int K0, int KB, const DeepStaging& st, cudaStream_t s) {
@@ -441,48 +446,111 @@ cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* 
   g.q = lu.q;
   g.overwrite = true;
   if (g.N <= 0) return cudaSuccess;
-  cudaError_t e = deep_stage(g, st, s);
+  cudaError_t e = deep_stage(g, st, s, 3);
   if (e != cudaSuccess) return e;
   return deep_run(g, 0, g.N, st, lu.flags, s);
 }
 
-cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, int KB, const float2* TL,
-                          const float2* TU, const DeepStaging& st, cudaStream_t s) {
+namespace {
+// The products of the blocked solves of one side, in order: for each diagonal
+// block I of the sweep, X_I = -T_I X_I (T_I = -D_I^{-1}, overwrite) and then
+// the rest of the sweep's rows -= op(S block) X_I.  f(L, ldl, strl, lr, lc,
+// M, K, rowC, rowU, overwrite) per product with M, K > 0.
+template <typename F>
+cudaError_t walk_solve(const LuBatch<float>& lu, int side, int KB, const float2* TL, const float2* TU, F f) {
   const int n = lu.n, q = lu.q, nB = (n + KB - 1) / KB;
-  if (m < 1 || m > st.cols_max || KB % 64 || KB > 256) return cudaErrorInvalidValue;
-  float2* S = reinterpret_cast<float2*>(lu.S);
-  const long long tstr = (long long)KB * KB, xs = (long long)n * m;
-  auto gemm = [&](const float2* L, long long ldl, long long strl, int lr, int lc, int opL, int M, int K, int rowC,
-                  int rowU, bool overwrite = false) -> cudaError_t {
-    if (M <= 0 || K <= 0) return cudaSuccess;
-    DeepGemm g;
-    g.C = X; g.ldc = n; g.strc = xs; g.cr = rowC; g.cc = 0;
-    g.L = L; g.ldl = ldl; g.strl = strl; g.lr = lr; g.lc = lc; g.opL = opL;
-    g.U = X; g.ldu = n; g.stru = xs; g.ur = rowU; g.uc = 0;
-    g.M = M; g.N = m; g.K = K; g.q = q;
-    g.overwrite = overwrite;
-    cudaError_t e = deep_stage(g, st, s);
-    if (e != cudaSuccess) return e;
-    return deep_run(g, 0, m, st, lu.flags, s);
-  };
-  auto Tof = [&](const float2* T, int I) { return T + (size_t)I * q * KB * KB; };
-  const int op = side == 0 ? OP_N : OP_C;
+  const float2* S = reinterpret_cast<const float2*>(lu.S);
+  const long long tstr = (long long)KB * KB;
+  auto Tof = [&](const float2* T, int I) { return T ? T + (size_t)I * q * KB * KB : T; };
   const float2* Tfwd = side == 0 ? TL : TU;  // forward sweep: L (right) or U^H (left)
   const float2* Tbwd = side == 0 ? TU : TL;  // backward sweep: U (right) or L^H (left)
   cudaError_t e;
   for (int I = 0; I < nB; ++I) {
     const int r0 = KB * I, nr = std::min(KB, n - r0);
-    if ((e = gemm(Tof(Tfwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0, true)) != cudaSuccess) return e;
+    if ((e = f(Tof(Tfwd, I), (long long)KB, tstr, 0, 0, nr, nr, r0, r0, true)) != cudaSuccess) return e;
     // rows below: right L[r0+nr:, r0:r0+nr]; left (U[r0:r0+nr, r0+nr:])^H
-    if ((e = gemm(S, lu.ld, lu.stride, r0 + nr, r0, op, n - r0 - nr, nr, r0 + nr, r0)) != cudaSuccess) return e;
+    if (n - r0 - nr > 0 && (e = f(S, lu.ld, lu.stride, r0 + nr, r0, n - r0 - nr, nr, r0 + nr, r0, false)) != cudaSuccess)
+      return e;
   }
   for (int I = nB - 1; I >= 0; --I) {
     const int r0 = KB * I, nr = std::min(KB, n - r0);
-    if ((e = gemm(Tof(Tbwd, I), KB, tstr, 0, 0, op, nr, nr, r0, r0, true)) != cudaSuccess) return e;
+    if ((e = f(Tof(Tbwd, I), (long long)KB, tstr, 0, 0, nr, nr, r0, r0, true)) != cudaSuccess) return e;
     // rows above: right U[0:r0, r0:r0+nr]; left (L[r0:r0+nr, 0:r0])^H
-    if ((e = gemm(S, lu.ld, lu.stride, 0, r0, op, r0, nr, 0, r0)) != cudaSuccess) return e;
+    if (r0 > 0 && (e = f(S, lu.ld, lu.stride, 0, r0, r0, nr, 0, r0, false)) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// bf16 elements of one product's staged factor operand: q x (hi, lo) x 2M x DEEP_KP
+size_t prestage_elems(int q, int M) { return (size_t)q * 2 * (2 * (size_t)M) * DEEP_KP; }
+}  // namespace
+
+size_t tc_solve_prestage_bytes(long long n, int q, int KB) {
+  LuBatch<float> lu;
+  lu.n = (int)n;
+  lu.q = q;
+  size_t elems = 0;
+  walk_solve(lu, 0, KB, nullptr, nullptr,
+             [&](const float2*, long long, long long, int, int, int M, int, int, int, bool) -> cudaError_t {
+               elems += prestage_elems(q, M);
+               return cudaSuccess;
+             });
+  return elems * 2;
+}
+
+cudaError_t tc_solve_prestage(const LuBatch<float>& lu, int side, int KB, const float2* TL, const float2* TU,
+                              void* pre, cudaStream_t s) {
+  if (!pre || KB % 64 || KB > 256) return cudaErrorInvalidValue;
+  const int op = side == 0 ? OP_N : OP_C;
+  __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(pre);
+  size_t off = 0;
+  return walk_solve(lu, side, KB, TL, TU,
+                    [&](const float2* L, long long ldl, long long strl, int lr, int lc, int M, int K, int, int,
+                        bool) -> cudaError_t {
+                      DeepGemm g;
+                      g.L = L; g.ldl = ldl; g.strl = strl; g.lr = lr; g.lc = lc; g.opL = op;
+                      g.M = M; g.N = 1; g.K = K; g.q = lu.q;
+                      DeepStaging sa;
+                      sa.Ast = base + off;
+                      sa.Bst = base;  // not written (A part only)
+                      sa.rows_max = 2LL * M;
+                      sa.cols_max = 1;
+                      sa.q = lu.q;
+                      off += prestage_elems(lu.q, M);
+                      return deep_stage(g, sa, s, 1);
+                    });
+}
+
+cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, int KB, const float2* TL,
+                          const float2* TU, const DeepStaging& st, cudaStream_t s, const void* pre) {
+  if (m < 1 || m > st.cols_max || KB % 64 || KB > 256) return cudaErrorInvalidValue;
+  const long long n = lu.n, xs = n * m;
+  const int op = side == 0 ? OP_N : OP_C;
+  const __nv_bfloat16* base = reinterpret_cast<const __nv_bfloat16*>(pre);
+  size_t off = 0;
+  return walk_solve(lu, side, KB, TL, TU,
+                    [&](const float2* L, long long ldl, long long strl, int lr, int lc, int M, int K, int rowC,
+                        int rowU, bool overwrite) -> cudaError_t {
+                      DeepGemm g;
+                      g.C = X; g.ldc = n; g.strc = xs; g.cr = rowC; g.cc = 0;
+                      g.L = L; g.ldl = ldl; g.strl = strl; g.lr = lr; g.lc = lc; g.opL = op;
+                      g.U = X; g.ldu = n; g.stru = xs; g.ur = rowU; g.uc = 0;
+                      g.M = M; g.N = m; g.K = K; g.q = lu.q;
+                      g.overwrite = overwrite;
+                      if (!base) {
+                        cudaError_t e = deep_stage(g, st, s, 3);
+                        if (e != cudaSuccess) return e;
+                        return deep_run(g, 0, m, st, lu.flags, s);
+                      }
+                      // the factor operand was staged after the factorisation: stage X_I only
+                      DeepStaging sa = st;
+                      sa.Ast = const_cast<__nv_bfloat16*>(base + off);
+                      sa.rows_max = 2LL * M;
+                      off += prestage_elems(lu.q, M);
+                      cudaError_t e = deep_stage(g, sa, s, 2);
+                      if (e != cudaSuccess) return e;
+                      return deep_run(g, 0, m, sa, lu.flags, s);
+                    });
 }
 
 double tc_deep_flops(long long n, int q, int K0, int KB) {

@@ -39,8 +39,9 @@ struct DeepGemm {
   bool overwrite = false;  // C = -op(L) U instead of C -= op(L) U (C is not read)
 };
 
-// Stage L (rows 0..M) and U (columns 0..N) as split BF16 (one launch).
-cudaError_t deep_stage(const DeepGemm& g, const DeepStaging& st, cudaStream_t s);
+// Stage L (rows 0..M; parts & 1) and/or U (columns 0..N; parts & 2) as split
+// BF16 (one launch).
+cudaError_t deep_stage(const DeepGemm& g, const DeepStaging& st, cudaStream_t s, int parts = 3);
 // C[:, c0 : c0 + nc] -= L U[:, c0 : c0 + nc] from the staged operands
 // (persistent: one CTA per SM, 128 x 256 tiles, K streamed through a
 // two-stage ring, double-buffered TMEM accumulators).
@@ -68,8 +69,17 @@ cudaError_t tc_far_gemm(const LuBatch<float>& lu, int K0, int KB, const float2* 
 // blocks, TU for the upper ones, conjugate-transposed on side 1; made by
 // block_inverse_negated), then the rest of the sweep's rows by
 // X_rest -= op(S_block) X_I with K = KB.
+// pre (or nullptr): the factor operands of every product of this side, staged
+// once after the factorisation by tc_solve_prestage; then each product stages
+// only its block of X.
 cudaError_t tc_solve_deep(const LuBatch<float>& lu, int side, float2* X, int m, int KB, const float2* TL,
-                          const float2* TU, const DeepStaging& st, cudaStream_t s);
+                          const float2* TU, const DeepStaging& st, cudaStream_t s, const void* pre = nullptr);
+// Bytes of one side's staged factor operands, and the staging itself (the
+// products of tc_solve_deep in its order: -T_I and the off-diagonal factor
+// blocks, conjugate-transposed on side 1, as split BF16 in the A' form).
+size_t tc_solve_prestage_bytes(long long n, int q, int KB);
+cudaError_t tc_solve_prestage(const LuBatch<float>& lu, int side, int KB, const float2* TL, const float2* TU,
+                              void* pre, cudaStream_t s);
 // Algorithmic flops and HBM bytes of one such update (8 flops per complex MAC;
 // C read and written once, L and U read once, 8 bytes per complex64 entry).
 double tc_deep_flops(long long n, int q, int K0, int KB);
