@@ -220,7 +220,7 @@ struct feast_handle {
   double upd_flops = 0, upd_bytes = 0;
   TcStaging staging_left;              // the left solves' own staging (they run beside the right ones)
   cudaStream_t side = nullptr;         // stream of the left solves
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr, join_ev2 = nullptr;
   void* schur_log = nullptr;
   double2* gemm_ws = nullptr;  // split-K partial products
   // mixed path: FP64-accurate n x n x m0 products on the BF16 tensor cores
@@ -229,6 +229,8 @@ struct feast_handle {
   OzOperator oz[4];
   bool oz_ready[4] = {false, false, false, false};
   OzWork ozw;
+  OzWork ozw2;           // the left side's products on the side stream (Bi-FEAST)
+  bool has_ozw2 = false;
   float2* s32 = nullptr;       // FP32 Schur work: C, Z, V, W, lambda (m0 x m0 each)
   size_t gemm_ws_elems = 0;
   std::vector<void*> allocs;
@@ -341,21 +343,25 @@ cudaError_t zg(feast_handle* h, int opA, int opB, int M, int N, int K, zc alpha,
 // C (n x cols, cols <= m0; default m0) = op(M) X for M = A (which = 0) or B (which = 1), op = OP_N or OP_C:
 // on the emulated-FP64 tensor-core path when the handle uses it (the digits of
 // op(M) are made on first use), else the DMMA GEMM.
-cudaError_t big_product(feast_handle* h, int which, int op, const double2* X, double2* C, int cols = -1) {
+// side = true: on the side stream with its own work area (the operator's
+// digits are made on that stream at first use, and only that side uses them)
+cudaError_t big_product(feast_handle* h, int which, int op, const double2* X, double2* C, int cols = -1,
+                        bool side = false) {
   const int n = (int)h->n, m = cols < 0 ? h->m0 : cols;
   const double2* Mx = which == 0 ? h->A : h->B;
   if (!h->use_oz) return zg(h, op, OP_N, n, m, n, zc(1.0), Mx, n, X, n, zc(0.0), C, n);
+  cudaStream_t s = side ? h->side : h->st;
   const int slot = which * 2 + (op == OP_C ? 1 : 0);
   if (!h->oz_ready[slot]) {
     void* base = nullptr;
     cudaError_t e = dalloc(h, &base, oz_operator_bytes(n));
     if (e != cudaSuccess) return e;
     oz_operator_layout(base, n, &h->oz[slot]);
-    e = oz_make_operator(Mx, n, op, h->oz[slot], h->st);
+    e = oz_make_operator(Mx, n, op, h->oz[slot], s);
     if (e != cudaSuccess) return e;
     h->oz_ready[slot] = true;
   }
-  return oz_apply(h->oz[slot], X, n, m, C, n, h->ozw, h->flags, h->st);
+  return oz_apply(h->oz[slot], X, n, m, C, n, side ? h->ozw2 : h->ozw, h->flags, s);
 }
 
 feast_status read_flags(feast_handle* h) {
@@ -827,11 +833,19 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   // the left block is orthonormalised on the side stream, beside the right one
   // and the products A Q, B Q (the two latency-bound kernels share the SMs)
   const bool par = bi && h->side && h->orth_scratch2;
+  // with its own work area the side stream also forms A^H Qhat and B^H Qhat,
+  // hidden behind the reduced problem (one-CTA kernels) on the main stream
+  const bool side_products = par && !h->opt.symmetric && h->use_oz && h->has_ozw2;
   if (par) {
     CK(cudaEventRecord(h->fork_ev, h->st));
     CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
     CK(orth_cgs2(h->Qho, n, m, h->orth_scratch2, h->flags, h->side));
     CK(cudaEventRecord(h->join_ev, h->side));
+    if (side_products) {
+      CK(big_product(h, 0, OP_C, h->Qho, h->AhQ, -1, true));
+      if (h->hasB) CK(big_product(h, 1, OP_C, h->Qho, h->BhQ, -1, true));
+      CK(cudaEventRecord(h->join_ev2, h->side));
+    }
   }
   CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st));
   if (bi && !par) CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
@@ -929,6 +943,9 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
         CK(conj_copy(h->BQ, h->BhQ, (size_t)n * m, h->st));
         BhQp = h->BhQ;
       }
+    } else if (side_products) {
+      CK(cudaStreamWaitEvent(h->st, h->join_ev2, 0));
+      if (h->hasB) BhQp = h->BhQ;
     } else {
       CK(big_product(h, 0, OP_C, h->Qho, h->AhQ));
       if (h->hasB) {
@@ -1184,6 +1201,7 @@ void feast_destroy(feast_handle* h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
+  if (h->join_ev2) cudaEventDestroy(h->join_ev2);
   if (h->norm_st) cudaStreamDestroy(h->norm_st);
   if (h->norm_ev) cudaEventDestroy(h->norm_ev);
   delete h;
@@ -1347,6 +1365,12 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     AL(ozbase, oz_work_bytes((int)n, m0));
     oz_work_layout(ozbase, (int)n, m0, &h->ozw);
     h->use_oz = true;
+    if (h->opt.algo == FEAST_ALGO_BI && !h->opt.symmetric) {
+      void* ozbase2 = nullptr;
+      AL(ozbase2, oz_work_bytes((int)n, m0));
+      oz_work_layout(ozbase2, (int)n, m0, &h->ozw2);
+      h->has_ozw2 = true;
+    }
   }
   if (mx) {
     AL(h->staging.Ast, tc_staging_bytes_A(n, h->q));
@@ -1418,6 +1442,7 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
     if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&h->join_ev2, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   }
 #undef AL
   if ((e = cudaStreamCreateWithFlags(&h->norm_st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
