@@ -701,6 +701,10 @@ def run_ours(args):
                       "converged": sol["converged"], "max_res": float(np.max(resid)),
                       "res_hist": sol["res_hist"], "t_factor_ms": sol["t_factor_ms"],
                       "t_filter_ms": sol["t_filter_ms"], "t_rr_ms": sol["t_rr_ms"], "eig_err": eig_err},
+            "rr_phase_ms": dict(zip(("orth_Q", "AQ_BQ_and_orth_Qhat", "projections", "Bhat_inverse_C",
+                                     "schur_eigvec_Winv", "fp64_refinement", "right_ritz_residuals",
+                                     "left_ritz_residuals"),
+                                    np.mean([st["t_rr_phase_ms"] for st in stats], axis=0).tolist())),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches), "batched": batched, "autotune": tune,
         }

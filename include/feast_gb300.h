@@ -181,6 +181,12 @@ typedef struct {
   double update_flops;   /* algorithmic flops of the K = 64 update launches         */
   double update_bytes;   /* and their algorithmic HBM bytes                         */
   int tuned;             /* 1 if lu_outer / panel_cluster came from options.tune_cache */
+  double t_rr_phase_ms[8]; /* the last Rayleigh-Ritz step by phase, on the main stream
+                            (timing): orthonormal basis of Q; A Q and B Q (and the
+                            wait for Qhat's basis); the projections Qhat^H A Q,
+                            Qhat^H B Q; Bhat^{-1} and C; Schur form, eigenvectors
+                            and W^{-1}; FP64 refinement sweeps; right Ritz vectors
+                            and residuals; left ones                               */
 } feast_stats;
 
 typedef struct feast_handle feast_handle;

@@ -73,7 +73,8 @@ class feast_stats(ctypes.Structure):
                 ("q", ctypes.c_int), ("shift_info", ctypes.c_int * 256), ("refine_sweeps", ctypes.c_int),
                 ("refactored", ctypes.c_int), ("lu_outer", ctypes.c_int), ("t_deep_ms", ctypes.c_double),
                 ("deep_launches", ctypes.c_int), ("deep_flops", ctypes.c_double), ("deep_bytes", ctypes.c_double),
-                ("update_flops", ctypes.c_double), ("update_bytes", ctypes.c_double), ("tuned", ctypes.c_int)]
+                ("update_flops", ctypes.c_double), ("update_bytes", ctypes.c_double), ("tuned", ctypes.c_int),
+                ("t_rr_phase_ms", ctypes.c_double * 8)]
 
 
 class FeastError(RuntimeError):
@@ -350,6 +351,7 @@ def feast_get_stats(h):
                 update_launches=st.update_launches, t_filter_ms=st.t_filter_ms, t_rr_ms=st.t_rr_ms,
                 q=st.q, shift_info=list(st.shift_info[:st.q]), refine_sweeps=st.refine_sweeps,
                 refactored=st.refactored, lu_outer=st.lu_outer, t_deep_ms=st.t_deep_ms,
+                t_rr_phase_ms=list(st.t_rr_phase_ms),
                 deep_launches=st.deep_launches, deep_flops=st.deep_flops, deep_bytes=st.deep_bytes,
                 update_flops=st.update_flops, update_bytes=st.update_bytes, tuned=st.tuned)
 

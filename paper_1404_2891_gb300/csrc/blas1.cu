@@ -26,6 +26,39 @@ __global__ void k_form_shifted(const double2* A, long long lda, const double2* B
   }
 }
 
+// complex64 with n even: two consecutive rows per thread, 16-byte stores
+// (n even keeps every pair 16-byte aligned in every shifted matrix)
+__global__ void k_form_shifted_pairs(const double2* A, long long lda, const double2* B, long long ldb,
+                                     const double2* z, int q, int n, float2* S, long long strideS) {
+  __shared__ float2 sz[256];
+  for (int k = threadIdx.x; k < q && k < 256; k += blockDim.x) sz[k] = make_float2((float)z[k].x, (float)z[k].y);
+  __syncthreads();
+  const int half = n >> 1;
+  for (int j = blockIdx.y; j < n; j += gridDim.y)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < half; p += gridDim.x * blockDim.x) {
+      const int i = 2 * p;
+      float2 a[2], b[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const double2 av = A[(size_t)(i + u) + (size_t)j * lda];
+        a[u] = make_float2((float)av.x, (float)av.y);
+        if (B) {
+          const double2 bv = B[(size_t)(i + u) + (size_t)j * ldb];
+          b[u] = make_float2((float)bv.x, (float)bv.y);
+        } else {
+          b[u] = make_float2(i + u == j ? 1.f : 0.f, 0.f);
+        }
+      }
+      const size_t idx = (size_t)i + (size_t)j * n;
+      for (int k = 0; k < q; ++k) {
+        const float2 zk = k < 256 ? sz[k] : make_float2((float)z[k].x, (float)z[k].y);
+        const float2 s0 = csub<float>(cmul<float>(zk, b[0]), a[0]);
+        const float2 s1 = csub<float>(cmul<float>(zk, b[1]), a[1]);
+        *reinterpret_cast<float4*>(S + (size_t)k * strideS + idx) = make_float4(s0.x, s0.y, s1.x, s1.y);
+      }
+    }
+}
+
 template <typename T>
 __global__ void k_accumulate(const cplx<T>* Xs, AccTree t, int n, int m, const double2* coef, const double2* c0,
                              const double2* Y, const int32_t* rowmap, double2* Q) {
@@ -255,6 +288,13 @@ cudaError_t form_shifted(const double2* A, long long lda, const double2* B, long
                          int q, int n, cplx<T>* S, long long strideS, cudaStream_t s) {
   feast_count_launch();
   dim3 grid((unsigned)((n + 255) / 256 < 8 ? (n + 255) / 256 : 8), (unsigned)(n < 65535 ? n : 65535));
+  if constexpr (std::is_same<T, float>::value) {
+    if (n % 2 == 0 && strideS % 2 == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
+      dim3 g2((unsigned)((n / 2 + 255) / 256 < 8 ? (n / 2 + 255) / 256 : 8), grid.y);
+      k_form_shifted_pairs<<<g2, 256, 0, s>>>(A, lda, B, ldb, z, q, n, S, strideS);
+      return cudaGetLastError();
+    }
+  }
   k_form_shifted<T><<<grid, 256, 0, s>>>(A, lda, B, ldb, z, q, n, S, strideS);
   return cudaGetLastError();
 }

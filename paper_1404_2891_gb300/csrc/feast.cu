@@ -176,6 +176,10 @@ struct feast_handle {
   // ||A||_2 is estimated on its own stream at creation, beside the first
   // factorisation; norm_ev marks its end and the value is read on first use
   cudaStream_t norm_st = nullptr;
+  // U's diagonal-block inverses for the blocked solves, made during the
+  // factorisation on a low-priority stream as each outer block finishes
+  cudaStream_t tinv_st = nullptr;
+  cudaEvent_t tinv_fork = nullptr, tinv_join = nullptr;
   cudaEvent_t norm_ev = nullptr;
   bool norm_ready = false;
   bool factored = false;
@@ -248,6 +252,7 @@ struct feast_handle {
   bool have_rr = false;
   // timing
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> rr_ev;  // phase marks of the Rayleigh-Ritz step (timing)
   double t_factor = 0, t_filter = 0, t_rr = 0, t_update = 0;
   int n_update = 0;
   std::vector<cudaEvent_t> upd_ev;
@@ -422,6 +427,14 @@ cudaError_t far_hook(const LuBatch<float>& lu, int K0, int KB, void* c, cudaStre
   feast_handle* h = reinterpret_cast<feast_handle*>(c);
   const int far0 = K0 + KB, nfar = lu.n - far0;
   if (nfar <= 0) return cudaSuccess;
+  // the block's U part is final: -U_II^{-1} on the low-priority stream
+  if (h->tinv_st) {
+    cudaError_t e2 = cudaEventRecord(h->tinv_fork, s);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(h->tinv_st, h->tinv_fork, 0);
+    if (e2 == cudaSuccess)
+      e2 = block_inverse_negated(lu, true, KB, K0 / KB, 1, h->TU + (size_t)(K0 / KB) * lu.q * KB * KB, h->tinv_st);
+    if (e2 != cudaSuccess) return e2;
+  }
   cudaError_t e = block_swaps_far(lu, K0, KB, s);
   if (e != cudaSuccess) return e;
   // T = -L11^{-1} of this block, kept for the solves (block-major, all blocks)
@@ -498,7 +511,14 @@ feast_status factor_impl(feast_handle* h) {
       const int KB = h->lu_outer;
       CK(block_inverse_negated(lu, false, KB, h->nblk - 1, 1, h->TL + (size_t)(h->nblk - 1) * h->q * KB * KB,
                                   h->st));
-      CK(block_inverse_negated(lu, true, KB, 0, h->nblk, h->TU, h->st));
+      if (h->tinv_st) {  // the far steps started the other blocks' U inverses on their stream
+        CK(block_inverse_negated(lu, true, KB, h->nblk - 1, 1, h->TU + (size_t)(h->nblk - 1) * h->q * KB * KB,
+                                    h->st));
+        CK(cudaEventRecord(h->tinv_join, h->tinv_st));
+        CK(cudaStreamWaitEvent(h->st, h->tinv_join, 0));
+      } else {
+        CK(block_inverse_negated(lu, true, KB, 0, h->nblk, h->TU, h->st));
+      }
     } else {
       CK(lu_factor_batched<T>(lu, h->nb, use_upd, use_ctx, h->st));
     }
@@ -825,6 +845,17 @@ feast_status run_filter(feast_handle* h, const double2* R, const double2* Yc0, b
 feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   const int n = (int)h->n, m = h->m0;
   const bool bi = Qhin != nullptr;
+  if (h->opt.timing) {
+    while (h->rr_ev.size() < 9) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->rr_ev.push_back(e);
+    }
+  }
+  auto mark = [&](int i) {
+    if (h->opt.timing) cudaEventRecord(h->rr_ev[i], h->st);
+  };
+  mark(0);
   const size_t blk = (size_t)n * m * sizeof(double2);
   const zc one(1.0), zero(0.0);
   CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned), h->st));
@@ -849,6 +880,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   }
   CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st));
   if (bi && !par) CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
+  mark(1);
   const double2* Vb = bi ? h->Qho : h->Qo;
   CK(big_product(h, 0, OP_N, h->Qo, h->AQ));
   const double2* BQp = h->Qo;
@@ -857,8 +889,10 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     BQp = h->BQ;
   }
   if (par) CK(cudaStreamWaitEvent(h->st, h->join_ev, 0));
+  mark(2);
   CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, h->AQ, n, zero, h->Ahat, m));
   CK(zg(h, OP_C, OP_N, m, m, n, one, Vb, n, BQp, n, zero, h->Bhat, m));
+  mark(3);
   // reduced problem: C = B^{-1} A^, Schur form, eigenvectors
   const size_t sm = (size_t)m * m * sizeof(double2);
   // X <- X (2I - M X): quadratic convergence to M^{-1} (DMMA products; LUW, Zs scratch)
@@ -885,6 +919,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   CK(newton_schulz(h->Bhat, h->Binv, 3));
   CK(inverse_guard(h->Bhat, h->Binv, h->LUB, h->pivB));
   CK(zg(h, OP_N, OP_N, m, m, m, one, h->Binv, m, h->Ahat, m, zero, h->Cm, m));
+  mark(4);
   // Schur form and eigenvectors in FP32, then two FP64 refinement sweeps:
   // E = W^{-1} C W (DMMA products), lam = diag(E), W <- W (I + Delta).
   {
@@ -913,6 +948,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     CK(to_c128(W32, h->Minv, mm, h->st));
     CK(newton_schulz(h->W, h->Minv, 3));
     CK(inverse_guard(h->W, h->Minv, h->LUW, h->pivW));
+    mark(5);
     for (int sweep = 0; sweep < 2; ++sweep) {
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->Cm, m, h->W, m, zero, h->V, m));
       CK(zg(h, OP_N, OP_N, m, m, m, one, h->Minv, m, h->V, m, zero, h->Zs, m));
@@ -923,6 +959,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
       CK(inverse_guard(h->W, h->Minv, h->LUW, h->pivW));
     }
   }
+  mark(6);
   // Ritz vectors and residuals
   CK(zg(h, OP_N, OP_N, n, m, m, one, h->Qo, n, h->W, m, zero, h->X, n));
   CK(zg(h, OP_N, OP_N, n, m, m, one, h->AQ, n, h->W, m, zero, h->AX, n));
@@ -934,6 +971,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   CK(column_norms(h->X, n, m, h->xn, h->st));
   CK(scale_columns_inv(h->X, h->AX, h->hasB ? h->BX : nullptr, n, m, h->xn, nullptr, h->st));
   CK(residual_columns(h->AX, BXp, h->lam, 0, n, m, h->E, h->res, nullptr, h->st));
+  mark(7);
   if (bi) {
     const double2* BhQp = h->Qho;
     if (h->opt.symmetric) {
@@ -967,6 +1005,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
     CK(column_norms(h->Xl, n, m, h->xln, h->st));
     CK(residual_columns(h->AhX, BhXp, h->lam, 1, n, m, h->Eh, h->resl, h->xln, h->st));
   }
+  mark(8);
   h->h_lam.resize(m);
   h->h_res.resize(m);
   h->h_resl.assign(m, 0.0);
@@ -1202,7 +1241,14 @@ void feast_destroy(feast_handle* h) {
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->join_ev2) cudaEventDestroy(h->join_ev2);
+  for (cudaEvent_t e : h->rr_ev) cudaEventDestroy(e);
   if (h->norm_st) cudaStreamDestroy(h->norm_st);
+  if (h->tinv_st) {
+    cudaStreamSynchronize(h->tinv_st);
+    cudaStreamDestroy(h->tinv_st);
+  }
+  if (h->tinv_fork) cudaEventDestroy(h->tinv_fork);
+  if (h->tinv_join) cudaEventDestroy(h->tinv_join);
   if (h->norm_ev) cudaEventDestroy(h->norm_ev);
   delete h;
 }
@@ -1446,6 +1492,13 @@ feast_status feast_create(feast_handle** out, int64_t n, const feast_z* A, int64
   }
 #undef AL
   if ((e = cudaStreamCreateWithFlags(&h->norm_st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+  if (h->lu_outer > 0) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if ((e = cudaStreamCreateWithPriority(&h->tinv_st, cudaStreamNonBlocking, lo)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&h->tinv_fork, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&h->tinv_join, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  }
   if ((e = cudaEventCreateWithFlags(&h->norm_ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   if (h->opt.timing)
     for (auto& ev : h->ev) cudaEventCreate(&ev);
@@ -1503,6 +1556,12 @@ feast_status feast_get_stats(const feast_handle* h, feast_stats* st) {
   st->tuned = h->tuned ? 1 : 0;
   st->t_filter_ms = h->t_filter;
   st->t_rr_ms = h->t_rr;
+  if (h->opt.timing && h->rr_ev.size() >= 9) {
+    for (int i = 0; i < 8; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->rr_ev[i], h->rr_ev[i + 1]) == cudaSuccess) st->t_rr_phase_ms[i] = ms;
+    }
+  }
   return FEAST_OK;
 }
 
