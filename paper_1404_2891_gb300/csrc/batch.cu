@@ -253,6 +253,11 @@ struct feast_batch {
     int32_t *mv = nullptr, *pinv = nullptr, *rowmaps = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
+    // the class's factorisation captured once into a graph, so that all
+    // classes are submitted at once and run side by side (one host call each
+    // instead of about a thousand launches one class after another)
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_failed = false;
   };
   std::vector<TcClass> tcc;
   int tc_min = 768;
@@ -469,19 +474,43 @@ cudaError_t factor_classes(feast_batch* b) {
     TrailingUpdateFn<float> upd = nullptr;
     void* ctx = nullptr;
     select_trailing_update<float>(&upd, &ctx, &c.st);
-    if (c.dst.Ast)
-      e = lu_factor_two_level(lu, 64, 256, upd, ctx, class_far, class_deep, &c, c.s);
-    else
-      e = lu_factor_batched<float>(lu, 64, upd, ctx, c.s);
+    auto run = [&]() -> cudaError_t {
+      return c.dst.Ast ? lu_factor_two_level(lu, 64, 256, upd, ctx, class_far, class_deep, &c, c.s)
+                       : lu_factor_batched<float>(lu, 64, upd, ctx, c.s);
+    };
+    if (!c.gexec && !c.graph_failed) {
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeRelaxed);
+      cudaError_t re = ce == cudaSuccess ? run() : ce;
+      if (ce == cudaSuccess) ce = cudaStreamEndCapture(c.s, &g);
+      if (ce == cudaSuccess && re == cudaSuccess && g) ce = cudaGraphInstantiate(&c.gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (ce != cudaSuccess || re != cudaSuccess || !c.gexec) {
+        c.graph_failed = true;  // direct launches from here on
+        if (c.gexec) cudaGraphExecDestroy(c.gexec);
+        c.gexec = nullptr;
+        cudaGetLastError();
+      }
+    }
+    e = c.gexec ? cudaGraphLaunch(c.gexec, c.s) : run();
     if (e != cudaSuccess) return e;
     if ((e = cudaEventRecord(c.done, c.s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(b->st, c.done, 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// Persistent launch over one of the task lists; a factorisation launch runs
-// the tensor-core classes first (the persistent kernel then solves them).
+// The batch's stream waits for every class.
+cudaError_t join_classes(feast_batch* b) {
+  cudaError_t e;
+  for (feast_batch::TcClass& c : b->tcc)
+    if ((e = cudaStreamWaitEvent(b->st, c.done, 0)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Persistent launch over one of the task lists.  A factorisation launch also
+// factors the tensor-core classes on their streams: beside the persistent
+// kernel when it only factors (its tasks never touch a class matrix), before it
+// when it also solves (the class matrices' solve tasks need their factors).
 cudaError_t launch_lu(feast_batch* b, const int4* tasks, int n) {
   if (tasks == b->t_factor || tasks == b->t_first) {
     cudaError_t e;
@@ -494,6 +523,9 @@ cudaError_t launch_lu(feast_batch* b, const int4* tasks, int n) {
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->info, 0, b->nmat * sizeof(int), b->st)) != cudaSuccess) return e;
     if ((e = factor_classes(b)) != cudaSuccess) return e;
+    if (tasks == b->t_first && (e = join_classes(b)) != cudaSuccess) return e;
+    if ((e = batch_lu_launch(lu_args(b, tasks, n), b->Nmax, b->grid, b->st)) != cudaSuccess) return e;
+    return tasks == b->t_factor ? join_classes(b) : cudaSuccess;
   }
   return batch_lu_launch(lu_args(b, tasks, n), b->Nmax, b->grid, b->st);
 }
@@ -664,6 +696,7 @@ void feast_batch_destroy(feast_batch* b) {
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
   for (auto& c : b->tcc) {
+    if (c.gexec) cudaGraphExecDestroy(c.gexec);
     if (c.s) cudaStreamDestroy(c.s);
     if (c.done) cudaEventDestroy(c.done);
   }
