@@ -92,9 +92,11 @@ struct OrthArgs {
   double2* Q;
   int n, m, rows_per;
   double2* part;  // 2 x grid x m
+  double2* fin = nullptr;  // 2 x (m + 1): the reduced slots of a phase (shared-memory kernel)
   unsigned* bar;  // 2 unsigned
   unsigned long long wait_ns = 1000000000ull;  // limit of each grid-barrier wait (spin form)
   unsigned* flags;
+  int col0 = 0;  // index of column 0 within a larger basis (restart rows differ per panel)
 };
 
 __device__ double block_sum(double v, double* red) {
@@ -191,7 +193,7 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
     tot = block_sum(tot, red);
     ++use;
     if ((!(tot > SAFE_MIN) || tot < 0.5 * r1sq) && retries < ORTH_RETRIES) {
-      const int rr = orth_restart_row(j, retries++, n);
+      const int rr = orth_restart_row(a.col0 + j, retries++, n);
       for (int r = r0 + tid; r < r1; r += ORTH_THREADS) qj[r] = make_double2(r == rr ? 1.0 : 0.0, 0.0);
       __syncthreads();
       continue;
@@ -272,24 +274,27 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
       for (int gr = 1; gr < groups; ++gr) acc = cadd<double>(acc, s_red[gr * ns + i]);
       part[(size_t)g * S + i] = acc;
     }
-    ++phase;
     if (!grid_barrier_spin(a.bar, G, a.flags, &s_ok, a.wait_ns)) return false;
-    // every CTA sums the G partials of every slot: thread (slot i, group k)
-    // takes the CTAs g = k mod K, the K groups meet in shared memory
-    const int K = ns <= ORTH_THREADS ? ORTH_THREADS / ns : 1;
-    for (int t = tid; t < ns * K; t += ORTH_THREADS) {
-      const int i = t % ns, k = t / ns;
+    // CTA g sums the G partials of slots g, g + G, ... (scalar FP64 is the
+    // slow pipe here, so no CTA sums every slot): thread t takes partial t,
+    // then a fixed tree over the threads, the same in every CTA; a second
+    // barrier publishes the sums
+    double2* fin = a.fin + (size_t)(phase & 1) * S;
+    ++phase;
+    for (int i = g; i < ns; i += G) {
       double2 acc = make_double2(0.0, 0.0);
-#pragma unroll 8
-      for (int gg = k; gg < G; gg += K) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * S + i));
-      s_red[t] = acc;
+      for (int gg = tid; gg < G; gg += ORTH_THREADS) acc = cadd<double>(acc, __ldcg(part + (size_t)gg * S + i));
+      s_red[tid] = acc;
+      __syncthreads();
+      for (int w = ORTH_THREADS / 2; w > 0; w >>= 1) {
+        if (tid < w) s_red[tid] = cadd<double>(s_red[tid], s_red[tid + w]);
+        __syncthreads();
+      }
+      if (tid == 0) fin[i] = s_red[0];
+      __syncthreads();
     }
-    __syncthreads();
-    for (int i = tid; i < ns; i += ORTH_THREADS) {
-      double2 acc = s_red[i];
-      for (int k = 1; k < K; ++k) acc = cadd<double>(acc, s_red[k * ns + i]);
-      s_r[i] = acc;
-    }
+    if (!grid_barrier_spin(a.bar, G, a.flags, &s_ok, a.wait_ns)) return false;
+    for (int i = tid; i < ns; i += ORTH_THREADS) s_r[i] = __ldcg(fin + i);
     __syncthreads();
     return true;
   };
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
     if (!reduce_phase(j, nc, j - 1)) return;
     const double nrm2 = s_r[nc].x;
     if ((!(nrm2 > SAFE_MIN) || nrm2 < 0.5 * r1sq) && retries < ORTH_RETRIES) {
-      const int c = j - 1, rr = orth_restart_row(c, retries++, n);
+      const int c = j - 1, rr = orth_restart_row(a.col0 + c, retries++, n);
       for (int rl = tid; rl < R; rl += ORTH_THREADS) sQ[rl * ld + c] = make_double2(r0 + rl == rr ? 1.0 : 0.0, 0.0);
       __syncthreads();
       if (c == 0) r1sq = 0.0;
@@ -668,18 +673,20 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inverse32(const double2* M, i
 }  // namespace
 
 size_t orth_scratch_bytes(int n, int m) {
-  return (size_t)2 * 160 * (m + 1) * sizeof(double2) + 256;
+  return (size_t)2 * 160 * (m + 1) * sizeof(double2) + (size_t)2 * (m + 1) * sizeof(double2) + 256;
 }
 
-cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s) {
+cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s, int col0) {
   if (m > ORTH_MAX_M || m < 1 || n < 1) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   OrthArgs a;
   a.Q = Q; a.n = n; a.m = m;
+  a.col0 = col0;
   a.bar = reinterpret_cast<unsigned*>(scratch);
   a.part = reinterpret_cast<double2*>(reinterpret_cast<char*>(scratch) + 256);
+  a.fin = a.part + (size_t)2 * 160 * (m + 1);
   a.flags = flags;
   a.wait_ns = feast_wait_limit_ns(1000000000ull);
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 256, s);

@@ -10,7 +10,9 @@
 // twice-is-enough test) restarts from a unit vector.
 // scratch: >= 2 * grid * m double2 + 4 unsigned (see orth_scratch_bytes).
 size_t orth_scratch_bytes(int n, int m);
-cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s);
+// col0: index of Q's column 0 within a larger basis (a panel of it), so that
+// dependent columns of different panels restart from different unit vectors.
+cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s, int col0 = 0);
 
 // Single-CTA dense kernels on m x m column-major matrices (ld m) in global memory.
 // LU with partial pivoting in place (piv: m ints).
