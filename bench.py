@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-pencil workload")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--batch-only", action="store_true", help="run only the batched workload (prints its object)")
+    p.add_argument("--batch-direct", action="store_true",
+                   help="batched workload: launch the size classes' factorisations kernel by kernel (no graphs)")
     p.add_argument("--panel-cluster", type=int, default=0,
                    help="0 = library default or tuned, k > 0 = cluster panels from k rows, -1 = one CTA")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
@@ -360,7 +362,8 @@ def run_batch(fg, torch, args, barrier):
     cfgs = workloads.batch_prescribed(count=args.batch_count, seed=rank_seeds(rank)["batch"])
     cons = [fg.make_contour(center=c["contour"]["c"], R=c["contour"]["R"], aspect=c["contour"]["a"],
                             rule=c["contour"]["rule"], N_e=c["N_e"]) for c in cfgs]
-    opts = fg.make_options(algo="R", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True)
+    opts = fg.make_options(algo="R", precision="mixed", tol=1e-10, max_iter=args.solve_iters, timing=True,
+                           batch_direct=args.batch_direct)
     A_d = [colmajor_device(torch, c["A"]) for c in cfgs]
     Y_d = [colmajor_device(torch, c["U0"]) for c in cfgs]
     b = fg.feast_batch_create(A_d, cons, [c["m0"] for c in cfgs], opts)
@@ -394,13 +397,27 @@ def run_batch(fg, torch, args, barrier):
     lu_ms = float(np.median(lu))
     it = st["t_iter_ms"]
     fg.feast_batch_destroy(b)
+    # the same factorisations with every matrix in the persistent launch (no size classes)
+    bp = fg.feast_batch_create(A_d, cons, [c["m0"] for c in cfgs],
+                               fg.make_options(algo="R", precision="mixed", timing=True, batch_tc_min=-1))
+    fg.feast_batch_factor(bp)
+    lu_p = []
+    for _ in range(max(1, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        fg.feast_batch_factor(bp)
+        e1.record()
+        barrier()
+        lu_p.append(e0.elapsed_time(e1))
+    fg.feast_batch_destroy(bp)
     fp64 = None if args.no_fp64 else run_batch_fp64(fg, torch, cfgs, cons, A_d, Y_d, barrier)
     return {"workload": (f"{args.batch_count} standard pencils A_p = V diag(lam) V^-1 (cond(V)=100), n log-uniform in "
                          "[256, 2048], 20-80 eigenvalues inside each circle, 8 midpoint nodes, m0 in 32..128, "
                          "R-FEAST mixed"),
             "pencils": info["count"], "shifted_matrices": info["nmat"], "persistent_ctas": info["grid"],
             "factor_tasks": info["tasks_factor"], "tc_min": tci["tc_min"], "tc_classes": tci["classes"],
-            "tc_matrices": tci["matrices"], "lu_ms": lu_ms,
+            "tc_matrices": tci["matrices"], "lu_ms": lu_ms, "lu_ms_persistent_only": float(np.median(lu_p)),
             "lu_tflops": info["lu_flops"] / (lu_ms * 1e-3) / 1e12,
             "iter1_ms": it[0] if it else None, "steady_iter_ms": float(np.median(it[1:])) if len(it) > 1 else None,
             "iters": st["iters"], "converged": st["converged"], "counts_exact": count_ok,

@@ -150,6 +150,10 @@ typedef struct {
                         by the persistent launch; 0 (default) = the tuned
                         value of options.tune_cache, else 768; -1 = every
                         matrix in the persistent launch                        */
+  int batch_direct;  /* batched path: nonzero = launch the classes'
+                        factorisations kernel by kernel instead of replaying
+                        the CUDA graph captured at their first use (for tools
+                        that cannot follow stream capture)                     */
 } feast_options;
 
 typedef struct {

@@ -55,7 +55,8 @@ class feast_options(ctypes.Structure):
                 ("timing", ctypes.c_int), ("symmetric", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("shift_begin", ctypes.c_int), ("shift_end", ctypes.c_int),
                 ("real_pencil", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("lu_outer", ctypes.c_int),
-                ("panel_cluster", ctypes.c_int), ("deep_solves", ctypes.c_int), ("batch_tc_min", ctypes.c_int)]
+                ("panel_cluster", ctypes.c_int), ("deep_solves", ctypes.c_int), ("batch_tc_min", ctypes.c_int),
+                ("batch_direct", ctypes.c_int)]
 
 
 class feast_segment(ctypes.Structure):
@@ -287,7 +288,7 @@ def make_contour(center=0.0, R=1.0, aspect=1.0, rule="trap_mid", N_e=8, nodes=No
 
 def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=1e-4, panel=0, timing=False,
                  symmetric=False, max_refine=0, refine_tol=1e-12, shifts=None, real_pencil=False, tune_cache=None,
-                 lu_outer=0, panel_cluster=0, deep_solves=0, batch_tc_min=0):
+                 lu_outer=0, panel_cluster=0, deep_solves=0, batch_tc_min=0, batch_direct=False):
     """shifts: (begin, end) range of the contour's nodes this handle owns (None = all)."""
     o = feast_options()
     load().feast_default_options(ctypes.byref(o))
@@ -304,6 +305,7 @@ def make_options(algo="BI", precision="mixed", tol=1e-10, max_iter=20, cand_tol=
     o.panel_cluster = int(panel_cluster)
     o.deep_solves = int(deep_solves)
     o.batch_tc_min = int(batch_tc_min)
+    o.batch_direct = int(batch_direct)
     return o
 
 

@@ -478,7 +478,7 @@ cudaError_t factor_classes(feast_batch* b) {
       return c.dst.Ast ? lu_factor_two_level(lu, 64, 256, upd, ctx, class_far, class_deep, &c, c.s)
                        : lu_factor_batched<float>(lu, 64, upd, ctx, c.s);
     };
-    if (!c.gexec && !c.graph_failed) {
+    if (!c.gexec && !c.graph_failed && !b->opt.batch_direct) {
       cudaGraph_t g = nullptr;
       cudaError_t ce = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeRelaxed);
       cudaError_t re = ce == cudaSuccess ? run() : ce;
