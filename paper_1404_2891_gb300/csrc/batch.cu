@@ -1016,7 +1016,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
     if ((e = upload(false, true, &b->t_solve, &b->n_solve, &mk)) != cudaSuccess) return bad(cuda_status(e));
   }
   // S_i = z_i I - A_p
-  if ((e = batch_form_shifted(b->A, b->d_pd, b->d_mats, b->dz, b->nmat, b->Nmax, b->S, b->st)) != cudaSuccess)
+  if ((e = batch_form_shifted(b->A, b->d_pd, b->d_mats, b->dz, b->nmat, b->Nmax, b->S, b->st, b->np)) != cudaSuccess)
     return bad(cuda_status(e));
   // grouped CGS2: CTAs per block in proportion to n, within the resident limit
   {
@@ -1102,7 +1102,7 @@ feast_status feast_batch_create(feast_batch** out, int count, const int64_t* n, 
 feast_status feast_batch_factor(feast_batch* b) {
   if (!b) return FEAST_ERR_ARG;
   if (b->factored) {  // an explicit call factors again
-    CK(batch_form_shifted(b->A, b->d_pd, b->d_mats, b->dz, b->nmat, b->Nmax, b->S, b->st));
+    CK(batch_form_shifted(b->A, b->d_pd, b->d_mats, b->dz, b->nmat, b->Nmax, b->S, b->st, b->np));
     b->factored = false;
   }
   return ensure_factored_first(b, false);

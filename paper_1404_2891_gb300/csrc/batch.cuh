@@ -64,8 +64,9 @@ size_t batch_lu_smem_bytes(int Nmax);
 int batch_lu_grid(int Nmax);  // resident CTAs on this device (0 if the kernel cannot run)
 cudaError_t batch_lu_launch(const BatchLuArgs& a, int Nmax, int grid, cudaStream_t s);
 // S_i = z_i I - A_p for every matrix of the batch (A_p FP64 n x n, ld n).
+// np > 0: one pass per pencil (A_p read once for all its shifts); else per matrix.
 cudaError_t batch_form_shifted(const double2* A, const GrpDesc* pd, const BMat* mats, const double2* z, int nmat,
-                               int Nmax, float2* S, cudaStream_t s);
+                               int Nmax, float2* S, cudaStream_t s, int np = 0);
 // Q_p = c0_p .* Y_p + sum_s coef_{p,s} .* X_{p,s}   (fixed order in s)
 cudaError_t batch_accumulate(const float2* X, const BMat* mats, const GrpDesc* pd, int np, int nmax, int mmax,
                              const double2* coef, const double2* c0, const double2* Y, const int* active,

@@ -450,6 +450,36 @@ __global__ void __launch_bounds__(NT, 1) k_batch_lu(BatchLuArgs a, int gcap) {
 }
 
 // ---------------------------------------------------------------- batch helpers
+// One CTA row per pencil: each entry of A_p is read once and written into all
+// of the pencil's shifted matrices (z_k - a, the padding as identity).
+__global__ void k_batch_form_p(const double2* A, const GrpDesc* pd, const BMat* mats, const double2* z, float2* S) {
+  __shared__ long long s_off[256];
+  const GrpDesc d = pd[blockIdx.y];
+  const int q = min(d.q, 256);
+  for (int k = threadIdx.x; k < q; k += blockDim.x) s_off[k] = mats[d.mat0 + k].soff;
+  __syncthreads();
+  const int N = mats[d.mat0].N, n = d.n;
+  const double2* Ap = A + d.onn;
+  for (int c = blockIdx.x; c < N; c += gridDim.x)
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const bool in = r < n && c < n;
+      double2 av = make_double2(0.0, 0.0);
+      if (in) av = Ap[(size_t)r + (size_t)c * n];
+      const size_t idx = (size_t)r + (size_t)c * N;
+      for (int k = 0; k < q; ++k) {
+        float2 v;
+        if (in) {
+          // the same arithmetic as the per-matrix form: FP64 difference, then rounding
+          const double2 zz = z[d.mat0 + k];
+          v = make_float2((float)((r == c ? zz.x : 0.0) - av.x), (float)((r == c ? zz.y : 0.0) - av.y));
+        } else {
+          v = make_float2(r == c ? 1.f : 0.f, 0.f);
+        }
+        S[s_off[k] + idx] = v;
+      }
+    }
+}
+
 __global__ void k_batch_form(const double2* A, const GrpDesc* pd, const BMat* mats, const double2* z, float2* S) {
   const BMat M = mats[blockIdx.y];
   const GrpDesc d = pd[M.pencil];
@@ -599,10 +629,14 @@ cudaError_t batch_lu_launch(const BatchLuArgs& a, int Nmax, int grid, cudaStream
 }
 
 cudaError_t batch_form_shifted(const double2* A, const GrpDesc* pd, const BMat* mats, const double2* z, int nmat,
-                               int Nmax, float2* S, cudaStream_t s) {
+                               int Nmax, float2* S, cudaStream_t s, int np) {
   if (nmat < 1) return cudaSuccess;
-  dim3 grid(std::min(Nmax, 256), nmat);
   feast_count_launch();
+  if (np > 0) {  // per pencil: A_p read once
+    k_batch_form_p<<<dim3(std::min(Nmax, 512), np), 256, 0, s>>>(A, pd, mats, z, S);
+    return cudaGetLastError();
+  }
+  dim3 grid(std::min(Nmax, 256), nmat);
   k_batch_form<<<grid, 256, 0, s>>>(A, pd, mats, z, S);
   return cudaGetLastError();
 }

@@ -74,10 +74,10 @@ def balanced_cuts(A, region, parts, trials=33, K=8, probes=32, seed=0):
     return sorted(cuts), counts
 
 
-def solve_region(A, region, parts, K=8, margin=1.5, extra=8, max_iter=20, seed=0, trials=33):
+def solve_region(A, region, parts, K=8, margin=1.5, extra=8, max_iter=20, seed=0, trials=33, tol=1e-10):
     """Eigenpairs of A (B = I) in the rectangle, found strip by strip in one
-    batched solve.  Returns dict(cuts, est_counts, strips=[dict(lam, X, res,
-    m_found)], stats)."""
+    batched solve (tol: the residual of the Sec. 5 stopping rule).  Returns
+    dict(cuts, est_counts, strips=[dict(lam, X, res, m_found)], stats)."""
     x0, x1, y0, y1 = region
     cuts, est = balanced_cuts(A, region, parts, trials=trials, K=K, seed=seed)
     edges = [x0] + cuts + [x1]
@@ -86,7 +86,8 @@ def solve_region(A, region, parts, K=8, margin=1.5, extra=8, max_iter=20, seed=0
     m0 = [int(min(160, n, max(8, math.ceil(margin * max(c, 0.0)) + extra))) for c in est]
     rng = np.random.default_rng(seed + 1)
     Y0 = [rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m)) for m in m0]
-    b = feast_batch_create([A] * parts, cons, m0, make_options(algo="R", precision="mixed", max_iter=max_iter))
+    b = feast_batch_create([A] * parts, cons, m0,
+                           make_options(algo="R", precision="mixed", max_iter=max_iter, tol=tol))
     try:
         out, st = feast_batch_solve(b, Y0)
     finally:
