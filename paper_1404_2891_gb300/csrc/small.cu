@@ -54,12 +54,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok,
                                   unsigned long long limit_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 32;
-    const unsigned gen = *vgen;
+    const unsigned* gptr = bar + 32;
+    const unsigned gen = ld_acquire_u32(gptr);
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
     int ok = 1;
@@ -68,9 +74,12 @@ __device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* fla
       __threadfence();
       atomicAdd(bar + 32, 1u);
     } else {
+      // poll with acquire loads; the global timer is read after the first
+      // unsuccessful poll and then once per 64 polls
       const unsigned long long t0 = global_ns();
-      while (*vgen == gen) {
-        if (global_ns() - t0 > limit_ns) {
+      for (unsigned polls = 1;; ++polls) {
+        if (ld_acquire_u32(gptr) != gen) break;
+        if ((polls & 63) == 1 && global_ns() - t0 > limit_ns) {
           atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
           ok = 0;
           break;
