@@ -114,6 +114,12 @@ def tune_single(n, m0, K=16, cache="tune.json", candidates=None, reps=2, seed=0,
         if verbose:
             print(f"lu_outer={outer} panel_cluster={pc}: {times[(outer, pc)]:.2f} ms")
     (outer, pc), t = min(times.items(), key=lambda kv: kv[1])
+    # within 1 % of the fastest, the library's default outer block (256 from
+    # n = 1024 on: the deepest K, the highest intensity) wins the tie
+    default_outer = 256 if n >= 1024 else -1
+    near = [(k, v) for k, v in times.items() if k[0] == default_outer and v <= 1.01 * t]
+    if near:
+        (outer, pc), t = min(near, key=lambda kv: kv[1])
     key = single_key(n, m0, q)
     entry = {"lu_outer": outer, "panel_cluster": pc, "t_factor_ms": t, "candidates": len(times),
              "note": f"median of {reps} factorisations of {q} shifted systems of order {n}"}
