@@ -13,41 +13,10 @@ namespace {
 
 constexpr double SAFE_MIN = 2.2250738585072014e-308;
 
-// ---------------------------------------------------------------- grid barrier
-// Sense-counting barrier for a cooperative launch.  Every wait is bounded: after
-// about a second the waiting CTA records DEVFLAG_TIMEOUT and the kernel returns.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    int ok = 1;
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*vgen == gen) {
-        if (++spins > (1ull << 24)) {
-          atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
-
-// The same barrier with the generation word on its own 128-byte line (bar + 32)
-// and the waiters polling without sleeping, bounded by the global timer.
+// ---------------------------------------------------------------- grid barriers
+// Sense-counting barriers for cooperative launches; every wait is bounded by
+// the global timer (the host's wait limit), after which the waiting CTA records
+// DEVFLAG_TIMEOUT and the kernel returns.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -60,6 +29,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
+// The generation word on its own 128-byte line (bar + 32).
 __device__ bool grid_barrier_spin(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok,
                                   unsigned long long limit_ns) {
   __syncthreads();
@@ -130,6 +100,40 @@ __device__ __forceinline__ int orth_restart_row(int c, int attempt, int n) {
   return (int)(((long long)c * 7919 + (long long)(attempt + 1) * 104729) % n);
 }
 
+// The sense-counting barrier with acquire-load polling, bounded by the global
+// timer (read after the first unsuccessful poll, then once per 64); the
+// generation word is bar + 1, as for grid_barrier.
+__device__ bool grid_barrier_poll(unsigned* bar, unsigned nblocks, unsigned* flags, int* s_ok,
+                                  unsigned long long limit_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned* gptr = bar + 1;
+    const unsigned gen = ld_acquire_u32(gptr);
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (unsigned polls = 1;; ++polls) {
+        if (ld_acquire_u32(gptr) != gen) break;
+        if ((polls & 63) == 1 && global_ns() - t0 > limit_ns) {
+          atomicOr(flags, (unsigned)DEVFLAG_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
 // CTA g of the G that share one block Q.
 __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const int G) {
   __shared__ double2 s_r[ORTH_MAX_M];
@@ -159,7 +163,7 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
         }
         part[(size_t)g * m + i] = acc;
       }
-      if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
+      if (!grid_barrier_poll(a.bar, G, a.flags, &s_ok, a.wait_ns)) return;
       // the G partial dot products of each coefficient: few partials are summed
       // by one thread each; many by one warp (parallel reads, shuffle sums)
       if (G <= 16) {
@@ -196,7 +200,7 @@ __device__ __forceinline__ void orth_body(const OrthArgs& a, const int g, const 
     for (int r = r0 + tid; r < r1; r += ORTH_THREADS) loc += cnorm2<double>(qj[r]);
     loc = block_sum(loc, red);
     if (tid == 0) part[(size_t)g * m] = make_double2(loc, 0.0);
-    if (!grid_barrier(a.bar, G, a.flags, &s_ok)) return;
+    if (!grid_barrier_poll(a.bar, G, a.flags, &s_ok, a.wait_ns)) return;
     double tot = 0.0;
     for (int gg = tid; gg < G; gg += ORTH_THREADS) tot += __ldcg(&part[(size_t)gg * m].x);
     tot = block_sum(tot, red);
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2(OrthArgs a) { orth_b
 // block, with a grid barrier of their own (bars + 2 p).
 __global__ void __launch_bounds__(ORTH_THREADS)
 k_orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, double2* part, unsigned* bars,
-                const int* active, unsigned* flags) {
+                const int* active, unsigned* flags, unsigned long long wait_ns) {
   int p = 0;
   while (p + 1 < np && cta0[p + 1] <= (int)blockIdx.x) ++p;
   if (!active[p]) return;  // the whole group leaves together
@@ -235,6 +239,7 @@ k_orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, double2*
   a.part = part + (size_t)2 * cta0[p] * ORTH_MAX_M;
   a.bar = bars + 2 * p;
   a.flags = flags;
+  a.wait_ns = wait_ns;
   orth_body(a, blockIdx.x - cta0[p], G);
 }
 
@@ -755,7 +760,8 @@ cudaError_t orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np
   if (np < 1) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(bars, 0, sizeof(unsigned) * 2 * np, s);
   if (e != cudaSuccess) return e;
-  void* args[] = {&Q, &pd, &cta0, &np, &part, &bars, &active, &flags};
+  unsigned long long wait_ns = feast_wait_limit_ns(1000000000ull);
+  void* args[] = {&Q, &pd, &cta0, &np, &part, &bars, &active, &flags, &wait_ns};
   feast_count_launch();
   return cudaLaunchCooperativeKernel((void*)k_orth_cgs2_grp, dim3(total_ctas), dim3(ORTH_THREADS), args, 0, s);
 }
