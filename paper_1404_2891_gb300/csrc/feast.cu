@@ -693,16 +693,12 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
   const int n = (int)h->n, m = h->m0;
   cplx<T>* Xs = reinterpret_cast<cplx<T>*>(h->Xs);
   const bool split = Rh && !h->opt.symmetric && h->side;
-  // the first filter after a factorisation stages the solves' factor operands
-  // (the left side's first, so that the left solves can start while the right
-  // side's are staged)
-  bool stage_right = false;
+  // the first filter after a factorisation stages the solves' factor operands,
+  // each side on the stream of its own solves (the two stagings side by side)
+  bool stage_right = false, stage_left = false;
   if constexpr (std::is_same<T, float>::value) {
     const bool deep = h->opt.deep_solves >= 0 && h->lu_outer > 0 && h->TU;
-    if (deep && Rh && !h->opt.symmetric && h->pre[1] && !h->pre_valid[1]) {
-      CK(tc_solve_prestage(lu, 1, h->lu_outer, h->TL, h->TU, h->pre[1], h->st));
-      h->pre_valid[1] = true;
-    }
+    stage_left = deep && Rh && !h->opt.symmetric && h->pre[1] && !h->pre_valid[1];
     stage_right = deep && h->pre[0] && !h->pre_valid[0];
   }
   if (split) CK(cudaEventRecord(h->fork_ev, h->st));  // the left solves start from here
@@ -763,6 +759,12 @@ feast_status filter_impl(feast_handle* h, const double2* R, const double2* Yc0, 
     if (std::is_same<T, float>::value) lul.tc = h->staging_left.Ast ? &h->staging_left : nullptr;
     cudaStream_t ls = split ? h->side : h->st;
     if (split) CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    if constexpr (std::is_same<T, float>::value) {
+      if (stage_left) {
+        CK(tc_solve_prestage(lu, 1, h->lu_outer, h->TL, h->TU, h->pre[1], ls));
+        h->pre_valid[1] = true;
+      }
+    }
     CK(rows_gather<T>(lul, Rh, Xsh, m, false, ls, h->realp));
     CK(solve_all<T>(h, lul, 1, Xsh, ms, ls));
     if (h->realp) {
