@@ -872,7 +872,7 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
   if (par) {
     CK(cudaEventRecord(h->fork_ev, h->st));
     CK(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    CK(orth_cgs2(h->Qho, n, m, h->orth_scratch2, h->flags, h->side));
+    CK(orth_cgs2(h->Qho, n, m, h->orth_scratch2, h->flags, h->side, 0, true));
     CK(cudaEventRecord(h->join_ev, h->side));
     if (side_products) {
       CK(big_product(h, 0, OP_C, h->Qho, h->AhQ, -1, true));
@@ -880,8 +880,10 @@ feast_status rr_impl(feast_handle* h, const double2* Qin, const double2* Qhin) {
       CK(cudaEventRecord(h->join_ev2, h->side));
     }
   }
-  CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st));
-  if (bi && !par) CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st));
+  // the bases need the span exactly and orthonormality only to FP32 level: the
+  // reduced problem forms and inverts their Gram matrix Bhat in FP64 below
+  CK(orth_cgs2(h->Qo, n, m, h->orth_scratch, h->flags, h->st, 0, true));
+  if (bi && !par) CK(orth_cgs2(h->Qho, n, m, h->orth_scratch, h->flags, h->st, 0, true));
   mark(1);
   const double2* Vb = bi ? h->Qho : h->Qo;
   CK(big_product(h, 0, OP_N, h->Qo, h->AQ));

@@ -251,6 +251,13 @@ k_orth_cgs2_grp(double2* Q, const GrpDesc* pd, const int* cta0, int np, double2*
 // partial sums of a phase sit in part[(phase & 1)][g * (m + 1) + slot].
 constexpr int ORTH_SM_BYTES_MAX = 200 * 1024;
 
+// F32DOT: the projection coefficients and norms from a complex64 copy of the
+// rows (kept beside the FP64 rows in shared memory), the updates in FP64.  Any
+// coefficients keep the span exact when the update is FP64; the basis is then
+// orthonormal to about 1e-7 instead of 1e-16, which suits a caller that forms
+// and inverts the basis' own Gram matrix in FP64 (the Rayleigh-Ritz step) and
+// halves the scalar FP64 work (the slow pipe on this GPU).
+template <bool F32DOT>
 __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
   extern __shared__ double2 sQ[];
   __shared__ double2 s_r[ORTH_MAX_M + 1];
@@ -259,9 +266,14 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int n = a.n, m = a.m, ld = m + 1, S = m + 1;
   const int r0 = min(n, g * a.rows_per), R = min(n, r0 + a.rows_per) - r0;
+  float2* sQ32 = reinterpret_cast<float2*>(sQ + (size_t)a.rows_per * ld);  // F32DOT only
+  auto set = [&](int rl, int c, double2 v) {
+    sQ[rl * ld + c] = v;
+    if (F32DOT) sQ32[rl * ld + c] = make_float2((float)v.x, (float)v.y);
+  };
   for (int idx = tid; idx < R * m; idx += ORTH_THREADS) {
     const int rl = idx % R, c = idx / R;
-    sQ[rl * ld + c] = a.Q[(size_t)c * n + r0 + rl];
+    set(rl, c, a.Q[(size_t)c * n + r0 + rl]);
   }
   __syncthreads();
   int phase = 0;
@@ -273,7 +285,16 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
     for (int t = tid; t < ns * groups; t += ORTH_THREADS) {
       const int i = t % ns, gr = t / ns;
       double2 acc = make_double2(0.0, 0.0);
-      if (i < nc) {
+      if (F32DOT) {
+        float2 a32 = make_float2(0.f, 0.f);
+        if (i < nc) {
+#pragma unroll 4
+          for (int rl = gr; rl < R; rl += groups) cfmac<float>(a32, sQ32[rl * ld + i], sQ32[rl * ld + j]);
+        } else {
+          for (int rl = gr; rl < R; rl += groups) a32.x += cnorm2<float>(sQ32[rl * ld + nc_norm]);
+        }
+        acc = make_double2(a32.x, a32.y);
+      } else if (i < nc) {
 #pragma unroll 4
         for (int rl = gr; rl < R; rl += groups) cfmac<double>(acc, sQ[rl * ld + i], sQ[rl * ld + j]);
       } else {
@@ -324,13 +345,13 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
       }
-      if (lane == 0) sQ[rl * ld + j] = csub<double>(sQ[rl * ld + j], acc);
+      if (lane == 0) set(rl, j, csub<double>(sQ[rl * ld + j], acc));
     }
     __syncthreads();
   };
   auto normalise = [&](int c, double nrm2) {
     const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
-    for (int rl = tid; rl < R; rl += ORTH_THREADS) sQ[rl * ld + c] = cscale<double>(sQ[rl * ld + c], inv);
+    for (int rl = tid; rl < R; rl += ORTH_THREADS) set(rl, c, cscale<double>(sQ[rl * ld + c], inv));
     return inv;
   };
   // column j: pass 1 carries the squared norm of column j - 1, which is then
@@ -347,7 +368,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_cgs2_sm(OrthArgs a) {
     const double nrm2 = s_r[nc].x;
     if ((!(nrm2 > SAFE_MIN) || nrm2 < 0.5 * r1sq) && retries < ORTH_RETRIES) {
       const int c = j - 1, rr = orth_restart_row(a.col0 + c, retries++, n);
-      for (int rl = tid; rl < R; rl += ORTH_THREADS) sQ[rl * ld + c] = make_double2(r0 + rl == rr ? 1.0 : 0.0, 0.0);
+      for (int rl = tid; rl < R; rl += ORTH_THREADS) set(rl, c, make_double2(r0 + rl == rr ? 1.0 : 0.0, 0.0));
       __syncthreads();
       if (c == 0) r1sq = 0.0;
       j = c > 0 ? c : 1;  // project the restarted column again (column 0 needs no projection)
@@ -690,7 +711,8 @@ size_t orth_scratch_bytes(int n, int m) {
   return (size_t)2 * 160 * (m + 1) * sizeof(double2) + (size_t)2 * (m + 1) * sizeof(double2) + 256;
 }
 
-cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s, int col0) {
+cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s, int col0,
+                      bool f32dots) {
   if (m > ORTH_MAX_M || m < 1 || n < 1) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
@@ -711,17 +733,22 @@ cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, 
     G = min(G, max(1, (n + 7) / 8));
     a.rows_per = (n + G - 1) / G;
     G = (n + a.rows_per - 1) / a.rows_per;
-    const size_t smem = (size_t)a.rows_per * (m + 1) * sizeof(double2);
+    const size_t smem = (size_t)a.rows_per * (m + 1) * (sizeof(double2) + (f32dots ? sizeof(float2) : 0));
     if (m >= 2 && smem <= (size_t)ORTH_SM_BYTES_MAX) {
       static bool attr = false;
       if (!attr) {
-        e = cudaFuncSetAttribute(k_orth_cgs2_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, ORTH_SM_BYTES_MAX);
+        e = cudaFuncSetAttribute(k_orth_cgs2_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 ORTH_SM_BYTES_MAX);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(k_orth_cgs2_sm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   ORTH_SM_BYTES_MAX);
         if (e != cudaSuccess) return e;
         attr = true;
       }
       void* args[] = {&a};
       feast_count_launch();
-      return cudaLaunchCooperativeKernel((void*)k_orth_cgs2_sm, dim3(G), dim3(ORTH_THREADS), args, smem, s);
+      void* fn = f32dots ? (void*)k_orth_cgs2_sm<true> : (void*)k_orth_cgs2_sm<false>;
+      return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(ORTH_THREADS), args, smem, s);
     }
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_orth_cgs2, ORTH_THREADS, 0);

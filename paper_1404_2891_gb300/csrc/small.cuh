@@ -12,7 +12,11 @@
 size_t orth_scratch_bytes(int n, int m);
 // col0: index of Q's column 0 within a larger basis (a panel of it), so that
 // dependent columns of different panels restart from different unit vectors.
-cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s, int col0 = 0);
+// f32dots: coefficients and norms from a complex64 copy of the rows, updates in
+// FP64 (the span stays exact, the orthonormality is about 1e-7), for callers
+// that form and invert the basis' Gram matrix in FP64 themselves.
+cudaError_t orth_cgs2(double2* Q, int n, int m, void* scratch, unsigned* flags, cudaStream_t s, int col0 = 0,
+                      bool f32dots = false);
 
 // Single-CTA dense kernels on m x m column-major matrices (ld m) in global memory.
 // LU with partial pivoting in place (piv: m ints).
