@@ -89,6 +89,17 @@ def _device(a):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(a).T)).to("cuda").mT
 
 
+def choose_single(times, n, tie=0.01):
+    """The fastest (lu_outer, panel_cluster) of {candidate: ms}; within `tie` of
+    it the library's default outer block (256 from n = 1024 on: the deepest K,
+    the highest arithmetic intensity; else one-level) wins.  Returns
+    ((lu_outer, panel_cluster), ms)."""
+    best, t = min(times.items(), key=lambda kv: kv[1])
+    default_outer = 256 if n >= 1024 else -1
+    near = [(k, v) for k, v in times.items() if k[0] == default_outer and v <= (1.0 + tie) * t]
+    return min(near, key=lambda kv: kv[1]) if near else (best, t)
+
+
 def tune_single(n, m0, K=16, cache="tune.json", candidates=None, reps=2, seed=0, verbose=False):
     """Time the factorisation for each (lu_outer, panel_cluster) candidate and
     store the fastest.  Returns (key, entry, all timings)."""
@@ -113,13 +124,7 @@ def tune_single(n, m0, K=16, cache="tune.json", candidates=None, reps=2, seed=0,
         times[(outer, pc)] = float(np.median(t))
         if verbose:
             print(f"lu_outer={outer} panel_cluster={pc}: {times[(outer, pc)]:.2f} ms")
-    (outer, pc), t = min(times.items(), key=lambda kv: kv[1])
-    # within 1 % of the fastest, the library's default outer block (256 from
-    # n = 1024 on: the deepest K, the highest intensity) wins the tie
-    default_outer = 256 if n >= 1024 else -1
-    near = [(k, v) for k, v in times.items() if k[0] == default_outer and v <= 1.01 * t]
-    if near:
-        (outer, pc), t = min(near, key=lambda kv: kv[1])
+    (outer, pc), t = choose_single(times, n)
     key = single_key(n, m0, q)
     entry = {"lu_outer": outer, "panel_cluster": pc, "t_factor_ms": t, "candidates": len(times),
              "note": f"median of {reps} factorisations of {q} shifted systems of order {n}"}
