@@ -901,11 +901,16 @@ cudaError_t lu_factor_batched(const LuBatch<T>& lu_in, int nb, TrailingUpdateFn<
     if ((e = cudaStreamWaitEvent(s, ev_panel, 0)) != cudaSuccess) return cleanup(e);
     if ((e = laswp(k1, w1)) != cudaSuccess) return cleanup(e);
   }
-  // the left interchanges are done before anything reads L
-  if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
-  if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+  // the left interchanges are done before anything reads L (the left stream
+  // has work only without row maps; an unused stream is not joined, so that a
+  // stream capture of this function never waits on an event from outside it)
+  const bool deferred = std::is_same<T, float>::value && use_mv && lu.rowmaps;
+  if (!deferred) {
+    if ((e = cudaEventRecord(ev_left, lstream)) != cudaSuccess) return cleanup(e);
+    if ((e = cudaStreamWaitEvent(s, ev_left, 0)) != cudaSuccess) return cleanup(e);
+  }
   if constexpr (std::is_same<T, float>::value) {
-    if (use_mv && lu.rowmaps && (e = deferred_left_swaps(lu, 64, 0, s)) != cudaSuccess) return cleanup(e);
+    if (deferred && (e = deferred_left_swaps(lu, 64, 0, s)) != cudaSuccess) return cleanup(e);
   }
   feast_count_launch();
   k_piv_to_perm<<<lu.q, 256, 0, s>>>(lu.piv, lu.perm, lu.pinv, lu.n);
