@@ -481,26 +481,31 @@ k_laswp_mv_cols(cplx<T>* S, long long ld, long long stride, int k0, int col0, in
 // T = -D^{-1} for diagonal blocks D of the factor: D = the unit lower part
 // (UPPER = false) or the upper part with its diagonal (UPPER = true) of
 // S[r0:r0+KB, r0:r0+KB], r0 = KB * block; rows and columns at or beyond n act as
-// the identity (a ragged last block).  One CTA per (64-column block j of the
+// the identity (a ragged last block).  One CTA per (CW-column block j of the
 // inverse, diagonal block, shift): X = D^{-1} E_j by block substitution -- for
-// each 64-row block I reached from j (downward for L, upward for U), the
-// products with the blocks of X already solved (D from global memory through
-// shared memory, X in shared memory), then the 64 x 64 triangular solve (four
-// threads per column, one barrier per step).  With T, a product that
-// overwrites its output (C = 0 - T X) gives D^{-1} X without cancelling
-// against X.  T goes to
+// each 64-row block I reached from the one holding column CW j (downward for
+// L, upward for U), the products with the blocks of X already solved (D from
+// global memory through shared memory, X in shared memory), then the 64 x 64
+// triangular solve (256 / CW threads per column, one barrier per step).  The
+// narrow column blocks keep two CTAs on an SM (each about 100 KB of shared
+// memory at CW = 32) and halve the work of the CTAs that hold the first
+// columns, which set the duration.  With T, a product that overwrites its
+// output (C = 0 - T X) gives D^{-1} X without cancelling against X.  T goes to
 // T + ((block - block0) q + shift) KB^2, column-major with leading dimension KB.
-template <bool UPPER>
+template <bool UPPER, int CW>
 __global__ void __launch_bounds__(256)
 k_block_tri_inv(const float2* S, long long ld, long long stride, int n, int KB, int block0, float2* T) {
+  constexpr int RG = 256 / CW;  // row groups: thread rows rq, rq + RG, ...
+  constexpr int RPT = 64 / RG;  // rows of a 64-row block per thread
+  constexpr int XS = CW + 1;    // padded row stride of X
   extern __shared__ __align__(16) unsigned char ti_smem[];
-  float2* X = reinterpret_cast<float2*>(ti_smem);  // [KB][64]
-  float2* Db = X + (size_t)KB * 64;                // [64][65]
+  float2* X = reinterpret_cast<float2*>(ti_smem);  // [KB][XS]
+  float2* Db = X + (size_t)KB * XS;                // [64][65]
   const int j = blockIdx.x, blk = block0 + blockIdx.y, b = blockIdx.z, q = gridDim.z;
-  const int tid = threadIdx.x, c = tid & 63, rq = tid >> 6;
+  const int tid = threadIdx.x, c = tid % CW, rq = tid / CW;
   const int r0 = KB * blk, nr = min(KB, n - r0);
   const float2* A = S + (size_t)b * stride + (size_t)r0 + (size_t)r0 * ld;
-  const int nbk = KB / 64;
+  const int nbk = KB / 64, jb = (CW * j) / 64;
   // D(r, t) of the block, identity outside the valid nr x nr part
   auto dval = [&](int r, int t) -> float2 {
     if (r == t && (!UPPER || r >= nr)) return make_float2(1.f, 0.f);
@@ -509,16 +514,16 @@ k_block_tri_inv(const float2* S, long long ld, long long stride, int n, int KB, 
     return A[(size_t)r + (size_t)t * ld];
   };
   for (int s2 = 0; s2 < nbk; ++s2) {
-    const int I = UPPER ? j - s2 : j + s2;
+    const int I = UPPER ? jb - s2 : jb + s2;
     if (I < 0 || I >= nbk) continue;
-    float2 acc[16];
+    float2 acc[RPT];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int r = rq + 4 * k;
-      acc[k] = make_float2(64 * I + r == 64 * j + c ? 1.f : 0.f, 0.f);
+    for (int k = 0; k < RPT; ++k) {
+      const int r = rq + RG * k;
+      acc[k] = make_float2(64 * I + r == CW * j + c ? 1.f : 0.f, 0.f);
     }
     for (int s3 = 0; s3 < s2; ++s3) {
-      const int J = UPPER ? j - s3 : j + s3;  // blocks of X solved before I
+      const int J = UPPER ? jb - s3 : jb + s3;  // blocks of X solved before I
       __syncthreads();
       for (int e = tid; e < 64 * 64; e += 256) {
         const int r = e & 63, t = e >> 6;
@@ -526,43 +531,43 @@ k_block_tri_inv(const float2* S, long long ld, long long stride, int n, int KB, 
       }
       __syncthreads();
       for (int t = 0; t < 64; ++t) {
-        const float2 xv = X[(size_t)(64 * J + t) * 64 + c];
+        const float2 xv = X[(size_t)(64 * J + t) * XS + c];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] = csub<float>(acc[k], cmul<float>(Db[(rq + 4 * k) * 65 + t], xv));
+        for (int k = 0; k < RPT; ++k) acc[k] = csub<float>(acc[k], cmul<float>(Db[(rq + RG * k) * 65 + t], xv));
       }
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) X[(size_t)(64 * I + rq + 4 * k) * 64 + c] = acc[k];
+    for (int k = 0; k < RPT; ++k) X[(size_t)(64 * I + rq + RG * k) * XS + c] = acc[k];
     __syncthreads();
     for (int e = tid; e < 64 * 64; e += 256) {
       const int r = e & 63, t = e >> 6;
       Db[r * 65 + t] = dval(64 * I + r, 64 * I + t);
     }
     __syncthreads();
-    float2* Xc = X + (size_t)(64 * I) * 64 + c;
+    float2* Xc = X + (size_t)(64 * I) * XS + c;
     if (!UPPER) {  // unit lower: forward
       for (int t = 0; t < 63; ++t) {
-        const float2 xt = Xc[(size_t)t * 64];
-        for (int r = t + 1 + ((rq - (t + 1)) & 3); r < 64; r += 4)
-          Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Db[r * 65 + t], xt));
+        const float2 xt = Xc[(size_t)t * XS];
+        for (int r = t + 1 + ((rq - (t + 1)) & (RG - 1)); r < 64; r += RG)
+          Xc[(size_t)r * XS] = csub<float>(Xc[(size_t)r * XS], cmul<float>(Db[r * 65 + t], xt));
         __syncthreads();
       }
     } else {  // upper with its diagonal: backward, the owner of row t divides first
       for (int t = 63; t >= 0; --t) {
-        if ((t & 3) == rq) Xc[(size_t)t * 64] = cdiv<float>(Xc[(size_t)t * 64], Db[t * 65 + t]);
+        if ((t & (RG - 1)) == rq) Xc[(size_t)t * XS] = cdiv<float>(Xc[(size_t)t * XS], Db[t * 65 + t]);
         __syncthreads();
-        const float2 xt = Xc[(size_t)t * 64];
-        for (int r = rq; r < t; r += 4)
-          Xc[(size_t)r * 64] = csub<float>(Xc[(size_t)r * 64], cmul<float>(Db[r * 65 + t], xt));
+        const float2 xt = Xc[(size_t)t * XS];
+        for (int r = rq; r < t; r += RG)
+          Xc[(size_t)r * XS] = csub<float>(Xc[(size_t)r * XS], cmul<float>(Db[r * 65 + t], xt));
       }
       __syncthreads();
     }
   }
   float2* Tb = T + ((size_t)(blk - block0) * q + b) * KB * KB;
-  for (int e = tid; e < KB * 64; e += 256) {
-    const int r = e % KB, cc = e / KB, col = 64 * j + cc;
-    const bool solved = UPPER ? r < 64 * (j + 1) : r >= 64 * j;
-    const float2 x = solved ? X[(size_t)r * 64 + cc] : make_float2(0.f, 0.f);
+  for (int e = tid; e < KB * CW; e += 256) {
+    const int r = e % KB, cc = e / KB, col = CW * j + cc;
+    const bool solved = UPPER ? r < 64 * (jb + 1) : r >= 64 * jb;
+    const float2 x = solved ? X[(size_t)r * XS + cc] : make_float2(0.f, 0.f);
     Tb[(size_t)r + (size_t)col * KB] = make_float2(-x.x, -x.y);
   }
 }
@@ -1022,21 +1027,26 @@ cudaError_t laswp_moved_rows(const LuBatch<float>& lu, int k0, int col0, int nco
   return cudaGetLastError();
 }
 
+// Columns of the inverse per CTA of k_block_tri_inv (16, 32 or 64).
+constexpr int kTriInvCols = 32;
+
 cudaError_t block_inverse_negated(const LuBatch<float>& lu, bool upper, int KB, int block0, int nblocks, float2* T,
                                    cudaStream_t s) {
   if (KB % 64 || KB > 256 || KB < 64 || nblocks < 1 || block0 < 0 || (long long)KB * (block0 + nblocks - 1) >= lu.n)
     return cudaErrorInvalidValue;
-  const size_t smem = (size_t)KB * 64 * sizeof(float2) + 64 * 65 * sizeof(float2);
-  cudaError_t e = upper ? cudaFuncSetAttribute(k_block_tri_inv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                        : cudaFuncSetAttribute(k_block_tri_inv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int CW = kTriInvCols;
+  const size_t smem = (size_t)KB * (CW + 1) * sizeof(float2) + 64 * 65 * sizeof(float2);
+  cudaError_t e = upper
+                      ? cudaFuncSetAttribute(k_block_tri_inv<true, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_block_tri_inv<false, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   feast_count_launch();
-  const dim3 grid(KB / 64, nblocks, lu.q);
+  const dim3 grid(KB / CW, nblocks, lu.q);
   const float2* S = reinterpret_cast<const float2*>(lu.S);
   if (upper)
-    k_block_tri_inv<true><<<grid, 256, smem, s>>>(S, lu.ld, lu.stride, lu.n, KB, block0, T);
+    k_block_tri_inv<true, CW><<<grid, 256, smem, s>>>(S, lu.ld, lu.stride, lu.n, KB, block0, T);
   else
-    k_block_tri_inv<false><<<grid, 256, smem, s>>>(S, lu.ld, lu.stride, lu.n, KB, block0, T);
+    k_block_tri_inv<false, CW><<<grid, 256, smem, s>>>(S, lu.ld, lu.stride, lu.n, KB, block0, T);
   return cudaGetLastError();
 }
 
