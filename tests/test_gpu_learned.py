@@ -84,3 +84,48 @@ def test_learned_m0_beats_plain_stochastic_count():
     assert mae_net < mae_plain, (mae_net, mae_plain)
     m0_net = np.array([lm.m0_rule(v) for v in pred])
     assert np.all(m0_net >= yte)
+
+
+def test_learned_m0_at_the_stated_size():
+    """Config 5 as stated: n = 1024, 2000 labelling draws and 200 held-out draws.
+    The disk holds about 130 to 260 eigenvalues, more than one subspace may
+    (m0 <= 160), so every draw is labelled by the method through four strips of
+    the disk solved in batches (label_strips).  Every batch converges, the labels
+    agree with brute force on a sample, and on the 200 held-out draws the network's
+    m0 covers the true count every time while its count error is below that of
+    the plain stochastic estimate Re mu_0."""
+    fg = lib()
+    from paper_1404_2891_gb300 import learned_m0 as lm
+    n = 1024
+    fam = workloads.parametric_family(n=n, seed=5, n_train=2000, n_test=200)
+    ps = np.concatenate([fam["p_train"], fam["p_test"]])
+    c = fam["contour"]
+    feats = np.array([lm.features(fam, p, workloads.rademacher(n, 32, 1000 + i)) for i, p in enumerate(ps)])
+    strips = lm.disk_strips(c["c"], c["R"], (-0.4, 0.0, 0.4), 0.04, K=12)
+    labels, stats = lm.label_strips(fam, ps, lambda i, k, n_, m: workloads.random_block(n_, m, 7000 + 8 * i + k),
+                                    strips, lambda p: n / (np.pi * (1.0 + p * p)), group=32)
+    assert sum(s["converged"] for s in stats) == len(ps) * len(strips), [s["converged"] for s in stats]
+    assert all(v is not None for v in labels)
+    labels = np.array(labels, dtype=float)
+    assert labels.min() >= 100 and labels.max() > 160  # beyond a single subspace
+    for i in (0, 999, 1999, 2000, 2199):
+        A = fam["A0"] + ps[i] * fam["A1"]
+        assert labels[i] == len(brute.inside_spectrum(A, None, c["c"], c["R"], c["a"])), i
+    ntr = len(fam["p_train"])
+    Xtr, ytr, Xte, yte = feats[:ntr], labels[:ntr], feats[ntr:], labels[ntr:]
+    model = lm.CountPredictor(Xtr, width=256, init_params=workloads.mlp_init(lm.D_IN, 256, 11))
+    model.fit(Xtr, ytr, workloads.batch_schedule(ntr, 64, 3000, seed=12), lr=1e-3)
+    pred = model.predict(Xte)
+    plain = Xte[:, 1]  # Re mu_0
+    mae_net, mae_plain = np.mean(np.abs(pred - yte)), np.mean(np.abs(plain - yte))
+    assert mae_net < 0.5 * mae_plain, (mae_net, mae_plain)
+    m0_net = np.array([lm.m0_rule(v, cap=n) for v in pred])
+    m0_plain = np.array([lm.m0_rule(v, cap=n) for v in plain])
+    print(f"stated size: counts {int(labels.min())}-{int(labels.max())}, held-out count error (mean abs) "
+          f"network {mae_net:.2f} / plain {mae_plain:.2f}, m0 below the count: network "
+          f"{int(np.sum(m0_net < yte))} / plain {int(np.sum(m0_plain < yte))} of {len(yte)}, mean m0 - count: "
+          f"network {np.mean(m0_net - yte):.1f} / plain {np.mean(m0_plain - yte):.1f}, "
+          f"batch iterations {min(s['iters'] for s in stats)}-{max(s['iters'] for s in stats)}")
+    assert np.all(m0_net >= yte)
+    # the plain estimate under-sizes the subspace on some held-out draws
+    assert np.sum(m0_plain < yte) > np.sum(m0_net < yte)
