@@ -92,9 +92,14 @@ def disk_strips(center, r, cuts, delta, K=12, rule="gauss"):
     piece, Sec. 5.4); the domain test of such a contour is the filter value.
     Returns a list of dict(lo, hi, segments, contour, area) with the area of the
     widened domain."""
+    ts = sorted(float(t) for t in cuts)
+    if not (float(r) > 0.0 and float(delta) > 0.0):
+        raise ValueError("disk_strips: r and delta must be positive")
+    if any(not -1.0 < t < 1.0 for t in ts) or any(b - a <= 0.0 for a, b in zip(ts, ts[1:])):
+        raise ValueError("disk_strips: cuts must be distinct and inside (-1, 1)")
     c = complex(center)
     R2 = float(r) + float(delta)
-    edges = [-math.inf] + [c.real + r * float(t) for t in sorted(cuts)] + [math.inf]
+    edges = [-math.inf] + [c.real + r * t for t in ts] + [math.inf]
     out = []
     for lo, hi in zip(edges, edges[1:]):
         segs = []
@@ -109,6 +114,8 @@ def disk_strips(center, r, cuts, delta, K=12, rule="gauss"):
                     ("arc", c, R2, tb, ta),
                     ("line", complex(lo - delta, c.imag + ha), complex(lo - delta, c.imag - ha)),
                     ("arc", c, R2, 2 * math.pi - ta, 2 * math.pi - tb)]
+        elif not math.isfinite(lo) and not math.isfinite(hi):  # no cut: the widened disk
+            segs = [("arc", c, R2, 0.0, 2 * math.pi)]
         elif math.isfinite(hi):  # the left cap
             segs = [("line", complex(hi + delta, c.imag - hb), complex(hi + delta, c.imag + hb)),
                     ("arc", c, R2, tb, 2 * math.pi - tb)]

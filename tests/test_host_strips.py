@@ -7,6 +7,7 @@ out."""
 import math
 
 import numpy as np
+import pytest
 
 from helpers import lib
 from oracle import contour as ct
@@ -92,3 +93,13 @@ def test_strip_subspace_sizes():
     for m, s in zip(m0, strips):
         assert m >= 1.3 * s["area"] * 1024 / math.pi + 8
     assert lm.strip_m0(strips, 1e6) == [160] * len(strips)
+
+
+def test_strips_reject_bad_cuts_and_bands():
+    lm, _ = _strips()
+    for cuts, delta in [((-1.0, 0.0), 0.04), ((0.2, 0.2), 0.04), ((0.0, 1.3), 0.04), ((0.0,), 0.0),
+                        ((0.0,), -0.1)]:
+        with pytest.raises(ValueError):
+            lm.disk_strips(C, R, cuts, delta)
+    whole = lm.disk_strips(C, R, (), 0.04)  # no cut: the whole widened disk
+    assert len(whole) == 1 and abs(whole[0]["area"] - math.pi * (R + 0.04) ** 2) < 1e-4
